@@ -1,0 +1,154 @@
+/*
+ * pmpm.h -- C ABI of the GB300 two-level particle-mesh (PM-PM) library.
+ *
+ * The library evolves cosmological N-body particles stored in the
+ * fixed-point format of CUBE (Cheng et al., arXiv:2003.03931): six 1-byte
+ * integers per particle (Sec. III-A, Eq. 2 and Eq. 3), grouped by coarse
+ * cell, with per-cell counts and a per-cell mean velocity.  One step decodes
+ * the particles, deposits them on a coarse mesh and on buffered fine-mesh
+ * tiles, multiplies by the force kernels in Fourier space (Sec. II, Eq. 1),
+ * interpolates the force, kicks and drifts, and re-encodes and re-sorts the
+ * particles by cell.
+ *
+ * Conventions
+ *  - Lengths are in fine cells; the box is 4*nc fine cells per side (the
+ *    coarse mesh is 4x coarser, Sec. II).  Cell indices are 0-based, flat
+ *    index cx + nc*(cy + nc*cz) (x fastest).
+ *  - Position code Q = c*256 + m; decoded position (Q + 1/2)/64 (Eq. 2).
+ *  - Velocity p = a^2 dx/dt; decoded p = v_c + sigma*T[u] in float32, T the
+ *    tangent of the bin-centre angle of 256 equal angle bins (Eq. 3; the
+ *    map f is the arctangent form of Sec. III-B.2).
+ *  - Memory: the caller owns all device memory.  pmpm_init borrows a device
+ *    workspace of pmpm_workspace_bytes() bytes and a CUDA stream; the library
+ *    allocates no device memory of its own.  Host buffers passed to fetch/
+ *    load are caller-owned and only read/written during the call.
+ *  - Every call returns PMPM_OK (0) or a negative error code; no exception
+ *    crosses the ABI.  pmpm_last_error(sim) describes the last failure.
+ *  - Calls enqueue work on the sim's stream and return without waiting,
+ *    except pmpm_fetch, pmpm_load, pmpm_power_spectrum and pmpm_sync, which
+ *    synchronise the stream and report device-side error flags
+ *    (PMPM_EOVERFLOW, PMPM_ECOUNT).  One sim must not be used from two
+ *    threads at once.
+ */
+#ifndef PMPM_H
+#define PMPM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* error codes */
+#define PMPM_OK         0
+#define PMPM_EINVAL    -1   /* bad argument or configuration */
+#define PMPM_ENOMEM    -2   /* workspace smaller than pmpm_workspace_bytes() */
+#define PMPM_ECUDA     -3   /* a CUDA runtime call failed */
+#define PMPM_EOVERFLOW -4   /* a fixed-point or integer range was exceeded */
+#define PMPM_ECOUNT    -5   /* particle count not conserved (internal error) */
+#define PMPM_ESTATE    -6   /* no particle state loaded yet */
+
+/* what to fetch / load */
+#define PMPM_STREAMS          1  /* uint8 [6][N]: m0 m1 m2 u0 u1 u2 in storage order */
+#define PMPM_COUNTS           2  /* int32 [nc^3] particles per coarse cell */
+#define PMPM_VC               3  /* float [3][nc^3] per-cell mean momentum v_c */
+#define PMPM_SCALARS          4  /* pmpm_scalars */
+#define PMPM_DECODED_Q        5  /* int32 [3][N] position codes Q (fetch only) */
+#define PMPM_DECODED_P        6  /* float [3][N] decoded momenta (fetch only) */
+#define PMPM_FORCE            7  /* float [3][N] unit-G field g at the particles,
+                                    current state, storage order (fetch only) */
+#define PMPM_COARSE_DENSITY   8  /* int64 [nc^3] integer CIC density, units 2^-27
+                                    per particle (fetch only) */
+#define PMPM_QP               9  /* load only: int32 Q[3][N] then float p[3][N];
+                                    encodes them into the store (Sec. III-A) */
+
+typedef struct pmpm_config {
+    int32_t np;              /* particles per side of the initial lattice, N = np^3 */
+    int32_t nc;              /* coarse cells per side (>= 8); fine mesh 4*nc */
+    int32_t tile_max;        /* largest tile edge in coarse cells: 4 or 5 */
+    int32_t buffer;          /* tile buffer in fine cells; must be 6 (Sec. IV-A.2) */
+    int32_t pos_bytes;       /* bytes per position coordinate; must be 1 (Eq. 2) */
+    int32_t vel_bytes;       /* bytes per velocity coordinate; must be 1 (Eq. 3) */
+    int32_t pk_mesh_max;     /* largest power-spectrum mesh; 0 = min(4*nc, 512) */
+    int32_t reserved;
+    double  a_init;          /* first scale factor of the equal-log-a schedule */
+    double  a_final;         /* last scale factor */
+    int32_t n_steps;         /* steps of the schedule */
+    int32_t reserved2;
+} pmpm_config;
+
+typedef struct pmpm_scalars {
+    double  a;               /* scale factor of the stored positions */
+    double  sigma;           /* velocity scale of Eq. 3 (a float32 value) */
+    int64_t step;            /* steps taken on the schedule */
+    int64_t n;               /* particles */
+} pmpm_scalars;
+
+typedef struct pmpm_sim pmpm_sim;
+
+/* Device bytes a sim of this configuration needs.  Host-only, no GPU call.
+ * Returns PMPM_EINVAL for unsupported configurations. */
+int pmpm_workspace_bytes(const pmpm_config* cfg, size_t* bytes);
+
+/* Create a sim on the current CUDA device.  d_workspace: device pointer,
+ * 256-byte aligned, at least pmpm_workspace_bytes() bytes, owned by the
+ * caller and borrowed until pmpm_destroy.  cuda_stream: a cudaStream_t (or
+ * NULL for the legacy default stream).  Builds the force-kernel tables
+ * (Sec. II) on the stream.  *out receives the handle. */
+int pmpm_init(const pmpm_config* cfg, void* d_workspace, size_t bytes,
+              void* cuda_stream, pmpm_sim** out);
+
+/* Zel'dovich initial conditions at a_init (Sec. IV-A.2) for a power-law
+ * spectrum P(k) = k^slope exp(-(k/k_c)^2), k in radians per fine cell;
+ * white noise from counter-based SplitMix64 at `seed`; displacements scaled
+ * so that their 3-D rms is rms_disp fine cells. */
+int pmpm_ic_zeldovich(pmpm_sim* sim, uint64_t seed, double slope, double k_c,
+                      double rms_disp);
+
+/* Advance nsteps kick-drift steps of the schedule (Sec. II).  Asynchronous. */
+int pmpm_step(pmpm_sim* sim, int32_t nsteps);
+
+/* Power spectrum of the CIC density on an nmesh^3 mesh (nmesh = 4*nc / 2^j,
+ * <= pk_mesh_max), Sec. IV-D: P(k) = L^3/nmesh^6 |DFT(delta)|^2 in shells
+ * j = round(|n|), j = 1..nbins (nbins <= nmesh/2).  Host arrays of nbins
+ * entries receive the mean |k|, mean P and mode count.  Synchronises. */
+int pmpm_power_spectrum(pmpm_sim* sim, int32_t nmesh, int32_t nbins,
+                        double* k, double* pk, int64_t* nmodes);
+
+/* Copy part of the state (see PMPM_* above) into a host buffer of exactly
+ * the listed size.  Synchronises. */
+int pmpm_fetch(pmpm_sim* sim, int32_t what, void* host_dst, size_t bytes);
+
+/* Replace part of the state from a host buffer (PMPM_STREAMS, PMPM_COUNTS,
+ * PMPM_VC, PMPM_SCALARS, or PMPM_QP which encodes raw codes and momenta).
+ * Synchronises. */
+int pmpm_load(pmpm_sim* sim, int32_t what, const void* host_src, size_t bytes);
+
+/* Wait for the sim's stream and report device-side error flags. */
+int pmpm_sync(pmpm_sim* sim);
+
+/* Per-stage device time (ms) accumulated since the last reset, measured
+ * with CUDA events on the sim's stream when enable != 0.  Stage order:
+ * 0 coarse deposit, 1 coarse FFT + Green multiply, 2 tile fine PM + kick +
+ * drift, 3 scan + cell means, 4 dispersion, 5 encode + scatter.  Calling
+ * with times == NULL sets the switch and resets the totals. */
+int pmpm_stage_times(pmpm_sim* sim, int32_t enable, double* times, int32_t n,
+                     int64_t* launches);
+
+/* Release the handle (not the caller's workspace or stream). */
+void pmpm_destroy(pmpm_sim* sim);
+
+/* Text of the last error on this sim (or of the last failed pmpm_init when
+ * sim is NULL). */
+const char* pmpm_last_error(const pmpm_sim* sim);
+
+/* Host copies of the float32 velocity tables the library uses: T[256]
+ * bin-centre values and E[256] bin edges (E[0] = -inf), Eq. 3.  Host only. */
+int pmpm_codec_tables(float* T, float* E);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PMPM_H */

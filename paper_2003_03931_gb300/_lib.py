@@ -1,0 +1,118 @@
+"""ctypes view of libpmpm.so (the C ABI declared in include/pmpm.h).
+
+Argument marshalling only.  Loading fails loudly when the library has not
+been built; there is no fallback implementation.
+"""
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpmpm.so")
+
+PMPM_OK = 0
+PMPM_EINVAL = -1
+PMPM_ENOMEM = -2
+PMPM_ECUDA = -3
+PMPM_EOVERFLOW = -4
+PMPM_ECOUNT = -5
+PMPM_ESTATE = -6
+
+STREAMS = 1
+COUNTS = 2
+VC = 3
+SCALARS = 4
+DECODED_Q = 5
+DECODED_P = 6
+FORCE = 7
+COARSE_DENSITY = 8
+QP = 9
+
+ERROR_NAMES = {
+    PMPM_EINVAL: "PMPM_EINVAL",
+    PMPM_ENOMEM: "PMPM_ENOMEM",
+    PMPM_ECUDA: "PMPM_ECUDA",
+    PMPM_EOVERFLOW: "PMPM_EOVERFLOW",
+    PMPM_ECOUNT: "PMPM_ECOUNT",
+    PMPM_ESTATE: "PMPM_ESTATE",
+}
+
+# every entry point the header declares, for the export check
+EXPORTS = [
+    "pmpm_workspace_bytes", "pmpm_init", "pmpm_ic_zeldovich", "pmpm_step",
+    "pmpm_power_spectrum", "pmpm_fetch", "pmpm_load", "pmpm_sync", "pmpm_stage_times",
+    "pmpm_destroy", "pmpm_last_error", "pmpm_codec_tables",
+]
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("np", ctypes.c_int32),
+        ("nc", ctypes.c_int32),
+        ("tile_max", ctypes.c_int32),
+        ("buffer", ctypes.c_int32),
+        ("pos_bytes", ctypes.c_int32),
+        ("vel_bytes", ctypes.c_int32),
+        ("pk_mesh_max", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("a_init", ctypes.c_double),
+        ("a_final", ctypes.c_double),
+        ("n_steps", ctypes.c_int32),
+        ("reserved2", ctypes.c_int32),
+    ]
+
+
+class Scalars(ctypes.Structure):
+    _fields_ = [
+        ("a", ctypes.c_double),
+        ("sigma", ctypes.c_double),
+        ("step", ctypes.c_int64),
+        ("n", ctypes.c_int64),
+    ]
+
+
+class PmpmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERROR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load():
+    """Load libpmpm.so once; raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built; run paper_2003_03931_gb300/build.py "
+                          "(or __graft_entry__.build())")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    lib.pmpm_workspace_bytes.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_size_t)]
+    lib.pmpm_init.argtypes = [ctypes.POINTER(Config), P, ctypes.c_size_t, P, ctypes.POINTER(P)]
+    lib.pmpm_ic_zeldovich.argtypes = [P, ctypes.c_uint64, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_double]
+    lib.pmpm_step.argtypes = [P, ctypes.c_int32]
+    lib.pmpm_power_spectrum.argtypes = [P, ctypes.c_int32, ctypes.c_int32, P, P, P]
+    lib.pmpm_fetch.argtypes = [P, ctypes.c_int32, P, ctypes.c_size_t]
+    lib.pmpm_load.argtypes = [P, ctypes.c_int32, P, ctypes.c_size_t]
+    lib.pmpm_sync.argtypes = [P]
+    lib.pmpm_stage_times.argtypes = [P, ctypes.c_int32, P, ctypes.c_int32, P]
+    lib.pmpm_destroy.argtypes = [P]
+    lib.pmpm_destroy.restype = None
+    lib.pmpm_last_error.argtypes = [P]
+    lib.pmpm_last_error.restype = ctypes.c_char_p
+    lib.pmpm_codec_tables.argtypes = [P, P]
+    for name in EXPORTS:
+        if name not in ("pmpm_destroy", "pmpm_last_error"):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def check(rc, handle=None):
+    if rc != PMPM_OK:
+        msg = load().pmpm_last_error(handle)
+        raise PmpmError(rc, msg.decode() if msg else "")

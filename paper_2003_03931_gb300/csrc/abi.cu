@@ -1,0 +1,517 @@
+// abi.cu -- the C ABI of pmpm.h: workspace layout, set-up, the step sequence
+// and the state transfers.
+//
+// One step (Sec. II, Sec. III):
+//   0 coarse CIC deposit of the current store
+//   1 coarse FFT, Green multiply (K~_l), two inverse FFTs -> F_l
+//   2 tile pass: fine CIC + FFT + K~_s + inverse per tile; interpolate F_s +
+//     F_l; kick; integer drift; new-cell counts and momentum sums
+//   3 scan of the new counts, cell means v_c
+//   4 dispersion sigma
+//   5 encode + scatter into the other store buffer; swap
+#include <math.h>
+#include <stdarg.h>
+#include <string.h>
+
+#include <new>
+
+#include "pmpm_impl.cuh"
+
+namespace pmpm {
+
+static char g_init_msg[512] = "";
+
+int set_error(Sim& s, int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(s.msg, sizeof(s.msg), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int check_launch(Sim& s, const char* what) {
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(s, PMPM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+    return PMPM_OK;
+}
+
+static bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+static int validate(const pmpm_config* c, char* msg, size_t len) {
+    if (!c) return snprintf(msg, len, "null config"), PMPM_EINVAL;
+    if (!pow2(c->np) || c->np < 4 || c->np > 4096)
+        return snprintf(msg, len, "np=%d must be a power of two in [4, 4096]", c->np), PMPM_EINVAL;
+    if (!pow2(c->nc) || c->nc < 8 || c->nc > 1024)
+        return snprintf(msg, len, "nc=%d must be a power of two in [8, 1024]", c->nc), PMPM_EINVAL;
+    if (c->tile_max != 4 && c->tile_max != 5)
+        return snprintf(msg, len, "tile_max=%d must be 4 or 5", c->tile_max), PMPM_EINVAL;
+    if (c->buffer != kBuffer)
+        return snprintf(msg, len, "buffer=%d: only %d is supported", c->buffer, kBuffer), PMPM_EINVAL;
+    if (c->pos_bytes != 1 || c->vel_bytes != 1)
+        return snprintf(msg, len, "only the 1-byte position/velocity format is built"), PMPM_EINVAL;
+    const int nf = 4 * c->nc;
+    if (c->pk_mesh_max && (!pow2(c->pk_mesh_max) || c->pk_mesh_max > nf || c->pk_mesh_max < 4))
+        return snprintf(msg, len, "pk_mesh_max=%d must be a power of two <= %d", c->pk_mesh_max, nf),
+               PMPM_EINVAL;
+    if (!(c->a_init > 0.0) || !(c->a_final >= c->a_init) || c->n_steps < 1)
+        return snprintf(msg, len, "need 0 < a_init <= a_final and n_steps >= 1"), PMPM_EINVAL;
+    return PMPM_OK;
+}
+
+static void derive(Sim& s, const pmpm_config* c) {
+    s.cfg = *c;
+    s.np = c->np;
+    s.nc = c->nc;
+    s.nf = 4 * c->nc;
+    s.n = (int64_t)c->np * c->np * c->np;
+    s.ncells = (int64_t)c->nc * c->nc * c->nc;
+    s.tile_max = c->tile_max;
+    s.nt = tile_count(c->nc, c->tile_max);
+    s.pk_max = c->pk_mesh_max ? c->pk_mesh_max : (s.nf < 512 ? s.nf : 512);
+    s.fft_max = s.nc;
+    if (s.np > s.fft_max) s.fft_max = s.np;
+    if (s.pk_max > s.fft_max) s.fft_max = s.pk_max;
+    s.nblocks_scan = (s.ncells + 4095) / 4096;
+}
+
+size_t layout(Sim& s, uint8_t* base) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> uint8_t* {
+        off = align_up(off);
+        uint8_t* p = base ? base + off : nullptr;
+        off += bytes;
+        return p;
+    };
+    const int64_t N = s.n, C = s.ncells;
+    for (int b = 0; b < 2; ++b) {
+        s.streams[b] = take(6 * (size_t)N);
+        s.counts[b] = reinterpret_cast<int32_t*>(take(4 * (size_t)C));
+        s.offsets[b] = reinterpret_cast<int64_t*>(take(8 * (size_t)(C + 1)));
+        s.vc[b] = reinterpret_cast<float*>(take(12 * (size_t)C));
+        s.sigma_d[b] = reinterpret_cast<float*>(take(4));
+    }
+    s.fill = reinterpret_cast<int32_t*>(take(4 * (size_t)C));
+    s.S = reinterpret_cast<unsigned long long*>(take(24 * (size_t)C));
+    s.d2 = reinterpret_cast<unsigned long long*>(take(16));
+    s.rho_c = reinterpret_cast<long long*>(take(8 * (size_t)C));
+    s.cA = reinterpret_cast<float2*>(take(8 * (size_t)C));
+    s.cB1 = reinterpret_cast<float2*>(take(8 * (size_t)C));
+    s.cB2 = reinterpret_cast<float2*>(take(8 * (size_t)C));
+    s.Fl = reinterpret_cast<float*>(take(12 * (size_t)C));
+    const size_t h = s.nc / 2 + 1;
+    s.green_coarse = reinterpret_cast<float*>(take(4 * h * h * h));
+    s.green_fine = reinterpret_cast<float*>(take(4 * (size_t)kGreenS * kGreenS * kGreenS));
+    s.Tdec = reinterpret_cast<float*>(take(4 * 256));
+    s.Eedge = reinterpret_cast<float*>(take(4 * 256));
+    s.tw_f = reinterpret_cast<float2*>(take(8 * (size_t)s.fft_max));
+    s.tw_d = reinterpret_cast<double2*>(take(16 * (size_t)s.fft_max));
+    s.err = reinterpret_cast<uint32_t*>(take(4));
+    s.blocksums = reinterpret_cast<long long*>(take(8 * (size_t)(s.nblocks_scan + 1)));
+    s.ic_partial = reinterpret_cast<double*>(take(8 * (3 * 1024 + 1)));
+    s.pk_bins = reinterpret_cast<double*>(take(8 * 3 * (size_t)(s.pk_max / 2 + 1)));
+    // transient scratch
+    const size_t step_b = 24 * (size_t)N + 512;
+    const size_t ic_b = 56 * (size_t)N + 1024;
+    const size_t green_b = green_scratch_bytes(s.nc);
+    const size_t pk3 = (size_t)s.pk_max * s.pk_max * s.pk_max;
+    const size_t pk_b = 16 * pk3 + 512;
+    size_t sb = step_b;
+    if (ic_b > sb) sb = ic_b;
+    if (green_b > sb) sb = green_b;
+    if (pk_b > sb) sb = pk_b;
+    s.scratch_bytes = sb;
+    s.scratch = take(sb);
+    if (base) {
+        s.Qn = reinterpret_cast<int32_t*>(s.scratch);
+        s.Pn = reinterpret_cast<float*>(align_up(reinterpret_cast<uintptr_t>(s.Qn + 3 * N)));
+    }
+    return align_up(off);
+}
+
+void prof_mark(Sim& s, int stage) {
+    if (!s.prof || !s.in_step) return;
+    if (s.ev_count >= kEventRing) return;   // full: further marks are dropped until read
+    cudaEventRecord(s.ev[s.ev_count], s.stream);
+    s.ev_stage[s.ev_count] = stage;
+    s.ev_count++;
+}
+
+static void prof_fold(Sim& s) {
+    if (s.ev_count == 0) return;
+    cudaEventSynchronize(s.ev[s.ev_count - 1]);
+    for (int i = 1; i < s.ev_count; ++i) {
+        const int st = s.ev_stage[i];
+        if (st < 0 || st >= kStages) continue;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, s.ev[i - 1], s.ev[i]) == cudaSuccess) s.stage_ms[st] += ms;
+    }
+    s.ev_count = 0;
+}
+
+// host-side float64 tables of Eq. 3: bin centres T[u] and edges E[k]
+static void codec_tables(float* T, float* E) {
+    const double pi = 3.141592653589793238462643383279502884;
+    for (int u = 0; u < 256; ++u) T[u] = (float)tan(pi * ((u + 0.5) / 256.0 - 0.5));
+    E[0] = -INFINITY;
+    for (int k = 1; k < 256; ++k) E[k] = (float)tan(pi * (k / 256.0 - 0.5));
+}
+
+__global__ void k_twiddles(int n, float2* tf, double2* td) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        double sv, cv;
+        sincospi(2.0 * (double)k / (double)n, &sv, &cv);
+        td[k] = make_double2(cv, -sv);
+        tf[k] = make_float2((float)cv, (float)-sv);
+    }
+}
+
+static int sync_and_check(Sim& s) {
+    cudaError_t e = cudaStreamSynchronize(s.stream);
+    if (e != cudaSuccess) return set_error(s, PMPM_ECUDA, "stream: %s", cudaGetErrorString(e));
+    uint32_t flags = 0;
+    e = cudaMemcpyAsync(&flags, s.err, 4, cudaMemcpyDeviceToHost, s.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s.stream);
+    if (e != cudaSuccess) return set_error(s, PMPM_ECUDA, "error word: %s", cudaGetErrorString(e));
+    if (flags) {
+        cudaMemsetAsync(s.err, 0, 4, s.stream);
+        cudaStreamSynchronize(s.stream);
+        if (flags & kErrCount) return set_error(s, PMPM_ECOUNT, "particle count not conserved");
+        return set_error(s, PMPM_EOVERFLOW,
+                         "device range check failed (flags 0x%x: 1 fine density, 2 momentum, "
+                         "4 velocity deviation, 16 non-finite, 32 drift)", flags);
+    }
+    return PMPM_OK;
+}
+
+static double sched_a(const Sim& s, int64_t n) {
+    return s.cfg.a_init * pow(s.cfg.a_final / s.cfg.a_init, (double)n / (double)s.cfg.n_steps);
+}
+
+static int one_step(Sim& s) {
+    if (s.step >= s.cfg.n_steps) return set_error(s, PMPM_EINVAL, "schedule exhausted");
+    const int64_t n = s.step;
+    const double an = sched_a(s, n), an1 = sched_a(s, n + 1);
+    const double a_lo = n == 0 ? s.cfg.a_init : sqrt(sched_a(s, n - 1) * an);
+    const double a_hi = sqrt(an * an1);
+    const double rho_bar = (double)s.n / ((double)s.nf * s.nf * s.nf);
+    const double kick = 3.0 / (8.0 * 3.141592653589793238462643383279502884 * rho_bar) * 2.0 *
+                        (sqrt(a_hi) - sqrt(a_lo));
+    const double drift = 2.0 * (1.0 / sqrt(an) - 1.0 / sqrt(an1));
+    int rc;
+    s.in_step = true;
+    if (!s.offsets_valid) {
+        if ((rc = scan_counts(s, s.counts[s.cur], s.offsets[s.cur]))) return rc;
+        s.offsets_valid = true;
+    }
+    prof_mark(s, -1);
+    if ((rc = coarse_deposit(s))) return rc;
+    prof_mark(s, 0);
+    if ((rc = coarse_force(s))) return rc;
+    prof_mark(s, 1);
+    cudaMemsetAsync(s.counts[1 - s.cur], 0, sizeof(int32_t) * s.ncells, s.stream);
+    cudaMemsetAsync(s.S, 0, sizeof(unsigned long long) * 3 * s.ncells, s.stream);
+    if ((rc = tile_pass(s, 1, (float)kick, (float)(drift * kCodesPerFine), nullptr))) return rc;
+    prof_mark(s, 2);
+    if ((rc = encode_from_qp(s, true))) return rc;
+    s.in_step = false;
+    s.step = n + 1;
+    s.a = an1;
+    return PMPM_OK;
+}
+
+}  // namespace pmpm
+
+using namespace pmpm;
+
+extern "C" {
+
+int pmpm_workspace_bytes(const pmpm_config* cfg, size_t* bytes) {
+    char msg[256];
+    int rc = validate(cfg, msg, sizeof(msg));
+    if (rc) {
+        snprintf(g_init_msg, sizeof(g_init_msg), "%s", msg);
+        return rc;
+    }
+    if (!bytes) return PMPM_EINVAL;
+    Sim* s = new (std::nothrow) Sim();
+    if (!s) return PMPM_ENOMEM;
+    derive(*s, cfg);
+    *bytes = layout(*s, nullptr);
+    delete s;
+    return PMPM_OK;
+}
+
+int pmpm_init(const pmpm_config* cfg, void* d_workspace, size_t bytes, void* cuda_stream,
+              pmpm_sim** out) {
+    char msg[256];
+    int rc = validate(cfg, msg, sizeof(msg));
+    if (rc) {
+        snprintf(g_init_msg, sizeof(g_init_msg), "%s", msg);
+        return rc;
+    }
+    if (!out || !d_workspace) {
+        snprintf(g_init_msg, sizeof(g_init_msg), "null workspace or output handle");
+        return PMPM_EINVAL;
+    }
+    if (reinterpret_cast<uintptr_t>(d_workspace) % 256) {
+        snprintf(g_init_msg, sizeof(g_init_msg), "workspace must be 256-byte aligned");
+        return PMPM_EINVAL;
+    }
+    pmpm_sim* h = new (std::nothrow) pmpm_sim();
+    if (!h) return PMPM_ENOMEM;
+    Sim& s = h->s;
+    derive(s, cfg);
+    const size_t need = layout(s, nullptr);
+    if (bytes < need) {
+        snprintf(g_init_msg, sizeof(g_init_msg), "workspace %zu bytes < required %zu", bytes, need);
+        delete h;
+        return PMPM_ENOMEM;
+    }
+    s.ws = static_cast<uint8_t*>(d_workspace);
+    s.ws_bytes = bytes;
+    s.stream = static_cast<cudaStream_t>(cuda_stream);
+    layout(s, s.ws);
+    cudaGetDevice(&s.device);
+    cudaMemsetAsync(s.err, 0, 4, s.stream);
+    float T[256], E[256];
+    codec_tables(T, E);
+    cudaMemcpyAsync(s.Tdec, T, sizeof(T), cudaMemcpyHostToDevice, s.stream);
+    cudaMemcpyAsync(s.Eedge, E, sizeof(E), cudaMemcpyHostToDevice, s.stream);
+    k_twiddles<<<grid_for(s.fft_max, 256), 256, 0, s.stream>>>(s.fft_max, s.tw_f, s.tw_d);
+    rc = check_launch(s, "twiddles");
+    if (!rc) rc = build_green_tables(s);
+    if (!rc) rc = sync_and_check(s);
+    if (rc) {
+        snprintf(g_init_msg, sizeof(g_init_msg), "%s", s.msg);
+        delete h;
+        return rc;
+    }
+    s.a = cfg->a_init;
+    *out = h;
+    return PMPM_OK;
+}
+
+int pmpm_ic_zeldovich(pmpm_sim* h, uint64_t seed, double slope, double k_c, double rms_disp) {
+    if (!h) return PMPM_EINVAL;
+    Sim& s = h->s;
+    if (!(k_c > 0.0) || !(rms_disp >= 0.0)) return set_error(s, PMPM_EINVAL, "bad spectrum");
+    return ic_zeldovich(s, seed, slope, k_c, rms_disp);
+}
+
+int pmpm_step(pmpm_sim* h, int32_t nsteps) {
+    if (!h) return PMPM_EINVAL;
+    Sim& s = h->s;
+    if (!s.have_state) return set_error(s, PMPM_ESTATE, "no particle state");
+    if (nsteps < 0 || s.step + nsteps > s.cfg.n_steps)
+        return set_error(s, PMPM_EINVAL, "%d steps exceed the schedule (%lld of %d taken)", nsteps,
+                         (long long)s.step, s.cfg.n_steps);
+    for (int i = 0; i < nsteps; ++i) {
+        const int rc = one_step(s);
+        if (rc) return rc;
+        if (s.prof && s.ev_count > kEventRing - 16) prof_fold(s);
+    }
+    return PMPM_OK;
+}
+
+int pmpm_power_spectrum(pmpm_sim* h, int32_t nmesh, int32_t nbins, double* k, double* pk,
+                        int64_t* nmodes) {
+    if (!h || !k || !pk || !nmodes) return PMPM_EINVAL;
+    Sim& s = h->s;
+    if (!s.have_state) return set_error(s, PMPM_ESTATE, "no particle state");
+    if (!s.offsets_valid) {
+        int rc = scan_counts(s, s.counts[s.cur], s.offsets[s.cur]);
+        if (rc) return rc;
+        s.offsets_valid = true;
+    }
+    int rc = power_spectrum(s, nmesh, nbins, k, pk, nmodes);
+    if (rc) return rc;
+    return sync_and_check(s);
+}
+
+static int copy_out(Sim& s, void* dst, const void* src, size_t bytes) {
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s.stream);
+    if (e != cudaSuccess) return set_error(s, PMPM_ECUDA, "fetch: %s", cudaGetErrorString(e));
+    return PMPM_OK;
+}
+
+int pmpm_fetch(pmpm_sim* h, int32_t what, void* dst, size_t bytes) {
+    if (!h || !dst) return PMPM_EINVAL;
+    Sim& s = h->s;
+    const size_t N = (size_t)s.n, C = (size_t)s.ncells;
+    size_t need = 0;
+    switch (what) {
+        case PMPM_STREAMS: need = 6 * N; break;
+        case PMPM_COUNTS: need = 4 * C; break;
+        case PMPM_VC: need = 12 * C; break;
+        case PMPM_SCALARS: need = sizeof(pmpm_scalars); break;
+        case PMPM_DECODED_Q: case PMPM_DECODED_P: case PMPM_FORCE: need = 12 * N; break;
+        case PMPM_COARSE_DENSITY: need = 8 * C; break;
+        default: return set_error(s, PMPM_EINVAL, "unknown fetch item %d", what);
+    }
+    if (bytes != need) return set_error(s, PMPM_EINVAL, "fetch %d needs %zu bytes, got %zu", what, need, bytes);
+    if (!s.have_state) return set_error(s, PMPM_ESTATE, "no particle state");
+    int rc = PMPM_OK;
+    if (!s.offsets_valid && what != PMPM_STREAMS && what != PMPM_COUNTS && what != PMPM_VC &&
+        what != PMPM_SCALARS) {
+        if ((rc = scan_counts(s, s.counts[s.cur], s.offsets[s.cur]))) return rc;
+        s.offsets_valid = true;
+    }
+    switch (what) {
+        case PMPM_STREAMS: rc = copy_out(s, dst, s.streams[s.cur], need); break;
+        case PMPM_COUNTS: rc = copy_out(s, dst, s.counts[s.cur], need); break;
+        case PMPM_VC: rc = copy_out(s, dst, s.vc[s.cur], need); break;
+        case PMPM_SCALARS: {
+            float sig = 0.f;
+            cudaError_t e = cudaMemcpyAsync(&sig, s.sigma_d[s.cur], 4, cudaMemcpyDeviceToHost, s.stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s.stream);
+            if (e != cudaSuccess) return set_error(s, PMPM_ECUDA, "fetch: %s", cudaGetErrorString(e));
+            pmpm_scalars sc;
+            sc.a = s.a;
+            sc.sigma = sig;
+            sc.step = s.step;
+            sc.n = s.n;
+            memcpy(dst, &sc, sizeof(sc));
+            break;
+        }
+        case PMPM_DECODED_Q:
+        case PMPM_DECODED_P:
+            if ((rc = decode_state(s))) return rc;
+            rc = copy_out(s, dst, what == PMPM_DECODED_Q ? (const void*)s.Qn : (const void*)s.Pn, need);
+            break;
+        case PMPM_FORCE:
+            if ((rc = coarse_deposit(s))) return rc;
+            if ((rc = coarse_force(s))) return rc;
+            if ((rc = tile_pass(s, 0, 0.f, 0.f, s.Pn))) return rc;
+            rc = copy_out(s, dst, s.Pn, need);
+            break;
+        case PMPM_COARSE_DENSITY:
+            if ((rc = coarse_deposit(s))) return rc;
+            rc = copy_out(s, dst, s.rho_c, need);
+            break;
+    }
+    if (rc) return rc;
+    return sync_and_check(s);
+}
+
+int pmpm_load(pmpm_sim* h, int32_t what, const void* src, size_t bytes) {
+    if (!h || !src) return PMPM_EINVAL;
+    Sim& s = h->s;
+    const size_t N = (size_t)s.n, C = (size_t)s.ncells;
+    cudaError_t e = cudaSuccess;
+    switch (what) {
+        case PMPM_STREAMS:
+            if (bytes != 6 * N) return set_error(s, PMPM_EINVAL, "streams need %zu bytes", 6 * N);
+            e = cudaMemcpyAsync(s.streams[s.cur], src, bytes, cudaMemcpyHostToDevice, s.stream);
+            s.loaded |= 1;
+            break;
+        case PMPM_COUNTS: {
+            if (bytes != 4 * C) return set_error(s, PMPM_EINVAL, "counts need %zu bytes", 4 * C);
+            // the kernels index the particle streams through these counts:
+            // they must be non-negative and add up to N
+            const int32_t* c = static_cast<const int32_t*>(src);
+            int64_t total = 0;
+            for (size_t i = 0; i < C; ++i) {
+                if (c[i] < 0) return set_error(s, PMPM_EINVAL, "negative count");
+                total += c[i];
+            }
+            if (total != s.n)
+                return set_error(s, PMPM_EINVAL, "counts add up to %lld, not N = %lld",
+                                 (long long)total, (long long)s.n);
+            e = cudaMemcpyAsync(s.counts[s.cur], src, bytes, cudaMemcpyHostToDevice, s.stream);
+            s.offsets_valid = false;
+            s.loaded |= 2;
+            break;
+        }
+        case PMPM_VC:
+            if (bytes != 12 * C) return set_error(s, PMPM_EINVAL, "v_c needs %zu bytes", 12 * C);
+            e = cudaMemcpyAsync(s.vc[s.cur], src, bytes, cudaMemcpyHostToDevice, s.stream);
+            s.loaded |= 4;
+            break;
+        case PMPM_SCALARS: {
+            if (bytes != sizeof(pmpm_scalars)) return set_error(s, PMPM_EINVAL, "scalars size");
+            pmpm_scalars sc;
+            memcpy(&sc, src, sizeof(sc));
+            if (sc.n != s.n) return set_error(s, PMPM_EINVAL, "scalars n=%lld != %lld", (long long)sc.n, (long long)s.n);
+            if (sc.step < 0 || sc.step > s.cfg.n_steps) return set_error(s, PMPM_EINVAL, "scalars step");
+            const float sig = (float)sc.sigma;
+            e = cudaMemcpyAsync(s.sigma_d[s.cur], &sig, 4, cudaMemcpyHostToDevice, s.stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s.stream);
+            s.a = sc.a;
+            s.step = sc.step;
+            s.loaded |= 8;
+            break;
+        }
+        case PMPM_QP: {
+            if (bytes != 24 * N) return set_error(s, PMPM_EINVAL, "Q/P need %zu bytes", 24 * N);
+            e = cudaMemcpyAsync(s.Qn, src, 12 * N, cudaMemcpyHostToDevice, s.stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(s.Pn, static_cast<const uint8_t*>(src) + 12 * N, 12 * N,
+                                    cudaMemcpyHostToDevice, s.stream);
+            if (e != cudaSuccess) break;
+            // the codes index cells: check their range before any kernel uses them
+            const int32_t* q = static_cast<const int32_t*>(src);
+            const int64_t M = (int64_t)s.nc * kBins;
+            for (size_t i = 0; i < 3 * N; ++i)
+                if (q[i] < 0 || q[i] >= M) {
+                    cudaStreamSynchronize(s.stream);
+                    return set_error(s, PMPM_EINVAL, "code out of range");
+                }
+            int rc = encode_from_qp(s, false);
+            if (rc) return rc;
+            s.loaded = 15;
+            break;
+        }
+        default:
+            return set_error(s, PMPM_EINVAL, "unknown load item %d", what);
+    }
+    if (e != cudaSuccess) return set_error(s, PMPM_ECUDA, "load: %s", cudaGetErrorString(e));
+    // a store is usable once streams, counts, v_c and scalars are all present
+    s.have_state = s.loaded == 15;
+    return sync_and_check(s);
+}
+
+int pmpm_sync(pmpm_sim* h) {
+    if (!h) return PMPM_EINVAL;
+    return sync_and_check(h->s);
+}
+
+int pmpm_stage_times(pmpm_sim* h, int32_t enable, double* times, int32_t n, int64_t* launches) {
+    if (!h) return PMPM_EINVAL;
+    Sim& s = h->s;
+    if (!s.ev_made) {
+        for (int i = 0; i < kEventRing; ++i) cudaEventCreate(&s.ev[i]);
+        s.ev_made = true;
+    }
+    prof_fold(s);
+    if (times) {
+        for (int i = 0; i < n && i < kStages; ++i) times[i] = s.stage_ms[i];
+        if (launches) *launches = s.launches;
+    } else {
+        for (int i = 0; i < kStages; ++i) s.stage_ms[i] = 0.0;
+        s.launches = 0;
+    }
+    s.prof = enable != 0;
+    return PMPM_OK;
+}
+
+void pmpm_destroy(pmpm_sim* h) {
+    if (!h) return;
+    Sim& s = h->s;
+    cudaStreamSynchronize(s.stream);
+    if (s.ev_made)
+        for (int i = 0; i < kEventRing; ++i) cudaEventDestroy(s.ev[i]);
+    delete h;
+}
+
+const char* pmpm_last_error(const pmpm_sim* h) {
+    if (!h) return g_init_msg;
+    return h->s.msg;
+}
+
+int pmpm_codec_tables(float* T, float* E) {
+    if (!T || !E) return PMPM_EINVAL;
+    codec_tables(T, E);
+    return PMPM_OK;
+}
+
+}  // extern "C"

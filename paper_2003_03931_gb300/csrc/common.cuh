@@ -1,0 +1,136 @@
+// common.cuh -- definitions shared by the PM-PM kernels: geometry constants,
+// error flags, the fixed-point codec of Sec. III-A (Eq. 2-4) and integer CIC.
+//
+// Functions marked PMPM_HD compile for host and device so that the tile
+// phases can be exercised one thread at a time on a CPU; the product path
+// runs them only inside CUDA kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define PMPM_HD __host__ __device__ __forceinline__
+
+namespace pmpm {
+
+// ---------------------------------------------------------------- geometry
+constexpr int kRatio = 4;        // coarse / fine cell size (Sec. II)
+constexpr int kBins = 256;       // bins per coarse cell per dimension (Eq. 2)
+constexpr int kCodesPerFine = kBins / kRatio;   // 64 codes per fine cell
+constexpr int kBuffer = 6;       // tile buffer = short-range cutoff, fine cells (Sec. IV-A.2)
+constexpr int kTileFFT = 32;     // edge of the tile FFT box (>= 20 + 2*6)
+constexpr int kTileMaxCoarse = 5;                // largest tile, coarse cells
+constexpr int kTileOut = kTileMaxCoarse * kRatio + 2;   // fine nodes a tile gathers from (22)
+constexpr int kGreenS = kTileFFT / 2 + 1;        // 17: |k| range of the tile Green table
+constexpr int kPFixBits = 24;    // momenta rounded to 2^-24 for the cell sums
+constexpr int kD2FixBits = 32;   // squared deviations rounded to 2^-32
+constexpr float kSigmaFloor = 5.9604644775390625e-08f;  // 2^-24
+
+// ---------------------------------------------------------------- error flags
+enum : uint32_t {
+    kErrFineOverflow = 1u,    // a fine tile node exceeded 2^32 - 1 weight units
+    kErrMomentum = 2u,        // |p| too large for the 2^-24 fixed-point sums
+    kErrDeviation = 4u,       // |p - v_c| >= 2^16 (dispersion sum range)
+    kErrCount = 8u,           // counts do not add up to N
+    kErrNaN = 16u,            // non-finite momentum or force
+    kErrDrift = 32u,          // drift larger than the int32 code range
+};
+
+#ifdef __CUDA_ARCH__
+PMPM_HD float fadd_rn(float a, float b) { return __fadd_rn(a, b); }
+PMPM_HD float fsub_rn(float a, float b) { return __fsub_rn(a, b); }
+PMPM_HD float fmul_rn(float a, float b) { return __fmul_rn(a, b); }
+PMPM_HD float fdiv_rn(float a, float b) { return __fdiv_rn(a, b); }
+PMPM_HD double dmul_rn(double a, double b) { return __dmul_rn(a, b); }
+PMPM_HD double dadd_rn(double a, double b) { return __dadd_rn(a, b); }
+PMPM_HD void flag_error(uint32_t* err, uint32_t bits) { atomicOr(err, bits); }
+#else
+PMPM_HD float fadd_rn(float a, float b) { volatile float r = a + b; return r; }
+PMPM_HD float fsub_rn(float a, float b) { volatile float r = a - b; return r; }
+PMPM_HD float fmul_rn(float a, float b) { volatile float r = a * b; return r; }
+PMPM_HD float fdiv_rn(float a, float b) { volatile float r = a / b; return r; }
+PMPM_HD double dmul_rn(double a, double b) { volatile double r = a * b; return r; }
+PMPM_HD double dadd_rn(double a, double b) { volatile double r = a + b; return r; }
+PMPM_HD void flag_error(uint32_t* err, uint32_t bits) { *err |= bits; }
+#endif
+
+// ---------------------------------------------------------------- codec
+// Eq. 3 decode: p = v_c + sigma * T[u], each operation an IEEE float32 op.
+PMPM_HD float decode_momentum(float vc, float sigma, float tu) {
+    return fadd_rn(vc, fmul_rn(sigma, tu));
+}
+
+// Eq. 4: the paper's fast arctangent, |x| <= 1 branch and its reflection
+// atan(x) = +-pi/2 - atan(1/x) for |x| > 1.
+PMPM_HD float atan_eq4(float x) {
+    const float q = 0.78539816339744831f;   // pi/4
+    const float c = 0.273f;
+    float ax = x < 0.f ? -x : x;
+    if (ax <= 1.f) return q * x + c * x * (1.f - ax);
+    float inv = 1.f / x;
+    float ainv = inv < 0.f ? -inv : inv;
+    float half_pi = x > 0.f ? 1.5707963267948966f : -1.5707963267948966f;
+    return half_pi - q * inv - c * inv * (1.f - ainv);
+}
+
+// Eq. 3 encode: u = #{k in 1..255 : E[k] <= t}, t = fl32(fl32(p - v_c) / sigma).
+// The Eq. 4 angle gives a first guess within one bin (its error 0.0038 rad is
+// below the bin width pi/256); one comparison on each side against the edge
+// table makes the result identical to the definition.
+PMPM_HD uint32_t encode_momentum(float p, float vc, float sigma, const float* E,
+                                 uint32_t* err) {
+    float t = fdiv_rn(fsub_rn(p, vc), sigma);
+    if (!(t == t)) {            // NaN
+        flag_error(err, kErrNaN);
+        return 128u;
+    }
+    float th = atan_eq4(t);
+    float g = th * 81.487330863050417f + 128.f;   // 256/pi, bin of the angle
+    int u = (int)floorf(g < 0.f ? 0.f : (g > 255.f ? 255.f : g));
+    if (u < 255 && E[u + 1] <= t) ++u;
+    else if (u > 0 && E[u] > t) --u;
+    return (uint32_t)u;
+}
+
+// ---------------------------------------------------------------- CIC
+// Nodes at cell centres.  For a mesh whose node spacing holds U position
+// codes, s = 2Q + 1 - U is the particle's offset from node 0 in units of
+// 1/(2U); the lower node is floor(s / 2U) and the upper weight s mod 2U.
+struct Cic1 {
+    int i0;      // lower node
+    int w1;      // weight of node i0+1, in 1/(2U) units
+};
+
+// fine mesh: U = 64, weights in 1/128
+PMPM_HD Cic1 cic_fine(int64_t Q) {
+    int64_t s = 2 * Q + 1 - kCodesPerFine;
+    Cic1 c;
+    c.i0 = (int)(s >> 7);
+    c.w1 = (int)(s & 127);
+    return c;
+}
+
+// coarse mesh: U = 256, weights in 1/512
+PMPM_HD Cic1 cic_coarse(int64_t Q) {
+    int64_t s = 2 * Q + 1 - kBins;
+    Cic1 c;
+    c.i0 = (int)(s >> 9);
+    c.w1 = (int)(s & 511);
+    return c;
+}
+
+PMPM_HD int wrap(int i, int n) {
+    int r = i % n;
+    return r < 0 ? r + n : r;
+}
+
+// Tile partition along one axis: n_t tiles of 4 or 5 coarse cells
+// (boundary i at floor(i * nc / n_t)).
+PMPM_HD int tile_count(int nc, int tile_max) {
+    return (nc + tile_max - 1) / tile_max;
+}
+PMPM_HD int tile_bound(int i, int nc, int nt) {
+    return (int)(((int64_t)i * nc) / nt);
+}
+
+}  // namespace pmpm

@@ -1,0 +1,143 @@
+// ic.cu -- Zel'dovich initial conditions (Sec. IV-A.2) for a power-law
+// spectrum P(k) = k^slope exp(-(k/k_c)^2), in float64 on the device:
+//   white noise (SplitMix64 counters 2i, 2i+1; Box-Muller) -> DFT ->
+//   Psi~_d = i k_d / k^2 sqrt(P) w~ (k = 0 and Nyquist planes zeroed) ->
+//   inverse DFT -> rms normalisation -> x = q + a Psi, p = a^(3/2) Psi ->
+//   Q = floor(64 x) mod (256 nc), p in float32 -> cell-ordered encode.
+#include "pmpm_impl.cuh"
+
+namespace pmpm {
+
+namespace {
+
+constexpr double kPi = 3.141592653589793238462643383279502884;
+
+// SplitMix64 output for counter j (Steele, Lea & Flood 2014)
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long seed,
+                                                         unsigned long long j) {
+    unsigned long long z = seed + (j + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_ic_noise(int64_t n, unsigned long long seed, double2* w) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long z1 = splitmix64(seed, 2ull * i);
+        const unsigned long long z2 = splitmix64(seed, 2ull * i + 1ull);
+        const double u1 = ((double)(z1 >> 11) + 1.0) * 0x1p-53;
+        const double u2 = (double)(z2 >> 11) * 0x1p-53;
+        w[i] = make_double2(sqrt(-2.0 * log(u1)) * cos(2.0 * kPi * u2), 0.0);
+    }
+}
+
+__global__ void k_ic_spectrum(int np, int nf, int d, double slope, double kc,
+                              const double2* __restrict__ w, double2* __restrict__ out) {
+    const int64_t n = (int64_t)np * np * np;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int ix = (int)(i % np), iy = (int)((i / np) % np), iz = (int)(i / ((int64_t)np * np));
+        const int h = np / 2;
+        const int nx = ix < h ? ix : ix - np, ny = iy < h ? iy : iy - np, nz = iz < h ? iz : iz - np;
+        double2 v = make_double2(0.0, 0.0);
+        if (!(nx == -h || ny == -h || nz == -h) && (nx | ny | nz)) {
+            const double kf = 2.0 * kPi / nf;
+            const double kx = kf * nx, ky = kf * ny, kz = kf * nz;
+            const double k2 = kx * kx + ky * ky + kz * kz;
+            const double k = sqrt(k2);
+            const double amp = sqrt(pow(k, slope) * exp(-(k / kc) * (k / kc)));
+            const double kd = d == 0 ? kx : (d == 1 ? ky : kz);
+            const double c = kd / k2 * amp;
+            const double2 a = w[i];
+            v = make_double2(-c * a.y, c * a.x);   // i c a
+        }
+        out[i] = v;
+    }
+}
+
+__global__ void k_ic_store(int64_t n, int d, const double2* __restrict__ in, double* __restrict__ psi,
+                           double* __restrict__ partial) {
+    double acc = 0.0;
+    const double inv_n = 1.0 / (double)n;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = in[i].x * inv_n;
+        psi[d * n + i] = v;
+        acc += v * v;
+    }
+    // deterministic block sum (fixed grid and order)
+    __shared__ double sh[256];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[d * gridDim.x + blockIdx.x] += sh[0];
+}
+
+__global__ void k_ic_scale(int nblk, int64_t n, double a_init, double rms_disp, const double* partial,
+                           double* scale) {
+    double s = 0.0;
+    for (int d = 0; d < 3; ++d)
+        for (int b = 0; b < nblk; ++b) s += partial[d * nblk + b];
+    const double rms = sqrt(s / (double)n);
+    *scale = rms > 0.0 ? rms_disp / (a_init * rms) : 0.0;
+}
+
+__global__ void k_ic_particles(int np, int nc, double a_init, const double* __restrict__ psi,
+                               const double* __restrict__ scale_p, int32_t* __restrict__ Qn,
+                               float* __restrict__ Pn) {
+    const int64_t n = (int64_t)np * np * np;
+    const double scale = *scale_p;
+    const double spacing = 4.0 * nc / (double)np;
+    const double a15 = pow(a_init, 1.5);
+    const int64_t M = (int64_t)nc * kBins;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int li[3] = {(int)(i % np), (int)((i / np) % np), (int)(i / ((int64_t)np * np))};
+        for (int d = 0; d < 3; ++d) {
+            const double ps = psi[d * n + i] * scale;
+            const double q = ((double)li[d] + 0.5) * spacing;
+            const double x = q + a_init * ps;
+            int64_t Q = (int64_t)floor(x * (double)kCodesPerFine) % M;
+            if (Q < 0) Q += M;
+            Qn[d * n + i] = (int32_t)Q;
+            Pn[d * n + i] = (float)(a15 * ps);
+        }
+    }
+}
+
+}  // namespace
+
+int ic_zeldovich(Sim& s, uint64_t seed, double slope, double kc, double rms) {
+    const int np = s.np;
+    const int64_t n = s.n;
+    cudaStream_t st = s.stream;
+    // scratch: w~ [n] double2, work [n] double2, psi [3][n] double; Q/P alias the first two
+    double2* w = reinterpret_cast<double2*>(s.scratch);
+    double2* work = w + n;
+    double* psi = reinterpret_cast<double*>(work + n);
+    double* partial = s.ic_partial;
+    const int nblk = 1024;
+    cudaMemsetAsync(partial, 0, sizeof(double) * (3 * nblk + 1), st);
+    k_ic_noise<<<grid_for(n, 256), 256, 0, st>>>(n, (unsigned long long)seed, w);
+    int rc = fft3d<double>(s, w, np, -1);
+    if (rc) return rc;
+    for (int d = 0; d < 3; ++d) {
+        k_ic_spectrum<<<grid_for(n, 256), 256, 0, st>>>(np, s.nf, d, slope, kc, w, work);
+        if ((rc = fft3d<double>(s, work, np, 1))) return rc;
+        k_ic_store<<<nblk, 256, 0, st>>>(n, d, work, psi, partial);
+    }
+    double* scale = partial + 3 * nblk;
+    k_ic_scale<<<1, 1, 0, st>>>(nblk, n, s.cfg.a_init, rms, partial, scale);
+    k_ic_particles<<<grid_for(n, 256), 256, 0, st>>>(np, s.nc, s.cfg.a_init, psi, scale, s.Qn, s.Pn);
+    s.launches += 4 + 3 * 2;
+    if ((rc = check_launch(s, "ic"))) return rc;
+    s.a = s.cfg.a_init;
+    s.step = 0;
+    return encode_from_qp(s, false);
+}
+
+}  // namespace pmpm

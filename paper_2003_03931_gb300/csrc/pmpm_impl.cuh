@@ -1,0 +1,116 @@
+// pmpm_impl.cuh -- the sim object, its workspace layout and the host-side
+// helpers shared by the translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include "../../include/pmpm.h"
+#include "common.cuh"
+
+namespace pmpm {
+
+constexpr int kStages = 6;          // see pmpm_stage_times
+constexpr int kEventRing = 4096;
+
+struct Sim {
+    pmpm_config cfg;
+    int device = 0;
+    int nc = 0, nf = 0, np = 0, nt = 0, tile_max = 0, pk_max = 0, fft_max = 0;
+    int64_t n = 0, ncells = 0;
+    cudaStream_t stream = nullptr;
+    uint8_t* ws = nullptr;
+    size_t ws_bytes = 0;
+
+    // particle store, double-buffered (Sec. III-A)
+    uint8_t* streams[2] = {nullptr, nullptr};   // [6][N]
+    int32_t* counts[2] = {nullptr, nullptr};    // [nc^3]
+    int64_t* offsets[2] = {nullptr, nullptr};   // [nc^3 + 1]
+    float* vc[2] = {nullptr, nullptr};          // [3][nc^3]
+    float* sigma_d[2] = {nullptr, nullptr};     // device scalar
+    int cur = 0;
+    bool have_state = false;
+    int loaded = 0;                              // bits: streams, counts, v_c, scalars
+    bool offsets_valid = false;
+    double a = 0.0;
+    int64_t step = 0;
+
+    // step buffers
+    int32_t* fill = nullptr;                    // [nc^3]
+    unsigned long long* S = nullptr;            // [3][nc^3] fixed-point momentum sums
+    unsigned long long* d2 = nullptr;           // [2] 128-bit dispersion sum (lo, hi)
+    long long* rho_c = nullptr;                 // [nc^3]
+    float2* cA = nullptr;                       // [nc^3] coarse spectra
+    float2* cB1 = nullptr;
+    float2* cB2 = nullptr;
+    float* Fl = nullptr;                        // [3][nc^3]
+    float* green_coarse = nullptr;              // [(nc/2+1)^3]
+    float* green_fine = nullptr;                // [17^3]
+    float* Tdec = nullptr;                      // [256]
+    float* Eedge = nullptr;                     // [256]
+    float2* tw_f = nullptr;                     // [fft_max] exp(-2 pi i k / fft_max)
+    double2* tw_d = nullptr;
+    uint32_t* err = nullptr;
+    long long* blocksums = nullptr;
+    int64_t nblocks_scan = 0;
+    double* ic_partial = nullptr;               // [3*1024 + 1] IC rms partial sums
+    double* pk_bins = nullptr;                  // [3][pk_max/2 + 1] power-spectrum sums
+
+    // transient scratch (step, init, ICs and power spectrum share it)
+    uint8_t* scratch = nullptr;
+    size_t scratch_bytes = 0;
+    int32_t* Qn = nullptr;                      // [3][N] (aliases scratch)
+    float* Pn = nullptr;                        // [3][N] (aliases scratch)
+
+    // stage timing
+    bool in_step = false;
+    bool prof = false;
+    cudaEvent_t ev[kEventRing];
+    int ev_stage[kEventRing];
+    int ev_count = 0;
+    bool ev_made = false;
+    double stage_ms[kStages] = {0, 0, 0, 0, 0, 0};
+    int64_t launches = 0;
+
+    char msg[512] = {0};
+};
+
+inline uintptr_t align_up(uintptr_t p, uintptr_t a = 256) { return (p + a - 1) & ~(a - 1); }
+
+inline int grid_for(int64_t n, int block, int cap = 152 * 64) {
+    int64_t g = (n + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (int)g;
+}
+
+int set_error(Sim& s, int code, const char* fmt, ...);
+int check_launch(Sim& s, const char* what);
+
+// workspace layout: fills the Sim's pointers when base != nullptr; returns bytes
+size_t layout(Sim& s, uint8_t* base);
+
+// kernels, by translation unit
+int build_green_tables(Sim& s);
+size_t green_scratch_bytes(int nc);
+template <typename R>
+int fft3d(Sim& s, void* data, int n, int sign);
+int fft_pass_count(int n);
+int coarse_force(Sim& s);             // deposit + FFT + Green -> s.Fl
+int coarse_deposit(Sim& s);           // -> s.rho_c
+int tile_pass(Sim& s, int mode, float kick, float drift, float* G);
+int scan_counts(Sim& s, const int32_t* counts, int64_t* offsets);
+int encode_from_qp(Sim& s, bool counts_ready);
+int decode_state(Sim& s);              // -> s.Qn, s.Pn
+int ic_zeldovich(Sim& s, uint64_t seed, double slope, double kc, double rms);
+int power_spectrum(Sim& s, int nmesh, int nbins, double* k, double* pk, int64_t* nm);
+void prof_mark(Sim& s, int stage);     // records an event closing `stage` (-1: opening)
+
+inline uint8_t* cur_stream(Sim& s, int which) { return s.streams[s.cur] + (size_t)which * s.n; }
+
+}  // namespace pmpm
+
+struct pmpm_sim {
+    pmpm::Sim s;
+};

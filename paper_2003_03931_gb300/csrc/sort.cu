@@ -1,0 +1,305 @@
+// sort.cu -- cell-ordered re-encode of the particles (Sec. III-A): "particles'
+// m^i must be stored in memory in a cell-ordered way", with the per-cell
+// counts and the cell-mean velocity v_c of Eq. 3.
+//
+// Input: new codes Q [3][N] and momenta p [3][N] (float32), any order.
+//   hist    counts[c] and fixed-point momentum sums S[d][c] (int64, p rounded
+//           to 2^-24): exact integers, independent of order
+//   scan    offsets = exclusive scan of counts (int64); v_c = fl32(fl64(S) /
+//           n * 2^-24)
+//   sigma   sum over particles of round((p - v_c)^2 * 2^32) in 128 bits;
+//           sigma = fl32(sqrt(sum 2^-32 / 3N))
+//   scatter slot = offsets[c] + rank (atomic per cell); m = Q mod 256 and the
+//           Eq. 3 code u (Eq. 4 guess + edge fix-up) written to the new store
+// Within-cell order is not specified; every quantity above is independent of
+// it, so the encoded store is the same multiset per cell on every run.
+#include "pmpm_impl.cuh"
+
+namespace pmpm {
+
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kScanThreads * kScanItems;   // 4096 cells per block
+
+__device__ __forceinline__ long long block_exclusive_scan(long long v, long long* sh, long long& total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        long long w = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        sh[lane] = w;
+    }
+    __syncthreads();
+    total = sh[(blockDim.x >> 5) - 1];
+    const long long before = warp > 0 ? sh[warp - 1] : 0;
+    __syncthreads();
+    return before + x - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(int64_t ncells, const int32_t* __restrict__ counts,
+                                                              long long* __restrict__ blocksums) {
+    __shared__ long long sh[32];
+    const int64_t b0 = (int64_t)blockIdx.x * kScanTile;
+    long long acc = 0;
+    for (int k = 0; k < kScanItems; ++k) {
+        const int64_t i = b0 + (int64_t)k * kScanThreads + threadIdx.x;
+        if (i < ncells) acc += counts[i];
+    }
+    long long total;
+    block_exclusive_scan(acc, sh, total);
+    if (threadIdx.x == 0) blocksums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_top(int64_t nb, long long* blocksums, int64_t n,
+                                                   int64_t* offsets_end, uint32_t* err) {
+    __shared__ long long sh[32];
+    long long carry = 0;
+    for (int64_t base = 0; base < nb; base += blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const long long v = i < nb ? blocksums[i] : 0;
+        long long total;
+        const long long ex = block_exclusive_scan(v, sh, total);
+        if (i < nb) blocksums[i] = carry + ex;
+        carry += total;
+    }
+    if (threadIdx.x == 0) {
+        *offsets_end = carry;
+        if (carry != n) atomicOr(err, kErrCount);
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(int64_t ncells, const int32_t* __restrict__ counts,
+                                                             const long long* __restrict__ blocksums,
+                                                             int64_t* __restrict__ offsets,
+                                                             const unsigned long long* __restrict__ S,
+                                                             float* __restrict__ vc,
+                                                             int32_t* __restrict__ fill) {
+    __shared__ long long sh[32];
+    const int64_t b0 = (int64_t)blockIdx.x * kScanTile;
+    // each thread owns kScanItems consecutive cells
+    const int64_t t0 = b0 + (int64_t)threadIdx.x * kScanItems;
+    int32_t c[kScanItems];
+    long long acc = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const int64_t i = t0 + k;
+        c[k] = i < ncells ? counts[i] : 0;
+        acc += c[k];
+    }
+    long long total;
+    long long run = blocksums[blockIdx.x] + block_exclusive_scan(acc, sh, total);
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const int64_t i = t0 + k;
+        if (i >= ncells) break;
+        offsets[i] = run;
+        run += c[k];
+        if (fill) fill[i] = 0;
+        if (S) {
+            for (int d = 0; d < 3; ++d) {
+                float v = 0.f;
+                if (c[k] > 0) {
+                    const double sum = __ll2double_rn((long long)S[d * ncells + i]);
+                    v = __double2float_rn(__dmul_rn(__ddiv_rn(sum, (double)c[k]), 0x1p-24));
+                }
+                vc[d * ncells + i] = v;
+            }
+        }
+    }
+}
+
+// counts and fixed-point momentum sums from codes and momenta
+__global__ void k_hist(int64_t n, int nc, const int32_t* __restrict__ Qn, const float* __restrict__ Pn,
+                       int32_t* counts, unsigned long long* S, uint32_t* err) {
+    const int64_t ncells = (int64_t)nc * nc * nc;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t key = (int64_t)(Qn[i] >> 8) +
+                            nc * ((int64_t)(Qn[n + i] >> 8) + (int64_t)nc * (Qn[2 * n + i] >> 8));
+        atomicAdd(&counts[key], 1);
+        for (int d = 0; d < 3; ++d) {
+            const float p = Pn[d * n + i];
+            if (!(fabsf(p) < 1048576.f)) atomicOr(err, p == p ? kErrMomentum : kErrNaN);
+            const long long fx = __double2ll_rn((double)p * 16777216.0);
+            atomicAdd(&S[d * ncells + key], (unsigned long long)fx);
+        }
+    }
+}
+
+__device__ __forceinline__ int64_t key_of(const int32_t* Qn, int64_t n, int nc, int64_t i) {
+    return (int64_t)(Qn[i] >> 8) + nc * ((int64_t)(Qn[n + i] >> 8) + (int64_t)nc * (Qn[2 * n + i] >> 8));
+}
+
+// 128-bit sum of round((p - v_c)^2 2^32)
+__global__ void __launch_bounds__(256) k_sigma(int64_t n, int nc, const int32_t* __restrict__ Qn,
+                                               const float* __restrict__ Pn,
+                                               const float* __restrict__ vc,
+                                               unsigned long long* d2, uint32_t* err) {
+    const int64_t ncells = (int64_t)nc * nc * nc;
+    unsigned long long lo = 0, hi = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t key = key_of(Qn, n, nc, i);
+        for (int d = 0; d < 3; ++d) {
+            const float dev = __fsub_rn(Pn[d * n + i], vc[d * ncells + key]);
+            if (!(fabsf(dev) < 65536.f)) {
+                atomicOr(err, kErrDeviation);
+                continue;
+            }
+            const double dd = (double)dev;
+            const unsigned long long t = __double2ull_rn(__dmul_rn(__dmul_rn(dd, dd), 4294967296.0));
+            lo += t;
+            if (lo < t) ++hi;
+        }
+    }
+    // warp then block reduction of (hi, lo) with carries
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long l2 = __shfl_down_sync(0xffffffffu, lo, o);
+        const unsigned long long h2 = __shfl_down_sync(0xffffffffu, hi, o);
+        lo += l2;
+        hi += h2 + (lo < l2 ? 1ull : 0ull);
+    }
+    __shared__ unsigned long long shl[8], shh[8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { shl[warp] = lo; shh[warp] = hi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        lo = 0; hi = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            lo += shl[w];
+            hi += shh[w] + (lo < shl[w] ? 1ull : 0ull);
+        }
+        const unsigned long long old = atomicAdd(&d2[0], lo);
+        const unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
+        if (hi + carry) atomicAdd(&d2[1], hi + carry);
+    }
+}
+
+__global__ void k_sigma_final(const unsigned long long* d2, int64_t n, float* sigma) {
+    const unsigned long long lo = d2[0], hi = d2[1];
+    float s;
+    if (lo == 0 && hi == 0) {
+        s = kSigmaFloor;
+    } else {
+        const double v = __dadd_rn(__dmul_rn(__ull2double_rn(hi), 18446744073709551616.0),
+                                   __ull2double_rn(lo));
+        const double s2 = __ddiv_rn(__dmul_rn(v, 0x1p-32), (double)(3 * n));
+        s = __double2float_rn(__dsqrt_rn(s2));
+    }
+    *sigma = s;
+}
+
+__global__ void k_scatter(int64_t n, int nc, const int32_t* __restrict__ Qn, const float* __restrict__ Pn,
+                          const float* __restrict__ vc, const int64_t* __restrict__ offsets,
+                          int32_t* fill, const float* __restrict__ sigma_p,
+                          const float* __restrict__ E, uint8_t* __restrict__ out, uint32_t* err) {
+    const int64_t ncells = (int64_t)nc * nc * nc;
+    const float sigma = *sigma_p;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t key = key_of(Qn, n, nc, i);
+        const int64_t slot = offsets[key] + atomicAdd(&fill[key], 1);
+        for (int d = 0; d < 3; ++d) {
+            out[d * n + slot] = (uint8_t)(Qn[d * n + i] & 255);
+            out[(3 + d) * n + slot] =
+                (uint8_t)encode_momentum(Pn[d * n + i], vc[d * ncells + key], sigma, E, err);
+        }
+    }
+}
+
+// decoded codes and momenta of the current store, storage order
+__global__ void k_decode(int64_t n, int nc, const int64_t* __restrict__ offsets,
+                         const uint8_t* __restrict__ st, const float* __restrict__ vc,
+                         const float* __restrict__ sigma_p, const float* __restrict__ T,
+                         int32_t* __restrict__ Qn, float* __restrict__ Pn) {
+    const int64_t ncells = (int64_t)nc * nc * nc;
+    const float sigma = *sigma_p;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        // cell c with offsets[c] <= j < offsets[c+1]
+        int64_t lo = 0, hi = ncells;   // invariant offsets[lo] <= j < offsets[hi]
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (offsets[mid] <= j) lo = mid; else hi = mid;
+        }
+        const int64_t c = lo;
+        const int cx = (int)(c % nc), cy = (int)((c / nc) % nc), cz = (int)(c / ((int64_t)nc * nc));
+        const int cc[3] = {cx, cy, cz};
+        for (int d = 0; d < 3; ++d) {
+            Qn[d * n + j] = cc[d] * kBins + st[d * n + j];
+            Pn[d * n + j] = decode_momentum(vc[d * ncells + c], sigma, T[st[(3 + d) * n + j]]);
+        }
+    }
+}
+
+}  // namespace
+
+int scan_counts(Sim& s, const int32_t* counts, int64_t* offsets) {
+    const int64_t nb = (s.ncells + kScanTile - 1) / kScanTile;
+    k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s.stream>>>(s.ncells, counts, s.blocksums);
+    k_scan_top<<<1, 1024, 0, s.stream>>>(nb, s.blocksums, s.n, offsets + s.ncells, s.err);
+    k_scan_apply<<<(unsigned)nb, kScanThreads, 0, s.stream>>>(s.ncells, counts, s.blocksums, offsets,
+                                                             nullptr, nullptr, nullptr);
+    s.launches += 3;
+    return check_launch(s, "scan");
+}
+
+// Encode s.Qn / s.Pn into the other store buffer and make it current.  With
+// counts_ready the new counts and momentum sums were accumulated already
+// (by the tile pass).
+int encode_from_qp(Sim& s, bool counts_ready) {
+    const int nxt = 1 - s.cur;
+    cudaStream_t st = s.stream;
+    if (!counts_ready) {
+        cudaMemsetAsync(s.counts[nxt], 0, sizeof(int32_t) * s.ncells, st);
+        cudaMemsetAsync(s.S, 0, sizeof(unsigned long long) * 3 * s.ncells, st);
+        k_hist<<<grid_for(s.n, 256), 256, 0, st>>>(s.n, s.nc, s.Qn, s.Pn, s.counts[nxt], s.S, s.err);
+        s.launches++;
+    }
+    const int64_t nb = (s.ncells + kScanTile - 1) / kScanTile;
+    k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, st>>>(s.ncells, s.counts[nxt], s.blocksums);
+    k_scan_top<<<1, 1024, 0, st>>>(nb, s.blocksums, s.n, s.offsets[nxt] + s.ncells, s.err);
+    k_scan_apply<<<(unsigned)nb, kScanThreads, 0, st>>>(s.ncells, s.counts[nxt], s.blocksums,
+                                                        s.offsets[nxt], s.S, s.vc[nxt], s.fill);
+    s.launches += 3;
+    prof_mark(s, 3);
+    cudaMemsetAsync(s.d2, 0, 16, st);
+    k_sigma<<<grid_for(s.n, 256, 152 * 8), 256, 0, st>>>(s.n, s.nc, s.Qn, s.Pn, s.vc[nxt], s.d2, s.err);
+    k_sigma_final<<<1, 1, 0, st>>>(s.d2, s.n, s.sigma_d[nxt]);
+    s.launches += 2;
+    prof_mark(s, 4);
+    k_scatter<<<grid_for(s.n, 256), 256, 0, st>>>(s.n, s.nc, s.Qn, s.Pn, s.vc[nxt], s.offsets[nxt],
+                                                  s.fill, s.sigma_d[nxt], s.Eedge, s.streams[nxt],
+                                                  s.err);
+    s.launches++;
+    prof_mark(s, 5);
+    s.cur = nxt;
+    s.offsets_valid = true;
+    s.have_state = true;
+    s.loaded = 15;
+    return check_launch(s, "encode");
+}
+
+int decode_state(Sim& s) {
+    k_decode<<<grid_for(s.n, 256), 256, 0, s.stream>>>(s.n, s.nc, s.offsets[s.cur], s.streams[s.cur],
+                                                       s.vc[s.cur], s.sigma_d[s.cur], s.Tdec, s.Qn,
+                                                       s.Pn);
+    s.launches++;
+    return check_launch(s, "decode");
+}
+
+}  // namespace pmpm

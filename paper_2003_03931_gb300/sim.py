@@ -1,0 +1,184 @@
+"""Python handle on one PM-PM simulation (a thin wrapper over include/pmpm.h).
+
+PyTorch supplies the device workspace and the stream; every step of the path
+runs inside libpmpm.  Host arrays are numpy.
+"""
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _lib
+
+
+@dataclass
+class SimConfig:
+    """Mirror of pmpm_config (include/pmpm.h)."""
+    np: int                 # particles per side of the initial lattice
+    nc: int                 # coarse cells per side (fine mesh 4 nc)
+    a_init: float = 0.02
+    a_final: float = 1.0
+    n_steps: int = 20
+    tile_max: int = 5       # largest tile edge in coarse cells (4 or 5)
+    buffer: int = 6         # tile buffer, fine cells (Sec. IV-A.2)
+    pos_bytes: int = 1
+    vel_bytes: int = 1
+    pk_mesh_max: int = 0
+
+    def to_c(self):
+        c = _lib.Config()
+        c.np, c.nc, c.tile_max, c.buffer = self.np, self.nc, self.tile_max, self.buffer
+        c.pos_bytes, c.vel_bytes, c.pk_mesh_max = self.pos_bytes, self.vel_bytes, self.pk_mesh_max
+        c.a_init, c.a_final, c.n_steps = self.a_init, self.a_final, self.n_steps
+        return c
+
+    @property
+    def n(self):
+        return self.np ** 3
+
+    @property
+    def ncells(self):
+        return self.nc ** 3
+
+
+def workspace_bytes(cfg):
+    lib = _lib.load()
+    out = ctypes.c_size_t(0)
+    c = cfg.to_c()
+    _lib.check(lib.pmpm_workspace_bytes(ctypes.byref(c), ctypes.byref(out)))
+    return out.value
+
+
+def codec_tables():
+    lib = _lib.load()
+    T = np.zeros(256, np.float32)
+    E = np.zeros(256, np.float32)
+    _lib.check(lib.pmpm_codec_tables(T.ctypes.data, E.ctypes.data))
+    return T, E
+
+
+class Simulation:
+    """One simulation on one GPU.  The workspace is a torch uint8 tensor."""
+
+    def __init__(self, cfg, device="cuda", stream=None, workspace=None):
+        import torch
+        self.cfg = cfg
+        self.lib = _lib.load()
+        self.device = torch.device(device)
+        nbytes = workspace_bytes(cfg)
+        if workspace is None:
+            workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        if workspace.numel() < nbytes:
+            raise ValueError("workspace too small")
+        self.workspace = workspace
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        handle = ctypes.c_void_p()
+        c = cfg.to_c()
+        with torch.cuda.device(self.device):
+            rc = self.lib.pmpm_init(ctypes.byref(c), ctypes.c_void_p(workspace.data_ptr()),
+                                    nbytes, ctypes.c_void_p(self.stream.cuda_stream),
+                                    ctypes.byref(handle))
+        _lib.check(rc, None)
+        self.h = handle
+
+    # -- lifecycle
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.pmpm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        _lib.check(rc, self.h)
+
+    # -- physics
+    def ic_zeldovich(self, seed, slope=-1.5, k_c=np.pi / 2, rms_disp=0.3):
+        self._check(self.lib.pmpm_ic_zeldovich(self.h, seed, slope, k_c, rms_disp))
+
+    def step(self, nsteps=1):
+        self._check(self.lib.pmpm_step(self.h, nsteps))
+
+    def sync(self):
+        self._check(self.lib.pmpm_sync(self.h))
+
+    def power_spectrum(self, nmesh, nbins):
+        k = np.zeros(nbins)
+        pk = np.zeros(nbins)
+        nm = np.zeros(nbins, np.int64)
+        self._check(self.lib.pmpm_power_spectrum(self.h, nmesh, nbins, k.ctypes.data,
+                                                 pk.ctypes.data, nm.ctypes.data))
+        return k, pk, nm
+
+    # -- transfers
+    def _fetch(self, what, arr):
+        self._check(self.lib.pmpm_fetch(self.h, what, arr.ctypes.data, arr.nbytes))
+        return arr
+
+    def fetch_streams(self):
+        return self._fetch(_lib.STREAMS, np.empty((6, self.cfg.n), np.uint8))
+
+    def fetch_counts(self):
+        return self._fetch(_lib.COUNTS, np.empty(self.cfg.ncells, np.int32))
+
+    def fetch_vc(self):
+        return self._fetch(_lib.VC, np.empty((3, self.cfg.ncells), np.float32))
+
+    def fetch_scalars(self):
+        sc = _lib.Scalars()
+        self._check(self.lib.pmpm_fetch(self.h, _lib.SCALARS, ctypes.addressof(sc),
+                                        ctypes.sizeof(sc)))
+        return {"a": sc.a, "sigma": sc.sigma, "step": sc.step, "n": sc.n}
+
+    def fetch_decoded(self):
+        Q = self._fetch(_lib.DECODED_Q, np.empty((3, self.cfg.n), np.int32))
+        P = self._fetch(_lib.DECODED_P, np.empty((3, self.cfg.n), np.float32))
+        return Q, P
+
+    def fetch_force(self):
+        return self._fetch(_lib.FORCE, np.empty((3, self.cfg.n), np.float32))
+
+    def fetch_coarse_density(self):
+        return self._fetch(_lib.COARSE_DENSITY, np.empty(self.cfg.ncells, np.int64))
+
+    def fetch_state(self):
+        return {"streams": self.fetch_streams(), "counts": self.fetch_counts(),
+                "vc": self.fetch_vc(), "scalars": self.fetch_scalars()}
+
+    def _load(self, what, arr):
+        arr = np.ascontiguousarray(arr)
+        self._check(self.lib.pmpm_load(self.h, what, arr.ctypes.data, arr.nbytes))
+
+    def load_scalars(self, a, sigma, step):
+        sc = _lib.Scalars(a, sigma, step, self.cfg.n)
+        self._check(self.lib.pmpm_load(self.h, _lib.SCALARS, ctypes.addressof(sc),
+                                       ctypes.sizeof(sc)))
+
+    def load_state(self, state):
+        self._load(_lib.STREAMS, np.asarray(state["streams"], np.uint8))
+        self._load(_lib.COUNTS, np.asarray(state["counts"], np.int32))
+        self._load(_lib.VC, np.asarray(state["vc"], np.float32))
+        sc = state["scalars"]
+        self.load_scalars(sc["a"], sc["sigma"], sc["step"])
+
+    def load_qp(self, Q, P, a, step=0):
+        """Encode codes Q [3, N] int32 and momenta P [3, N] float32 (Sec. III-A)."""
+        self.load_scalars(a, 1.0, step)
+        buf = np.concatenate([np.ascontiguousarray(Q, np.int32).view(np.uint8).ravel(),
+                              np.ascontiguousarray(P, np.float32).view(np.uint8).ravel()])
+        self._check(self.lib.pmpm_load(self.h, _lib.QP, buf.ctypes.data, buf.nbytes))
+
+    def stage_times(self, enable=True, reset=False):
+        if reset:
+            self._check(self.lib.pmpm_stage_times(self.h, int(enable), None, 0, None))
+            return None
+        t = np.zeros(6)
+        nl = ctypes.c_int64(0)
+        self._check(self.lib.pmpm_stage_times(self.h, int(enable), t.ctypes.data, 6,
+                                              ctypes.byref(nl)))
+        return t, nl.value

@@ -1,0 +1,69 @@
+"""Host-side checks of the C ABI (no GPU): the library builds and loads,
+exports every entry point include/pmpm.h declares, sizes workspaces, rejects
+bad configurations, and ships the same Eq. 3 tables as the oracle."""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2003_03931_gb300 import _lib, build
+    build.build()
+    return _lib.load()
+
+
+def test_header_and_exports(lib):
+    from paper_2003_03931_gb300 import _lib
+    header = open(os.path.join(ROOT, "include", "pmpm.h")).read()
+    declared = set(re.findall(r"\b(pmpm_[a-z_]+)\s*\(", header))
+    assert declared == set(_lib.EXPORTS)
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def test_workspace_bytes_and_validation(lib):
+    from paper_2003_03931_gb300.sim import SimConfig, workspace_bytes
+    from paper_2003_03931_gb300._lib import PmpmError
+    b1 = workspace_bytes(SimConfig(np=32, nc=16))
+    b2 = workspace_bytes(SimConfig(np=128, nc=64))
+    b3 = workspace_bytes(SimConfig(np=512, nc=256))
+    assert 0 < b1 < b2 < b3
+    # the persistent particle store is 2 x 6 bytes per particle plus cell fields
+    assert b3 > 2 * 6 * 512 ** 3
+    for bad in (dict(np=30, nc=16), dict(np=32, nc=12), dict(np=32, nc=16, tile_max=6),
+                dict(np=32, nc=16, buffer=4), dict(np=32, nc=16, pos_bytes=2),
+                dict(np=32, nc=16, a_init=0.5, a_final=0.1)):
+        with pytest.raises(PmpmError):
+            workspace_bytes(SimConfig(**bad))
+
+
+def test_codec_tables_match_oracle(lib):
+    from oracle import codec
+    from paper_2003_03931_gb300.sim import codec_tables
+    T, E = codec_tables()
+    To, Eo = codec.velocity_tables()
+    np.testing.assert_array_equal(T, To)
+    np.testing.assert_array_equal(E, Eo)
+
+
+def test_init_without_device_fails_cleanly(lib):
+    # no GPU here: pmpm_init must return an error code, not crash
+    from paper_2003_03931_gb300 import _lib
+    from paper_2003_03931_gb300.sim import SimConfig
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pytest.skip("a GPU is present")
+    except ImportError:
+        pass
+    c = SimConfig(np=16, nc=8).to_c()
+    h = ctypes.c_void_p()
+    rc = lib.pmpm_init(ctypes.byref(c), ctypes.c_void_p(256), 1 << 30, None, ctypes.byref(h))
+    assert rc != _lib.PMPM_OK
