@@ -1,0 +1,331 @@
+#!/usr/bin/env python3
+"""Benchmark of the PM-PM step (particle-steps/s) on GB300.
+
+Default workload: 512^3 particles, 256^3 coarse cells, 1024^3 fine cells in
+tiles of 16/20 fine cells + 6-cell buffer, Zel'dovich ICs (power-law
+spectrum, seeded), a = 0.02 -> 1 over warmup + steps steps.  One JSON line
+on rank 0; see the round contract in the design doc for every key.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank evolves its own box (independent replicas, weak
+scaling); value is the particle-steps of all ranks over the slowest rank's
+time.  --impl reference times the FP64 oracle on the host cores instead.
+"""
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PMPM particle-steps/s"
+UNIT = "particle-steps/s"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+TILE_FFT = 32
+TILE_FILES = ["paper_2003_03931_gb300/csrc/tile_core.cuh", "paper_2003_03931_gb300/csrc/regfft.cuh",
+              "paper_2003_03931_gb300/csrc/tile.cu", "paper_2003_03931_gb300/csrc/common.cuh"]
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="c3_512")
+    ap.add_argument("--e2e-steps", type=int, default=8)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args(argv)
+
+
+# ------------------------------------------------------------------ helpers
+
+def tile_flops_per_launch(nc, tile_max=5):
+    """Algorithmic FLOPs of one tile pass: per tile one real 32^3 forward
+    transform and three real inverse transforms, 2.5 M log2 M each
+    (M = 32^3 points), over all tiles."""
+    nt = -(-nc // tile_max)
+    m = TILE_FFT ** 3
+    return 4 * 2.5 * m * math.log2(m) * nt ** 3
+
+
+def fp32_peak_tflops(sm_mhz):
+    """152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x SM clock."""
+    return SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+def source_hash(paths):
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload):
+    """DRAM bytes per tile-pass launch from the committed ncu summary, if it
+    was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", f"tile_pass_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as f:
+        for line in f:
+            if ":" in line and line.startswith("- "):
+                k, v = line[2:].split(":", 1)
+                vals[k.strip()] = v.strip()
+    try:
+        if vals.get("source_sha") != source_hash(TILE_FILES):
+            return None
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f)
+    return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.dev), "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ------------------------------------------------------------------ oracle timing
+
+def time_oracle_steps(np_side, nc, warmup, steps):
+    """Time the FP64 oracle on this host: `steps` steps of an np_side^3 box
+    after `warmup` untimed ones.  Returns (particle-steps/s, seconds)."""
+    from oracle import dynamics, ic
+    st, _, _ = ic.zeldovich(1, np_side, nc, 0.02)
+    sim = dynamics.Simulation(nc, 0.02, 1.0, warmup + steps)
+    sim.op.Ks_hat()
+    sim.op.Kl_hat()
+    st = sim.run(st, warmup)
+    t0 = time.perf_counter()
+    st = sim.run(st, steps)
+    dt = time.perf_counter() - t0
+    return np_side ** 3 * steps / dt, dt
+
+
+def oracle_cores():
+    # numpy.fft (pocketfft) and np.add.at run on one thread; no BLAS is used
+    return 1
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2003_03931_gb300 import synth
+    from paper_2003_03931_gb300.sim import SimConfig, Simulation
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    w = dict(synth.WORKLOADS[args.workload])
+    K, W = args.steps, args.warmup
+    E = 0 if args.no_e2e else args.e2e_steps
+    w["n_steps"] = W + K + E
+    cfg = SimConfig(**w)
+    sim = Simulation(cfg, device=f"cuda:{local}")
+    stream = sim.stream
+    sim.ic_zeldovich(1 + rank, **synth.IC_SPECTRUM)
+    sim.step(W)
+    sim.sync()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    sim.stage_times(enable=True, reset=True)
+    sampler = ClockSampler(local)
+    barrier()
+    sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(K)
+    e1.record(stream)
+    e1.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    t = e0.elapsed_time(e1) / 1000.0
+    stages, launches = sim.stage_times(enable=False)
+    sim.sync()
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t], device=f"cuda:{local}")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if E:
+        n, C = cfg.n, cfg.ncells
+        pin = lambda shape, dt: torch.empty(shape, dtype=dt, pin_memory=True).numpy()
+        host = {"streams": pin((6, n), torch.uint8), "counts": pin((C,), torch.int32),
+                "vc": pin((3, C), torch.float32)}
+        sim.fetch_into(host)
+        host["scalars"] = sim.fetch_scalars()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(E):
+            sim.load_state(host)
+            sim.step(1)
+            sim.fetch_into(host)
+            host["scalars"] = sim.fetch_scalars()
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        if world > 1:
+            import torch.distributed as dist
+            tt = torch.tensor([te], device=f"cuda:{local}")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            te = float(tt.item())
+        per = 6 * n + 4 * C + 12 * C + 32
+        e2e = {"value": world * n * E / te, "unit": UNIT, "h2d_bytes_per_step": per,
+               "d2h_bytes_per_step": per, "steps": E}
+
+    if rank != 0:
+        sim.close()
+        return None
+
+    n = cfg.n
+    value = world * n * K / t
+    flops = tile_flops_per_launch(cfg.nc, cfg.tile_max)
+    tile_s = stages[2] / 1000.0 / K
+    sm_max = clocks.get("sm_max_mhz") or measured_peaks().get("sm_max_mhz") or 2070.0
+    peak = fp32_peak_tflops(sm_max)
+    achieved = flops / tile_s / 1e12 if tile_s > 0 else None
+    roofline = {"bound": "alu", "kernel": "k_tile (tile fine PM + kick + drift)",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if achieved else None,
+                "traffic": recorded_traffic(args.workload),
+                "peak_basis": "FP32 FMA: 152 SMs x 128 lanes x 2 x %d MHz (max SM clock)" % sm_max,
+                "flops_per_launch": flops, "avg_launch_ms": tile_s * 1000.0}
+    hbm = measured_peaks().get("hbm_gbs")
+    stage_names = ["coarse_deposit", "coarse_fft_green", "tile_pm_kick_drift", "scan_cell_means",
+                   "dispersion", "encode_scatter"]
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": W, "ms_per_step": t / K * 1000.0, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "particles": n, "np": cfg.np, "nc": cfg.nc,
+                   "nf": 4 * cfg.nc, "tile_fine": "16/20 + 6 buffer in 32^3",
+                   "schedule": f"a 0.02->1 in {cfg.n_steps} steps, timed steps {W + 1}..{W + K}",
+                   "parallelism": f"replicas x{world}", "bytes_per_particle_store": 6,
+                   "l2": "inputs larger than L2 (%.0f MB particle store)" % (6 * n / 1e6)},
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "roofline": roofline,
+        "stage_ms_per_step": {k: v / K for k, v in zip(stage_names, stages)},
+        "hbm_peak_gbs": hbm,
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        v, dt = time_oracle_steps(128, 64, 0, 1)
+        out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": oracle_cores(), "kind": "oracle",
+                               "sample": "one FP64 oracle step of a 128^3-particle box "
+                                         "(64^3 coarse, 256^3 fine: the same 8 particles per "
+                                         "coarse cell and 8 fine cells per particle), %.1f s" % dt}
+    sim.close()
+    return out
+
+
+def run_reference(args):
+    world, rank, local = dist_setup(args)
+    if rank != 0:
+        return None
+    K, W = args.steps, args.warmup
+    # a bounded sample of the workload per step: a 64^3-particle box with the
+    # same per-particle work (8 particles per coarse cell, 8 fine cells each)
+    v, dt = time_oracle_steps(64, 32, W, K)
+    sample = ("FP64 oracle, %d timed steps of a 64^3-particle box (32^3 coarse, 128^3 fine; "
+              "same per-particle work as the %s workload), %.1f s" % (K, args.workload, dt))
+    return {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": K,
+            "warmup": W, "ms_per_step": dt / K * 1000.0, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": args.workload, "parallelism": "host cores"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle_cores(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    out = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if out is not None:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

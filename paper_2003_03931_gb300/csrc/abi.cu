@@ -204,12 +204,12 @@ static int one_step(Sim& s) {
         s.offsets_valid = true;
     }
     prof_mark(s, -1);
+    cudaMemsetAsync(s.counts[1 - s.cur], 0, sizeof(int32_t) * s.ncells, s.stream);
+    cudaMemsetAsync(s.S, 0, sizeof(unsigned long long) * 3 * s.ncells, s.stream);
     if ((rc = coarse_deposit(s))) return rc;
     prof_mark(s, 0);
     if ((rc = coarse_force(s))) return rc;
     prof_mark(s, 1);
-    cudaMemsetAsync(s.counts[1 - s.cur], 0, sizeof(int32_t) * s.ncells, s.stream);
-    cudaMemsetAsync(s.S, 0, sizeof(unsigned long long) * 3 * s.ncells, s.stream);
     if ((rc = tile_pass(s, 1, (float)kick, (float)(drift * kCodesPerFine), nullptr))) return rc;
     prof_mark(s, 2);
     if ((rc = encode_from_qp(s, true))) return rc;

@@ -146,6 +146,14 @@ class Simulation:
     def fetch_coarse_density(self):
         return self._fetch(_lib.COARSE_DENSITY, np.empty(self.cfg.ncells, np.int64))
 
+    def fetch_into(self, host):
+        """Fetch streams, counts and v_c into preallocated host arrays (e.g.
+        pinned), shaped like fetch_state()'s."""
+        self._fetch(_lib.STREAMS, host["streams"])
+        self._fetch(_lib.COUNTS, host["counts"])
+        self._fetch(_lib.VC, host["vc"])
+        return host
+
     def fetch_state(self):
         return {"streams": self.fetch_streams(), "counts": self.fetch_counts(),
                 "vc": self.fetch_vc(), "scalars": self.fetch_scalars()}
