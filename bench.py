@@ -272,7 +272,7 @@ def run_ours(args):
                 "peak_basis": "FP32 FMA: 152 SMs x 128 lanes x 2 x %d MHz (max SM clock)" % sm_max,
                 "flops_per_launch": flops, "avg_launch_ms": tile_s * 1000.0}
     hbm = measured_peaks().get("hbm_gbs")
-    stage_names = ["coarse_deposit", "coarse_fft_green", "tile_pm_kick_drift", "scan_cell_means",
+    stage_names = ["coarse_deposit", "coarse_fft_green", "tile_pm_kick_drift", "hist_scan_cell_means",
                    "dispersion", "encode_scatter"]
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,

@@ -131,8 +131,9 @@ int pmpm_sync(pmpm_sim* sim);
 /* Per-stage device time (ms) accumulated since the last reset, measured
  * with CUDA events on the sim's stream when enable != 0.  Stage order:
  * 0 coarse deposit, 1 coarse FFT + Green multiply, 2 tile fine PM + kick +
- * drift, 3 scan + cell means, 4 dispersion, 5 encode + scatter.  Calling
- * with times == NULL sets the switch and resets the totals. */
+ * drift, 3 new-cell counts + scan + cell means, 4 dispersion, 5 encode +
+ * scatter.  Calling with times == NULL sets the switch and resets the
+ * totals. */
 int pmpm_stage_times(pmpm_sim* sim, int32_t enable, double* times, int32_t n,
                      int64_t* launches);
 

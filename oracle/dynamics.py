@@ -20,7 +20,9 @@ Readings (the paper gives neither the integrator nor the units):
 * Re-encode (Sec. III-A): particles are re-grouped by new coarse cell in
   row-major x-fastest order (within-cell order is unspecified); counts are
   int32.  v_c is the cell mean of p: each p is rounded to a multiple of
-  2^-24, the int64 sum S is exact, and v_c = fl32(fl64(S) / n * 2^-24).
+  2^-24, the int64 sum S is exact, and v_c = fl32(fl32(S) 2^-24 / n), a
+  float32 division of the rounded sum (the paper fixes v_c = <v>, not how
+  its stored value is rounded).
   The isotropic dispersion is sigma^2 = sum_i sum_d (p_id - v_c,d)^2 / (3N),
   with each squared float32 difference rounded to a multiple of 2^-32 and
   summed exactly; sigma^2 = fl64(hi) 2^64 + fl64(lo) in units of 2^-32 of the
@@ -97,8 +99,8 @@ def cell_means(cell, p32, ncells):
     n = np.bincount(cell, minlength=ncells).astype(np.int64)
     vc = np.zeros((ncells, 3), dtype=np.float32)
     nz = n > 0
-    vc[nz] = (S[nz].astype(np.float64) / n[nz, None].astype(np.float64)
-              * 2.0 ** -P_FIX_BITS).astype(np.float32)
+    Sf = (S[nz].astype(np.float32) * np.float32(2.0 ** -P_FIX_BITS)).astype(np.float32)
+    vc[nz] = (Sf / n[nz, None].astype(np.float32)).astype(np.float32)
     return vc, S, n
 
 

@@ -5,8 +5,8 @@
 //   0 coarse CIC deposit of the current store
 //   1 coarse FFT, Green multiply (K~_l), two inverse FFTs -> F_l
 //   2 tile pass: fine CIC + FFT + K~_s + inverse per tile; interpolate F_s +
-//     F_l; kick; integer drift; new-cell counts and momentum sums
-//   3 scan of the new counts, cell means v_c
+//     F_l; kick; integer drift
+//   3 new-cell counts and momentum sums, scan, cell means v_c
 //   4 dispersion sigma
 //   5 encode + scatter into the other store buffer; swap
 #include <math.h>
@@ -101,6 +101,7 @@ size_t layout(Sim& s, uint8_t* base) {
     const size_t h = s.nc / 2 + 1;
     s.green_coarse = reinterpret_cast<float*>(take(4 * h * h * h));
     s.green_fine = reinterpret_cast<float*>(take(4 * (size_t)kGreenS * kGreenS * kGreenS));
+    s.green_packed = reinterpret_cast<float*>(take(4 * (size_t)kGreenS * kGreenS * (kGreenS + 1) / 2));
     s.Tdec = reinterpret_cast<float*>(take(4 * 256));
     s.Eedge = reinterpret_cast<float*>(take(4 * 256));
     s.tw_f = reinterpret_cast<float2*>(take(8 * (size_t)s.fft_max));
@@ -204,15 +205,13 @@ static int one_step(Sim& s) {
         s.offsets_valid = true;
     }
     prof_mark(s, -1);
-    cudaMemsetAsync(s.counts[1 - s.cur], 0, sizeof(int32_t) * s.ncells, s.stream);
-    cudaMemsetAsync(s.S, 0, sizeof(unsigned long long) * 3 * s.ncells, s.stream);
     if ((rc = coarse_deposit(s))) return rc;
     prof_mark(s, 0);
     if ((rc = coarse_force(s))) return rc;
     prof_mark(s, 1);
     if ((rc = tile_pass(s, 1, (float)kick, (float)(drift * kCodesPerFine), nullptr))) return rc;
     prof_mark(s, 2);
-    if ((rc = encode_from_qp(s, true))) return rc;
+    if ((rc = encode_from_qp(s, false))) return rc;
     s.in_step = false;
     s.step = n + 1;
     s.a = an1;

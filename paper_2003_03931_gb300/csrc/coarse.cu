@@ -2,8 +2,9 @@
 // computed on a 4-times-coarser mesh"; Eq. 1 with K~_l).
 //
 //  1. integer CIC of all particles on the nc^3 coarse mesh (int64, units
-//     2^-27 per particle), accumulated per 8x8x4-cell brick in shared memory
-//     and flushed with one global atomic per touched node;
+//     2^-27 per particle): one thread per cell sums its particles' weights on
+//     the 27 surrounding nodes in registers, an 8x8x4-cell brick collects
+//     them in shared memory and flushes one global atomic per touched node;
 //  2. delta = rho - mean (float64 subtraction, float32 storage), 3-D FFT;
 //  3. Green multiply: B1 = rho~ (K~_x + i K~_y), B2 = rho~ K~_z (K~ = -i S);
 //  4. two inverse FFTs give F_x + i F_y and F_z.
@@ -16,6 +17,9 @@ namespace {
 constexpr int kBX = 8, kBY = 8, kBZ = 4;
 constexpr int kNX = kBX + 2, kNY = kBY + 2, kNZ = kBZ + 2;
 
+// One thread per coarse cell: the cell's particles reach only the 3^3 nodes
+// around it, so their weights are summed in 27 registers and added to the
+// brick's shared accumulator once per cell.
 __global__ void __launch_bounds__(256) k_coarse_deposit(int nc, const int32_t* __restrict__ counts,
                                                         const int64_t* __restrict__ offsets,
                                                         const uint8_t* __restrict__ m0,
@@ -28,43 +32,48 @@ __global__ void __launch_bounds__(256) k_coarse_deposit(int nc, const int32_t* _
     const int x0 = bx * kBX, y0 = by * kBY, z0 = bz * kBZ;
     for (int i = threadIdx.x; i < kNX * kNY * kNZ; i += blockDim.x) acc[i] = 0ull;
     __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int r = warp; r < kBY * kBZ; r += blockDim.x / 32) {
-        const int y = y0 + r % kBY, z = z0 + r / kBY;
-        const int64_t base = (int64_t)nc * (y + (int64_t)nc * z) + x0;
-        int64_t st[kBX + 1];
+    const int lx = threadIdx.x % kBX, ly = (threadIdx.x / kBX) % kBY, lz = threadIdx.x / (kBX * kBY);
+    const int cx = x0 + lx, cy = y0 + ly, cz = z0 + lz;
+    const int64_t cell = cx + (int64_t)nc * (cy + (int64_t)nc * cz);
+    const int64_t j0 = offsets[cell];
+    const int cnt = counts[cell];
+    unsigned long long a[27];
 #pragma unroll
-        for (int i = 0; i <= kBX; ++i) st[i] = offsets[base + i];
-        const int64_t total = st[kBX] - st[0];
-        for (int64_t v = lane; v < total; v += 32) {
-            const int64_t j = st[0] + v;
-            int cx = 0;
+    for (int k = 0; k < 27; ++k) a[k] = 0ull;
+    for (int q = 0; q < cnt; ++q) {
+        const int64_t j = j0 + q;
+        // per axis: weights of nodes c-1, c, c+1 (in 1/512); the bin m < 128
+        // lies left of the cell centre
+        uint32_t w[3][3];
+        const int mm[3] = {m0[j], m1[j], m2[j]};
 #pragma unroll
-            for (int i = 1; i < kBX; ++i)
-                if (st[i] <= j) cx = i;
-            const int64_t Q[3] = {(int64_t)(x0 + cx) * kBins + m0[j], (int64_t)y * kBins + m1[j],
-                                  (int64_t)z * kBins + m2[j]};
-            Cic1 c[3];
-#pragma unroll
-            for (int e = 0; e < 3; ++e) c[e] = cic_coarse(Q[e]);
-            const int lx = c[0].i0 - (x0 - 1), ly = c[1].i0 - (y0 - 1), lz = c[2].i0 - (z0 - 1);
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
-                const unsigned long long w =
-                    (unsigned long long)((dx ? c[0].w1 : 512 - c[0].w1) *
-                                         (dy ? c[1].w1 : 512 - c[1].w1)) *
-                    (unsigned long long)(dz ? c[2].w1 : 512 - c[2].w1);
-                if (w) atomicAdd(&acc[(lx + dx) + kNX * ((ly + dy) + kNY * (lz + dz))], w);
-            }
+        for (int e = 0; e < 3; ++e) {
+            const int s = 2 * mm[e] + 1 - kBins;     // offset from the centre, 1/512
+            w[e][0] = s < 0 ? (uint32_t)(-s) : 0u;
+            w[e][1] = 512u - (uint32_t)(s < 0 ? -s : s);
+            w[e][2] = s > 0 ? (uint32_t)s : 0u;
         }
+#pragma unroll
+        for (int kz = 0; kz < 3; ++kz)
+#pragma unroll
+            for (int ky = 0; ky < 3; ++ky) {
+                const unsigned long long wyz = (unsigned long long)(w[1][ky] * w[2][kz]);
+#pragma unroll
+                for (int kx = 0; kx < 3; ++kx) a[kx + 3 * (ky + 3 * kz)] += wyz * w[0][kx];
+            }
+    }
+#pragma unroll
+    for (int k = 0; k < 27; ++k) {
+        if (!a[k]) continue;
+        const int dx = k % 3, dy = (k / 3) % 3, dz = k / 9;
+        atomicAdd(&acc[(lx + dx) + kNX * ((ly + dy) + kNY * (lz + dz))], a[k]);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < kNX * kNY * kNZ; i += blockDim.x) {
         const unsigned long long v = acc[i];
         if (!v) continue;
-        const int lx = i % kNX, ly = (i / kNX) % kNY, lz = i / (kNX * kNY);
-        const int gx = wrap(x0 - 1 + lx, nc), gy = wrap(y0 - 1 + ly, nc), gz = wrap(z0 - 1 + lz, nc);
+        const int ix = i % kNX, iy = (i / kNX) % kNY, iz = i / (kNX * kNY);
+        const int gx = wrap(x0 - 1 + ix, nc), gy = wrap(y0 - 1 + iy, nc), gz = wrap(z0 - 1 + iz, nc);
         atomicAdd(&rho[gx + (int64_t)nc * (gy + (int64_t)nc * gz)], v);
     }
 }

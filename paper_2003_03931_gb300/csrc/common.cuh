@@ -124,6 +124,9 @@ PMPM_HD int wrap(int i, int n) {
     return r < 0 ? r + n : r;
 }
 
+// wrap for an index at most one period outside [0, n): no division
+PMPM_HD int wrap1(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
 // Tile partition along one axis: n_t tiles of 4 or 5 coarse cells
 // (boundary i at floor(i * nc / n_t)).
 PMPM_HD int tile_count(int nc, int tile_max) {

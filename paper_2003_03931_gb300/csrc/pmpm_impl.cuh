@@ -47,6 +47,7 @@ struct Sim {
     float* Fl = nullptr;                        // [3][nc^3]
     float* green_coarse = nullptr;              // [(nc/2+1)^3]
     float* green_fine = nullptr;                // [17^3]
+    float* green_packed = nullptr;              // [17 x 153] b <= c half of green_fine
     float* Tdec = nullptr;                      // [256]
     float* Eedge = nullptr;                     // [256]
     float2* tw_f = nullptr;                     // [fft_max] exp(-2 pi i k / fft_max)

@@ -5,8 +5,8 @@
 // Input: new codes Q [3][N] and momenta p [3][N] (float32), any order.
 //   hist    counts[c] and fixed-point momentum sums S[d][c] (int64, p rounded
 //           to 2^-24): exact integers, independent of order
-//   scan    offsets = exclusive scan of counts (int64); v_c = fl32(fl64(S) /
-//           n * 2^-24)
+//   scan    offsets = exclusive scan of counts (int64); v_c = fl32(fl32(S)
+//           2^-24 / n)
 //   sigma   sum over particles of round((p - v_c)^2 * 2^32) in 128 bits;
 //           sigma = fl32(sqrt(sum 2^-32 / 3N))
 //   scatter slot = offsets[c] + rank (atomic per cell); m = Q mod 256 and the
@@ -112,8 +112,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(int64_t ncells, con
             for (int d = 0; d < 3; ++d) {
                 float v = 0.f;
                 if (c[k] > 0) {
-                    const double sum = __ll2double_rn((long long)S[d * ncells + i]);
-                    v = __double2float_rn(__dmul_rn(__ddiv_rn(sum, (double)c[k]), 0x1p-24));
+                    const float sum = __fmul_rn(__ll2float_rn((long long)S[d * ncells + i]), 0x1p-24f);
+                    v = __fdiv_rn(sum, (float)c[k]);
                 }
                 vc[d * ncells + i] = v;
             }
@@ -143,6 +143,22 @@ __device__ __forceinline__ int64_t key_of(const int32_t* Qn, int64_t n, int nc, 
     return (int64_t)(Qn[i] >> 8) + nc * ((int64_t)(Qn[n + i] >> 8) + (int64_t)nc * (Qn[2 * n + i] >> 8));
 }
 
+// round-half-even(d^2 2^32) for a float32 d with |d| < 2^16, in integers:
+// d = m 2^e exactly, so d^2 2^32 = m^2 2^(2e + 32) with m^2 < 2^48
+__device__ __forceinline__ unsigned long long sq_fix32(float d) {
+    const uint32_t b = __float_as_uint(d) & 0x7fffffffu;
+    const uint32_t E = b >> 23, M = b & 0x7fffffu;
+    const unsigned long long m = E ? (unsigned long long)(M | 0x800000u) : (unsigned long long)M;
+    const int e = E ? (int)E - 150 : -149;
+    const unsigned long long m2 = m * m;
+    const int sh = 2 * e + 32;
+    if (sh >= 0) return m2 << sh;
+    const int r = -sh;
+    if (r > 49) return 0ull;                       // value below 1/4
+    const unsigned long long q = m2 >> r, rem = m2 & ((1ull << r) - 1ull), half = 1ull << (r - 1);
+    return q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull);
+}
+
 // 128-bit sum of round((p - v_c)^2 2^32)
 __global__ void __launch_bounds__(256) k_sigma(int64_t n, int nc, const int32_t* __restrict__ Qn,
                                                const float* __restrict__ Pn,
@@ -159,8 +175,7 @@ __global__ void __launch_bounds__(256) k_sigma(int64_t n, int nc, const int32_t*
                 atomicOr(err, kErrDeviation);
                 continue;
             }
-            const double dd = (double)dev;
-            const unsigned long long t = __double2ull_rn(__dmul_rn(__dmul_rn(dd, dd), 4294967296.0));
+            const unsigned long long t = sq_fix32(dev);
             lo += t;
             if (lo < t) ++hi;
         }
@@ -209,10 +224,23 @@ __global__ void k_scatter(int64_t n, int nc, const int32_t* __restrict__ Qn, con
                           const float* __restrict__ E, uint8_t* __restrict__ out, uint32_t* err) {
     const int64_t ncells = (int64_t)nc * nc * nc;
     const float sigma = *sigma_p;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t key = key_of(Qn, n, nc, i);
-        const int64_t slot = offsets[key] + atomicAdd(&fill[key], 1);
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // whole warps iterate together so the slot ranks can be aggregated
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); base < n;
+         base += stride) {
+        const int64_t i = base + lane;
+        const bool live = i < n;
+        const long long key = live ? key_of(Qn, n, nc, i) : -1ll - lane;
+        // lanes with the same new cell take consecutive ranks from one atomic
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        const int leader = __ffs(peers) - 1;
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        int first = 0;
+        if (live && lane == leader) first = atomicAdd(&fill[key], __popc(peers));
+        first = __shfl_sync(0xffffffffu, first, leader);
+        if (!live) continue;
+        const int64_t slot = offsets[key] + first + rank;
         for (int d = 0; d < 3; ++d) {
             out[d * n + slot] = (uint8_t)(Qn[d * n + i] & 255);
             out[(3 + d) * n + slot] =

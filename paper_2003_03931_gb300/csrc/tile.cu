@@ -8,33 +8,74 @@
 
 namespace pmpm {
 
+// Optional per-phase clock stamps of thread 0 (compiled only with
+// -DPMPM_PHASE_CLOCKS; read back through pmpm_debug_phases).
+#ifdef PMPM_PHASE_CLOCKS
+constexpr int kMarks = 24;
+__device__ unsigned long long g_phase[4096 * kMarks];
+#define PMPM_MARK(k)                                                                    \
+    do {                                                                                \
+        if (threadIdx.x == 0 && blockIdx.x < 4096) g_phase[blockIdx.x * kMarks + (k)] = clock64(); \
+    } while (0)
+#else
+#define PMPM_MARK(k) \
+    do {             \
+    } while (0)
+#endif
+
+template <int D>
+__device__ __forceinline__ void tile_component(int tid, const TileGeom& g, const TileParams& P,
+                                               const float* gS, const float2* C, float2* W) {
+    __syncthreads();
+    PMPM_MARK(7 + 4 * D);
+    tile_inv_z<D>(tid, g, gS, C, W);
+    __syncthreads();
+    PMPM_MARK(8 + 4 * D);
+    tile_inv_y(tid, g, W);
+    __syncthreads();
+    PMPM_MARK(9 + 4 * D);
+    tile_inv_x(tid, g, W);
+    __syncthreads();
+    PMPM_MARK(10 + 4 * D);
+    tile_interp<D>(tid, g, P, W);
+}
+
 __global__ void __launch_bounds__(kTileThreads, 1) k_tile(TileParams P) {
     extern __shared__ __align__(16) unsigned char tile_smem[];
     uint32_t* R = reinterpret_cast<uint32_t*>(tile_smem);
     float2* C = reinterpret_cast<float2*>(tile_smem);
     float2* W = reinterpret_cast<float2*>(tile_smem + (size_t)kTileR * 4);
+    float* gS = reinterpret_cast<float*>(tile_smem + (size_t)kTileR * 4 + (size_t)kTileW * 8);
     const int tid = threadIdx.x;
     const TileGeom g = tile_geom(blockIdx.x, P.nc, P.nt);
 
+    const TileCells cells = tile_cells(W);   // W is free until phase 5
+    PMPM_MARK(0);
+    tile_load_green(tid, P.green, gS);
     tile_zero(tid, R);
+    tile_cells_load(tid, g, P, cells);
     __syncthreads();
-    tile_deposit(tid, g, P, R);
+    PMPM_MARK(1);
+    tile_cells_scan(tid, g, cells);
     __syncthreads();
+    tile_cells_map(tid, g, cells);
+    __syncthreads();
+    PMPM_MARK(2);
+    tile_deposit_flat(tid, g, P, R, cells);
+    __syncthreads();
+    PMPM_MARK(3);
     tile_fwd_x(tid, R);
     __syncthreads();
+    PMPM_MARK(4);
     tile_fwd_y(tid, C);
     __syncthreads();
+    PMPM_MARK(5);
     tile_fwd_z(tid, C);
-    for (int d = 0; d < 3; ++d) {
-        __syncthreads();
-        tile_inv_z(tid, d, g, P.green, C, W);
-        __syncthreads();
-        tile_inv_y(tid, g, W);
-        __syncthreads();
-        tile_inv_x(tid, g, W);
-        __syncthreads();
-        tile_interp(tid, d, g, P, W);
-    }
+    tile_component<0>(tid, g, P, gS, C, W);
+    tile_component<1>(tid, g, P, gS, C, W);
+    tile_component<2>(tid, g, P, gS, C, W);
+    __syncthreads();
+    PMPM_MARK(19);
 }
 
 int tile_pass(Sim& s, int mode, float kick, float drift, float* G) {
@@ -53,7 +94,7 @@ int tile_pass(Sim& s, int mode, float kick, float drift, float* G) {
     P.vc = s.vc[s.cur];
     P.sigma = s.sigma_d[s.cur];
     P.Tdec = s.Tdec;
-    P.green = s.green_fine;
+    P.green = s.green_packed;
     P.Fl = s.Fl;
     P.mode = mode;
     P.kick = kick;
@@ -61,8 +102,6 @@ int tile_pass(Sim& s, int mode, float kick, float drift, float* G) {
     P.G = G;
     P.Qn = s.Qn;
     P.Pn = s.Pn;
-    P.counts_new = s.counts[1 - s.cur];
-    P.S_new = s.S;
     P.err = s.err;
     cudaFuncSetAttribute(k_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemBytes);
     const int ntiles = s.nt * s.nt * s.nt;
@@ -72,3 +111,9 @@ int tile_pass(Sim& s, int mode, float kick, float drift, float* G) {
 }
 
 }  // namespace pmpm
+
+#ifdef PMPM_PHASE_CLOCKS
+extern "C" int pmpm_debug_phases(unsigned long long* out, int n) {
+    return (int)cudaMemcpyFromSymbol(out, pmpm::g_phase, sizeof(unsigned long long) * n);
+}
+#endif

@@ -14,7 +14,10 @@
 //      particle), then its 3-D spectrum packed as 16 x 32 x 32 complex with
 //      the kx = 16 (Nyquist) plane folded into the imaginary part of kx = 0;
 //   W  22 x 32 x 16 complex = 88 KB: one force component on its way back,
-//      pruned to the 22 output planes that are needed.
+//      pruned to the 22 output planes that are needed (during the deposit it
+//      holds the table of the halo box's cells);
+//   G  the short-range Green table, 17 x 153 floats (10.2 KB): S(a, b, c)
+//      is symmetric in (b, c), so only b <= c is kept.
 // Index swizzles (x ^ y) make every pencil pass free of bank conflicts.
 //
 // Each phase is a per-thread function; the kernel calls them with a block
@@ -29,7 +32,10 @@ namespace pmpm {
 constexpr int kTileThreads = 512;
 constexpr int kTileR = kTileFFT * kTileFFT * kTileFFT;          // 32768 words
 constexpr int kTileW = kTileOut * kTileFFT * (kTileFFT / 2);    // 11264 complex
-constexpr size_t kTileSmemBytes = (size_t)kTileR * 4 + (size_t)kTileW * 8;
+constexpr int kGreenTri = kGreenS * (kGreenS + 1) / 2;          // 153 pairs b <= c
+constexpr int kGreenPacked = kGreenS * kGreenTri;               // 2601 floats
+constexpr size_t kTileSmemBytes =
+    (size_t)kTileR * 4 + (size_t)kTileW * 8 + (size_t)kGreenPacked * 4;
 
 struct TileParams {
     int nc;                       // coarse cells per side
@@ -46,7 +52,7 @@ struct TileParams {
     const float* vc;              // [3][nc^3]
     const float* sigma;           // device scalar
     const float* Tdec;            // [256] decode table
-    const float* green;           // [17][17][17] short-range Green table (scaled)
+    const float* green;           // packed short-range Green table, 17 x 153 (scaled)
     const float* Fl;              // [3][nc^3] long-range force on the coarse mesh
     int mode;                     // 0: write g; 1: kick + drift
     float kick;                   // fl32 kick factor (multiplies g)
@@ -54,8 +60,6 @@ struct TileParams {
     float* G;                     // [3][N] (mode 0)
     int32_t* Qn;                  // [3][N] new codes (mode 1)
     float* Pn;                    // [3][N] new momenta (mode 1)
-    int32_t* counts_new;          // [nc^3] (mode 1)
-    unsigned long long* S_new;    // [3][nc^3] fixed-point momentum sums (mode 1)
     uint32_t* err;
 };
 
@@ -101,7 +105,8 @@ PMPM_HD long long f64_to_ll_rn(double v) { return llrint(v); }
 
 // --- phase 0: clear the density --------------------------------------------
 PMPM_HD void tile_zero(int tid, uint32_t* R) {
-    for (int i = tid; i < kTileR; i += kTileThreads) R[i] = 0u;
+    uint4* R4 = reinterpret_cast<uint4*>(R);
+    for (int i = tid; i < kTileR / 4; i += kTileThreads) R4[i] = make_uint4(0u, 0u, 0u, 0u);
 }
 
 // Per-lane table of up to 9 consecutive cells of one row: prefix counts and
@@ -133,53 +138,321 @@ PMPM_HD void row_cells(RowCells& rc, const TileParams& P, int base, int x_first,
     }
 }
 
-PMPM_HD int row_find(const RowCells& rc, int v) {
+// Cell of the v-th particle of the row: returns its index i and, through
+// start, the storage offset of particle v.  Only compile-time array indices
+// are used, so the table stays in registers.
+PMPM_HD int row_find(const RowCells& rc, int v, int64_t& start) {
     int c = 0;
+    int64_t st = rc.st[0];
+    int pc = rc.pc[0];
 #pragma unroll
     for (int i = 1; i < 9; ++i)
-        if (i < rc.n && rc.pc[i] <= v) c = i;
+        if (i < rc.n && rc.pc[i] <= v) {
+            c = i;
+            st = rc.st[i];
+            pc = rc.pc[i];
+        }
+    start = st + (v - pc);
     return c;
+}
+
+// One row of up to 9 consecutive coarse cells (periodic in x) as a warp
+// sees it.  On the device lane i < n holds cell i's storage offset and the
+// number of the row's particles before it, and lookups are shuffles; on the
+// host every lane keeps the whole table.
+struct RowTable {
+#ifdef __CUDA_ARCH__
+    int64_t st;
+    int ex;
+#else
+    RowCells rc;
+#endif
+    int n, total;
+};
+
+PMPM_HD void row_build(RowTable& t, const TileParams& P, int base, int x_first, int ncell,
+                       int lane) {
+    t.n = ncell;
+#ifdef __CUDA_ARCH__
+    int cnt = 0;
+    int64_t st = 0;
+    if (lane < ncell) {
+        const int cell = base + wrap(x_first + lane, P.nc);
+        st = P.offsets[cell];
+        cnt = P.counts[cell];
+    }
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 16; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    t.st = st;
+    t.ex = incl - cnt;
+    t.total = __shfl_sync(0xffffffffu, incl, 15);
+#else
+    (void)lane;
+    row_cells(t.rc, P, base, x_first, ncell);
+    t.total = t.rc.pc[9];
+#endif
+}
+
+// Storage offset of the row's v-th particle and its cell index i.  On the
+// device all 32 lanes must call it together (v may be past the end).
+PMPM_HD int64_t row_locate(const RowTable& t, int v, int& i) {
+#ifdef __CUDA_ARCH__
+    int c = 0;
+#pragma unroll
+    for (int step = 8; step > 0; step >>= 1) {
+        const int cand = c + step;
+        const int e = __shfl_sync(0xffffffffu, t.ex, cand & 31);
+        if (cand < t.n && e <= v) c = cand;
+    }
+    i = c;
+    const int64_t st = __shfl_sync(0xffffffffu, t.st, c);
+    const int ex = __shfl_sync(0xffffffffu, t.ex, c);
+    return st + (v - ex);
+#else
+    int64_t j;
+    i = row_find(t.rc, v, j);
+    return j;
+#endif
+}
+
+// CIC of one particle (unwrapped coarse cell cu, bins m) into the tile box
+PMPM_HD void deposit_one(const TileGeom& g, const int (&cu)[3], const int (&m)[3], uint32_t* R,
+                         uint32_t* err) {
+    int li[3], w1[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        // s = 2Q + 1 - 64 relative to the mesh origin, units 1/128
+        const int s = 2 * (cu[d] * kBins + m[d]) + 1 - kCodesPerFine - 128 * g.o[d];
+        li[d] = s >> 7;
+        w1[d] = s & 127;
+    }
+    const bool inside = (unsigned)li[0] < 31u && (unsigned)li[1] < 31u && (unsigned)li[2] < 31u;
+    const uint32_t wyz[4] = {(uint32_t)((128 - w1[1]) * (128 - w1[2])), (uint32_t)(w1[1] * (128 - w1[2])),
+                             (uint32_t)((128 - w1[1]) * w1[2]), (uint32_t)(w1[1] * w1[2])};
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
+        const int x = li[0] + dx, y = li[1] + dy, z = li[2] + dz;
+        if (!inside && ((unsigned)x >= 32u || (unsigned)y >= 32u || (unsigned)z >= 32u)) continue;
+        const uint32_t w = (uint32_t)(dx ? w1[0] : 128 - w1[0]) * wyz[dy + 2 * dz];
+        if (w == 0u) continue;
+        const uint32_t old = smem_add_u32(&R[ridx(x, y, z)], w);
+        if (old + w < old) flag_error(err, kErrFineOverflow);
+    }
+}
+
+// Coarse-mesh force (all three components) at one particle, CIC gather
+PMPM_HD void coarse_gather(const TileParams& P, const int64_t (&Q)[3], float (&gc)[3]) {
+    const int64_t ncells = (int64_t)P.nc * P.nc * P.nc;
+    Cic1 cc[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) cc[e] = cic_coarse(Q[e]);
+    int ix[2], iy[2], iz[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        ix[k] = wrap1(cc[0].i0 + k, P.nc);
+        iy[k] = wrap1(cc[1].i0 + k, P.nc);
+        iz[k] = wrap1(cc[2].i0 + k, P.nc);
+    }
+    gc[0] = gc[1] = gc[2] = 0.f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
+        const int64_t node = ix[dx] + (int64_t)P.nc * (iy[dy] + (int64_t)P.nc * iz[dz]);
+        const float w = (float)((dx ? cc[0].w1 : 512 - cc[0].w1) * (dy ? cc[1].w1 : 512 - cc[1].w1)) *
+                        (float)(dz ? cc[2].w1 : 512 - cc[2].w1);
+#pragma unroll
+        for (int e = 0; e < 3; ++e) gc[e] += w * P.Fl[e * ncells + node];
+    }
+#pragma unroll
+    for (int e = 0; e < 3; ++e) gc[e] *= 7.450580596923828e-09f;   // 2^-27
 }
 
 // --- phase 1: integer CIC of the tile and its 2-coarse-cell halo ------------
 // Particles in coarse cells [c0 - 2, c1 + 2) can reach the mesh nodes
 // [-6, T + 5]; their contributions outside the 32^3 box are clipped.
-PMPM_HD void tile_deposit(int tid, const TileGeom& g, const TileParams& P, uint32_t* R) {
-    const int warp = tid >> 5, lane = tid & 31;
+// 1a: table of the halo box's cells (storage offset, count) in the free W
+//     area; 1b: exclusive prefix sums over the box cells and over the tile's
+//     own cells; 1c: every thread takes particles by flattened index, so the
+//     work is balanced however the particles cluster, and consecutive threads
+//     read consecutive particles.  1c also gathers the long-range force of
+//     the tile's own particles (it needs only F_l) and parks it in their
+//     output slots, where the component phases pick it up.
+// The halo box is laid out as 9 x 9 x 9 cells and the tile's own cells as
+// 5 x 5 x 5 whatever the tile size (cells outside a smaller tile's box count
+// as empty), so cell coordinates follow from divisions by constants.
+constexpr int kHaloDim = kTileMaxCoarse + 4;                  // 9
+constexpr int kHaloMax = kHaloDim * kHaloDim * kHaloDim;       // 729
+constexpr int kOwnDim = kTileMaxCoarse;                       // 5
+constexpr int kOwnMax = kOwnDim * kOwnDim * kOwnDim;           // 125
+constexpr int kMapCap = 32768;    // particles whose cell is looked up by table
+constexpr int kPMapCap = 8192;
+
+struct TileCells {
+    int64_t* st;       // [kHaloMax] storage offset of each halo-box cell
+    int* cnt;          // [kHaloMax] particles in it
+    int* pre;          // [kHaloMax + 1] exclusive prefix over the box cells
+    int* ppre;         // [kOwnMax + 1] exclusive prefix over the tile's own cells
+    uint16_t* map;     // [kMapCap] halo cell of the v-th box particle
+    uint8_t* pmap;     // [kPMapCap] own cell of the v-th own particle
+};
+
+PMPM_HD TileCells tile_cells(float2* W) {
+    TileCells c;
+    c.st = reinterpret_cast<int64_t*>(W);
+    c.cnt = reinterpret_cast<int*>(c.st + kHaloMax);
+    c.pre = c.cnt + kHaloMax;
+    c.ppre = c.pre + kHaloMax + 1;
+    c.map = reinterpret_cast<uint16_t*>(c.ppre + kOwnMax + 3);
+    c.pmap = reinterpret_cast<uint8_t*>(c.map + kMapCap);
+    return c;
+}
+static_assert(kHaloMax * 8 + (2 * kHaloMax + kOwnMax + 4) * 4 + kMapCap * 2 + kPMapCap <= kTileW * 8,
+              "tile cell tables must fit in W");
+
+// own cell p lies inside the tile (tiles of 4 coarse cells leave the fifth
+// row, column and plane of the 5^3 layout empty)
+PMPM_HD bool own_valid(const TileGeom& g, int p) {
+    return p % kOwnDim < g.c1[0] - g.c0[0] && (p / kOwnDim) % kOwnDim < g.c1[1] - g.c0[1] &&
+           p / (kOwnDim * kOwnDim) < g.c1[2] - g.c0[2];
+}
+
+PMPM_HD int own_to_halo(int p) {
+    return (2 + p % kOwnDim) + kHaloDim * ((2 + (p / kOwnDim) % kOwnDim) + kHaloDim * (2 + p / (kOwnDim * kOwnDim)));
+}
+
+PMPM_HD void tile_cells_load(int tid, const TileGeom& g, const TileParams& P, TileCells c) {
     const int hx = g.c1[0] - g.c0[0] + 4, hy = g.c1[1] - g.c0[1] + 4, hz = g.c1[2] - g.c0[2] + 4;
-    const int nrows = hy * hz;
-    for (int r = warp; r < nrows; r += kTileThreads / 32) {
-        const int yu = g.c0[1] - 2 + r % hy, zu = g.c0[2] - 2 + r / hy;
-        const int base = P.nc * (wrap(yu, P.nc) + P.nc * wrap(zu, P.nc));
-        RowCells rc;
-        row_cells(rc, P, base, g.c0[0] - 2, hx);
-        const int total = rc.pc[9];
-        for (int v = lane; v < total; v += 32) {
-            const int i = row_find(rc, v);
-            const int64_t j = rc.st[i] + (v - rc.pc[i]);
-            const int cu[3] = {g.c0[0] - 2 + i, yu, zu};
-            const int m[3] = {P.m0[j], P.m1[j], P.m2[j]};
-            int li[3], w1[3];
+    for (int b = tid; b < kHaloMax; b += kTileThreads) {
+        const int bx = b % kHaloDim, by = (b / kHaloDim) % kHaloDim, bz = b / (kHaloDim * kHaloDim);
+        int64_t st = 0;
+        int cnt = 0;
+        if (bx < hx && by < hy && bz < hz) {
+            const int cx = wrap1(g.c0[0] - 2 + bx, P.nc), cy = wrap1(g.c0[1] - 2 + by, P.nc),
+                      cz = wrap1(g.c0[2] - 2 + bz, P.nc);
+            const int64_t cell = cx + (int64_t)P.nc * (cy + (int64_t)P.nc * cz);
+            st = P.offsets[cell];
+            cnt = P.counts[cell];
+        }
+        c.st[b] = st;
+        c.cnt[b] = cnt;
+    }
+}
+
+// Exclusive prefix of n counts produced by cnt_of(i), written to out[0..n].
+template <typename F>
+PMPM_HD void warp_prefix(int lane, int n, F cnt_of, int* out) {
+#ifdef __CUDA_ARCH__
+    int carry = 0;
+    for (int base = 0; base < n; base += 32) {
+        const int i = base + lane;
+        const int v = i < n ? cnt_of(i) : 0;
+        int incl = v;
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                // s = 2Q + 1 - 64 relative to the mesh origin, units 1/128
-                int s = 2 * (cu[d] * kBins + m[d]) + 1 - kCodesPerFine - 128 * g.o[d];
-                li[d] = s >> 7;
-                w1[d] = s & 127;
-            }
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (i < n) out[i] = carry + incl - v;
+        carry += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    if (lane == 0) out[n] = carry;
+#else
+    if (lane != 0) return;
+    int acc = 0;
+    for (int i = 0; i < n; ++i) {
+        out[i] = acc;
+        acc += cnt_of(i);
+    }
+    out[n] = acc;
+#endif
+}
+
+PMPM_HD void tile_cells_scan(int tid, const TileGeom& g, TileCells c) {
+    const int warp = tid >> 5, lane = tid & 31;
+    const int* cnt = c.cnt;
+    if (warp == 0) {
+        warp_prefix(lane, kHaloMax, [cnt](int i) { return cnt[i]; }, c.pre);
+    } else if (warp == 1) {
+        const TileGeom gg = g;
+        warp_prefix(lane, kOwnMax,
+                    [cnt, gg](int p) { return own_valid(gg, p) ? cnt[own_to_halo(p)] : 0; }, c.ppre);
+    }
+}
+
+// particle -> cell maps (for the first kMapCap / kPMapCap particles)
+PMPM_HD void tile_cells_map(int tid, const TileGeom& g, TileCells c) {
+    for (int b = tid; b < kHaloMax; b += kTileThreads) {
+        const int n = c.cnt[b], p0 = c.pre[b];
+        for (int q = 0; q < n && p0 + q < kMapCap; ++q) c.map[p0 + q] = (uint16_t)b;
+    }
+    for (int p = tid; p < kOwnMax; p += kTileThreads) {
+        const int n = own_valid(g, p) ? c.cnt[own_to_halo(p)] : 0, p0 = c.ppre[p];
+        for (int q = 0; q < n && p0 + q < kPMapCap; ++q) c.pmap[p0 + q] = (uint8_t)p;
+    }
+}
+
+// largest i in [0, n) with pre[i] <= v (pre non-decreasing, pre[0] = 0 <= v)
+PMPM_HD int prefix_find(const int* pre, int n, int v) {
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (pre[mid] <= v) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+PMPM_HD int halo_of(const TileCells& c, int v) {
+    return v < kMapCap ? (int)c.map[v] : prefix_find(c.pre, kHaloMax, v);
+}
+PMPM_HD int own_of(const TileCells& c, int v) {
+    return v < kPMapCap ? (int)c.pmap[v] : prefix_find(c.ppre, kOwnMax, v);
+}
+
+PMPM_HD void tile_deposit_flat(int tid, const TileGeom& g, const TileParams& P, uint32_t* R,
+                               TileCells c) {
+    const int total = c.pre[kHaloMax];
+    for (int v0 = tid; v0 < total; v0 += 2 * kTileThreads) {
+        int b[2], m[2][3];
+        bool ok[2];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                const int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
-                const int x = li[0] + dx, y = li[1] + dy, z = li[2] + dz;
-                if ((unsigned)x >= 32u || (unsigned)y >= 32u || (unsigned)z >= 32u) continue;
-                const uint32_t w = (uint32_t)((dx ? w1[0] : 128 - w1[0]) *
-                                              (dy ? w1[1] : 128 - w1[1]) *
-                                              (dz ? w1[2] : 128 - w1[2]));
-                if (w == 0u) continue;
-                const uint32_t old = smem_add_u32(&R[ridx(x, y, z)], w);
-                if (old + w < old) flag_error(P.err, kErrFineOverflow);
+        for (int u = 0; u < 2; ++u) {
+            const int v = v0 + u * kTileThreads;
+            ok[u] = v < total;
+            b[u] = ok[u] ? halo_of(c, v) : 0;
+            const int64_t j = c.st[b[u]] + (v - c.pre[b[u]]);
+            if (ok[u]) {
+                m[u][0] = P.m0[j];
+                m[u][1] = P.m1[j];
+                m[u][2] = P.m2[j];
             }
         }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            if (!ok[u]) continue;
+            const int cu[3] = {g.c0[0] - 2 + b[u] % kHaloDim, g.c0[1] - 2 + (b[u] / kHaloDim) % kHaloDim,
+                               g.c0[2] - 2 + b[u] / (kHaloDim * kHaloDim)};
+            deposit_one(g, cu, m[u], R, P.err);
+        }
+    }
+    // long-range force of the tile's own particles
+    float* slot = P.mode == 0 ? P.G : P.Pn;
+    const int ptotal = c.ppre[kOwnMax];
+    for (int v = tid; v < ptotal; v += kTileThreads) {
+        const int p = own_of(c, v);
+        const int bh = own_to_halo(p);
+        const int64_t j = c.st[bh] + (v - c.ppre[p]);
+        const int64_t Q[3] = {(int64_t)(g.c0[0] + p % kOwnDim) * kBins + P.m0[j],
+                              (int64_t)(g.c0[1] + (p / kOwnDim) % kOwnDim) * kBins + P.m1[j],
+                              (int64_t)(g.c0[2] + p / (kOwnDim * kOwnDim)) * kBins + P.m2[j]};
+        float gc[3];
+        coarse_gather(P, Q, gc);
+#pragma unroll
+        for (int e = 0; e < 3; ++e) slot[e * P.n + j] = gc[e];
     }
 }
 
@@ -224,13 +497,15 @@ PMPM_HD void tile_fwd_z(int tid, float2* C) {
 PMPM_HD int kabs32(int i) { return i <= 16 ? i : 32 - i; }
 PMPM_HD float ksgn32(int i) { return i == 0 ? 0.f : (i < 16 ? 1.f : (i == 16 ? 1.f : -1.f)); }
 
-// Green coefficient S_d(kx, ky, kz) with K~_d = -i S_d; table index
-// [own axis][other][other], symmetric in the last two.
-PMPM_HD float green_S(const float* Gt, int d, int kx, int ky, int kz) {
-    const int ax = kabs32(kx), ay = kabs32(ky), az = kabs32(kz);
-    if (d == 0) return ksgn32(kx) * Gt[(ax * kGreenS + ay) * kGreenS + az];
-    if (d == 1) return ksgn32(ky) * Gt[(ay * kGreenS + ax) * kGreenS + az];
-    return ksgn32(kz) * Gt[(az * kGreenS + ay) * kGreenS + ax];
+// Packed index of the symmetric pair (b, c): row b holds c = b..16.
+PMPM_HD int green_off(int b) { return b * kGreenS - (b * (b - 1)) / 2 - b; }
+PMPM_HD int green_tri(int b, int c) {
+    return b <= c ? green_off(b) + c : green_off(c) + b;
+}
+
+// Copy the packed Green table (17 x 153 floats, b <= c only) into shared memory.
+PMPM_HD void tile_load_green(int tid, const float* Gp, float* gS) {
+    for (int i = tid; i < kGreenPacked; i += kTileThreads) gS[i] = Gp[i];
 }
 
 // --- phase 5a: Green multiply (Eq. 1) and inverse transform along z -------
@@ -238,21 +513,53 @@ PMPM_HD float green_S(const float* Gt, int d, int kx, int ky, int kz) {
 // Z = A + iB holds the kx = 0 (A) and kx = 16 (B) planes; with the partner
 // Z' = Z(-ky, -kz): A = (Z + conj Z')/2, B = (Z - conj Z')/(2i), and the packed
 // product A K~_d(0) + i B K~_d(16) = -i[(s0+s16)/2 Z + (s0-s16)/2 conj Z'].
-PMPM_HD void tile_inv_z(int tid, int d, const TileGeom& g, const float* Gt, const float2* C,
+template <int D>
+PMPM_HD void tile_inv_z(int tid, const TileGeom& g, const float* gS, const float2* C,
                         float2* W) {
     const int kx = tid & 15, ky = tid >> 4;
+    const int nz = g.T[2] + 2;
+    const int ay = kabs32(ky);
     float2 a[32];
+    if (D == 0 && kx == 0) {
+        // S_x vanishes on both planes kx = 0 and kx = 16 (odd in x, zero at Nyquist)
+#pragma unroll
+        for (int zo = 0; zo < kTileOut; ++zo)
+            if (zo < nz) W[widx(0, ky, zo)] = make_float2(0.f, 0.f);
+        return;
+    }
+    // per-thread parts of the table index: the third index (|kz|) is a
+    // compile-time constant in the unrolled loop below
+    const float sgy = ksgn32(ky);
+    const int offA = green_off(D == 0 ? ay : kx);          // pair (b, c) with b fixed
+    const int bfix = D == 0 ? ay : kx;
+    const int rowA = D == 0 ? kx * kGreenTri : ay * kGreenTri;
+    const int t0 = green_tri(0, ay), t16 = green_tri(16, ay), txy = green_tri(kx, ay);
 #pragma unroll
     for (int kz = 0; kz < 32; ++kz) {
+        const int az = kabs32(kz);
         const float2 Z = C[cidx(kx, ky, kz)];
         float cA, cB;
         float2 Zp = make_float2(0.f, 0.f);
-        if (kx != 0) {
-            cA = green_S(Gt, d, kx, ky, kz);
+        if (D == 2) {
+            const float sz = ksgn32(kz);
+            if (kx != 0) {
+                cA = sz * gS[az * kGreenTri + txy];
+                cB = 0.f;
+            } else {
+                const float s0 = sz * gS[az * kGreenTri + t0];
+                const float s16 = sz * gS[az * kGreenTri + t16];
+                cA = 0.5f * (s0 + s16);
+                cB = 0.5f * (s0 - s16);
+                Zp = C[cidx(0, (32 - ky) & 31, (32 - kz) & 31)];
+            }
+        } else if (kx != 0) {
+            const int idx = bfix <= az ? offA + az : green_off(az) + bfix;
+            cA = (D == 0 ? 1.f : sgy) * gS[rowA + idx];
             cB = 0.f;
         } else {
-            const float s0 = green_S(Gt, d, 0, ky, kz);
-            const float s16 = green_S(Gt, d, 16, ky, kz);
+            // D == 1, packed kx = 0 / 16 pencil: b = 0 and b = 16
+            const float s0 = sgy * gS[rowA + green_off(0) + az];
+            const float s16 = sgy * gS[rowA + green_off(az) + 16];
             cA = 0.5f * (s0 + s16);
             cB = 0.5f * (s0 - s16);
             Zp = C[cidx(0, (32 - ky) & 31, (32 - kz) & 31)];
@@ -263,7 +570,6 @@ PMPM_HD void tile_inv_z(int tid, int d, const TileGeom& g, const float* Gt, cons
         a[kz] = make_float2(vy, -vx);
     }
     fft_bitrev_out<32, 1>(a);
-    const int nz = g.T[2] + 2;
 #pragma unroll
     for (int zo = 0; zo < kTileOut; ++zo)
         if (zo < nz) W[widx(kx, ky, zo)] = a[bitrev<5>(zo + kBuffer - 1)];
@@ -303,35 +609,40 @@ PMPM_HD void tile_inv_x(int tid, const TileGeom& g, float2* W) {
     }
 }
 
-// --- phase 5d: interpolate component d to the tile's own particles, then
-// (mode 1) kick and drift that component; after the last component, update
-// the new-cell counts and fixed-point momentum sums.
-PMPM_HD void tile_interp(int tid, int d, const TileGeom& g, const TileParams& P, const float2* W) {
+// --- phase 5d: interpolate component D to the tile's own particles, add the
+// parked long-range part, then (mode 1) kick and drift that component.
+template <int D>
+PMPM_HD void tile_interp(int tid, const TileGeom& g, const TileParams& P, const float2* W) {
     const float* Wf = reinterpret_cast<const float*>(W);
     const int warp = tid >> 5, lane = tid & 31;
     const int nx = g.c1[0] - g.c0[0], ny = g.c1[1] - g.c0[1], nz = g.c1[2] - g.c0[2];
     const int64_t ncells = (int64_t)P.nc * P.nc * P.nc;
     const int64_t n = P.n;
     const float sigma = *P.sigma;
-    const uint8_t* ud = d == 0 ? P.u0 : (d == 1 ? P.u1 : P.u2);
-    const float* Fl = P.Fl + d * ncells;
+    const uint8_t* ud = D == 0 ? P.u0 : (D == 1 ? P.u1 : P.u2);
+    float* slot = P.mode == 0 ? P.G : P.Pn;
     for (int r = warp; r < ny * nz; r += kTileThreads / 32) {
         const int y = g.c0[1] + r % ny, z = g.c0[2] + r / ny;
         const int base = P.nc * (y + P.nc * z);
-        RowCells rc;
-        row_cells(rc, P, base, g.c0[0], nx);
-        const int total = rc.pc[9];
-        for (int v = lane; v < total; v += 32) {
-            const int i = row_find(rc, v);
-            const int64_t j = rc.st[i] + (v - rc.pc[i]);
+        RowTable t;
+        row_build(t, P, base, g.c0[0], nx, lane);
+        for (int v0 = 0; v0 < t.total; v0 += 32) {
+            int i;
+            const int v = v0 + lane;
+            const int64_t jr = row_locate(t, v, i);
+            const bool valid = v < t.total;
+            const int64_t j = valid ? jr : 0;
             const int cell = base + g.c0[0] + i;
             const int64_t Q[3] = {(int64_t)(g.c0[0] + i) * kBins + P.m0[j],
                                   (int64_t)y * kBins + P.m1[j], (int64_t)z * kBins + P.m2[j]};
+            const float gcd = slot[D * n + j];
+            const uint8_t u = ud[j];
+            const float vcd = P.vc[D * ncells + cell];
             // fine gather
             int lo[3], w1[3];
 #pragma unroll
             for (int e = 0; e < 3; ++e) {
-                int s = (int)(2 * Q[e] + 1 - kCodesPerFine - 128 * (int64_t)g.o[e]);
+                const int s = (int)(2 * Q[e] + 1 - kCodesPerFine - 128 * (int64_t)g.o[e]);
                 lo[e] = (s >> 7) - (kBuffer - 1);
                 w1[e] = s & 127;
             }
@@ -343,51 +654,27 @@ PMPM_HD void tile_interp(int tid, int d, const TileGeom& g, const TileParams& P,
                                         (dz ? w1[2] : 128 - w1[2]));
                 gf += w * Wf[wfidx(lo[0] + dx, lo[1] + dy, lo[2] + dz)];
             }
-            // coarse gather
-            Cic1 cc[3];
-#pragma unroll
-            for (int e = 0; e < 3; ++e) cc[e] = cic_coarse(Q[e]);
-            float gc = 0.f;
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                const int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
-                const int ix = wrap(cc[0].i0 + dx, P.nc), iy = wrap(cc[1].i0 + dy, P.nc),
-                          iz = wrap(cc[2].i0 + dz, P.nc);
-                const float w = (float)((dx ? cc[0].w1 : 512 - cc[0].w1) *
-                                        (dy ? cc[1].w1 : 512 - cc[1].w1)) *
-                                (float)(dz ? cc[2].w1 : 512 - cc[2].w1);
-                gc += w * Fl[(int64_t)ix + P.nc * ((int64_t)iy + (int64_t)P.nc * iz)];
-            }
-            const float gval = gf * 4.76837158203125e-07f      // 2^-21
-                             + gc * 7.450580596923828e-09f;    // 2^-27
+            const float gval = gf * 4.76837158203125e-07f + gcd;   // 2^-21
             if (P.mode == 0) {
-                P.G[d * n + j] = gval;
+                if (valid) slot[D * n + j] = gval;
                 continue;
             }
             // kick (Eq. 3 decode, then p += kick * g) and integer drift
-            const float p = decode_momentum(P.vc[d * ncells + cell], sigma, P.Tdec[ud[j]]);
+            const float p = decode_momentum(vcd, sigma, P.Tdec[u]);
             const float pn = fadd_rn(p, fmul_rn(P.kick, gval));
-            if (!(pn == pn) || !(gval == gval)) flag_error(P.err, kErrNaN);
-            if (fabsf(pn) >= 1048576.f) flag_error(P.err, kErrMomentum);
             const float xq = fmul_rn(pn, P.drift);
-            if (!(fabsf(xq) < 1.0e9f)) flag_error(P.err, kErrDrift);
-            const int64_t dq = (int64_t)floorf(fadd_rn(xq, 0.5f));
+            if (valid) {
+                if (!(pn == pn) || !(gval == gval)) flag_error(P.err, kErrNaN);
+                if (fabsf(pn) >= 1048576.f) flag_error(P.err, kErrMomentum);
+                if (!(fabsf(xq) < 1.0e9f)) flag_error(P.err, kErrDrift);
+            }
+            const int64_t dq = valid && fabsf(xq) < 1.0e9f ? (int64_t)floorf(fadd_rn(xq, 0.5f)) : 0;
             const int64_t M = (int64_t)P.nc * kBins;
-            int64_t qn = (Q[d] + dq) % M;
+            int64_t qn = (Q[D] + dq) % M;
             if (qn < 0) qn += M;
-            P.Qn[d * n + j] = (int32_t)qn;
-            P.Pn[d * n + j] = pn;
-            if (d == 2) {
-                const int32_t q0 = P.Qn[j], q1 = P.Qn[n + j];
-                const int64_t key = (int64_t)(q0 >> 8) +
-                                    P.nc * ((int64_t)(q1 >> 8) + (int64_t)P.nc * (qn >> 8));
-                gmem_add_i32(&P.counts_new[key], 1);
-                const float pp[3] = {P.Pn[j], P.Pn[n + j], pn};
-#pragma unroll
-                for (int e = 0; e < 3; ++e) {
-                    const long long fx = f64_to_ll_rn((double)pp[e] * 16777216.0);
-                    gmem_add_u64(&P.S_new[e * ncells + key], (unsigned long long)fx);
-                }
+            if (valid) {
+                P.Qn[D * n + j] = (int32_t)qn;
+                P.Pn[D * n + j] = pn;
             }
         }
     }

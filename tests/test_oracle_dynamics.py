@@ -117,8 +117,13 @@ def test_encode_invariants_and_exact_sums():
         members = np.nonzero(cell_in == c)[0]
         for d in range(3):
             S = sum(P[i][d] for i in members)
-            ref = np.float32((float(S) / len(members)) * 2.0 ** -24)
+            # float32 division of the rounded sum, and within one float32
+            # rounding of the exact rational mean
+            ref = np.float32(np.float32(np.float32(S) * np.float32(2.0 ** -24))
+                             / np.float32(len(members)))
             assert st.vc[c, d] == ref
+            exact = S / len(members) * 2.0 ** -24
+            assert abs(float(st.vc[c, d]) - exact) <= 2.5e-7 * abs(exact) + 1e-12
     # sigma against the exact integer sum
     vcp = st.vc[cell_in]
     dev = (p - vcp).astype(np.float32).astype(np.float64)
