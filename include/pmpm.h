@@ -144,6 +144,34 @@ void pmpm_destroy(pmpm_sim* sim);
  * sim is NULL). */
 const char* pmpm_last_error(const pmpm_sim* sim);
 
+/* Power spectrum without any device allocation, for callers that may not
+ * allocate GPU memory themselves: for example code running inside a host
+ * application that owns a fixed device-memory budget, or a loop that cannot
+ * afford the device-wide synchronisation an allocation may cause.  The paper
+ * has no counterpart; it computes the same P(k) as pmpm_power_spectrum for
+ * a cell-ordered store the caller already holds on the device:
+ *   nc         coarse cells per side, a power of two in [8, 64]
+ *   n          particles; d_m0..d_m2 their position bins (Eq. 2), n bytes
+ *              each, and d_counts the nc^3 per-cell counts (device pointers)
+ *   nmesh      power of two dividing 4*nc, 4*nc/4 <= nmesh <= 64
+ *   nbins      in [1, nmesh/2]; k, pk, nmodes are host arrays of nbins
+ *   cuda_stream the stream to run on (NULL: legacy default stream)
+ * Its scratch is one fixed array of about 4.2 MB in the library's device
+ * memory, held by every GPU that loads the library until the process exits.
+ * The first call on a device looks up that array's address and fills a
+ * twiddle table there, synchronising the stream; make that first call before
+ * any stream capture.  All calls share the array: calls whose GPU work
+ * overlaps (other streams, other host threads) race and give wrong results.
+ * Larger sizes return PMPM_EINVAL; pmpm_noalloc_last_error() explains. */
+int pmpm_power_spectrum_noalloc(int32_t nc, int64_t n, const uint8_t* d_m0,
+                                const uint8_t* d_m1, const uint8_t* d_m2,
+                                const int32_t* d_counts, int32_t nmesh, int32_t nbins,
+                                double* k, double* pk, int64_t* nmodes,
+                                void* cuda_stream);
+
+/* Text of the last failure of pmpm_power_spectrum_noalloc. */
+const char* pmpm_noalloc_last_error(void);
+
 /* Host copies of the float32 velocity tables the library uses: T[256]
  * bin-centre values and E[256] bin edges (E[0] = -inf), Eq. 3.  Host only. */
 int pmpm_codec_tables(float* T, float* E);

@@ -41,7 +41,8 @@ ERROR_NAMES = {
 EXPORTS = [
     "pmpm_workspace_bytes", "pmpm_init", "pmpm_ic_zeldovich", "pmpm_step",
     "pmpm_power_spectrum", "pmpm_fetch", "pmpm_load", "pmpm_sync", "pmpm_stage_times",
-    "pmpm_destroy", "pmpm_last_error", "pmpm_codec_tables",
+    "pmpm_destroy", "pmpm_last_error", "pmpm_codec_tables", "pmpm_power_spectrum_noalloc",
+    "pmpm_noalloc_last_error",
 ]
 
 
@@ -105,8 +106,12 @@ def load():
     lib.pmpm_last_error.argtypes = [P]
     lib.pmpm_last_error.restype = ctypes.c_char_p
     lib.pmpm_codec_tables.argtypes = [P, P]
+    lib.pmpm_power_spectrum_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int64, P, P, P, P,
+                                                ctypes.c_int32, ctypes.c_int32, P, P, P, P]
+    lib.pmpm_noalloc_last_error.argtypes = []
+    lib.pmpm_noalloc_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name not in ("pmpm_destroy", "pmpm_last_error"):
+        if name not in ("pmpm_destroy", "pmpm_last_error", "pmpm_noalloc_last_error"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib

@@ -113,6 +113,21 @@ int fft3d(Sim& s, void* data, int n, int sign) {
 }
 
 template int fft3d<float>(Sim&, void*, int, int);
+
+// The same three float passes for a caller-supplied twiddle table of tw_n
+// entries (n divides tw_n); used where no Sim exists.
+cudaError_t fft3d_float_raw(cudaStream_t st, float2* data, int n, int sign, const float2* tw,
+                            int tw_n) {
+    int log2n = 0;
+    while ((1 << log2n) < n) ++log2n;
+    const int P = pencils_per_block<float>(n);
+    const size_t smem = 2 * (size_t)P * n * sizeof(float2);
+    cudaFuncSetAttribute(k_fft_pass<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536);
+    const int64_t groups = (int64_t)n * n / P;
+    for (int axis = 0; axis < 3; ++axis)
+        k_fft_pass<float><<<(unsigned)groups, 256, smem, st>>>(data, n, log2n, axis, sign, P, tw, tw_n);
+    return cudaGetLastError();
+}
 template int fft3d<double>(Sim&, void*, int, int);
 
 }  // namespace pmpm
