@@ -146,6 +146,22 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def reduce_max(value, device):
+    """Max of a float over all ranks (identity without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, t_max):
+    """Whole-job throughput: the units of all ranks over the slowest rank's time."""
+    return world * units_per_rank / t_max
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -221,11 +237,7 @@ def run_ours(args):
     t = e0.elapsed_time(e1) / 1000.0
     stages, launches = sim.stage_times(enable=False)
     sim.sync()
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t], device=f"cuda:{local}")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
+    t = reduce_max(t, f"cuda:{local}")
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
@@ -244,14 +256,9 @@ def run_ours(args):
             sim.fetch_into(host)
             host["scalars"] = sim.fetch_scalars()
         torch.cuda.synchronize()
-        te = time.perf_counter() - t0
-        if world > 1:
-            import torch.distributed as dist
-            tt = torch.tensor([te], device=f"cuda:{local}")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            te = float(tt.item())
+        te = reduce_max(time.perf_counter() - t0, f"cuda:{local}")
         per = 6 * n + 4 * C + 12 * C + 32
-        e2e = {"value": world * n * E / te, "unit": UNIT, "h2d_bytes_per_step": per,
+        e2e = {"value": job_rate(n * E, world, te), "unit": UNIT, "h2d_bytes_per_step": per,
                "d2h_bytes_per_step": per, "steps": E}
 
     if rank != 0:
@@ -259,7 +266,7 @@ def run_ours(args):
         return None
 
     n = cfg.n
-    value = world * n * K / t
+    value = job_rate(n * K, world, t)
     flops = tile_flops_per_launch(cfg.nc, cfg.tile_max)
     tile_s = stages[2] / 1000.0 / K
     sm_max = clocks.get("sm_max_mhz") or measured_peaks().get("sm_max_mhz") or 2070.0
