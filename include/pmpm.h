@@ -99,6 +99,19 @@ int pmpm_workspace_bytes(const pmpm_config* cfg, size_t* bytes);
 int pmpm_init(const pmpm_config* cfg, void* d_workspace, size_t bytes,
               void* cuda_stream, pmpm_sim** out);
 
+/* As pmpm_init, but the force-kernel tables (Sec. II) are copied from a live
+ * sim `donor` of the same nc instead of being computed again; the donor is
+ * only read, on cuda_stream, during the call. */
+int pmpm_init_like(const pmpm_config* cfg, void* d_workspace, size_t bytes,
+                   void* cuda_stream, const pmpm_sim* donor, pmpm_sim** out);
+
+/* enable != 0: each step is captured once per store buffer into a CUDA graph
+ * and replayed (one launch per step instead of ~30).  Stage timing is not
+ * recorded for replayed steps.  The sim's stream must be one the caller
+ * created: a legacy or per-thread default stream cannot be captured, and
+ * enabling on one returns PMPM_EINVAL. */
+int pmpm_graph_mode(pmpm_sim* sim, int32_t enable);
+
 /* Zel'dovich initial conditions at a_init (Sec. IV-A.2) for a power-law
  * spectrum P(k) = k^slope exp(-(k/k_c)^2), k in radians per fine cell;
  * white noise from counter-based SplitMix64 at `seed`; displacements scaled

@@ -39,7 +39,8 @@ ERROR_NAMES = {
 
 # every entry point the header declares, for the export check
 EXPORTS = [
-    "pmpm_workspace_bytes", "pmpm_init", "pmpm_ic_zeldovich", "pmpm_step",
+    "pmpm_workspace_bytes", "pmpm_init", "pmpm_init_like", "pmpm_graph_mode",
+    "pmpm_ic_zeldovich", "pmpm_step",
     "pmpm_power_spectrum", "pmpm_fetch", "pmpm_load", "pmpm_sync", "pmpm_stage_times",
     "pmpm_destroy", "pmpm_last_error", "pmpm_codec_tables", "pmpm_power_spectrum_noalloc",
     "pmpm_noalloc_last_error",
@@ -93,6 +94,9 @@ def load():
     P = ctypes.c_void_p
     lib.pmpm_workspace_bytes.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_size_t)]
     lib.pmpm_init.argtypes = [ctypes.POINTER(Config), P, ctypes.c_size_t, P, ctypes.POINTER(P)]
+    lib.pmpm_init_like.argtypes = [ctypes.POINTER(Config), P, ctypes.c_size_t, P, P,
+                                   ctypes.POINTER(P)]
+    lib.pmpm_graph_mode.argtypes = [P, ctypes.c_int32]
     lib.pmpm_ic_zeldovich.argtypes = [P, ctypes.c_uint64, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_double]
     lib.pmpm_step.argtypes = [P, ctypes.c_int32]

@@ -110,6 +110,8 @@ size_t layout(Sim& s, uint8_t* base) {
     s.blocksums = reinterpret_cast<long long*>(take(8 * (size_t)(s.nblocks_scan + 1)));
     s.ic_partial = reinterpret_cast<double*>(take(8 * (3 * 1024 + 1)));
     s.pk_bins = reinterpret_cast<double*>(take(8 * 3 * (size_t)(s.pk_max / 2 + 1)));
+    s.d_factors = reinterpret_cast<float*>(take(8 * (size_t)s.cfg.n_steps));
+    s.d_step = reinterpret_cast<int*>(take(4));
     // transient scratch
     const size_t step_b = 24 * (size_t)N + 512;
     const size_t ic_b = 56 * (size_t)N + 1024;
@@ -188,33 +190,157 @@ static double sched_a(const Sim& s, int64_t n) {
     return s.cfg.a_init * pow(s.cfg.a_final / s.cfg.a_init, (double)n / (double)s.cfg.n_steps);
 }
 
-static int one_step(Sim& s) {
-    if (s.step >= s.cfg.n_steps) return set_error(s, PMPM_EINVAL, "schedule exhausted");
-    const int64_t n = s.step;
-    const double an = sched_a(s, n), an1 = sched_a(s, n + 1);
-    const double a_lo = n == 0 ? s.cfg.a_init : sqrt(sched_a(s, n - 1) * an);
-    const double a_hi = sqrt(an * an1);
+__global__ void k_step_set(int* step, int v) { *step = v; }
+__global__ void k_step_advance(int* step) { *step += 1; }
+
+// float32 kick and drift factors of every step of the schedule (R7), in
+// device memory so that a captured step can replay at any step index
+static void fill_factors(Sim& s) {
+    const int S = s.cfg.n_steps;
+    float* f = new float[2 * S];
     const double rho_bar = (double)s.n / ((double)s.nf * s.nf * s.nf);
-    const double kick = 3.0 / (8.0 * 3.141592653589793238462643383279502884 * rho_bar) * 2.0 *
-                        (sqrt(a_hi) - sqrt(a_lo));
-    const double drift = 2.0 * (1.0 / sqrt(an) - 1.0 / sqrt(an1));
-    int rc;
-    s.in_step = true;
-    if (!s.offsets_valid) {
-        if ((rc = scan_counts(s, s.counts[s.cur], s.offsets[s.cur]))) return rc;
-        s.offsets_valid = true;
+    for (int n = 0; n < S; ++n) {
+        const double an = sched_a(s, n), an1 = sched_a(s, n + 1);
+        const double a_lo = n == 0 ? s.cfg.a_init : sqrt(sched_a(s, n - 1) * an);
+        const double a_hi = sqrt(an * an1);
+        const double kick = 3.0 / (8.0 * 3.141592653589793238462643383279502884 * rho_bar) * 2.0 *
+                            (sqrt(a_hi) - sqrt(a_lo));
+        const double drift = 2.0 * (1.0 / sqrt(an) - 1.0 / sqrt(an1));
+        f[2 * n] = (float)kick;
+        f[2 * n + 1] = (float)(drift * kCodesPerFine);
     }
+    cudaMemcpyAsync(s.d_factors, f, sizeof(float) * 2 * S, cudaMemcpyHostToDevice, s.stream);
+    cudaStreamSynchronize(s.stream);
+    delete[] f;
+}
+
+void set_device_step(Sim& s, int64_t step) {
+    k_step_set<<<1, 1, 0, s.stream>>>(s.d_step, (int)step);
+}
+
+// Device work of one step; swaps the store buffers (s.cur).
+static int enqueue_step(Sim& s) {
+    int rc;
     prof_mark(s, -1);
     if ((rc = coarse_deposit(s))) return rc;
     prof_mark(s, 0);
     if ((rc = coarse_force(s))) return rc;
     prof_mark(s, 1);
-    if ((rc = tile_pass(s, 1, (float)kick, (float)(drift * kCodesPerFine), nullptr))) return rc;
+    if ((rc = tile_pass(s, 1, nullptr))) return rc;
     prof_mark(s, 2);
     if ((rc = encode_from_qp(s, false))) return rc;
+    k_step_advance<<<1, 1, 0, s.stream>>>(s.d_step);
+    s.launches++;
+    return check_launch(s, "step");
+}
+
+static int one_step(Sim& s) {
+    if (s.step >= s.cfg.n_steps) return set_error(s, PMPM_EINVAL, "schedule exhausted");
+    int rc;
+    if (!s.offsets_valid) {
+        if ((rc = scan_counts(s, s.counts[s.cur], s.offsets[s.cur]))) return rc;
+        s.offsets_valid = true;
+    }
+    s.in_step = true;
+    if (s.graphs) {
+        const int c = s.cur;
+        if (!s.graph_ready[c]) {
+            const bool prof = s.prof;
+            const int64_t l0 = s.launches;
+            s.prof = false;
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) return set_error(s, PMPM_ECUDA, "capture: %s", cudaGetErrorString(e));
+            rc = enqueue_step(s);
+            e = cudaStreamEndCapture(s.stream, &g);
+            s.prof = prof;
+            s.cur = c;   // capturing ran nothing
+            s.graph_launches[c] = s.launches - l0;
+            s.launches = l0;
+            if (rc || e != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                return rc ? rc : set_error(s, PMPM_ECUDA, "capture: %s", cudaGetErrorString(e));
+            }
+            e = cudaGraphInstantiate(&s.graph_exec[c], g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return set_error(s, PMPM_ECUDA, "instantiate: %s", cudaGetErrorString(e));
+            s.graph_ready[c] = true;
+        }
+        const cudaError_t e = cudaGraphLaunch(s.graph_exec[c], s.stream);
+        if (e != cudaSuccess) return set_error(s, PMPM_ECUDA, "graph launch: %s", cudaGetErrorString(e));
+        s.launches += s.graph_launches[c];
+        s.cur = 1 - c;
+    } else {
+        if ((rc = enqueue_step(s))) return rc;
+    }
     s.in_step = false;
-    s.step = n + 1;
-    s.a = an1;
+    s.step += 1;
+    s.a = sched_a(s, s.step);
+    return PMPM_OK;
+}
+
+// Shared by pmpm_init and pmpm_init_like: everything but the force tables.
+static pmpm_sim* init_common(const pmpm_config* cfg, void* d_workspace, size_t bytes,
+                             void* cuda_stream, int* rc_out) {
+    char msg[256];
+    int rc = validate(cfg, msg, sizeof(msg));
+    if (rc) {
+        snprintf(g_init_msg, sizeof(g_init_msg), "%s", msg);
+        *rc_out = rc;
+        return nullptr;
+    }
+    if (!d_workspace) {
+        snprintf(g_init_msg, sizeof(g_init_msg), "null workspace");
+        *rc_out = PMPM_EINVAL;
+        return nullptr;
+    }
+    if (reinterpret_cast<uintptr_t>(d_workspace) % 256) {
+        snprintf(g_init_msg, sizeof(g_init_msg), "workspace must be 256-byte aligned");
+        *rc_out = PMPM_EINVAL;
+        return nullptr;
+    }
+    pmpm_sim* h = new (std::nothrow) pmpm_sim();
+    if (!h) {
+        *rc_out = PMPM_ENOMEM;
+        return nullptr;
+    }
+    Sim& s = h->s;
+    derive(s, cfg);
+    const size_t need = layout(s, nullptr);
+    if (bytes < need) {
+        snprintf(g_init_msg, sizeof(g_init_msg), "workspace %zu bytes < required %zu", bytes, need);
+        delete h;
+        *rc_out = PMPM_ENOMEM;
+        return nullptr;
+    }
+    s.ws = static_cast<uint8_t*>(d_workspace);
+    s.ws_bytes = bytes;
+    s.stream = static_cast<cudaStream_t>(cuda_stream);
+    layout(s, s.ws);
+    cudaGetDevice(&s.device);
+    tile_setup();
+    fft_setup();
+    cudaMemsetAsync(s.err, 0, 4, s.stream);
+    float T[256], E[256];
+    codec_tables(T, E);
+    cudaMemcpyAsync(s.Tdec, T, sizeof(T), cudaMemcpyHostToDevice, s.stream);
+    cudaMemcpyAsync(s.Eedge, E, sizeof(E), cudaMemcpyHostToDevice, s.stream);
+    k_twiddles<<<grid_for(s.fft_max, 256), 256, 0, s.stream>>>(s.fft_max, s.tw_f, s.tw_d);
+    fill_factors(s);
+    set_device_step(s, 0);
+    s.a = cfg->a_init;
+    *rc_out = check_launch(s, "init");
+    return h;
+}
+
+static int init_finish(pmpm_sim* h, pmpm_sim** out) {
+    int rc = sync_and_check(h->s);
+    if (rc) {
+        snprintf(g_init_msg, sizeof(g_init_msg), "%s", h->s.msg);
+        delete h;
+        return rc;
+    }
+    *out = h;
     return PMPM_OK;
 }
 
@@ -242,51 +368,56 @@ int pmpm_workspace_bytes(const pmpm_config* cfg, size_t* bytes) {
 
 int pmpm_init(const pmpm_config* cfg, void* d_workspace, size_t bytes, void* cuda_stream,
               pmpm_sim** out) {
-    char msg[256];
-    int rc = validate(cfg, msg, sizeof(msg));
+    if (!out) return PMPM_EINVAL;
+    int rc = PMPM_OK;
+    pmpm_sim* h = init_common(cfg, d_workspace, bytes, cuda_stream, &rc);
+    if (!h) return rc;
+    if (!rc) rc = build_green_tables(h->s);
     if (rc) {
-        snprintf(g_init_msg, sizeof(g_init_msg), "%s", msg);
+        snprintf(g_init_msg, sizeof(g_init_msg), "%s", h->s.msg);
+        delete h;
         return rc;
     }
-    if (!out || !d_workspace) {
-        snprintf(g_init_msg, sizeof(g_init_msg), "null workspace or output handle");
+    return init_finish(h, out);
+}
+
+int pmpm_init_like(const pmpm_config* cfg, void* d_workspace, size_t bytes, void* cuda_stream,
+                   const pmpm_sim* donor, pmpm_sim** out) {
+    if (!out || !donor) return PMPM_EINVAL;
+    if (donor->s.nc != cfg->nc) {
+        snprintf(g_init_msg, sizeof(g_init_msg), "donor has nc=%d, config nc=%d", donor->s.nc, cfg->nc);
         return PMPM_EINVAL;
     }
-    if (reinterpret_cast<uintptr_t>(d_workspace) % 256) {
-        snprintf(g_init_msg, sizeof(g_init_msg), "workspace must be 256-byte aligned");
-        return PMPM_EINVAL;
-    }
-    pmpm_sim* h = new (std::nothrow) pmpm_sim();
-    if (!h) return PMPM_ENOMEM;
+    int rc = PMPM_OK;
+    pmpm_sim* h = init_common(cfg, d_workspace, bytes, cuda_stream, &rc);
+    if (!h) return rc;
     Sim& s = h->s;
-    derive(s, cfg);
-    const size_t need = layout(s, nullptr);
-    if (bytes < need) {
-        snprintf(g_init_msg, sizeof(g_init_msg), "workspace %zu bytes < required %zu", bytes, need);
+    const Sim& d = donor->s;
+    const size_t hc = (size_t)(s.nc / 2 + 1);
+    cudaError_t e = cudaMemcpyAsync(s.green_coarse, d.green_coarse, 4 * hc * hc * hc,
+                                    cudaMemcpyDeviceToDevice, s.stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s.green_fine, d.green_fine, 4 * (size_t)kGreenS * kGreenS * kGreenS,
+                            cudaMemcpyDeviceToDevice, s.stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s.green_packed, d.green_packed,
+                            4 * (size_t)(kGreenS - 2) * kGreenS * (kGreenS + 1) / 2,
+                            cudaMemcpyDeviceToDevice, s.stream);
+    if (e != cudaSuccess || rc) {
+        snprintf(g_init_msg, sizeof(g_init_msg), "table copy: %s", cudaGetErrorString(e));
         delete h;
-        return PMPM_ENOMEM;
+        return rc ? rc : PMPM_ECUDA;
     }
-    s.ws = static_cast<uint8_t*>(d_workspace);
-    s.ws_bytes = bytes;
-    s.stream = static_cast<cudaStream_t>(cuda_stream);
-    layout(s, s.ws);
-    cudaGetDevice(&s.device);
-    cudaMemsetAsync(s.err, 0, 4, s.stream);
-    float T[256], E[256];
-    codec_tables(T, E);
-    cudaMemcpyAsync(s.Tdec, T, sizeof(T), cudaMemcpyHostToDevice, s.stream);
-    cudaMemcpyAsync(s.Eedge, E, sizeof(E), cudaMemcpyHostToDevice, s.stream);
-    k_twiddles<<<grid_for(s.fft_max, 256), 256, 0, s.stream>>>(s.fft_max, s.tw_f, s.tw_d);
-    rc = check_launch(s, "twiddles");
-    if (!rc) rc = build_green_tables(s);
-    if (!rc) rc = sync_and_check(s);
-    if (rc) {
-        snprintf(g_init_msg, sizeof(g_init_msg), "%s", s.msg);
-        delete h;
-        return rc;
-    }
-    s.a = cfg->a_init;
-    *out = h;
+    return init_finish(h, out);
+}
+
+int pmpm_graph_mode(pmpm_sim* h, int32_t enable) {
+    if (!h) return PMPM_EINVAL;
+    Sim& s = h->s;
+    const cudaStream_t st = s.stream;
+    if (enable && (st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread))
+        return set_error(s, PMPM_EINVAL, "graph mode needs a created stream, not a default stream");
+    s.graphs = enable != 0;
     return PMPM_OK;
 }
 
@@ -380,7 +511,7 @@ int pmpm_fetch(pmpm_sim* h, int32_t what, void* dst, size_t bytes) {
         case PMPM_FORCE:
             if ((rc = coarse_deposit(s))) return rc;
             if ((rc = coarse_force(s))) return rc;
-            if ((rc = tile_pass(s, 0, 0.f, 0.f, s.Pn))) return rc;
+            if ((rc = tile_pass(s, 0, s.Pn))) return rc;
             rc = copy_out(s, dst, s.Pn, need);
             break;
         case PMPM_COARSE_DENSITY:
@@ -437,6 +568,7 @@ int pmpm_load(pmpm_sim* h, int32_t what, const void* src, size_t bytes) {
             if (e == cudaSuccess) e = cudaStreamSynchronize(s.stream);
             s.a = sc.a;
             s.step = sc.step;
+            set_device_step(s, sc.step);
             s.loaded |= 8;
             break;
         }
@@ -497,6 +629,8 @@ void pmpm_destroy(pmpm_sim* h) {
     if (!h) return;
     Sim& s = h->s;
     cudaStreamSynchronize(s.stream);
+    for (int c = 0; c < 2; ++c)
+        if (s.graph_ready[c]) cudaGraphExecDestroy(s.graph_exec[c]);
     if (s.ev_made)
         for (int i = 0; i < kEventRing; ++i) cudaEventDestroy(s.ev[i]);
     delete h;

@@ -99,7 +99,6 @@ int fft3d(Sim& s, void* data, int n, int sign) {
     while ((1 << log2n) < n) ++log2n;
     const int P = pencils_per_block<R>(n);
     const size_t smem = 2 * (size_t)P * n * sizeof(C);
-    cudaFuncSetAttribute(k_fft_pass<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536);
     const C* tw = sizeof(R) == 4 ? reinterpret_cast<const C*>(s.tw_f)
                                  : reinterpret_cast<const C*>(s.tw_d);
     const int64_t groups = (int64_t)n * n / P;
@@ -113,6 +112,11 @@ int fft3d(Sim& s, void* data, int n, int sign) {
 }
 
 template int fft3d<float>(Sim&, void*, int, int);
+
+void fft_setup() {
+    cudaFuncSetAttribute(k_fft_pass<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536);
+    cudaFuncSetAttribute(k_fft_pass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536);
+}
 
 // The same three float passes for a caller-supplied twiddle table of tw_n
 // entries (n divides tw_n); used where no Sim exists.

@@ -167,12 +167,13 @@ __global__ void k_fine_table(const double* Ks, float* table) {
     table[i] = (float)(acc * 0x1p-36);
 }
 
-// b <= c half of the 17^3 table, row-major over (a, b, c = b..16)
+// b <= c half of the 17^3 table for own-axis rows a = 1..15 (rows 0 and 16
+// vanish), row-major over (a - 1, b, c = b..16)
 __global__ void k_pack_fine(const float* table, float* packed) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int tri = kGreenS * (kGreenS + 1) / 2;
-    if (i >= kGreenS * tri) return;
-    const int a = i / tri;
+    if (i >= (kGreenS - 2) * tri) return;
+    const int a = 1 + i / tri;
     int r = i % tri, b = 0;
     while (r >= kGreenS - b) { r -= kGreenS - b; ++b; }
     packed[i] = table[(a * kGreenS + b) * kGreenS + (b + r)];
@@ -232,7 +233,7 @@ int build_green_tables(Sim& s) {
     k_coarse_small<<<2, 256, 0, st>>>(L, Tsmall);
     k_fine_values<<<6, 256, 0, st>>>(L, Tsmall, Ks);
     k_fine_table<<<(kGreenS * kGreenS * kGreenS + 255) / 256, 256, 0, st>>>(Ks, s.green_fine);
-    k_pack_fine<<<(kGreenS * kGreenS * (kGreenS + 1) / 2 + 255) / 256, 256, 0, st>>>(s.green_fine,
+    k_pack_fine<<<((kGreenS - 2) * kGreenS * (kGreenS + 1) / 2 + 255) / 256, 256, 0, st>>>(s.green_fine,
                                                                                    s.green_packed);
     const Ewald e = make_ewald(L, nc / 2 - 1);
     k_coarse_real<<<grid_for(s.ncells, 256), 256, 0, st>>>(nc, e, mesh);

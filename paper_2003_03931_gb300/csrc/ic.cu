@@ -137,6 +137,7 @@ int ic_zeldovich(Sim& s, uint64_t seed, double slope, double kc, double rms) {
     if ((rc = check_launch(s, "ic"))) return rc;
     s.a = s.cfg.a_init;
     s.step = 0;
+    set_device_step(s, 0);
     return encode_from_qp(s, false);
 }
 

@@ -56,6 +56,8 @@ struct Sim {
     long long* blocksums = nullptr;
     int64_t nblocks_scan = 0;
     double* ic_partial = nullptr;               // [3*1024 + 1] IC rms partial sums
+    float* d_factors = nullptr;                 // [2 n_steps] kick, drift (codes) per step
+    int* d_step = nullptr;                      // device copy of the step counter
     double* pk_bins = nullptr;                  // [3][pk_max/2 + 1] power-spectrum sums
 
     // transient scratch (step, init, ICs and power spectrum share it)
@@ -63,6 +65,12 @@ struct Sim {
     size_t scratch_bytes = 0;
     int32_t* Qn = nullptr;                      // [3][N] (aliases scratch)
     float* Pn = nullptr;                        // [3][N] (aliases scratch)
+
+    // captured steps, one per buffer parity
+    bool graphs = false;
+    bool graph_ready[2] = {false, false};
+    cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
+    int64_t graph_launches[2] = {0, 0};
 
     // stage timing
     bool in_step = false;
@@ -100,13 +108,16 @@ int fft3d(Sim& s, void* data, int n, int sign);
 int fft_pass_count(int n);
 int coarse_force(Sim& s);             // deposit + FFT + Green -> s.Fl
 int coarse_deposit(Sim& s);           // -> s.rho_c
-int tile_pass(Sim& s, int mode, float kick, float drift, float* G);
+int tile_pass(Sim& s, int mode, float* G);
+void tile_setup();
+void fft_setup();
 int scan_counts(Sim& s, const int32_t* counts, int64_t* offsets);
 int encode_from_qp(Sim& s, bool counts_ready);
 int decode_state(Sim& s);              // -> s.Qn, s.Pn
 int ic_zeldovich(Sim& s, uint64_t seed, double slope, double kc, double rms);
 int power_spectrum(Sim& s, int nmesh, int nbins, double* k, double* pk, int64_t* nm);
 void prof_mark(Sim& s, int stage);     // records an event closing `stage` (-1: opening)
+void set_device_step(Sim& s, int64_t step);
 
 inline uint8_t* cur_stream(Sim& s, int which) { return s.streams[s.cur] + (size_t)which * s.n; }
 

@@ -25,7 +25,8 @@ __device__ unsigned long long g_phase[4096 * kMarks];
 
 template <int D>
 __device__ __forceinline__ void tile_component(int tid, const TileGeom& g, const TileParams& P,
-                                               const float* gS, const float2* C, float2* W) {
+                                               const float* gS, const float2* C, float2* W,
+                                               TileCells cells) {
     __syncthreads();
     PMPM_MARK(7 + 4 * D);
     tile_inv_z<D>(tid, g, gS, C, W);
@@ -37,7 +38,7 @@ __device__ __forceinline__ void tile_component(int tid, const TileGeom& g, const
     tile_inv_x(tid, g, W);
     __syncthreads();
     PMPM_MARK(10 + 4 * D);
-    tile_interp<D>(tid, g, P, W);
+    tile_interp<D>(tid, g, P, W, cells);
 }
 
 __global__ void __launch_bounds__(kTileThreads, 1) k_tile(TileParams P) {
@@ -46,13 +47,16 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(TileParams P) {
     float2* C = reinterpret_cast<float2*>(tile_smem);
     float2* W = reinterpret_cast<float2*>(tile_smem + (size_t)kTileR * 4);
     float* gS = reinterpret_cast<float*>(tile_smem + (size_t)kTileR * 4 + (size_t)kTileW * 8);
+    int* O = reinterpret_cast<int*>(gS + kGreenPacked);
     const int tid = threadIdx.x;
     const TileGeom g = tile_geom(blockIdx.x, P.nc, P.nt);
 
-    const TileCells cells = tile_cells(W);   // W is free until phase 5
+    const TileCells cells = tile_cells(W, O);   // W is free until phase 5
     PMPM_MARK(0);
     tile_load_green(tid, P.green, gS);
     tile_zero(tid, R);
+    if (tid == 0) cells.misc[2] = 0;
+    __syncthreads();
     tile_cells_load(tid, g, P, cells);
     __syncthreads();
     PMPM_MARK(1);
@@ -71,14 +75,18 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(TileParams P) {
     __syncthreads();
     PMPM_MARK(5);
     tile_fwd_z(tid, C);
-    tile_component<0>(tid, g, P, gS, C, W);
-    tile_component<1>(tid, g, P, gS, C, W);
-    tile_component<2>(tid, g, P, gS, C, W);
+    tile_component<0>(tid, g, P, gS, C, W, cells);
+    tile_component<1>(tid, g, P, gS, C, W, cells);
+    tile_component<2>(tid, g, P, gS, C, W, cells);
     __syncthreads();
     PMPM_MARK(19);
 }
 
-int tile_pass(Sim& s, int mode, float kick, float drift, float* G) {
+void tile_setup() {
+    cudaFuncSetAttribute(k_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemBytes);
+}
+
+int tile_pass(Sim& s, int mode, float* G) {
     TileParams P;
     P.nc = s.nc;
     P.nt = s.nt;
@@ -97,13 +105,12 @@ int tile_pass(Sim& s, int mode, float kick, float drift, float* G) {
     P.green = s.green_packed;
     P.Fl = s.Fl;
     P.mode = mode;
-    P.kick = kick;
-    P.drift = drift;
+    P.factors = s.d_factors;
+    P.step = s.d_step;
     P.G = G;
     P.Qn = s.Qn;
     P.Pn = s.Pn;
     P.err = s.err;
-    cudaFuncSetAttribute(k_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemBytes);
     const int ntiles = s.nt * s.nt * s.nt;
     k_tile<<<ntiles, kTileThreads, kTileSmemBytes, s.stream>>>(P);
     s.launches++;

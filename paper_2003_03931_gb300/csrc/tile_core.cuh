@@ -16,8 +16,11 @@
 //   W  22 x 32 x 16 complex = 88 KB: one force component on its way back,
 //      pruned to the 22 output planes that are needed (during the deposit it
 //      holds the table of the halo box's cells);
-//   G  the short-range Green table, 17 x 153 floats (10.2 KB): S(a, b, c)
-//      is symmetric in (b, c), so only b <= c is kept.
+//   G  the short-range Green table, 15 x 153 floats (9 KB): S(a, b, c) is
+//      symmetric in (b, c), so only b <= c is kept, and it vanishes for own-
+//      axis |k| = 0 and 16, so those rows are not stored;
+//   O  the tile's own-cell table (prefix counts and storage offsets), built
+//      during the deposit and used by every interpolation phase (1 KB).
 // Index swizzles (x ^ y) make every pencil pass free of bank conflicts.
 //
 // Each phase is a per-thread function; the kernel calls them with a block
@@ -33,9 +36,11 @@ constexpr int kTileThreads = 512;
 constexpr int kTileR = kTileFFT * kTileFFT * kTileFFT;          // 32768 words
 constexpr int kTileW = kTileOut * kTileFFT * (kTileFFT / 2);    // 11264 complex
 constexpr int kGreenTri = kGreenS * (kGreenS + 1) / 2;          // 153 pairs b <= c
-constexpr int kGreenPacked = kGreenS * kGreenTri;               // 2601 floats
-constexpr size_t kTileSmemBytes =
-    (size_t)kTileR * 4 + (size_t)kTileW * 8 + (size_t)kGreenPacked * 4;
+constexpr int kGreenRows = kGreenS - 2;                         // own-axis |k| = 1..15
+constexpr int kGreenPacked = kGreenRows * kGreenTri;            // 2295 floats
+constexpr int kOwnTail = 126 + 125 + 4;                         // own-cell table, ints
+constexpr size_t kTileSmemBytes = (size_t)kTileR * 4 + (size_t)kTileW * 8 +
+                                  (size_t)kGreenPacked * 4 + (size_t)kOwnTail * 4;
 
 struct TileParams {
     int nc;                       // coarse cells per side
@@ -55,8 +60,9 @@ struct TileParams {
     const float* green;           // packed short-range Green table, 17 x 153 (scaled)
     const float* Fl;              // [3][nc^3] long-range force on the coarse mesh
     int mode;                     // 0: write g; 1: kick + drift
-    float kick;                   // fl32 kick factor (multiplies g)
-    float drift;                  // fl32 drift factor in position codes (multiplies p)
+    const float* factors;         // [2 n_steps]: fl32 kick factor (multiplies g) and drift
+                                  // factor in position codes (multiplies p), per step
+    const int* step;              // device step counter (index into factors)
     float* G;                     // [3][N] (mode 0)
     int32_t* Qn;                  // [3][N] new codes (mode 1)
     float* Pn;                    // [3][N] new momenta (mode 1)
@@ -219,7 +225,22 @@ PMPM_HD int64_t row_locate(const RowTable& t, int v, int& i) {
 #endif
 }
 
-// CIC of one particle (unwrapped coarse cell cu, bins m) into the tile box
+// shared-memory add without a returned value
+PMPM_HD void smem_red_u32(uint32_t* p, uint32_t v) {
+#ifdef __CUDA_ARCH__
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "r"(v)
+                 : "memory");
+#else
+    *p += v;
+#endif
+}
+
+// CIC of one particle (unwrapped coarse cell cu, bins m) into the tile box.
+// A node gathers from the particles of at most 8 coarse cells, each weighing
+// at most 2^21; with at most 255 particles per cell no node can pass 2^32, so
+// CHECK (overflow detection on the returned old value) is needed only when
+// some halo cell holds more.
+template <bool CHECK>
 PMPM_HD void deposit_one(const TileGeom& g, const int (&cu)[3], const int (&m)[3], uint32_t* R,
                          uint32_t* err) {
     int li[3], w1[3];
@@ -240,8 +261,12 @@ PMPM_HD void deposit_one(const TileGeom& g, const int (&cu)[3], const int (&m)[3
         if (!inside && ((unsigned)x >= 32u || (unsigned)y >= 32u || (unsigned)z >= 32u)) continue;
         const uint32_t w = (uint32_t)(dx ? w1[0] : 128 - w1[0]) * wyz[dy + 2 * dz];
         if (w == 0u) continue;
-        const uint32_t old = smem_add_u32(&R[ridx(x, y, z)], w);
-        if (old + w < old) flag_error(err, kErrFineOverflow);
+        if (CHECK) {
+            const uint32_t old = smem_add_u32(&R[ridx(x, y, z)], w);
+            if (old + w < old) flag_error(err, kErrFineOverflow);
+        } else {
+            smem_red_u32(&R[ridx(x, y, z)], w);
+        }
     }
 }
 
@@ -293,26 +318,33 @@ constexpr int kMapCap = 32768;    // particles whose cell is looked up by table
 constexpr int kPMapCap = 8192;
 
 struct TileCells {
-    int64_t* st;       // [kHaloMax] storage offset of each halo-box cell
-    int* cnt;          // [kHaloMax] particles in it
-    int* pre;          // [kHaloMax + 1] exclusive prefix over the box cells
-    int* ppre;         // [kOwnMax + 1] exclusive prefix over the tile's own cells
-    uint16_t* map;     // [kMapCap] halo cell of the v-th box particle
-    uint8_t* pmap;     // [kPMapCap] own cell of the v-th own particle
+    int64_t* st;       // [kHaloMax] storage offset of each halo-box cell (W)
+    int* cnt;          // [kHaloMax] particles in it (W)
+    int* pre;          // [kHaloMax + 1] exclusive prefix over the box cells (W)
+    uint16_t* map;     // [kMapCap] halo cell of the v-th box particle (W)
+    uint8_t* pmap;     // [kPMapCap] own cell of the v-th own particle (W)
+    int* ppre;         // [kOwnMax + 1] exclusive prefix over the tile's own cells (O)
+    int* prel;         // [kOwnMax] storage offset of own cell p minus own_base (O)
+    int* misc;         // [0..1] own_base (int64), [2] largest halo-cell count (O)
 };
 
-PMPM_HD TileCells tile_cells(float2* W) {
+PMPM_HD TileCells tile_cells(float2* W, int* O) {
     TileCells c;
     c.st = reinterpret_cast<int64_t*>(W);
     c.cnt = reinterpret_cast<int*>(c.st + kHaloMax);
     c.pre = c.cnt + kHaloMax;
-    c.ppre = c.pre + kHaloMax + 1;
-    c.map = reinterpret_cast<uint16_t*>(c.ppre + kOwnMax + 3);
+    c.map = reinterpret_cast<uint16_t*>(c.pre + kHaloMax + 1 + 1);
     c.pmap = reinterpret_cast<uint8_t*>(c.map + kMapCap);
+    c.ppre = O;
+    c.prel = O + 126;
+    c.misc = O + 126 + 125;
     return c;
 }
-static_assert(kHaloMax * 8 + (2 * kHaloMax + kOwnMax + 4) * 4 + kMapCap * 2 + kPMapCap <= kTileW * 8,
+static_assert(kHaloMax * 8 + (2 * kHaloMax + 2) * 4 + kMapCap * 2 + kPMapCap <= kTileW * 8,
               "tile cell tables must fit in W");
+PMPM_HD int64_t own_base(const TileCells& c) {
+    return (int64_t)(((uint64_t)(uint32_t)c.misc[1] << 32) | (uint32_t)c.misc[0]);
+}
 
 // own cell p lies inside the tile (tiles of 4 coarse cells leave the fifth
 // row, column and plane of the 5^3 layout empty)
@@ -340,6 +372,11 @@ PMPM_HD void tile_cells_load(int tid, const TileGeom& g, const TileParams& P, Ti
         }
         c.st[b] = st;
         c.cnt[b] = cnt;
+#ifdef __CUDA_ARCH__
+        if (cnt) atomicMax(&c.misc[2], cnt);
+#else
+        if (cnt > c.misc[2]) c.misc[2] = cnt;
+#endif
     }
 }
 
@@ -381,6 +418,16 @@ PMPM_HD void tile_cells_scan(int tid, const TileGeom& g, TileCells c) {
         const TileGeom gg = g;
         warp_prefix(lane, kOwnMax,
                     [cnt, gg](int p) { return own_valid(gg, p) ? cnt[own_to_halo(p)] : 0; }, c.ppre);
+    } else if (warp == 2) {
+        // storage offsets of the own cells relative to own cell 0 (increasing
+        // in flat cell order, spanning less than 2^31 particles)
+        const int64_t base = c.st[own_to_halo(0)];
+        for (int p = lane; p < kOwnMax; p += 32)
+            c.prel[p] = own_valid(g, p) ? (int)(c.st[own_to_halo(p)] - base) : 0;
+        if (lane == 0) {
+            c.misc[0] = (int)(uint32_t)((uint64_t)base & 0xffffffffu);
+            c.misc[1] = (int)(uint32_t)((uint64_t)base >> 32);
+        }
     }
 }
 
@@ -416,6 +463,7 @@ PMPM_HD int own_of(const TileCells& c, int v) {
 PMPM_HD void tile_deposit_flat(int tid, const TileGeom& g, const TileParams& P, uint32_t* R,
                                TileCells c) {
     const int total = c.pre[kHaloMax];
+    const bool check = c.misc[2] > 255;
     for (int v0 = tid; v0 < total; v0 += 2 * kTileThreads) {
         int b[2], m[2][3];
         bool ok[2];
@@ -436,7 +484,8 @@ PMPM_HD void tile_deposit_flat(int tid, const TileGeom& g, const TileParams& P, 
             if (!ok[u]) continue;
             const int cu[3] = {g.c0[0] - 2 + b[u] % kHaloDim, g.c0[1] - 2 + (b[u] / kHaloDim) % kHaloDim,
                                g.c0[2] - 2 + b[u] / (kHaloDim * kHaloDim)};
-            deposit_one(g, cu, m[u], R, P.err);
+            if (check) deposit_one<true>(g, cu, m[u], R, P.err);
+            else deposit_one<false>(g, cu, m[u], R, P.err);
         }
     }
     // long-range force of the tile's own particles
@@ -444,8 +493,7 @@ PMPM_HD void tile_deposit_flat(int tid, const TileGeom& g, const TileParams& P, 
     const int ptotal = c.ppre[kOwnMax];
     for (int v = tid; v < ptotal; v += kTileThreads) {
         const int p = own_of(c, v);
-        const int bh = own_to_halo(p);
-        const int64_t j = c.st[bh] + (v - c.ppre[p]);
+        const int64_t j = own_base(c) + c.prel[p] + (v - c.ppre[p]);
         const int64_t Q[3] = {(int64_t)(g.c0[0] + p % kOwnDim) * kBins + P.m0[j],
                               (int64_t)(g.c0[1] + (p / kOwnDim) % kOwnDim) * kBins + P.m1[j],
                               (int64_t)(g.c0[2] + p / (kOwnDim * kOwnDim)) * kBins + P.m2[j]};
@@ -503,7 +551,8 @@ PMPM_HD int green_tri(int b, int c) {
     return b <= c ? green_off(b) + c : green_off(c) + b;
 }
 
-// Copy the packed Green table (17 x 153 floats, b <= c only) into shared memory.
+// Copy the packed Green table (15 x 153 floats: own-axis |k| = 1..15, b <= c)
+// into shared memory.
 PMPM_HD void tile_load_green(int tid, const float* Gp, float* gS) {
     for (int i = tid; i < kGreenPacked; i += kTileThreads) gS[i] = Gp[i];
 }
@@ -513,10 +562,13 @@ PMPM_HD void tile_load_green(int tid, const float* Gp, float* gS) {
 // Z = A + iB holds the kx = 0 (A) and kx = 16 (B) planes; with the partner
 // Z' = Z(-ky, -kz): A = (Z + conj Z')/2, B = (Z - conj Z')/(2i), and the packed
 // product A K~_d(0) + i B K~_d(16) = -i[(s0+s16)/2 Z + (s0-s16)/2 conj Z'].
+// Thread mapping of the z passes: warp w owns kx = w and lane l owns ky = l,
+// so warp 0 alone carries the packed kx = 0 / 16 pencils and the other warps
+// run without divergence; every half-warp touches 16 distinct bank pairs.
 template <int D>
 PMPM_HD void tile_inv_z(int tid, const TileGeom& g, const float* gS, const float2* C,
                         float2* W) {
-    const int kx = tid & 15, ky = tid >> 4;
+    const int kx = tid >> 5, ky = tid & 31;
     const int nz = g.T[2] + 2;
     const int ay = kabs32(ky);
     float2 a[32];
@@ -527,12 +579,12 @@ PMPM_HD void tile_inv_z(int tid, const TileGeom& g, const float* gS, const float
             if (zo < nz) W[widx(0, ky, zo)] = make_float2(0.f, 0.f);
         return;
     }
-    // per-thread parts of the table index: the third index (|kz|) is a
-    // compile-time constant in the unrolled loop below
-    const float sgy = ksgn32(ky);
+    // per-thread parts of the table index (own-axis row a is stored at a - 1);
+    // the third index |kz| is a compile-time constant in the unrolled loop
+    const float sgy = (D == 1 && (ay == 0 || ay == 16)) ? 0.f : ksgn32(ky);
     const int offA = green_off(D == 0 ? ay : kx);          // pair (b, c) with b fixed
     const int bfix = D == 0 ? ay : kx;
-    const int rowA = D == 0 ? kx * kGreenTri : ay * kGreenTri;
+    const int rowA = D == 0 ? (kx - 1) * kGreenTri : (ay >= 1 && ay <= 15 ? ay - 1 : 0) * kGreenTri;
     const int t0 = green_tri(0, ay), t16 = green_tri(16, ay), txy = green_tri(kx, ay);
 #pragma unroll
     for (int kz = 0; kz < 32; ++kz) {
@@ -541,13 +593,14 @@ PMPM_HD void tile_inv_z(int tid, const TileGeom& g, const float* gS, const float
         float cA, cB;
         float2 Zp = make_float2(0.f, 0.f);
         if (D == 2) {
-            const float sz = ksgn32(kz);
+            const float sz = (az == 0 || az == 16) ? 0.f : ksgn32(kz);
+            const int rz = (az >= 1 && az <= 15 ? az - 1 : 0) * kGreenTri;
             if (kx != 0) {
-                cA = sz * gS[az * kGreenTri + txy];
+                cA = sz * gS[rz + txy];
                 cB = 0.f;
             } else {
-                const float s0 = sz * gS[az * kGreenTri + t0];
-                const float s16 = sz * gS[az * kGreenTri + t16];
+                const float s0 = sz * gS[rz + t0];
+                const float s16 = sz * gS[rz + t16];
                 cA = 0.5f * (s0 + s16);
                 cB = 0.5f * (s0 - s16);
                 Zp = C[cidx(0, (32 - ky) & 31, (32 - kz) & 31)];
@@ -612,71 +665,68 @@ PMPM_HD void tile_inv_x(int tid, const TileGeom& g, float2* W) {
 // --- phase 5d: interpolate component D to the tile's own particles, add the
 // parked long-range part, then (mode 1) kick and drift that component.
 template <int D>
-PMPM_HD void tile_interp(int tid, const TileGeom& g, const TileParams& P, const float2* W) {
+PMPM_HD void tile_interp(int tid, const TileGeom& g, const TileParams& P, const float2* W,
+                         TileCells c) {
     const float* Wf = reinterpret_cast<const float*>(W);
-    const int warp = tid >> 5, lane = tid & 31;
-    const int nx = g.c1[0] - g.c0[0], ny = g.c1[1] - g.c0[1], nz = g.c1[2] - g.c0[2];
     const int64_t ncells = (int64_t)P.nc * P.nc * P.nc;
     const int64_t n = P.n;
     const float sigma = *P.sigma;
     const uint8_t* ud = D == 0 ? P.u0 : (D == 1 ? P.u1 : P.u2);
     float* slot = P.mode == 0 ? P.G : P.Pn;
-    for (int r = warp; r < ny * nz; r += kTileThreads / 32) {
-        const int y = g.c0[1] + r % ny, z = g.c0[2] + r / ny;
-        const int base = P.nc * (y + P.nc * z);
-        RowTable t;
-        row_build(t, P, base, g.c0[0], nx, lane);
-        for (int v0 = 0; v0 < t.total; v0 += 32) {
-            int i;
-            const int v = v0 + lane;
-            const int64_t jr = row_locate(t, v, i);
-            const bool valid = v < t.total;
-            const int64_t j = valid ? jr : 0;
-            const int cell = base + g.c0[0] + i;
-            const int64_t Q[3] = {(int64_t)(g.c0[0] + i) * kBins + P.m0[j],
-                                  (int64_t)y * kBins + P.m1[j], (int64_t)z * kBins + P.m2[j]};
-            const float gcd = slot[D * n + j];
-            const uint8_t u = ud[j];
-            const float vcd = P.vc[D * ncells + cell];
-            // fine gather
-            int lo[3], w1[3];
+    const int ptotal = c.ppre[kOwnMax];
+    const int64_t base = own_base(c);
+    float kick = 0.f, drift = 0.f;
+    if (P.mode == 1) {
+        const int st = *P.step;
+        kick = P.factors[2 * st];
+        drift = P.factors[2 * st + 1];
+    }
+    for (int v = tid; v < ptotal; v += kTileThreads) {
+        const int p = prefix_find(c.ppre, kOwnMax, v);
+        const int64_t j = base + c.prel[p] + (v - c.ppre[p]);
+        const int cx = g.c0[0] + p % kOwnDim, cy = g.c0[1] + (p / kOwnDim) % kOwnDim,
+                  cz = g.c0[2] + p / (kOwnDim * kOwnDim);
+        const int64_t cell = cx + (int64_t)P.nc * (cy + (int64_t)P.nc * cz);
+        const int64_t Q[3] = {(int64_t)cx * kBins + P.m0[j], (int64_t)cy * kBins + P.m1[j],
+                              (int64_t)cz * kBins + P.m2[j]};
+        const float gcd = slot[D * n + j];
+        const uint8_t u = ud[j];
+        const float vcd = P.vc[D * ncells + cell];
+        // fine gather
+        int lo[3], w1[3];
 #pragma unroll
-            for (int e = 0; e < 3; ++e) {
-                const int s = (int)(2 * Q[e] + 1 - kCodesPerFine - 128 * (int64_t)g.o[e]);
-                lo[e] = (s >> 7) - (kBuffer - 1);
-                w1[e] = s & 127;
-            }
-            float gf = 0.f;
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                const int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
-                const float w = (float)((dx ? w1[0] : 128 - w1[0]) * (dy ? w1[1] : 128 - w1[1]) *
-                                        (dz ? w1[2] : 128 - w1[2]));
-                gf += w * Wf[wfidx(lo[0] + dx, lo[1] + dy, lo[2] + dz)];
-            }
-            const float gval = gf * 4.76837158203125e-07f + gcd;   // 2^-21
-            if (P.mode == 0) {
-                if (valid) slot[D * n + j] = gval;
-                continue;
-            }
-            // kick (Eq. 3 decode, then p += kick * g) and integer drift
-            const float p = decode_momentum(vcd, sigma, P.Tdec[u]);
-            const float pn = fadd_rn(p, fmul_rn(P.kick, gval));
-            const float xq = fmul_rn(pn, P.drift);
-            if (valid) {
-                if (!(pn == pn) || !(gval == gval)) flag_error(P.err, kErrNaN);
-                if (fabsf(pn) >= 1048576.f) flag_error(P.err, kErrMomentum);
-                if (!(fabsf(xq) < 1.0e9f)) flag_error(P.err, kErrDrift);
-            }
-            const int64_t dq = valid && fabsf(xq) < 1.0e9f ? (int64_t)floorf(fadd_rn(xq, 0.5f)) : 0;
-            const int64_t M = (int64_t)P.nc * kBins;
-            int64_t qn = (Q[D] + dq) % M;
-            if (qn < 0) qn += M;
-            if (valid) {
-                P.Qn[D * n + j] = (int32_t)qn;
-                P.Pn[D * n + j] = pn;
-            }
+        for (int e = 0; e < 3; ++e) {
+            const int s = (int)(2 * Q[e] + 1 - kCodesPerFine - 128 * (int64_t)g.o[e]);
+            lo[e] = (s >> 7) - (kBuffer - 1);
+            w1[e] = s & 127;
         }
+        float gf = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
+            const float w = (float)((dx ? w1[0] : 128 - w1[0]) * (dy ? w1[1] : 128 - w1[1]) *
+                                    (dz ? w1[2] : 128 - w1[2]));
+            gf += w * Wf[wfidx(lo[0] + dx, lo[1] + dy, lo[2] + dz)];
+        }
+        const float gval = gf * 4.76837158203125e-07f + gcd;   // 2^-21
+        if (P.mode == 0) {
+            slot[D * n + j] = gval;
+            continue;
+        }
+        // kick (Eq. 3 decode, then p += kick * g) and integer drift
+        const float pv = decode_momentum(vcd, sigma, P.Tdec[u]);
+        const float pn = fadd_rn(pv, fmul_rn(kick, gval));
+        const float xq = fmul_rn(pn, drift);
+        if (!(pn == pn) || !(gval == gval)) flag_error(P.err, kErrNaN);
+        if (fabsf(pn) >= 1048576.f) flag_error(P.err, kErrMomentum);
+        int64_t dq = 0;
+        if (fabsf(xq) < 1.0e9f) dq = (int64_t)floorf(fadd_rn(xq, 0.5f));
+        else flag_error(P.err, kErrDrift);
+        const int64_t M = (int64_t)P.nc * kBins;
+        int64_t qn = (Q[D] + dq) % M;
+        if (qn < 0) qn += M;
+        P.Qn[D * n + j] = (int32_t)qn;
+        P.Pn[D * n + j] = pn;
     }
 }
 

@@ -61,7 +61,7 @@ def codec_tables():
 class Simulation:
     """One simulation on one GPU.  The workspace is a torch uint8 tensor."""
 
-    def __init__(self, cfg, device="cuda", stream=None, workspace=None):
+    def __init__(self, cfg, device="cuda", stream=None, workspace=None, donor=None):
         import torch
         self.cfg = cfg
         self.lib = _lib.load()
@@ -76,9 +76,14 @@ class Simulation:
         handle = ctypes.c_void_p()
         c = cfg.to_c()
         with torch.cuda.device(self.device):
-            rc = self.lib.pmpm_init(ctypes.byref(c), ctypes.c_void_p(workspace.data_ptr()),
-                                    nbytes, ctypes.c_void_p(self.stream.cuda_stream),
-                                    ctypes.byref(handle))
+            if donor is None:
+                rc = self.lib.pmpm_init(ctypes.byref(c), ctypes.c_void_p(workspace.data_ptr()),
+                                        nbytes, ctypes.c_void_p(self.stream.cuda_stream),
+                                        ctypes.byref(handle))
+            else:
+                rc = self.lib.pmpm_init_like(ctypes.byref(c), ctypes.c_void_p(workspace.data_ptr()),
+                                             nbytes, ctypes.c_void_p(self.stream.cuda_stream),
+                                             donor.h, ctypes.byref(handle))
         _lib.check(rc, None)
         self.h = handle
 
@@ -100,6 +105,9 @@ class Simulation:
     # -- physics
     def ic_zeldovich(self, seed, slope=-1.5, k_c=np.pi / 2, rms_disp=0.3):
         self._check(self.lib.pmpm_ic_zeldovich(self.h, seed, slope, k_c, rms_disp))
+
+    def graph_mode(self, enable=True):
+        self._check(self.lib.pmpm_graph_mode(self.h, int(enable)))
 
     def step(self, nsteps=1):
         self._check(self.lib.pmpm_step(self.h, nsteps))

@@ -119,3 +119,36 @@ def test_runs_are_bitwise_deterministic_and_resume():
     for a, b in zip(outs[0], _state_bytes(sim)):
         np.testing.assert_array_equal(a, b)
     sim.close()
+
+
+def test_graph_mode_and_shared_tables_are_bitwise_identical():
+    # a sim that copies its force tables from a donor and replays captured
+    # steps must evolve exactly like an eager sim that built its own tables
+    need_gpu()
+    from paper_2003_03931_gb300.sim import SimConfig, Simulation
+    w = synth.WORKLOADS["ragged_32"]
+    eager = make_sim(**w)
+    eager.ic_zeldovich(9, **synth.IC_SPECTRUM)
+    eager.step(5)
+    ref = _state_bytes(eager)
+    import torch
+    with pytest.raises(Exception, match="created stream"):
+        eager.graph_mode(True)     # eager runs on the default stream
+    graph = Simulation(SimConfig(**w), device="cuda:0", stream=torch.cuda.Stream("cuda:0"),
+                       donor=eager)
+    graph.graph_mode(True)
+    graph.ic_zeldovich(9, **synth.IC_SPECTRUM)
+    graph.step(2)
+    graph.step(3)
+    for a, b in zip(ref, _state_bytes(graph)):
+        np.testing.assert_array_equal(a, b)
+    assert graph.fetch_scalars()["step"] == 5
+    # loading a checkpoint resets the replayed step counter
+    ck = eager.fetch_state()
+    graph.load_state(ck)
+    graph.step(2)
+    eager.step(2)
+    for a, b in zip(_state_bytes(eager), _state_bytes(graph)):
+        np.testing.assert_array_equal(a, b)
+    eager.close()
+    graph.close()
