@@ -4,7 +4,9 @@
 Default workload: 512^3 particles, 256^3 coarse cells, 1024^3 fine cells in
 tiles of 16/20 fine cells + 6-cell buffer, Zel'dovich ICs (power-law
 spectrum, seeded), a = 0.02 -> 1 over warmup + steps steps.  One JSON line
-on rank 0; see the round contract in the design doc for every key.
+on rank 0.  With one GPU the line also carries a serving measurement: a
+mixed stream of whole-box requests through the batched engine against
+sequential plain stepping (--serving, --serving-rates, --serving-only).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -13,11 +15,16 @@ scaling); value is the particle-steps of all ranks over the slowest rank's
 time.  --impl reference times the FP64 oracle on the host cores instead.
 """
 
+import os
+
+# separate hardware queues for the serving engine's per-box streams; must be
+# set before the CUDA context exists
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 import argparse
 import hashlib
 import json
 import math
-import os
 import statistics
 import subprocess
 import sys
@@ -45,6 +52,12 @@ def parse_args(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving", type=int, default=120,
+                    help="requests in the serving measurement (0: skip)")
+    ap.add_argument("--serving-rates", default="1.0",
+                    help="Poisson arrival rates for the latency runs, as fractions of the "
+                         "sequential capacity (comma list; empty: skip)")
+    ap.add_argument("--serving-only", action="store_true")
     return ap.parse_args(argv)
 
 
@@ -304,6 +317,62 @@ def run_ours(args):
                                          "(64^3 coarse, 256^3 fine: the same 8 particles per "
                                          "coarse cell and 8 fine cells per particle), %.1f s" % dt}
     sim.close()
+    if world == 1 and args.serving:
+        out["serving"] = run_serving(args, f"cuda:{local}")
+    return out
+
+
+SERVING_ARENA = 48 << 30
+SEQUENTIAL = dict(max_active=1, share_tables=False, graphs=False, priorities=False,
+                  steps_per_chunk=4, chunks_in_flight=2)
+SEQUENTIAL_SHARED = dict(SEQUENTIAL, share_tables=True)
+BATCHED = dict(max_active=16, share_tables=True, graphs=True, priorities=True, steps_per_chunk=4,
+               chunks_in_flight=2)
+
+
+def run_serving(args, device):
+    """Mixed stream of whole-box requests (32^3..256^3 particles, 10-40 steps,
+    weights 0.4/0.3/0.2/0.1): the batched engine against sequential plain
+    stepping (one box at a time, each building its own force tables), first
+    with every request queued at t=0 (throughput), then on Poisson arrivals
+    at fractions of the sequential capacity (latency)."""
+    from paper_2003_03931_gb300.serve import (Engine, latency_summary, mixed_requests, run_stream,
+                                              with_arrivals)
+
+    def go(kw, reqs):
+        eng = Engine(SERVING_ARENA, device=device, **kw)
+        res = run_stream(eng, reqs, timeout=1800)
+        st = eng.stats()
+        eng.close()
+        s = latency_summary(res)
+        s.update(table_builds=st["table_builds"], gpu_launches=st["launches"],
+                 arena_peak_gb=st["arena_peak"] / 2 ** 30)
+        return s
+
+    reqs = mixed_requests(args.serving, seed=0)
+    go(BATCHED, mixed_requests(8, seed=9, sizes=(32, 64), weights=(1, 1)))    # warm-up
+    seq = go(SEQUENTIAL, reqs)
+    seq_shared = go(SEQUENTIAL_SHARED, reqs)
+    bat = go(BATCHED, reqs)
+    out = {
+        "workload": "%d requests: 32^3/64^3/128^3/256^3 particles (weights .4/.3/.2/.1, nc = np/2), "
+                    "10-40 steps a 0.02->1, slopes U[-2,-1], seeds 1000+i; P(k) on an np^3 mesh "
+                    "at the end" % len(reqs),
+        "unit": UNIT,
+        "sequential": dict(seq, config=SEQUENTIAL),
+        "sequential_shared_tables": dict(seq_shared, config=SEQUENTIAL_SHARED),
+        "batched": dict(bat, config=BATCHED),
+        "throughput_ratio_vs_sequential": bat["particle_steps_per_s"] / seq["particle_steps_per_s"],
+        "throughput_ratio_vs_sequential_shared_tables":
+            bat["particle_steps_per_s"] / seq_shared["particle_steps_per_s"],
+        "latency": [],
+    }
+    cap = seq["requests_per_s"]
+    for f in [float(x) for x in args.serving_rates.split(",") if x.strip()]:
+        arr = with_arrivals(reqs, rate=f * cap, seed=1)
+        out["latency"].append({"rate_fraction_of_sequential_capacity": f,
+                               "rate_requests_per_s": f * cap,
+                               "sequential": go(SEQUENTIAL, arr), "batched": go(BATCHED, arr)})
     return out
 
 
@@ -329,7 +398,10 @@ def run_reference(args):
 
 def main(argv=None):
     args = parse_args(argv)
-    out = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if args.serving_only:
+        out = {"metric": "serving", "serving": run_serving(args, "cuda:0")}
+    else:
+        out = run_reference(args) if args.impl == "reference" else run_ours(args)
     if out is not None:
         print(json.dumps(out))
 

@@ -48,6 +48,7 @@ extern "C" {
 #define PMPM_EOVERFLOW -4   /* a fixed-point or integer range was exceeded */
 #define PMPM_ECOUNT    -5   /* particle count not conserved (internal error) */
 #define PMPM_ESTATE    -6   /* no particle state loaded yet */
+#define PMPM_ETIMEOUT  -7   /* a host-side time limit ran out; the work goes on */
 
 /* what to fetch / load */
 #define PMPM_STREAMS          1  /* uint8 [6][N]: m0 m1 m2 u0 u1 u2 in storage order */
@@ -184,6 +185,117 @@ int pmpm_power_spectrum_noalloc(int32_t nc, int64_t n, const uint8_t* d_m0,
 
 /* Text of the last failure of pmpm_power_spectrum_noalloc. */
 const char* pmpm_noalloc_last_error(void);
+
+/* ------------------------------------------------------------------------
+ * Serving many boxes on one GPU.  The paper runs one box and processes its
+ * fine-mesh tiles as independent units in turn (Sec. II, Sec. IV-A); it has
+ * no serving layer.  These calls hold many independent boxes on the device
+ * at once: each request is a whole simulation (Zel'dovich ICs, n_steps
+ * steps, the final power spectrum, Sec. IV-D), admitted when a slot and
+ * enough of one caller-owned device arena are free, in arrival order, and
+ * stepped with exactly the calls above, so its result is bit for bit the
+ * one it would give alone.
+ * ------------------------------------------------------------------------ */
+
+/* Offset allocator over a device range the caller owns; host bookkeeping
+ * only, no CUDA call.  Sizes round up to 256 bytes, offsets are multiples of
+ * 256; first fit in address order; freed neighbours merge. */
+typedef struct pmpm_arena pmpm_arena;
+int pmpm_arena_create(size_t bytes, pmpm_arena** out);      /* EINVAL if bytes < 256 */
+int pmpm_arena_alloc(pmpm_arena* arena, size_t bytes, size_t* offset);  /* ENOMEM: no range fits */
+int pmpm_arena_free(pmpm_arena* arena, size_t offset);      /* EINVAL: not a live allocation */
+int pmpm_arena_stats(const pmpm_arena* arena, size_t* used, size_t* largest_free,
+                     int64_t* live);
+void pmpm_arena_destroy(pmpm_arena* arena);
+
+typedef struct pmpm_request {
+    int32_t np, nc;          /* as pmpm_config; tile_max 5, buffer 6, 1-byte codes */
+    int32_t n_steps;         /* steps of the equal-log-a schedule a_init -> a_final */
+    int32_t pk_nmesh;        /* final P(k) mesh: power of two in [nc, 4*nc]; 0 = min(np, 4*nc) */
+    int32_t pk_nbins;        /* 1..pk_nmesh/2; 0 = pk_nmesh/2 */
+    int32_t reserved;
+    double  a_init, a_final;
+    uint64_t seed;           /* initial conditions as pmpm_ic_zeldovich */
+    double  slope, k_c, rms_disp;
+    double  arrival;         /* engine clock (s): not admitted before this time */
+    double*  k;              /* host, pk_nbins entries: mean |k| per shell (required) */
+    double*  pk;             /* host, pk_nbins entries: P(k) (required) */
+    int64_t* nmodes;         /* host, pk_nbins entries: modes per shell (required) */
+    uint8_t* streams;        /* host, 6*np^3 bytes: final store, or NULL */
+    int32_t* counts;         /* host, nc^3 entries: final per-cell counts, or NULL */
+} pmpm_request;
+
+typedef struct pmpm_result {
+    int64_t id;              /* as returned by pmpm_batch_submit */
+    int32_t status;          /* PMPM_OK or the error code of the failing call */
+    int32_t reserved;
+    double  t_arrival, t_admit, t_done;   /* engine clock (s) */
+    double  a, sigma;        /* final scale factor and velocity scale (Eq. 3) */
+    int64_t particle_steps;  /* np^3 * n_steps when status is PMPM_OK */
+} pmpm_result;
+
+typedef struct pmpm_batch_config {
+    int32_t max_active;      /* boxes resident at once, 1..1024 (1 = one after another) */
+    int32_t share_tables;    /* 1: force tables built once per nc, kept in the arena */
+    int32_t graphs;          /* 1: steps replayed as CUDA graphs (pmpm_graph_mode) */
+    int32_t priorities;      /* 1: smaller boxes on higher-priority streams */
+    int32_t steps_per_chunk; /* steps enqueued at a time per box (>= 1) */
+    int32_t chunks_in_flight;/* chunks a box may have queued ahead (>= 1) */
+} pmpm_batch_config;
+
+typedef struct pmpm_batch_stats {
+    int64_t submitted, admitted, completed, failed;
+    int64_t table_builds;    /* force-table computations (once per nc when shared) */
+    int64_t launches;        /* library kernels launched for completed boxes */
+    int64_t particle_steps;  /* of completed boxes */
+    int64_t active;          /* boxes resident now */
+    size_t  arena_used, arena_peak;
+} pmpm_batch_stats;
+
+typedef struct pmpm_batch pmpm_batch;
+
+/* d_arena: device memory of arena_bytes, 256-byte aligned, owned by the
+ * caller and borrowed until pmpm_batch_destroy.  Each admitted box takes
+ * pmpm_workspace_bytes() of it; shared force tables stay in it for the
+ * engine's life.  Every box gets its own non-blocking stream; set
+ * CUDA_DEVICE_MAX_CONNECTIONS (up to 32) before the CUDA context exists so
+ * that these streams do not share hardware queues.  The engine allocates
+ * pinned host staging (max_active blocks of 49 KB) and no device memory. */
+int pmpm_batch_create(const pmpm_batch_config* cfg, void* d_arena, size_t arena_bytes,
+                      pmpm_batch** out);
+
+/* Queue a request (copied; its host arrays must stay valid until its result
+ * is polled).  PMPM_EINVAL for an invalid request, PMPM_ENOMEM when its
+ * workspace is larger than the whole arena.  *id receives its id. */
+int pmpm_batch_submit(pmpm_batch* batch, const pmpm_request* request, int64_t* id);
+
+/* One scheduling pass without blocking on the device: retire finished
+ * work, admit arrived requests (FIFO; the head waits for arena space), and
+ * queue more steps.  *n_unfinished: requests queued or active. */
+int pmpm_batch_progress(pmpm_batch* batch, int32_t* n_unfinished);
+
+/* Call pmpm_batch_progress until every submitted request is finished, or
+ * return PMPM_ETIMEOUT after max_seconds (the requests stay queued). */
+int pmpm_batch_run(pmpm_batch* batch, double max_seconds);
+
+/* Move up to max finished results into out; *n receives how many.  A request
+ * that failed has a negative status (its message: pmpm_batch_last_error). */
+int pmpm_batch_poll(pmpm_batch* batch, pmpm_result* out, int32_t max, int32_t* n);
+
+/* Seconds since pmpm_batch_create on the engine's steady clock. */
+double pmpm_batch_clock(const pmpm_batch* batch);
+
+int pmpm_batch_get_stats(const pmpm_batch* batch, pmpm_batch_stats* out);
+
+/* Wait for and release every box still resident; the arena is not freed. */
+void pmpm_batch_destroy(pmpm_batch* batch);
+
+/* Text of the last failure on this engine (or of pmpm_batch_create when NULL). */
+const char* pmpm_batch_last_error(const pmpm_batch* batch);
+
+/* sizeof pmpm_config, pmpm_scalars, pmpm_request, pmpm_result,
+ * pmpm_batch_config, pmpm_batch_stats, for binding checks.  Host only. */
+int pmpm_abi_sizes(int64_t* sizes, int32_t n);
 
 /* Host copies of the float32 velocity tables the library uses: T[256]
  * bin-centre values and E[256] bin edges (E[0] = -inf), Eq. 3.  Host only. */

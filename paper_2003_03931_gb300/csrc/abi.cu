@@ -344,6 +344,61 @@ static int init_finish(pmpm_sim* h, pmpm_sim** out) {
     return PMPM_OK;
 }
 
+
+GreenRefs sim_tables(const Sim& s) {
+    return GreenRefs{s.green_coarse, s.green_fine, s.green_packed};
+}
+
+size_t green_table_bytes(int nc, size_t part[3]) {
+    const size_t hc = (size_t)(nc / 2 + 1);
+    part[0] = 4 * hc * hc * hc;
+    part[1] = 4 * (size_t)kGreenS * kGreenS * kGreenS;
+    part[2] = 4 * (size_t)(kGreenS - 2) * kGreenS * (kGreenS + 1) / 2;
+    return part[0] + part[1] + part[2];
+}
+
+int copy_tables(cudaStream_t st, const GreenRefs& dst, const GreenRefs& src, int nc) {
+    size_t part[3];
+    green_table_bytes(nc, part);
+    cudaError_t e = cudaMemcpyAsync(const_cast<float*>(dst.coarse), src.coarse, part[0],
+                                    cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(const_cast<float*>(dst.fine), src.fine, part[1], cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(const_cast<float*>(dst.packed), src.packed, part[2],
+                            cudaMemcpyDeviceToDevice, st);
+    return e == cudaSuccess ? PMPM_OK : PMPM_ECUDA;
+}
+
+pmpm_sim* sim_create(const pmpm_config* cfg, void* d_workspace, size_t bytes, cudaStream_t st,
+                     const GreenRefs* tables, int* rc_out) {
+    int rc = PMPM_OK;
+    pmpm_sim* h = init_common(cfg, d_workspace, bytes, st, &rc);
+    if (!h) {
+        *rc_out = rc;
+        return nullptr;
+    }
+    if (!rc) {
+        if (tables) {
+            rc = copy_tables(h->s.stream, sim_tables(h->s), *tables, h->s.nc);
+            if (rc) set_error(h->s, rc, "table copy: %s", cudaGetErrorString(cudaGetLastError()));
+        } else {
+            rc = build_green_tables(h->s);
+        }
+    }
+    if (rc) {
+        snprintf(g_init_msg, sizeof(g_init_msg), "%s", h->s.msg);
+        delete h;
+        *rc_out = rc;
+        return nullptr;
+    }
+    pmpm_sim* out = nullptr;
+    *rc_out = init_finish(h, &out);
+    return out;
+}
+
+const char* init_message() { return g_init_msg; }
+
 }  // namespace pmpm
 
 using namespace pmpm;
@@ -370,45 +425,21 @@ int pmpm_init(const pmpm_config* cfg, void* d_workspace, size_t bytes, void* cud
               pmpm_sim** out) {
     if (!out) return PMPM_EINVAL;
     int rc = PMPM_OK;
-    pmpm_sim* h = init_common(cfg, d_workspace, bytes, cuda_stream, &rc);
-    if (!h) return rc;
-    if (!rc) rc = build_green_tables(h->s);
-    if (rc) {
-        snprintf(g_init_msg, sizeof(g_init_msg), "%s", h->s.msg);
-        delete h;
-        return rc;
-    }
-    return init_finish(h, out);
+    *out = sim_create(cfg, d_workspace, bytes, static_cast<cudaStream_t>(cuda_stream), nullptr, &rc);
+    return rc;
 }
 
 int pmpm_init_like(const pmpm_config* cfg, void* d_workspace, size_t bytes, void* cuda_stream,
                    const pmpm_sim* donor, pmpm_sim** out) {
-    if (!out || !donor) return PMPM_EINVAL;
+    if (!out || !donor || !cfg) return PMPM_EINVAL;
     if (donor->s.nc != cfg->nc) {
         snprintf(g_init_msg, sizeof(g_init_msg), "donor has nc=%d, config nc=%d", donor->s.nc, cfg->nc);
         return PMPM_EINVAL;
     }
+    const GreenRefs t = sim_tables(donor->s);
     int rc = PMPM_OK;
-    pmpm_sim* h = init_common(cfg, d_workspace, bytes, cuda_stream, &rc);
-    if (!h) return rc;
-    Sim& s = h->s;
-    const Sim& d = donor->s;
-    const size_t hc = (size_t)(s.nc / 2 + 1);
-    cudaError_t e = cudaMemcpyAsync(s.green_coarse, d.green_coarse, 4 * hc * hc * hc,
-                                    cudaMemcpyDeviceToDevice, s.stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(s.green_fine, d.green_fine, 4 * (size_t)kGreenS * kGreenS * kGreenS,
-                            cudaMemcpyDeviceToDevice, s.stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(s.green_packed, d.green_packed,
-                            4 * (size_t)(kGreenS - 2) * kGreenS * (kGreenS + 1) / 2,
-                            cudaMemcpyDeviceToDevice, s.stream);
-    if (e != cudaSuccess || rc) {
-        snprintf(g_init_msg, sizeof(g_init_msg), "table copy: %s", cudaGetErrorString(e));
-        delete h;
-        return rc ? rc : PMPM_ECUDA;
-    }
-    return init_finish(h, out);
+    *out = sim_create(cfg, d_workspace, bytes, static_cast<cudaStream_t>(cuda_stream), &t, &rc);
+    return rc;
 }
 
 int pmpm_graph_mode(pmpm_sim* h, int32_t enable) {

@@ -116,10 +116,36 @@ int encode_from_qp(Sim& s, bool counts_ready);
 int decode_state(Sim& s);              // -> s.Qn, s.Pn
 int ic_zeldovich(Sim& s, uint64_t seed, double slope, double kc, double rms);
 int power_spectrum(Sim& s, int nmesh, int nbins, double* k, double* pk, int64_t* nm);
+// The same in two halves: enqueue the kernels and an async copy of the raw
+// [3][nbins] sums into host_bins (pinned for a truly async copy), then, once
+// the stream has reached that point, turn the sums into k, P(k), mode counts.
+int power_spectrum_enqueue(Sim& s, int nmesh, int nbins, double* host_bins);
+void power_spectrum_finish(const double* host_bins, int nbins, double* k, double* pk, int64_t* nm);
 void prof_mark(Sim& s, int stage);     // records an event closing `stage` (-1: opening)
 void set_device_step(Sim& s, int64_t step);
 
 inline uint8_t* cur_stream(Sim& s, int which) { return s.streams[s.cur] + (size_t)which * s.n; }
+
+}  // namespace pmpm
+
+namespace pmpm {
+
+// Device pointers of the three force tables (Sec. II): the coarse-kernel
+// spectrum, the fine kernel K_s spectrum and its packed tile copy.
+struct GreenRefs {
+    const float* coarse;
+    const float* fine;
+    const float* packed;
+};
+
+GreenRefs sim_tables(const Sim& s);
+size_t green_table_bytes(int nc, size_t part[3]);     // bytes of the three tables for this nc
+int copy_tables(cudaStream_t st, const GreenRefs& dst, const GreenRefs& src, int nc);
+// Create a sim on `st`; force tables copied from `tables` when non-null, else
+// built.  Returns null with *rc set on failure (message: init_message()).
+struct ::pmpm_sim* sim_create(const pmpm_config* cfg, void* d_workspace, size_t bytes,
+                              cudaStream_t st, const GreenRefs* tables, int* rc);
+const char* init_message();
 
 }  // namespace pmpm
 

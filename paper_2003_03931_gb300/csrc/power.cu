@@ -1,6 +1,8 @@
 // power.cu -- power spectrum of the particle density (Sec. IV-D): CIC density
 // on an nmesh^3 mesh (integer weights, exact), delta = rho/rho_bar - 1, DFT,
 // P(k) = L^3 / nmesh^6 |delta~|^2 averaged in shells j = round(|n|).
+#include <new>
+
 #include "pmpm_impl.cuh"
 
 namespace pmpm {
@@ -81,7 +83,7 @@ __global__ void k_pk_bin(int nmesh, int nbins, double L, const float2* __restric
 
 }  // namespace
 
-int power_spectrum(Sim& s, int nmesh, int nbins, double* k, double* pk, int64_t* nm) {
+int power_spectrum_enqueue(Sim& s, int nmesh, int nbins, double* host_bins) {
     if (nmesh < 2 || (nmesh & (nmesh - 1)) || nmesh > s.pk_max || s.nf % nmesh)
         return set_error(s, PMPM_EINVAL, "nmesh %d must be a power of two dividing %d, <= %d",
                          nmesh, s.nf, s.pk_max);
@@ -107,22 +109,33 @@ int power_spectrum(Sim& s, int nmesh, int nbins, double* k, double* pk, int64_t*
         nmesh, nbins, (double)s.nf, dk, s.pk_bins);
     s.launches += 4;
     if ((rc = check_launch(s, "power spectrum"))) return rc;
-    double* hb = new double[3 * nbins];
-    cudaError_t e = cudaMemcpyAsync(hb, s.pk_bins, sizeof(double) * 3 * nbins,
-                                    cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) {
-        delete[] hb;
+    const cudaError_t e = cudaMemcpyAsync(host_bins, s.pk_bins, sizeof(double) * 3 * nbins,
+                                          cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess)
         return set_error(s, PMPM_ECUDA, "power spectrum copy: %s", cudaGetErrorString(e));
-    }
+    return PMPM_OK;
+}
+
+void power_spectrum_finish(const double* hb, int nbins, double* k, double* pk, int64_t* nm) {
     for (int j = 0; j < nbins; ++j) {
         const double c = hb[2 * nbins + j];
         nm[j] = (int64_t)c;
         k[j] = c > 0 ? hb[nbins + j] / c : 0.0;
         pk[j] = c > 0 ? hb[j] / c : 0.0;
     }
+}
+
+int power_spectrum(Sim& s, int nmesh, int nbins, double* k, double* pk, int64_t* nm) {
+    double* hb = new (std::nothrow) double[3 * (size_t)(nbins > 0 ? nbins : 1)];
+    if (!hb) return set_error(s, PMPM_ENOMEM, "host bins");
+    int rc = power_spectrum_enqueue(s, nmesh, nbins, hb);
+    if (!rc) {
+        const cudaError_t e = cudaStreamSynchronize(s.stream);
+        if (e != cudaSuccess) rc = set_error(s, PMPM_ECUDA, "power spectrum: %s", cudaGetErrorString(e));
+    }
+    if (!rc) power_spectrum_finish(hb, nbins, k, pk, nm);
     delete[] hb;
-    return PMPM_OK;
+    return rc;
 }
 
 }  // namespace pmpm
