@@ -112,6 +112,7 @@ size_t layout(Sim& s, uint8_t* base) {
     s.pk_bins = reinterpret_cast<double*>(take(8 * 3 * (size_t)(s.pk_max / 2 + 1)));
     s.d_factors = reinterpret_cast<float*>(take(8 * (size_t)s.cfg.n_steps));
     s.d_step = reinterpret_cast<int*>(take(4));
+    s.d_kd = reinterpret_cast<float*>(take(8));
     // transient scratch
     const size_t step_b = 24 * (size_t)N + 512;
     const size_t ic_b = 56 * (size_t)N + 1024;
@@ -190,8 +191,19 @@ static double sched_a(const Sim& s, int64_t n) {
     return s.cfg.a_init * pow(s.cfg.a_final / s.cfg.a_init, (double)n / (double)s.cfg.n_steps);
 }
 
-__global__ void k_step_set(int* step, int v) { *step = v; }
-__global__ void k_step_advance(int* step) { *step += 1; }
+// The device step counter and the kick/drift factors of that step, which
+// the tile pass reads (one pair per step, so a captured step replays as is).
+__global__ void k_step_set(int* step, float* kd, const float* factors, int n_steps, int v) {
+    *step = v;
+    kd[0] = v < n_steps ? factors[2 * v] : 0.f;
+    kd[1] = v < n_steps ? factors[2 * v + 1] : 0.f;
+}
+__global__ void k_step_advance(int* step, float* kd, const float* factors, int n_steps) {
+    const int v = *step + 1;
+    *step = v;
+    kd[0] = v < n_steps ? factors[2 * v] : 0.f;
+    kd[1] = v < n_steps ? factors[2 * v + 1] : 0.f;
+}
 
 // float32 kick and drift factors of every step of the schedule (R7), in
 // device memory so that a captured step can replay at any step index
@@ -215,7 +227,7 @@ static void fill_factors(Sim& s) {
 }
 
 void set_device_step(Sim& s, int64_t step) {
-    k_step_set<<<1, 1, 0, s.stream>>>(s.d_step, (int)step);
+    k_step_set<<<1, 1, 0, s.stream>>>(s.d_step, s.d_kd, s.d_factors, s.cfg.n_steps, (int)step);
 }
 
 // Device work of one step; swaps the store buffers (s.cur).
@@ -229,7 +241,7 @@ static int enqueue_step(Sim& s) {
     if ((rc = tile_pass(s, 1, nullptr))) return rc;
     prof_mark(s, 2);
     if ((rc = encode_from_qp(s, false))) return rc;
-    k_step_advance<<<1, 1, 0, s.stream>>>(s.d_step);
+    k_step_advance<<<1, 1, 0, s.stream>>>(s.d_step, s.d_kd, s.d_factors, s.cfg.n_steps);
     s.launches++;
     return check_launch(s, "step");
 }

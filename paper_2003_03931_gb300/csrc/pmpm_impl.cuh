@@ -58,6 +58,7 @@ struct Sim {
     double* ic_partial = nullptr;               // [3*1024 + 1] IC rms partial sums
     float* d_factors = nullptr;                 // [2 n_steps] kick, drift (codes) per step
     int* d_step = nullptr;                      // device copy of the step counter
+    float* d_kd = nullptr;                      // [2] kick and drift factors of that step
     double* pk_bins = nullptr;                  // [3][pk_max/2 + 1] power-spectrum sums
 
     // transient scratch (step, init, ICs and power spectrum share it)

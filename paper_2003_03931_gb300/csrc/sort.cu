@@ -122,19 +122,47 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(int64_t ncells, con
 }
 
 // counts and fixed-point momentum sums from codes and momenta
+__device__ __forceinline__ int64_t key_of(const int32_t* Qn, int64_t n, int nc, int64_t i);
+
+// New-cell counts and fixed-point momentum sums.  Lanes of a warp whose
+// particles land in the same new cell (common: the input is in old cell
+// order) add their values with warp reductions first, so one lane per cell
+// issues the global atomics.  The sums are integers, so the result does not
+// depend on how particles are grouped.
 __global__ void k_hist(int64_t n, int nc, const int32_t* __restrict__ Qn, const float* __restrict__ Pn,
                        int32_t* counts, unsigned long long* S, uint32_t* err) {
     const int64_t ncells = (int64_t)nc * nc * nc;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t key = (int64_t)(Qn[i] >> 8) +
-                            nc * ((int64_t)(Qn[n + i] >> 8) + (int64_t)nc * (Qn[2 * n + i] >> 8));
-        atomicAdd(&counts[key], 1);
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); base < n;
+         base += stride) {
+        const int64_t i = base + lane;
+        const bool live = i < n;
+        const long long key = live ? key_of(Qn, n, nc, i) : -1ll - lane;
+        long long fx[3] = {0, 0, 0};
+        if (live) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const float p = Pn[d * n + i];
+                if (fabsf(p) < 1048576.f) fx[d] = __double2ll_rn((double)p * 16777216.0);
+                else atomicOr(err, p == p ? kErrMomentum : kErrNaN);
+            }
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        // |fx| < 2^44: sum the low 22 bits and the signed high part separately;
+        // 32 lanes keep both sums inside 32 bits
+        long long sum[3];
+#pragma unroll
         for (int d = 0; d < 3; ++d) {
-            const float p = Pn[d * n + i];
-            if (!(fabsf(p) < 1048576.f)) atomicOr(err, p == p ? kErrMomentum : kErrNaN);
-            const long long fx = __double2ll_rn((double)p * 16777216.0);
-            atomicAdd(&S[d * ncells + key], (unsigned long long)fx);
+            const unsigned lo = __reduce_add_sync(peers, (unsigned)(fx[d] & 0x3fffffll));
+            const unsigned hi = __reduce_add_sync(peers, (unsigned)(int)(fx[d] >> 22));
+            sum[d] = (long long)(int)hi * 4194304ll + (long long)lo;
+        }
+        if (live && lane == __ffs(peers) - 1) {
+            atomicAdd(&counts[key], __popc(peers));
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                atomicAdd(&S[d * ncells + key], (unsigned long long)sum[d]);
         }
     }
 }
@@ -159,25 +187,45 @@ __device__ __forceinline__ unsigned long long sq_fix32(float d) {
     return q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull);
 }
 
-// 128-bit sum of round((p - v_c)^2 2^32)
+// 128-bit sum of round((p - v_c)^2 2^32).  Each thread takes kSigmaIlp
+// particles at a time and issues all their loads before using any.
+constexpr int kSigmaIlp = 4;
 __global__ void __launch_bounds__(256) k_sigma(int64_t n, int nc, const int32_t* __restrict__ Qn,
                                                const float* __restrict__ Pn,
                                                const float* __restrict__ vc,
                                                unsigned long long* d2, uint32_t* err) {
     const int64_t ncells = (int64_t)nc * nc * nc;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     unsigned long long lo = 0, hi = 0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t key = key_of(Qn, n, nc, i);
-        for (int d = 0; d < 3; ++d) {
-            const float dev = __fsub_rn(Pn[d * n + i], vc[d * ncells + key]);
-            if (!(fabsf(dev) < 65536.f)) {
-                atomicOr(err, kErrDeviation);
-                continue;
+    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < n;
+         i0 += stride * kSigmaIlp) {
+        int64_t key[kSigmaIlp];
+        float p[kSigmaIlp][3], v[kSigmaIlp][3];
+#pragma unroll
+        for (int u = 0; u < kSigmaIlp; ++u) {
+            const int64_t i = i0 + u * stride;
+            key[u] = i < n ? key_of(Qn, n, nc, i) : -1;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) p[u][d] = i < n ? Pn[d * n + i] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < kSigmaIlp; ++u)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) v[u][d] = key[u] >= 0 ? vc[d * ncells + key[u]] : 0.f;
+#pragma unroll
+        for (int u = 0; u < kSigmaIlp; ++u) {
+            if (key[u] < 0) continue;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const float dev = __fsub_rn(p[u][d], v[u][d]);
+                if (!(fabsf(dev) < 65536.f)) {
+                    atomicOr(err, kErrDeviation);
+                    continue;
+                }
+                const unsigned long long t = sq_fix32(dev);
+                lo += t;
+                if (lo < t) ++hi;
             }
-            const unsigned long long t = sq_fix32(dev);
-            lo += t;
-            if (lo < t) ++hi;
         }
     }
     // warp then block reduction of (hi, lo) with carries
@@ -218,6 +266,10 @@ __global__ void k_sigma_final(const unsigned long long* d2, int64_t n, float* si
     *sigma = s;
 }
 
+// Re-encode (Eq. 2-3) into the slot offsets[cell] + rank of each particle.
+// Lanes with the same new cell take consecutive ranks from one atomic.  Each
+// warp handles two particles per lane at a time, and the cell's offset and
+// mean momentum are loaded before the rank atomic returns.
 __global__ void k_scatter(int64_t n, int nc, const int32_t* __restrict__ Qn, const float* __restrict__ Pn,
                           const float* __restrict__ vc, const int64_t* __restrict__ offsets,
                           int32_t* fill, const float* __restrict__ sigma_p,
@@ -226,25 +278,46 @@ __global__ void k_scatter(int64_t n, int nc, const int32_t* __restrict__ Qn, con
     const float sigma = *sigma_p;
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    // whole warps iterate together so the slot ranks can be aggregated
     for (int64_t base = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); base < n;
-         base += stride) {
-        const int64_t i = base + lane;
-        const bool live = i < n;
-        const long long key = live ? key_of(Qn, n, nc, i) : -1ll - lane;
-        // lanes with the same new cell take consecutive ranks from one atomic
-        const unsigned peers = __match_any_sync(0xffffffffu, key);
-        const int leader = __ffs(peers) - 1;
-        const int rank = __popc(peers & ((1u << lane) - 1u));
-        int first = 0;
-        if (live && lane == leader) first = atomicAdd(&fill[key], __popc(peers));
-        first = __shfl_sync(0xffffffffu, first, leader);
-        if (!live) continue;
-        const int64_t slot = offsets[key] + first + rank;
-        for (int d = 0; d < 3; ++d) {
-            out[d * n + slot] = (uint8_t)(Qn[d * n + i] & 255);
-            out[(3 + d) * n + slot] =
-                (uint8_t)encode_momentum(Pn[d * n + i], vc[d * ncells + key], sigma, E, err);
+         base += 2 * stride) {
+        int64_t i[2], key[2], off[2];
+        int32_t q[2][3];
+        float p[2][3], v[2][3];
+        int first[2];
+        unsigned peers[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            i[u] = base + u * stride + lane;
+            const bool live = i[u] < n;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                q[u][d] = live ? Qn[d * n + i[u]] : 0;
+                p[u][d] = live ? Pn[d * n + i[u]] : 0.f;
+            }
+            key[u] = live ? (int64_t)(q[u][0] >> 8) +
+                                nc * ((int64_t)(q[u][1] >> 8) + (int64_t)nc * (q[u][2] >> 8))
+                          : -1ll - lane;
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const bool live = key[u] >= 0;
+            off[u] = live ? offsets[key[u]] : 0;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) v[u][d] = live ? vc[d * ncells + key[u]] : 0.f;
+            peers[u] = __match_any_sync(0xffffffffu, key[u]);
+            first[u] = 0;
+            if (live && lane == __ffs(peers[u]) - 1) first[u] = atomicAdd(&fill[key[u]], __popc(peers[u]));
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            first[u] = __shfl_sync(0xffffffffu, first[u], __ffs(peers[u]) - 1);
+            if (key[u] < 0) continue;
+            const int64_t slot = off[u] + first[u] + __popc(peers[u] & ((1u << lane) - 1u));
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                out[d * n + slot] = (uint8_t)(q[u][d] & 255);
+                out[(3 + d) * n + slot] = (uint8_t)encode_momentum(p[u][d], v[u][d], sigma, E, err);
+            }
         }
     }
 }

@@ -53,11 +53,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(TileParams P) {
 
     const TileCells cells = tile_cells(W, O);   // W is free until phase 5
     PMPM_MARK(0);
-    tile_load_green(tid, P.green, gS);
-    tile_zero(tid, R);
-    if (tid == 0) cells.misc[2] = 0;
-    __syncthreads();
-    tile_cells_load(tid, g, P, cells);
+    tile_prologue(tid, g, P, cells, R, gS);
     __syncthreads();
     PMPM_MARK(1);
     tile_cells_scan(tid, g, cells);
@@ -105,8 +101,7 @@ int tile_pass(Sim& s, int mode, float* G) {
     P.green = s.green_packed;
     P.Fl = s.Fl;
     P.mode = mode;
-    P.factors = s.d_factors;
-    P.step = s.d_step;
+    P.kd = s.d_kd;
     P.G = G;
     P.Qn = s.Qn;
     P.Pn = s.Pn;

@@ -38,7 +38,7 @@ constexpr int kTileW = kTileOut * kTileFFT * (kTileFFT / 2);    // 11264 complex
 constexpr int kGreenTri = kGreenS * (kGreenS + 1) / 2;          // 153 pairs b <= c
 constexpr int kGreenRows = kGreenS - 2;                         // own-axis |k| = 1..15
 constexpr int kGreenPacked = kGreenRows * kGreenTri;            // 2295 floats
-constexpr int kOwnTail = 126 + 125 + 4;                         // own-cell table, ints
+constexpr int kOwnTail = 126 + 125 + 8;                         // own-cell table, ints
 constexpr size_t kTileSmemBytes = (size_t)kTileR * 4 + (size_t)kTileW * 8 +
                                   (size_t)kGreenPacked * 4 + (size_t)kOwnTail * 4;
 
@@ -60,9 +60,8 @@ struct TileParams {
     const float* green;           // packed short-range Green table, 17 x 153 (scaled)
     const float* Fl;              // [3][nc^3] long-range force on the coarse mesh
     int mode;                     // 0: write g; 1: kick + drift
-    const float* factors;         // [2 n_steps]: fl32 kick factor (multiplies g) and drift
-                                  // factor in position codes (multiplies p), per step
-    const int* step;              // device step counter (index into factors)
+    const float* kd;              // [2] of the current step: fl32 kick factor (multiplies g)
+                                  // and drift factor in position codes (multiplies p)
     float* G;                     // [3][N] (mode 0)
     int32_t* Qn;                  // [3][N] new codes (mode 1)
     float* Pn;                    // [3][N] new momenta (mode 1)
@@ -251,6 +250,8 @@ PMPM_HD void deposit_one(const TileGeom& g, const int (&cu)[3], const int (&m)[3
         li[d] = s >> 7;
         w1[d] = s & 127;
     }
+    // a cloud whose lower node is below -1 or above 31 on some axis misses the box
+    if ((unsigned)(li[0] + 1) > 32u || (unsigned)(li[1] + 1) > 32u || (unsigned)(li[2] + 1) > 32u) return;
     const bool inside = (unsigned)li[0] < 31u && (unsigned)li[1] < 31u && (unsigned)li[2] < 31u;
     const uint32_t wyz[4] = {(uint32_t)((128 - w1[1]) * (128 - w1[2])), (uint32_t)(w1[1] * (128 - w1[2])),
                              (uint32_t)((128 - w1[1]) * w1[2]), (uint32_t)(w1[1] * w1[2])};
@@ -316,6 +317,7 @@ constexpr int kOwnDim = kTileMaxCoarse;                       // 5
 constexpr int kOwnMax = kOwnDim * kOwnDim * kOwnDim;           // 125
 constexpr int kMapCap = 32768;    // particles whose cell is looked up by table
 constexpr int kPMapCap = 8192;
+constexpr int kHaloChunks = (kHaloMax + 31) / 32;               // 23
 
 struct TileCells {
     int64_t* st;       // [kHaloMax] storage offset of each halo-box cell (W)
@@ -325,7 +327,10 @@ struct TileCells {
     uint8_t* pmap;     // [kPMapCap] own cell of the v-th own particle (W)
     int* ppre;         // [kOwnMax + 1] exclusive prefix over the tile's own cells (O)
     int* prel;         // [kOwnMax] storage offset of own cell p minus own_base (O)
-    int* misc;         // [0..1] own_base (int64), [2] largest halo-cell count (O)
+    int* misc;         // [0..1] own_base (int64), [2] largest halo-cell count,
+                       // [4] sigma, [5] kick, [6] drift as float bits (O)
+    int* tot;          // [kHaloChunks] particles per 32-cell chunk of the halo box (W)
+    int* cmax;         // [kHaloChunks] largest cell count per chunk (W)
 };
 
 PMPM_HD TileCells tile_cells(float2* W, int* O) {
@@ -338,10 +343,24 @@ PMPM_HD TileCells tile_cells(float2* W, int* O) {
     c.ppre = O;
     c.prel = O + 126;
     c.misc = O + 126 + 125;
+    c.tot = reinterpret_cast<int*>(c.pmap + kPMapCap);
+    c.cmax = c.tot + 32;
     return c;
 }
-static_assert(kHaloMax * 8 + (2 * kHaloMax + 2) * 4 + kMapCap * 2 + kPMapCap <= kTileW * 8,
+static_assert(kHaloMax * 8 + (2 * kHaloMax + 2) * 4 + kMapCap * 2 + kPMapCap + 64 * 4 <= kTileW * 8,
               "tile cell tables must fit in W");
+static_assert(kHaloChunks <= 32, "one lane per halo chunk");
+
+PMPM_HD float bits_to_f32(int v) {
+    union { int i; float f; } u;
+    u.i = v;
+    return u.f;
+}
+PMPM_HD int f32_to_bits(float v) {
+    union { int i; float f; } u;
+    u.f = v;
+    return u.i;
+}
 PMPM_HD int64_t own_base(const TileCells& c) {
     return (int64_t)(((uint64_t)(uint32_t)c.misc[1] << 32) | (uint32_t)c.misc[0]);
 }
@@ -357,26 +376,58 @@ PMPM_HD int own_to_halo(int p) {
     return (2 + p % kOwnDim) + kHaloDim * ((2 + (p / kOwnDim) % kOwnDim) + kHaloDim * (2 + p / (kOwnDim * kOwnDim)));
 }
 
-PMPM_HD void tile_cells_load(int tid, const TileGeom& g, const TileParams& P, TileCells c) {
+// 1a: every global load of the prologue (the halo cells' offsets and counts,
+// the packed Green table, sigma and the step factors) is issued before the
+// first shared-memory store, so the tile waits for one memory round trip.
+PMPM_HD void tile_prologue(int tid, const TileGeom& g, const TileParams& P, TileCells c,
+                           uint32_t* R, float* gS) {
     const int hx = g.c1[0] - g.c0[0] + 4, hy = g.c1[1] - g.c0[1] + 4, hz = g.c1[2] - g.c0[2] + 4;
-    for (int b = tid; b < kHaloMax; b += kTileThreads) {
+    int64_t st[2] = {0, 0};
+    int cnt[2] = {0, 0};
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int b = tid + u * kTileThreads;
         const int bx = b % kHaloDim, by = (b / kHaloDim) % kHaloDim, bz = b / (kHaloDim * kHaloDim);
-        int64_t st = 0;
-        int cnt = 0;
-        if (bx < hx && by < hy && bz < hz) {
+        if (b < kHaloMax && bx < hx && by < hy && bz < hz) {
             const int cx = wrap1(g.c0[0] - 2 + bx, P.nc), cy = wrap1(g.c0[1] - 2 + by, P.nc),
                       cz = wrap1(g.c0[2] - 2 + bz, P.nc);
             const int64_t cell = cx + (int64_t)P.nc * (cy + (int64_t)P.nc * cz);
-            st = P.offsets[cell];
-            cnt = P.counts[cell];
+            st[u] = P.offsets[cell];
+            cnt[u] = P.counts[cell];
         }
-        c.st[b] = st;
-        c.cnt[b] = cnt;
-#ifdef __CUDA_ARCH__
-        if (cnt) atomicMax(&c.misc[2], cnt);
-#else
-        if (cnt > c.misc[2]) c.misc[2] = cnt;
-#endif
+    }
+    float gv[(kGreenPacked + kTileThreads - 1) / kTileThreads];
+#pragma unroll
+    for (int u = 0; u < (kGreenPacked + kTileThreads - 1) / kTileThreads; ++u) {
+        const int i = tid + u * kTileThreads;
+        gv[u] = i < kGreenPacked ? P.green[i] : 0.f;
+    }
+    float sc[3] = {0.f, 0.f, 0.f};
+    if (tid == 0) {
+        sc[0] = *P.sigma;
+        if (P.mode == 1) {
+            sc[1] = P.kd[0];
+            sc[2] = P.kd[1];
+        }
+    }
+    tile_zero(tid, R);
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int b = tid + u * kTileThreads;
+        if (b < kHaloMax) {
+            c.st[b] = st[u];
+            c.cnt[b] = cnt[u];
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < (kGreenPacked + kTileThreads - 1) / kTileThreads; ++u) {
+        const int i = tid + u * kTileThreads;
+        if (i < kGreenPacked) gS[i] = gv[u];
+    }
+    if (tid == 0) {
+        c.misc[4] = f32_to_bits(sc[0]);
+        c.misc[5] = f32_to_bits(sc[1]);
+        c.misc[6] = f32_to_bits(sc[2]);
     }
 }
 
@@ -409,16 +460,49 @@ PMPM_HD void warp_prefix(int lane, int n, F cnt_of, int* out) {
 #endif
 }
 
+// 1b: exclusive prefix over the halo box's cells in 32-cell chunks, one warp
+// per chunk (chunk-local prefix, chunk total and largest count); the last
+// two warps also build the own-cell prefix and the own cells' offsets.
 PMPM_HD void tile_cells_scan(int tid, const TileGeom& g, TileCells c) {
     const int warp = tid >> 5, lane = tid & 31;
+    constexpr int kWarps = kTileThreads / 32;
+#ifdef __CUDA_ARCH__
+    for (int ch = warp; ch < kHaloChunks; ch += kWarps) {
+        const int i = ch * 32 + lane;
+        const int v = i < kHaloMax ? c.cnt[i] : 0;
+        int incl = v, mx = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+            mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        }
+        if (i < kHaloMax) c.pre[i] = incl - v;
+        if (lane == 31) c.tot[ch] = incl;
+        if (lane == 0) c.cmax[ch] = mx;
+    }
+#else
+    if (lane == 0) {
+        for (int ch = warp; ch < kHaloChunks; ch += kWarps) {
+            int acc = 0, mx = 0;
+            for (int l = 0; l < 32; ++l) {
+                const int i = ch * 32 + l;
+                const int v = i < kHaloMax ? c.cnt[i] : 0;
+                if (i < kHaloMax) c.pre[i] = acc;
+                acc += v;
+                mx = v > mx ? v : mx;
+            }
+            c.tot[ch] = acc;
+            c.cmax[ch] = mx;
+        }
+    }
+#endif
     const int* cnt = c.cnt;
-    if (warp == 0) {
-        warp_prefix(lane, kHaloMax, [cnt](int i) { return cnt[i]; }, c.pre);
-    } else if (warp == 1) {
+    if (warp == kWarps - 1) {
         const TileGeom gg = g;
         warp_prefix(lane, kOwnMax,
                     [cnt, gg](int p) { return own_valid(gg, p) ? cnt[own_to_halo(p)] : 0; }, c.ppre);
-    } else if (warp == 2) {
+    } else if (warp == kWarps - 2) {
         // storage offsets of the own cells relative to own cell 0 (increasing
         // in flat cell order, spanning less than 2^31 particles)
         const int64_t base = c.st[own_to_halo(0)];
@@ -431,16 +515,87 @@ PMPM_HD void tile_cells_scan(int tid, const TileGeom& g, TileCells c) {
     }
 }
 
-// particle -> cell maps (for the first kMapCap / kPMapCap particles)
+// 1c: the chunk bases turn the chunk-local prefix into the box prefix, and
+// the particle -> cell maps (first kMapCap / kPMapCap particles) are filled:
+// each warp takes 32 cells at a time, one per lane; a lane writes its own
+// cell when it holds at most kMapLane particles, and the whole warp writes
+// each larger cell in turn, so a crowded cell is shared by 32 lanes.
+constexpr int kMapLane = 16;
 PMPM_HD void tile_cells_map(int tid, const TileGeom& g, TileCells c) {
-    for (int b = tid; b < kHaloMax; b += kTileThreads) {
-        const int n = c.cnt[b], p0 = c.pre[b];
-        for (int q = 0; q < n && p0 + q < kMapCap; ++q) c.map[p0 + q] = (uint16_t)b;
+    const int warp = tid >> 5, lane = tid & 31;
+    constexpr int kWarps = kTileThreads / 32;
+    constexpr int kOwnGroups = (kOwnMax + 31) / 32;
+#ifdef __CUDA_ARCH__
+    const int t = lane < kHaloChunks ? c.tot[lane] : 0;
+    int incl = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
     }
-    for (int p = tid; p < kOwnMax; p += kTileThreads) {
-        const int n = own_valid(g, p) ? c.cnt[own_to_halo(p)] : 0, p0 = c.ppre[p];
-        for (int q = 0; q < n && p0 + q < kPMapCap; ++q) c.pmap[p0 + q] = (uint8_t)p;
+    const int base = incl - t;
+    if (warp == 0) {
+        int mx = lane < kHaloChunks ? c.cmax[lane] : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 31) c.pre[kHaloMax] = incl;
+        if (lane == 0) c.misc[2] = mx;
     }
+    for (int b0 = warp * 32; b0 < kHaloMax; b0 += kTileThreads) {
+        const int b = b0 + lane;
+        const int n = b < kHaloMax ? c.cnt[b] : 0;
+        const int p = (b < kHaloMax ? c.pre[b] : 0) + __shfl_sync(0xffffffffu, base, b0 >> 5);
+        if (b < kHaloMax) c.pre[b] = p;
+        if (n <= kMapLane)
+            for (int q = 0; q < n && p + q < kMapCap; ++q) c.map[p + q] = (uint16_t)b;
+        unsigned live = __ballot_sync(0xffffffffu, n > kMapLane && p < kMapCap);
+        while (live) {
+            const int src = __ffs(live) - 1;
+            live &= live - 1u;
+            const int nn = __shfl_sync(0xffffffffu, n, src), pp = __shfl_sync(0xffffffffu, p, src);
+            for (int q = lane; q < nn && pp + q < kMapCap; q += 32) c.map[pp + q] = (uint16_t)(b0 + src);
+        }
+    }
+    if (warp >= kWarps - kOwnGroups) {
+        const int p0 = (warp - (kWarps - kOwnGroups)) * 32, p = p0 + lane;
+        const int n = (p < kOwnMax && own_valid(g, p)) ? c.cnt[own_to_halo(p)] : 0;
+        const int pp = p < kOwnMax ? c.ppre[p] : 0;
+        if (n <= kMapLane)
+            for (int q = 0; q < n && pp + q < kPMapCap; ++q) c.pmap[pp + q] = (uint8_t)p;
+        unsigned live = __ballot_sync(0xffffffffu, n > kMapLane && pp < kPMapCap);
+        while (live) {
+            const int src = __ffs(live) - 1;
+            live &= live - 1u;
+            const int nn = __shfl_sync(0xffffffffu, n, src), q0 = __shfl_sync(0xffffffffu, pp, src);
+            for (int q = lane; q < nn && q0 + q < kPMapCap; q += 32) c.pmap[q0 + q] = (uint8_t)(p0 + src);
+        }
+    }
+#else
+    if (lane != 0) return;
+    int base[32], acc = 0, mx = 0;
+    for (int l = 0; l < 32; ++l) {
+        base[l] = acc;
+        acc += l < kHaloChunks ? c.tot[l] : 0;
+        if (l < kHaloChunks && c.cmax[l] > mx) mx = c.cmax[l];
+    }
+    if (warp == 0) {
+        c.pre[kHaloMax] = acc;
+        c.misc[2] = mx;
+    }
+    for (int b0 = warp * 32; b0 < kHaloMax; b0 += kTileThreads)
+        for (int b = b0; b < b0 + 32 && b < kHaloMax; ++b) {
+            const int n = c.cnt[b], p = c.pre[b] + base[b0 >> 5];
+            c.pre[b] = p;
+            for (int q = 0; q < n && p + q < kMapCap; ++q) c.map[p + q] = (uint16_t)b;
+        }
+    if (warp >= kWarps - kOwnGroups) {
+        const int p0 = (warp - (kWarps - kOwnGroups)) * 32;
+        for (int p = p0; p < p0 + 32 && p < kOwnMax; ++p) {
+            const int n = own_valid(g, p) ? c.cnt[own_to_halo(p)] : 0, q0 = c.ppre[p];
+            for (int q = 0; q < n && q0 + q < kPMapCap; ++q) c.pmap[q0 + q] = (uint8_t)p;
+        }
+    }
+#endif
 }
 
 // largest i in [0, n) with pre[i] <= v (pre non-decreasing, pre[0] = 0 <= v)
@@ -460,15 +615,18 @@ PMPM_HD int own_of(const TileCells& c, int v) {
     return v < kPMapCap ? (int)c.pmap[v] : prefix_find(c.ppre, kOwnMax, v);
 }
 
+constexpr int kDepositIlp = 4;   // halo particles per thread per iteration
+constexpr int kGatherIlp = 2;    // own particles per thread per iteration
+
 PMPM_HD void tile_deposit_flat(int tid, const TileGeom& g, const TileParams& P, uint32_t* R,
                                TileCells c) {
     const int total = c.pre[kHaloMax];
     const bool check = c.misc[2] > 255;
-    for (int v0 = tid; v0 < total; v0 += 2 * kTileThreads) {
-        int b[2], m[2][3];
-        bool ok[2];
+    for (int v0 = tid; v0 < total; v0 += kDepositIlp * kTileThreads) {
+        int b[kDepositIlp], m[kDepositIlp][3];
+        bool ok[kDepositIlp];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < kDepositIlp; ++u) {
             const int v = v0 + u * kTileThreads;
             ok[u] = v < total;
             b[u] = ok[u] ? halo_of(c, v) : 0;
@@ -480,7 +638,7 @@ PMPM_HD void tile_deposit_flat(int tid, const TileGeom& g, const TileParams& P, 
             }
         }
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < kDepositIlp; ++u) {
             if (!ok[u]) continue;
             const int cu[3] = {g.c0[0] - 2 + b[u] % kHaloDim, g.c0[1] - 2 + (b[u] / kHaloDim) % kHaloDim,
                                g.c0[2] - 2 + b[u] / (kHaloDim * kHaloDim)};
@@ -491,16 +649,28 @@ PMPM_HD void tile_deposit_flat(int tid, const TileGeom& g, const TileParams& P, 
     // long-range force of the tile's own particles
     float* slot = P.mode == 0 ? P.G : P.Pn;
     const int ptotal = c.ppre[kOwnMax];
-    for (int v = tid; v < ptotal; v += kTileThreads) {
-        const int p = own_of(c, v);
-        const int64_t j = own_base(c) + c.prel[p] + (v - c.ppre[p]);
-        const int64_t Q[3] = {(int64_t)(g.c0[0] + p % kOwnDim) * kBins + P.m0[j],
-                              (int64_t)(g.c0[1] + (p / kOwnDim) % kOwnDim) * kBins + P.m1[j],
-                              (int64_t)(g.c0[2] + p / (kOwnDim * kOwnDim)) * kBins + P.m2[j]};
-        float gc[3];
-        coarse_gather(P, Q, gc);
+    const int64_t obase = own_base(c);
+    for (int v0 = tid; v0 < ptotal; v0 += kGatherIlp * kTileThreads) {
+        int64_t Q[kGatherIlp][3], j[kGatherIlp];
 #pragma unroll
-        for (int e = 0; e < 3; ++e) slot[e * P.n + j] = gc[e];
+        for (int u = 0; u < kGatherIlp; ++u) {
+            const int v = v0 + u * kTileThreads;
+            const int p = v < ptotal ? own_of(c, v) : 0;
+            j[u] = v < ptotal ? obase + c.prel[p] + (v - c.ppre[p]) : -1;
+            if (j[u] >= 0) {
+                Q[u][0] = (int64_t)(g.c0[0] + p % kOwnDim) * kBins + P.m0[j[u]];
+                Q[u][1] = (int64_t)(g.c0[1] + (p / kOwnDim) % kOwnDim) * kBins + P.m1[j[u]];
+                Q[u][2] = (int64_t)(g.c0[2] + p / (kOwnDim * kOwnDim)) * kBins + P.m2[j[u]];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kGatherIlp; ++u) {
+            if (j[u] < 0) continue;
+            float gc[3];
+            coarse_gather(P, Q[u], gc);
+#pragma unroll
+            for (int e = 0; e < 3; ++e) slot[e * P.n + j[u]] = gc[e];
+        }
     }
 }
 
@@ -667,66 +837,78 @@ PMPM_HD void tile_inv_x(int tid, const TileGeom& g, float2* W) {
 template <int D>
 PMPM_HD void tile_interp(int tid, const TileGeom& g, const TileParams& P, const float2* W,
                          TileCells c) {
+    constexpr int U = 2;   // particles per thread per iteration, loads issued together
     const float* Wf = reinterpret_cast<const float*>(W);
     const int64_t ncells = (int64_t)P.nc * P.nc * P.nc;
     const int64_t n = P.n;
-    const float sigma = *P.sigma;
+    const float sigma = bits_to_f32(c.misc[4]);
+    const float kick = bits_to_f32(c.misc[5]), drift = bits_to_f32(c.misc[6]);
     const uint8_t* ud = D == 0 ? P.u0 : (D == 1 ? P.u1 : P.u2);
     float* slot = P.mode == 0 ? P.G : P.Pn;
     const int ptotal = c.ppre[kOwnMax];
     const int64_t base = own_base(c);
-    float kick = 0.f, drift = 0.f;
-    if (P.mode == 1) {
-        const int st = *P.step;
-        kick = P.factors[2 * st];
-        drift = P.factors[2 * st + 1];
-    }
-    for (int v = tid; v < ptotal; v += kTileThreads) {
-        const int p = prefix_find(c.ppre, kOwnMax, v);
-        const int64_t j = base + c.prel[p] + (v - c.ppre[p]);
-        const int cx = g.c0[0] + p % kOwnDim, cy = g.c0[1] + (p / kOwnDim) % kOwnDim,
-                  cz = g.c0[2] + p / (kOwnDim * kOwnDim);
-        const int64_t cell = cx + (int64_t)P.nc * (cy + (int64_t)P.nc * cz);
-        const int64_t Q[3] = {(int64_t)cx * kBins + P.m0[j], (int64_t)cy * kBins + P.m1[j],
-                              (int64_t)cz * kBins + P.m2[j]};
-        const float gcd = slot[D * n + j];
-        const uint8_t u = ud[j];
-        const float vcd = P.vc[D * ncells + cell];
-        // fine gather
-        int lo[3], w1[3];
+    for (int v0 = tid; v0 < ptotal; v0 += U * kTileThreads) {
+        int64_t j[U], Q[U][3], cell[U];
+        float gcd[U], vcd[U];
+        int u8[U];
 #pragma unroll
-        for (int e = 0; e < 3; ++e) {
-            const int s = (int)(2 * Q[e] + 1 - kCodesPerFine - 128 * (int64_t)g.o[e]);
-            lo[e] = (s >> 7) - (kBuffer - 1);
-            w1[e] = s & 127;
+        for (int u = 0; u < U; ++u) {
+            const int v = v0 + u * kTileThreads;
+            const int p = v < ptotal ? prefix_find(c.ppre, kOwnMax, v) : 0;
+            j[u] = v < ptotal ? base + c.prel[p] + (v - c.ppre[p]) : -1;
+            const int cx = g.c0[0] + p % kOwnDim, cy = g.c0[1] + (p / kOwnDim) % kOwnDim,
+                      cz = g.c0[2] + p / (kOwnDim * kOwnDim);
+            cell[u] = cx + (int64_t)P.nc * (cy + (int64_t)P.nc * cz);
+            if (j[u] >= 0) {
+                Q[u][0] = (int64_t)cx * kBins + P.m0[j[u]];
+                Q[u][1] = (int64_t)cy * kBins + P.m1[j[u]];
+                Q[u][2] = (int64_t)cz * kBins + P.m2[j[u]];
+                gcd[u] = slot[D * n + j[u]];
+                if (P.mode == 1) {
+                    u8[u] = ud[j[u]];
+                    vcd[u] = P.vc[D * ncells + cell[u]];
+                }
+            }
         }
-        float gf = 0.f;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
-            const float w = (float)((dx ? w1[0] : 128 - w1[0]) * (dy ? w1[1] : 128 - w1[1]) *
-                                    (dz ? w1[2] : 128 - w1[2]));
-            gf += w * Wf[wfidx(lo[0] + dx, lo[1] + dy, lo[2] + dz)];
+        for (int u = 0; u < U; ++u) {
+            if (j[u] < 0) continue;
+            // fine gather
+            int lo[3], w1[3];
+#pragma unroll
+            for (int e = 0; e < 3; ++e) {
+                const int s = (int)(2 * Q[u][e] + 1 - kCodesPerFine - 128 * (int64_t)g.o[e]);
+                lo[e] = (s >> 7) - (kBuffer - 1);
+                w1[e] = s & 127;
+            }
+            float gf = 0.f;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
+                const float w = (float)((dx ? w1[0] : 128 - w1[0]) * (dy ? w1[1] : 128 - w1[1]) *
+                                        (dz ? w1[2] : 128 - w1[2]));
+                gf += w * Wf[wfidx(lo[0] + dx, lo[1] + dy, lo[2] + dz)];
+            }
+            const float gval = gf * 4.76837158203125e-07f + gcd[u];   // 2^-21
+            if (P.mode == 0) {
+                slot[D * n + j[u]] = gval;
+                continue;
+            }
+            // kick (Eq. 3 decode, then p += kick * g) and integer drift
+            const float pv = decode_momentum(vcd[u], sigma, P.Tdec[u8[u]]);
+            const float pn = fadd_rn(pv, fmul_rn(kick, gval));
+            const float xq = fmul_rn(pn, drift);
+            if (!(pn == pn) || !(gval == gval)) flag_error(P.err, kErrNaN);
+            if (fabsf(pn) >= 1048576.f) flag_error(P.err, kErrMomentum);
+            int64_t dq = 0;
+            if (fabsf(xq) < 1.0e9f) dq = (int64_t)floorf(fadd_rn(xq, 0.5f));
+            else flag_error(P.err, kErrDrift);
+            const int64_t M = (int64_t)P.nc * kBins;
+            int64_t qn = (Q[u][D] + dq) % M;
+            if (qn < 0) qn += M;
+            P.Qn[D * n + j[u]] = (int32_t)qn;
+            P.Pn[D * n + j[u]] = pn;
         }
-        const float gval = gf * 4.76837158203125e-07f + gcd;   // 2^-21
-        if (P.mode == 0) {
-            slot[D * n + j] = gval;
-            continue;
-        }
-        // kick (Eq. 3 decode, then p += kick * g) and integer drift
-        const float pv = decode_momentum(vcd, sigma, P.Tdec[u]);
-        const float pn = fadd_rn(pv, fmul_rn(kick, gval));
-        const float xq = fmul_rn(pn, drift);
-        if (!(pn == pn) || !(gval == gval)) flag_error(P.err, kErrNaN);
-        if (fabsf(pn) >= 1048576.f) flag_error(P.err, kErrMomentum);
-        int64_t dq = 0;
-        if (fabsf(xq) < 1.0e9f) dq = (int64_t)floorf(fadd_rn(xq, 0.5f));
-        else flag_error(P.err, kErrDrift);
-        const int64_t M = (int64_t)P.nc * kBins;
-        int64_t qn = (Q[D] + dq) % M;
-        if (qn < 0) qn += M;
-        P.Qn[D * n + j] = (int32_t)qn;
-        P.Pn[D * n + j] = pn;
     }
 }
 
