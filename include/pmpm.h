@@ -64,6 +64,24 @@ extern "C" {
 #define PMPM_QP               9  /* load only: int32 Q[3][N] then float p[3][N];
                                     encodes them into the store (Sec. III-A) */
 
+/* pmpm_config.flags */
+#define PMPM_FLAG_LOWMEM 1   /* Low-memory step for the largest boxes.  The step
+                                keeps no per-particle intermediate: the tile pass
+                                (Sec. II) runs three times per step, first to count
+                                the particles of every new cell and sum their
+                                momenta, then to sum the squared deviations that
+                                give sigma (Eq. 3), then to re-encode and scatter
+                                (Sec. III-A).  Every pass recomputes the same forces,
+                                so the new store is the one the default step writes.
+                                About 24.5 bytes per particle of workspace instead
+                                of 83 (2048^3 particles fit in one GB300), for about
+                                three times the tile work.  A tile may hold at most
+                                65,536 of its own particles (PMPM_EOVERFLOW above).
+                                Initial conditions use float32 transforms and a
+                                float32 displacement field (the default uses
+                                float64).  PMPM_DECODED_Q/P, PMPM_FORCE and loading
+                                PMPM_QP are not available. */
+
 typedef struct pmpm_config {
     int32_t np;              /* particles per side of the initial lattice, N = np^3 */
     int32_t nc;              /* coarse cells per side (>= 8); fine mesh 4*nc */
@@ -72,7 +90,7 @@ typedef struct pmpm_config {
     int32_t pos_bytes;       /* bytes per position coordinate; must be 1 (Eq. 2) */
     int32_t vel_bytes;       /* bytes per velocity coordinate; must be 1 (Eq. 3) */
     int32_t pk_mesh_max;     /* largest power-spectrum mesh; 0 = min(4*nc, 512) */
-    int32_t reserved;
+    int32_t flags;           /* PMPM_FLAG_* below; 0 = default */
     double  a_init;          /* first scale factor of the equal-log-a schedule */
     double  a_final;         /* last scale factor */
     int32_t n_steps;         /* steps of the schedule */

@@ -29,6 +29,8 @@ FORCE = 7
 COARSE_DENSITY = 8
 QP = 9
 
+FLAG_LOWMEM = 1
+
 ERROR_NAMES = {
     PMPM_EINVAL: "PMPM_EINVAL",
     PMPM_ENOMEM: "PMPM_ENOMEM",
@@ -64,7 +66,7 @@ class Config(ctypes.Structure):
         ("pos_bytes", ctypes.c_int32),
         ("vel_bytes", ctypes.c_int32),
         ("pk_mesh_max", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("flags", ctypes.c_int32),
         ("a_init", ctypes.c_double),
         ("a_final", ctypes.c_double),
         ("n_steps", ctypes.c_int32),

@@ -55,6 +55,8 @@ static int validate(const pmpm_config* c, char* msg, size_t len) {
                PMPM_EINVAL;
     if (!(c->a_init > 0.0) || !(c->a_final >= c->a_init) || c->n_steps < 1)
         return snprintf(msg, len, "need 0 < a_init <= a_final and n_steps >= 1"), PMPM_EINVAL;
+    if (c->flags & ~PMPM_FLAG_LOWMEM)
+        return snprintf(msg, len, "unknown flags 0x%x", (unsigned)c->flags), PMPM_EINVAL;
     return PMPM_OK;
 }
 
@@ -72,9 +74,106 @@ static void derive(Sim& s, const pmpm_config* c) {
     if (s.np > s.fft_max) s.fft_max = s.np;
     if (s.pk_max > s.fft_max) s.fft_max = s.pk_max;
     s.nblocks_scan = (s.ncells + 4095) / 4096;
+    s.lowmem = (c->flags & PMPM_FLAG_LOWMEM) != 0;
+    s.lm_ctas = s.lowmem ? kLowmemCtas : 0;
+}
+
+// Low-memory layout (PMPM_FLAG_LOWMEM).  No per-particle intermediate; the
+// temporaries of the different phases share one region U, and the float32
+// initial-condition fields overlay the store:
+//   [small][P1: store 0, counts 0, offsets 0, v_c 0][U][P2: store 1, counts 1,
+//    offsets 1, v_c 1, F_l][tile scratch]
+//   U holds, at different times: the new-cell sums S and slot counters (tile
+//   passes and IC encode), the coarse mesh and spectra (coarse force), the
+//   power-spectrum mesh, the force-table scratch (init).
+//   ICs: the transform work array (8N) starts at P1; the displacement field
+//   psi (12N) starts after P1 + S + fill (and after the work array), so the
+//   IC encode can write store 0 and its cell arrays while psi is read.
+static size_t layout_lowmem(Sim& s, uint8_t* base) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> uint8_t* {
+        off = align_up(off);
+        uint8_t* p = base ? base + off : nullptr;
+        off += bytes;
+        return p;
+    };
+    const int64_t N = s.n, C = s.ncells;
+    // small persistent items
+    const size_t h = s.nc / 2 + 1;
+    s.green_coarse = reinterpret_cast<float*>(take(4 * h * h * h));
+    s.green_fine = reinterpret_cast<float*>(take(4 * (size_t)kGreenS * kGreenS * kGreenS));
+    s.green_packed = reinterpret_cast<float*>(take(4 * (size_t)kGreenS * kGreenS * (kGreenS + 1) / 2));
+    s.Tdec = reinterpret_cast<float*>(take(4 * 256));
+    s.Eedge = reinterpret_cast<float*>(take(4 * 256));
+    s.tw_f = reinterpret_cast<float2*>(take(8 * (size_t)s.fft_max));
+    s.tw_d = reinterpret_cast<double2*>(take(16 * (size_t)s.fft_max));
+    s.err = reinterpret_cast<uint32_t*>(take(4));
+    s.blocksums = reinterpret_cast<long long*>(take(8 * (size_t)(s.nblocks_scan + 1)));
+    s.ic_partial = reinterpret_cast<double*>(take(8 * (3 * 1024 + 1)));
+    s.pk_bins = reinterpret_cast<double*>(take(8 * 3 * (size_t)(s.pk_max / 2 + 1)));
+    s.d_factors = reinterpret_cast<float*>(take(8 * (size_t)s.cfg.n_steps));
+    s.d_step = reinterpret_cast<int*>(take(4));
+    s.d_kd = reinterpret_cast<float*>(take(8));
+    s.d2 = reinterpret_cast<unsigned long long*>(take(16));
+    for (int b = 0; b < 2; ++b) s.sigma_d[b] = reinterpret_cast<float*>(take(4));
+    s.lm_sp = reinterpret_cast<float*>(take(4 * 3 * (size_t)kLowmemCap * s.lm_ctas));
+    s.lm_sq = reinterpret_cast<int32_t*>(take(4 * 2 * (size_t)kLowmemCap * s.lm_ctas));
+    s.lm_next = reinterpret_cast<int*>(take(4));
+    off = align_up(off);
+    const size_t p1 = off;
+    // P1
+    s.streams[0] = take(6 * (size_t)N);
+    s.counts[0] = reinterpret_cast<int32_t*>(take(4 * (size_t)C));
+    s.offsets[0] = reinterpret_cast<int64_t*>(take(8 * (size_t)(C + 1)));
+    s.vc[0] = reinterpret_cast<float*>(take(12 * (size_t)C));
+    off = align_up(off);
+    // U
+    const size_t u0 = off;
+    const size_t sf = align_up(24 * (size_t)C) + align_up(4 * (size_t)C);
+    const size_t coarse_b = 4 * align_up(8 * (size_t)C);
+    const size_t pk3 = (size_t)s.pk_max * s.pk_max * s.pk_max;
+    const size_t pk_b = 16 * pk3 + 512;
+    const size_t green_b = green_scratch_bytes(s.nc);
+    size_t ub = sf;
+    if (coarse_b > ub) ub = coarse_b;
+    if (pk_b > ub) ub = pk_b;
+    if (green_b > ub) ub = green_b;
+    if (base) {
+        uint8_t* u = base + u0;
+        s.S = reinterpret_cast<unsigned long long*>(u);
+        s.fill = reinterpret_cast<int32_t*>(u + align_up(24 * (size_t)C));
+        s.rho_c = reinterpret_cast<long long*>(u);
+        s.cA = reinterpret_cast<float2*>(u + align_up(8 * (size_t)C));
+        s.cB1 = reinterpret_cast<float2*>(u + 2 * align_up(8 * (size_t)C));
+        s.cB2 = reinterpret_cast<float2*>(u + 3 * align_up(8 * (size_t)C));
+        s.scratch = u;
+    }
+    s.scratch_bytes = ub;
+    off = u0 + ub;
+    // P2
+    s.streams[1] = take(6 * (size_t)N);
+    s.counts[1] = reinterpret_cast<int32_t*>(take(4 * (size_t)C));
+    s.offsets[1] = reinterpret_cast<int64_t*>(take(8 * (size_t)(C + 1)));
+    s.vc[1] = reinterpret_cast<float*>(take(12 * (size_t)C));
+    s.Fl = reinterpret_cast<float*>(take(12 * (size_t)C));
+    off = align_up(off);
+    // IC overlay
+    size_t psi0 = align_up(u0 + sf);
+    const size_t work_end = p1 + 8 * (size_t)N;
+    if (align_up(work_end) > psi0) psi0 = align_up(work_end);
+    const size_t psi_end = psi0 + 12 * (size_t)N;
+    if (base) {
+        s.ic_work = reinterpret_cast<float2*>(base + p1);
+        s.ic_psi = reinterpret_cast<float*>(base + psi0);
+    }
+    s.Qn = nullptr;
+    s.Pn = nullptr;
+    if (psi_end > off) off = psi_end;
+    return align_up(off);
 }
 
 size_t layout(Sim& s, uint8_t* base) {
+    if (s.lowmem) return layout_lowmem(s, base);
     size_t off = 0;
     auto take = [&](size_t bytes) -> uint8_t* {
         off = align_up(off);
@@ -182,7 +281,8 @@ static int sync_and_check(Sim& s) {
         if (flags & kErrCount) return set_error(s, PMPM_ECOUNT, "particle count not conserved");
         return set_error(s, PMPM_EOVERFLOW,
                          "device range check failed (flags 0x%x: 1 fine density, 2 momentum, "
-                         "4 velocity deviation, 16 non-finite, 32 drift)", flags);
+                         "4 velocity deviation, 16 non-finite, 32 drift, 64 more than %d own "
+                         "particles in a tile)", flags, kLowmemCap);
     }
     return PMPM_OK;
 }
@@ -238,9 +338,13 @@ static int enqueue_step(Sim& s) {
     prof_mark(s, 0);
     if ((rc = coarse_force(s))) return rc;
     prof_mark(s, 1);
-    if ((rc = tile_pass(s, 1, nullptr))) return rc;
-    prof_mark(s, 2);
-    if ((rc = encode_from_qp(s, false))) return rc;
+    if (s.lowmem) {
+        if ((rc = lowmem_passes(s))) return rc;
+    } else {
+        if ((rc = tile_pass(s, 1, nullptr))) return rc;
+        prof_mark(s, 2);
+        if ((rc = encode_from_qp(s, false))) return rc;
+    }
     k_step_advance<<<1, 1, 0, s.stream>>>(s.d_step, s.d_kd, s.d_factors, s.cfg.n_steps);
     s.launches++;
     return check_launch(s, "step");
@@ -330,6 +434,11 @@ static pmpm_sim* init_common(const pmpm_config* cfg, void* d_workspace, size_t b
     s.stream = static_cast<cudaStream_t>(cuda_stream);
     layout(s, s.ws);
     cudaGetDevice(&s.device);
+    if (s.lowmem) {
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s.device);
+        s.lm_grid = sms < 1 ? 1 : (sms < s.lm_ctas ? sms : s.lm_ctas);
+    }
     tile_setup();
     fft_setup();
     cudaMemsetAsync(s.err, 0, 4, s.stream);
@@ -521,6 +630,9 @@ int pmpm_fetch(pmpm_sim* h, int32_t what, void* dst, size_t bytes) {
         case PMPM_COARSE_DENSITY: need = 8 * C; break;
         default: return set_error(s, PMPM_EINVAL, "unknown fetch item %d", what);
     }
+    if (s.lowmem && (what == PMPM_DECODED_Q || what == PMPM_DECODED_P || what == PMPM_FORCE))
+        return set_error(s, PMPM_EINVAL, "fetch %d needs the per-particle buffers a low-memory sim "
+                         "does not have", what);
     if (bytes != need) return set_error(s, PMPM_EINVAL, "fetch %d needs %zu bytes, got %zu", what, need, bytes);
     if (!s.have_state) return set_error(s, PMPM_ESTATE, "no particle state");
     int rc = PMPM_OK;
@@ -616,6 +728,9 @@ int pmpm_load(pmpm_sim* h, int32_t what, const void* src, size_t bytes) {
             break;
         }
         case PMPM_QP: {
+            if (s.lowmem)
+                return set_error(s, PMPM_EINVAL, "loading Q/P needs the per-particle buffers a "
+                                 "low-memory sim does not have");
             if (bytes != 24 * N) return set_error(s, PMPM_EINVAL, "Q/P need %zu bytes", 24 * N);
             e = cudaMemcpyAsync(s.Qn, src, 12 * N, cudaMemcpyHostToDevice, s.stream);
             if (e == cudaSuccess)

@@ -25,6 +25,7 @@ constexpr int kGreenS = kTileFFT / 2 + 1;        // 17: |k| range of the tile Gr
 constexpr int kPFixBits = 24;    // momenta rounded to 2^-24 for the cell sums
 constexpr int kD2FixBits = 32;   // squared deviations rounded to 2^-32
 constexpr float kSigmaFloor = 5.9604644775390625e-08f;  // 2^-24
+constexpr int kLowmemCap = 65536;   // own particles per tile the low-memory scratch holds
 
 // ---------------------------------------------------------------- error flags
 enum : uint32_t {
@@ -34,6 +35,7 @@ enum : uint32_t {
     kErrCount = 8u,           // counts do not add up to N
     kErrNaN = 16u,            // non-finite momentum or force
     kErrDrift = 32u,          // drift larger than the int32 code range
+    kErrScratch = 64u,        // a tile has more own particles than the low-memory scratch holds
 };
 
 #ifdef __CUDA_ARCH__
@@ -44,6 +46,7 @@ PMPM_HD float fdiv_rn(float a, float b) { return __fdiv_rn(a, b); }
 PMPM_HD double dmul_rn(double a, double b) { return __dmul_rn(a, b); }
 PMPM_HD double dadd_rn(double a, double b) { return __dadd_rn(a, b); }
 PMPM_HD void flag_error(uint32_t* err, uint32_t bits) { atomicOr(err, bits); }
+PMPM_HD int fetch_add_i32(int32_t* p, int32_t v) { return atomicAdd(p, v); }
 #else
 PMPM_HD float fadd_rn(float a, float b) { volatile float r = a + b; return r; }
 PMPM_HD float fsub_rn(float a, float b) { volatile float r = a - b; return r; }
@@ -52,6 +55,7 @@ PMPM_HD float fdiv_rn(float a, float b) { volatile float r = a / b; return r; }
 PMPM_HD double dmul_rn(double a, double b) { volatile double r = a * b; return r; }
 PMPM_HD double dadd_rn(double a, double b) { volatile double r = a + b; return r; }
 PMPM_HD void flag_error(uint32_t* err, uint32_t bits) { *err |= bits; }
+PMPM_HD int fetch_add_i32(int32_t* p, int32_t v) { int o = *p; *p = o + v; return o; }
 #endif
 
 // ---------------------------------------------------------------- codec
@@ -90,6 +94,25 @@ PMPM_HD uint32_t encode_momentum(float p, float vc, float sigma, const float* E,
     if (u < 255 && E[u + 1] <= t) ++u;
     else if (u > 0 && E[u] > t) --u;
     return (uint32_t)u;
+}
+
+// round-half-even(d^2 2^32) for a float32 d with |d| < 2^16, in integers:
+// d = m 2^e exactly, so d^2 2^32 = m^2 2^(2e + 32) with m^2 < 2^48.  The
+// dispersion of Eq. 3 is the exact sum of these terms.
+PMPM_HD unsigned long long sq_fix32(float d) {
+    union { float f; uint32_t u; } bits;
+    bits.f = d;
+    const uint32_t b = bits.u & 0x7fffffffu;
+    const uint32_t E = b >> 23, M = b & 0x7fffffu;
+    const unsigned long long m = E ? (unsigned long long)(M | 0x800000u) : (unsigned long long)M;
+    const int e = E ? (int)E - 150 : -149;
+    const unsigned long long m2 = m * m;
+    const int sh = 2 * e + 32;
+    if (sh >= 0) return m2 << sh;
+    const int r = -sh;
+    if (r > 49) return 0ull;                       // value below 1/4
+    const unsigned long long q = m2 >> r, rem = m2 & ((1ull << r) - 1ull), half = 1ull << (r - 1);
+    return q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull);
 }
 
 // ---------------------------------------------------------------- CIC

@@ -109,9 +109,91 @@ __global__ void k_ic_particles(int np, int nc, double a_init, const double* __re
     }
 }
 
+// float32 variants for low-memory sims: the same noise, spectrum and
+// normalisation, one float2 work array (noise regenerated per component) and
+// a float32 displacement field
+__global__ void k_ic_noise_f(int64_t n, unsigned long long seed, float2* w) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long z1 = splitmix64(seed, 2ull * i);
+        const unsigned long long z2 = splitmix64(seed, 2ull * i + 1ull);
+        const double u1 = ((double)(z1 >> 11) + 1.0) * 0x1p-53;
+        const double u2 = (double)(z2 >> 11) * 0x1p-53;
+        w[i] = make_float2((float)(sqrt(-2.0 * log(u1)) * cos(2.0 * kPi * u2)), 0.f);
+    }
+}
+__global__ void k_ic_spectrum_f(int np, int nf, int d, double slope, double kc, float2* w) {
+    const int64_t n = (int64_t)np * np * np;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int ix = (int)(i % np), iy = (int)((i / np) % np), iz = (int)(i / ((int64_t)np * np));
+        const int h = np / 2;
+        const int nx = ix < h ? ix : ix - np, ny = iy < h ? iy : iy - np, nz = iz < h ? iz : iz - np;
+        float2 v = make_float2(0.f, 0.f);
+        if (!(nx == -h || ny == -h || nz == -h) && (nx | ny | nz)) {
+            const double kf = 2.0 * kPi / nf;
+            const double kx = kf * nx, ky = kf * ny, kz = kf * nz;
+            const double k2 = kx * kx + ky * ky + kz * kz;
+            const double k = sqrt(k2);
+            const double amp = sqrt(pow(k, slope) * exp(-(k / kc) * (k / kc)));
+            const double kd = d == 0 ? kx : (d == 1 ? ky : kz);
+            const double c = kd / k2 * amp;
+            const float2 a = w[i];
+            v = make_float2((float)(-c * a.y), (float)(c * a.x));   // i c a
+        }
+        w[i] = v;
+    }
+}
+__global__ void k_ic_store_f(int64_t n, int d, const float2* __restrict__ in, float* __restrict__ psi,
+                             double* __restrict__ partial) {
+    double acc = 0.0;
+    const double inv_n = 1.0 / (double)n;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float v = (float)((double)in[i].x * inv_n);
+        psi[d * n + i] = v;
+        acc += (double)v * v;
+    }
+    __shared__ double sh[256];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[d * gridDim.x + blockIdx.x] += sh[0];
+}
+
 }  // namespace
 
+static int ic_zeldovich_lowmem(Sim& s, uint64_t seed, double slope, double kc, double rms) {
+    const int np = s.np;
+    const int64_t n = s.n;
+    cudaStream_t st = s.stream;
+    float2* w = s.ic_work;
+    double* partial = s.ic_partial;
+    const int nblk = 1024;
+    cudaMemsetAsync(partial, 0, sizeof(double) * (3 * nblk + 1), st);
+    int rc;
+    for (int d = 0; d < 3; ++d) {
+        k_ic_noise_f<<<grid_for(n, 256), 256, 0, st>>>(n, (unsigned long long)seed, w);
+        if ((rc = fft3d<float>(s, w, np, -1))) return rc;
+        k_ic_spectrum_f<<<grid_for(n, 256), 256, 0, st>>>(np, s.nf, d, slope, kc, w);
+        if ((rc = fft3d<float>(s, w, np, 1))) return rc;
+        k_ic_store_f<<<nblk, 256, 0, st>>>(n, d, w, s.ic_psi, partial);
+    }
+    double* scale = partial + 3 * nblk;
+    k_ic_scale<<<1, 1, 0, st>>>(nblk, n, s.cfg.a_init, rms, partial, scale);
+    s.launches += 3 * 3 + 1;
+    if ((rc = check_launch(s, "ic"))) return rc;
+    s.a = s.cfg.a_init;
+    s.step = 0;
+    set_device_step(s, 0);
+    return encode_from_psi(s, scale);
+}
+
 int ic_zeldovich(Sim& s, uint64_t seed, double slope, double kc, double rms) {
+    if (s.lowmem) return ic_zeldovich_lowmem(s, seed, slope, kc, rms);
     const int np = s.np;
     const int64_t n = s.n;
     cudaStream_t st = s.stream;

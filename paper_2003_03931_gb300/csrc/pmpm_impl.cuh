@@ -12,6 +12,7 @@
 namespace pmpm {
 
 constexpr int kStages = 6;          // see pmpm_stage_times
+constexpr int kLowmemCtas = 160;    // persistent tile CTAs of the low-memory step (>= SMs)
 constexpr int kEventRing = 4096;
 
 struct Sim {
@@ -64,8 +65,18 @@ struct Sim {
     // transient scratch (step, init, ICs and power spectrum share it)
     uint8_t* scratch = nullptr;
     size_t scratch_bytes = 0;
-    int32_t* Qn = nullptr;                      // [3][N] (aliases scratch)
-    float* Pn = nullptr;                        // [3][N] (aliases scratch)
+    int32_t* Qn = nullptr;                      // [3][N] (aliases scratch; default step)
+    float* Pn = nullptr;                        // [3][N] (aliases scratch; default step)
+
+    // low-memory step (PMPM_FLAG_LOWMEM)
+    bool lowmem = false;
+    int lm_ctas = 0;                            // scratch slots (kLowmemCtas)
+    int lm_grid = 0;                            // persistent tile CTAs: min(SMs, slots)
+    int* lm_next = nullptr;                     // tile counter of a low-memory pass
+    float* lm_sp = nullptr;                     // [ctas][3][kLowmemCap] per-CTA momenta
+    int32_t* lm_sq = nullptr;                   // [ctas][2][kLowmemCap] per-CTA codes
+    float2* ic_work = nullptr;                  // [N] float32 IC transform (overlays the store)
+    float* ic_psi = nullptr;                    // [3][N] float32 displacement field
 
     // captured steps, one per buffer parity
     bool graphs = false;
@@ -114,6 +125,9 @@ void tile_setup();
 void fft_setup();
 int scan_counts(Sim& s, const int32_t* counts, int64_t* offsets);
 int encode_from_qp(Sim& s, bool counts_ready);
+int scan_and_means(Sim& s, int nxt);
+int lowmem_passes(Sim& s);             // the three tile passes of a low-memory step
+int encode_from_psi(Sim& s, const double* scale);   // low-memory ICs -> store 0
 int decode_state(Sim& s);              // -> s.Qn, s.Pn
 int ic_zeldovich(Sim& s, uint64_t seed, double slope, double kc, double rms);
 int power_spectrum(Sim& s, int nmesh, int nbins, double* k, double* pk, int64_t* nm);

@@ -121,16 +121,57 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(int64_t ncells, con
     }
 }
 
-// counts and fixed-point momentum sums from codes and momenta
-__device__ __forceinline__ int64_t key_of(const int32_t* Qn, int64_t n, int nc, int64_t i);
+// Where the encode kernels read each particle's new codes Q and momenta p:
+// the per-particle buffers of the default step, or, for the low-memory
+// initial conditions, the float32 displacement field (x = q + a Psi,
+// p = a^(3/2) Psi, Q = floor(64 x) mod 256 nc; Sec. IV-A.2).
+struct QPArrays {
+    const int32_t* Q;
+    const float* P;
+    int64_t n;
+    __device__ __forceinline__ void load(int64_t i, int32_t (&q)[3], float (&p)[3]) const {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            q[d] = Q[d * n + i];
+            p[d] = P[d * n + i];
+        }
+    }
+};
+
+struct QPFromPsi {
+    const float* psi;      // [3][N]
+    const double* scale;   // device scalar: rms normalisation
+    int np, nc;
+    double a, a15, spacing;
+    int64_t n;
+    __device__ __forceinline__ void load(int64_t i, int32_t (&q)[3], float (&p)[3]) const {
+        const double sc = *scale;
+        const int li[3] = {(int)(i % np), (int)((i / np) % np), (int)(i / ((int64_t)np * np))};
+        const int64_t M = (int64_t)nc * kBins;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const double ps = (double)psi[d * n + i] * sc;
+            const double x = ((double)li[d] + 0.5) * spacing + a * ps;
+            int64_t Q = (int64_t)floor(x * (double)kCodesPerFine) % M;
+            if (Q < 0) Q += M;
+            q[d] = (int32_t)Q;
+            p[d] = (float)(a15 * ps);
+        }
+    }
+};
+
+__device__ __forceinline__ int64_t key3(const int32_t (&q)[3], int nc) {
+    return (int64_t)(q[0] >> 8) + nc * ((int64_t)(q[1] >> 8) + (int64_t)nc * (q[2] >> 8));
+}
 
 // New-cell counts and fixed-point momentum sums.  Lanes of a warp whose
 // particles land in the same new cell (common: the input is in old cell
 // order) add their values with warp reductions first, so one lane per cell
 // issues the global atomics.  The sums are integers, so the result does not
 // depend on how particles are grouped.
-__global__ void k_hist(int64_t n, int nc, const int32_t* __restrict__ Qn, const float* __restrict__ Pn,
-                       int32_t* counts, unsigned long long* S, uint32_t* err) {
+template <class Src>
+__global__ void k_hist(Src src, int64_t n, int nc, int32_t* counts, unsigned long long* S,
+                       uint32_t* err) {
     const int64_t ncells = (int64_t)nc * nc * nc;
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -138,14 +179,16 @@ __global__ void k_hist(int64_t n, int nc, const int32_t* __restrict__ Qn, const 
          base += stride) {
         const int64_t i = base + lane;
         const bool live = i < n;
-        const long long key = live ? key_of(Qn, n, nc, i) : -1ll - lane;
+        int32_t q[3] = {0, 0, 0};
+        float p[3] = {0.f, 0.f, 0.f};
+        if (live) src.load(i, q, p);
+        const long long key = live ? key3(q, nc) : -1ll - lane;
         long long fx[3] = {0, 0, 0};
         if (live) {
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                const float p = Pn[d * n + i];
-                if (fabsf(p) < 1048576.f) fx[d] = __double2ll_rn((double)p * 16777216.0);
-                else atomicOr(err, p == p ? kErrMomentum : kErrNaN);
+                if (fabsf(p[d]) < 1048576.f) fx[d] = __double2ll_rn((double)p[d] * 16777216.0);
+                else atomicOr(err, p[d] == p[d] ? kErrMomentum : kErrNaN);
             }
         }
         const unsigned peers = __match_any_sync(0xffffffffu, key);
@@ -167,31 +210,11 @@ __global__ void k_hist(int64_t n, int nc, const int32_t* __restrict__ Qn, const 
     }
 }
 
-__device__ __forceinline__ int64_t key_of(const int32_t* Qn, int64_t n, int nc, int64_t i) {
-    return (int64_t)(Qn[i] >> 8) + nc * ((int64_t)(Qn[n + i] >> 8) + (int64_t)nc * (Qn[2 * n + i] >> 8));
-}
-
-// round-half-even(d^2 2^32) for a float32 d with |d| < 2^16, in integers:
-// d = m 2^e exactly, so d^2 2^32 = m^2 2^(2e + 32) with m^2 < 2^48
-__device__ __forceinline__ unsigned long long sq_fix32(float d) {
-    const uint32_t b = __float_as_uint(d) & 0x7fffffffu;
-    const uint32_t E = b >> 23, M = b & 0x7fffffu;
-    const unsigned long long m = E ? (unsigned long long)(M | 0x800000u) : (unsigned long long)M;
-    const int e = E ? (int)E - 150 : -149;
-    const unsigned long long m2 = m * m;
-    const int sh = 2 * e + 32;
-    if (sh >= 0) return m2 << sh;
-    const int r = -sh;
-    if (r > 49) return 0ull;                       // value below 1/4
-    const unsigned long long q = m2 >> r, rem = m2 & ((1ull << r) - 1ull), half = 1ull << (r - 1);
-    return q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull);
-}
-
 // 128-bit sum of round((p - v_c)^2 2^32).  Each thread takes kSigmaIlp
 // particles at a time and issues all their loads before using any.
 constexpr int kSigmaIlp = 4;
-__global__ void __launch_bounds__(256) k_sigma(int64_t n, int nc, const int32_t* __restrict__ Qn,
-                                               const float* __restrict__ Pn,
+template <class Src>
+__global__ void __launch_bounds__(256) k_sigma(Src src, int64_t n, int nc,
                                                const float* __restrict__ vc,
                                                unsigned long long* d2, uint32_t* err) {
     const int64_t ncells = (int64_t)nc * nc * nc;
@@ -204,9 +227,10 @@ __global__ void __launch_bounds__(256) k_sigma(int64_t n, int nc, const int32_t*
 #pragma unroll
         for (int u = 0; u < kSigmaIlp; ++u) {
             const int64_t i = i0 + u * stride;
-            key[u] = i < n ? key_of(Qn, n, nc, i) : -1;
-#pragma unroll
-            for (int d = 0; d < 3; ++d) p[u][d] = i < n ? Pn[d * n + i] : 0.f;
+            int32_t q[3] = {0, 0, 0};
+            p[u][0] = p[u][1] = p[u][2] = 0.f;
+            if (i < n) src.load(i, q, p[u]);
+            key[u] = i < n ? key3(q, nc) : -1;
         }
 #pragma unroll
         for (int u = 0; u < kSigmaIlp; ++u)
@@ -270,10 +294,11 @@ __global__ void k_sigma_final(const unsigned long long* d2, int64_t n, float* si
 // Lanes with the same new cell take consecutive ranks from one atomic.  Each
 // warp handles two particles per lane at a time, and the cell's offset and
 // mean momentum are loaded before the rank atomic returns.
-__global__ void k_scatter(int64_t n, int nc, const int32_t* __restrict__ Qn, const float* __restrict__ Pn,
-                          const float* __restrict__ vc, const int64_t* __restrict__ offsets,
-                          int32_t* fill, const float* __restrict__ sigma_p,
-                          const float* __restrict__ E, uint8_t* __restrict__ out, uint32_t* err) {
+template <class Src>
+__global__ void k_scatter(Src src, int64_t n, int nc, const float* __restrict__ vc,
+                          const int64_t* __restrict__ offsets, int32_t* fill,
+                          const float* __restrict__ sigma_p, const float* __restrict__ E,
+                          uint8_t* __restrict__ out, uint32_t* err) {
     const int64_t ncells = (int64_t)nc * nc * nc;
     const float sigma = *sigma_p;
     const int lane = threadIdx.x & 31;
@@ -289,14 +314,10 @@ __global__ void k_scatter(int64_t n, int nc, const int32_t* __restrict__ Qn, con
         for (int u = 0; u < 2; ++u) {
             i[u] = base + u * stride + lane;
             const bool live = i[u] < n;
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                q[u][d] = live ? Qn[d * n + i[u]] : 0;
-                p[u][d] = live ? Pn[d * n + i[u]] : 0.f;
-            }
-            key[u] = live ? (int64_t)(q[u][0] >> 8) +
-                                nc * ((int64_t)(q[u][1] >> 8) + (int64_t)nc * (q[u][2] >> 8))
-                          : -1ll - lane;
+            q[u][0] = q[u][1] = q[u][2] = 0;
+            p[u][0] = p[u][1] = p[u][2] = 0.f;
+            if (live) src.load(i[u], q[u], p[u]);
+            key[u] = live ? key3(q[u], nc) : -1ll - lane;
         }
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
@@ -359,6 +380,19 @@ int scan_counts(Sim& s, const int32_t* counts, int64_t* offsets) {
     return check_launch(s, "scan");
 }
 
+// Offsets of the new counts, zeroed slot counters, and the new cell means
+// v_c = fl32(fl32(S 2^-24) / count) of buffer nxt.
+int scan_and_means(Sim& s, int nxt) {
+    const int64_t nb = (s.ncells + kScanTile - 1) / kScanTile;
+    cudaStream_t st = s.stream;
+    k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, st>>>(s.ncells, s.counts[nxt], s.blocksums);
+    k_scan_top<<<1, 1024, 0, st>>>(nb, s.blocksums, s.n, s.offsets[nxt] + s.ncells, s.err);
+    k_scan_apply<<<(unsigned)nb, kScanThreads, 0, st>>>(s.ncells, s.counts[nxt], s.blocksums,
+                                                        s.offsets[nxt], s.S, s.vc[nxt], s.fill);
+    s.launches += 3;
+    return check_launch(s, "scan");
+}
+
 // Encode s.Qn / s.Pn into the other store buffer and make it current.  With
 // counts_ready the new counts and momentum sums were accumulated already
 // (by the tile pass).
@@ -368,24 +402,22 @@ int encode_from_qp(Sim& s, bool counts_ready) {
     if (!counts_ready) {
         cudaMemsetAsync(s.counts[nxt], 0, sizeof(int32_t) * s.ncells, st);
         cudaMemsetAsync(s.S, 0, sizeof(unsigned long long) * 3 * s.ncells, st);
-        k_hist<<<grid_for(s.n, 256), 256, 0, st>>>(s.n, s.nc, s.Qn, s.Pn, s.counts[nxt], s.S, s.err);
+        k_hist<<<grid_for(s.n, 256), 256, 0, st>>>(QPArrays{s.Qn, s.Pn, s.n}, s.n, s.nc, s.counts[nxt],
+                                                   s.S, s.err);
         s.launches++;
     }
-    const int64_t nb = (s.ncells + kScanTile - 1) / kScanTile;
-    k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, st>>>(s.ncells, s.counts[nxt], s.blocksums);
-    k_scan_top<<<1, 1024, 0, st>>>(nb, s.blocksums, s.n, s.offsets[nxt] + s.ncells, s.err);
-    k_scan_apply<<<(unsigned)nb, kScanThreads, 0, st>>>(s.ncells, s.counts[nxt], s.blocksums,
-                                                        s.offsets[nxt], s.S, s.vc[nxt], s.fill);
-    s.launches += 3;
+    int rc = scan_and_means(s, nxt);
+    if (rc) return rc;
     prof_mark(s, 3);
     cudaMemsetAsync(s.d2, 0, 16, st);
-    k_sigma<<<grid_for(s.n, 256, 152 * 8), 256, 0, st>>>(s.n, s.nc, s.Qn, s.Pn, s.vc[nxt], s.d2, s.err);
+    k_sigma<<<grid_for(s.n, 256, 152 * 8), 256, 0, st>>>(QPArrays{s.Qn, s.Pn, s.n}, s.n, s.nc,
+                                                         s.vc[nxt], s.d2, s.err);
     k_sigma_final<<<1, 1, 0, st>>>(s.d2, s.n, s.sigma_d[nxt]);
     s.launches += 2;
     prof_mark(s, 4);
-    k_scatter<<<grid_for(s.n, 256), 256, 0, st>>>(s.n, s.nc, s.Qn, s.Pn, s.vc[nxt], s.offsets[nxt],
-                                                  s.fill, s.sigma_d[nxt], s.Eedge, s.streams[nxt],
-                                                  s.err);
+    k_scatter<<<grid_for(s.n, 256), 256, 0, st>>>(QPArrays{s.Qn, s.Pn, s.n}, s.n, s.nc, s.vc[nxt],
+                                                  s.offsets[nxt], s.fill, s.sigma_d[nxt], s.Eedge,
+                                                  s.streams[nxt], s.err);
     s.launches++;
     prof_mark(s, 5);
     s.cur = nxt;
@@ -393,6 +425,61 @@ int encode_from_qp(Sim& s, bool counts_ready) {
     s.have_state = true;
     s.loaded = 15;
     return check_launch(s, "encode");
+}
+
+// Low-memory initial conditions: encode (Q, p) computed from the float32
+// displacement field straight into store 0 (the same kernels as the step's
+// re-encode, reading the field instead of per-particle buffers).
+int encode_from_psi(Sim& s, const double* scale) {
+    cudaStream_t st = s.stream;
+    const QPFromPsi src{s.ic_psi, scale, s.np, s.nc, s.cfg.a_init, pow(s.cfg.a_init, 1.5),
+                        4.0 * s.nc / (double)s.np, s.n};
+    s.cur = 1;
+    const int nxt = 0;
+    cudaMemsetAsync(s.counts[nxt], 0, sizeof(int32_t) * s.ncells, st);
+    cudaMemsetAsync(s.S, 0, sizeof(unsigned long long) * 3 * s.ncells, st);
+    k_hist<<<grid_for(s.n, 256), 256, 0, st>>>(src, s.n, s.nc, s.counts[nxt], s.S, s.err);
+    s.launches++;
+    int rc = scan_and_means(s, nxt);
+    if (rc) return rc;
+    cudaMemsetAsync(s.d2, 0, 16, st);
+    k_sigma<<<grid_for(s.n, 256, 152 * 8), 256, 0, st>>>(src, s.n, s.nc, s.vc[nxt], s.d2, s.err);
+    k_sigma_final<<<1, 1, 0, st>>>(s.d2, s.n, s.sigma_d[nxt]);
+    k_scatter<<<grid_for(s.n, 256), 256, 0, st>>>(src, s.n, s.nc, s.vc[nxt], s.offsets[nxt], s.fill,
+                                                  s.sigma_d[nxt], s.Eedge, s.streams[nxt], s.err);
+    s.launches += 3;
+    s.cur = nxt;
+    s.offsets_valid = true;
+    s.have_state = true;
+    s.loaded = 15;
+    return check_launch(s, "encode");
+}
+
+// The three low-memory tile passes of one step (PMPM_FLAG_LOWMEM): new-cell
+// counts and momentum sums, scan and cell means, the exact dispersion sum,
+// then re-encode and scatter into the other store buffer.
+int lowmem_passes(Sim& s) {
+    const int nxt = 1 - s.cur;
+    cudaStream_t st = s.stream;
+    int rc;
+    cudaMemsetAsync(s.counts[nxt], 0, sizeof(int32_t) * s.ncells, st);
+    cudaMemsetAsync(s.S, 0, sizeof(unsigned long long) * 3 * s.ncells, st);
+    if ((rc = tile_pass(s, 2, nullptr))) return rc;
+    prof_mark(s, 2);
+    if ((rc = scan_and_means(s, nxt))) return rc;
+    prof_mark(s, 3);
+    cudaMemsetAsync(s.d2, 0, 16, st);
+    if ((rc = tile_pass(s, 3, nullptr))) return rc;
+    k_sigma_final<<<1, 1, 0, st>>>(s.d2, s.n, s.sigma_d[nxt]);
+    s.launches++;
+    prof_mark(s, 4);
+    if ((rc = tile_pass(s, 4, nullptr))) return rc;
+    prof_mark(s, 5);
+    s.cur = nxt;
+    s.offsets_valid = true;
+    s.have_state = true;
+    s.loaded = 15;
+    return check_launch(s, "low-memory step");
 }
 
 int decode_state(Sim& s) {

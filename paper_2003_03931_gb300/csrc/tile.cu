@@ -23,10 +23,11 @@ __device__ unsigned long long g_phase[4096 * kMarks];
     } while (0)
 #endif
 
-template <int D>
+template <int D, bool LM>
 __device__ __forceinline__ void tile_component(int tid, const TileGeom& g, const TileParams& P,
                                                const float* gS, const float2* C, float2* W,
-                                               TileCells cells) {
+                                               TileCells cells, CtaScratch cs,
+                                               unsigned long long& lo, unsigned long long& hi) {
     __syncthreads();
     PMPM_MARK(7 + 4 * D);
     tile_inv_z<D>(tid, g, gS, C, W);
@@ -38,22 +39,58 @@ __device__ __forceinline__ void tile_component(int tid, const TileGeom& g, const
     tile_inv_x(tid, g, W);
     __syncthreads();
     PMPM_MARK(10 + 4 * D);
-    tile_interp<D>(tid, g, P, W, cells);
+    tile_interp<D, LM>(tid, g, P, W, cells, cs, lo, hi);
 }
 
-__global__ void __launch_bounds__(kTileThreads, 1) k_tile(TileParams P) {
-    extern __shared__ __align__(16) unsigned char tile_smem[];
+// 128-bit block sum of the dispersion terms (low-memory mode 3), staged in
+// the free W area, added to d2 by thread 0.
+__device__ __forceinline__ void tile_sigma_flush(int tid, const TileParams& P, float2* W,
+                                                 unsigned long long lo, unsigned long long hi) {
+    unsigned long long* sh = reinterpret_cast<unsigned long long*>(W);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long l2 = __shfl_down_sync(0xffffffffu, lo, o);
+        const unsigned long long h2 = __shfl_down_sync(0xffffffffu, hi, o);
+        lo += l2;
+        hi += h2 + (lo < l2 ? 1ull : 0ull);
+    }
+    __syncthreads();
+    if ((tid & 31) == 0) {
+        sh[2 * (tid >> 5)] = lo;
+        sh[2 * (tid >> 5) + 1] = hi;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        lo = 0;
+        hi = 0;
+        for (int w = 0; w < kTileThreads / 32; ++w) {
+            lo += sh[2 * w];
+            hi += sh[2 * w + 1] + (lo < sh[2 * w] ? 1ull : 0ull);
+        }
+        if (lo | hi) {
+            const unsigned long long old = atomicAdd(&P.d2[0], lo);
+            const unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
+            if (hi + carry) atomicAdd(&P.d2[1], hi + carry);
+        }
+    }
+}
+
+// The whole tile: prologue, cell tables, deposit, forward transform, then
+// per force component the Green multiply, inverse transform and
+// interpolation (phases of tile_core.cuh with a block barrier between).
+template <bool LM>
+__device__ __forceinline__ void tile_body(int tile, bool first, const TileParams& P,
+                                          unsigned char* tile_smem, CtaScratch cs) {
     uint32_t* R = reinterpret_cast<uint32_t*>(tile_smem);
     float2* C = reinterpret_cast<float2*>(tile_smem);
     float2* W = reinterpret_cast<float2*>(tile_smem + (size_t)kTileR * 4);
     float* gS = reinterpret_cast<float*>(tile_smem + (size_t)kTileR * 4 + (size_t)kTileW * 8);
     int* O = reinterpret_cast<int*>(gS + kGreenPacked);
     const int tid = threadIdx.x;
-    const TileGeom g = tile_geom(blockIdx.x, P.nc, P.nt);
-
+    const TileGeom g = tile_geom(tile, P.nc, P.nt);
     const TileCells cells = tile_cells(W, O);   // W is free until phase 5
     PMPM_MARK(0);
-    tile_prologue(tid, g, P, cells, R, gS);
+    tile_prologue(tid, g, P, cells, R, gS, first);
     __syncthreads();
     PMPM_MARK(1);
     tile_cells_scan(tid, g, cells);
@@ -61,7 +98,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(TileParams P) {
     tile_cells_map(tid, g, cells);
     __syncthreads();
     PMPM_MARK(2);
-    tile_deposit_flat(tid, g, P, R, cells);
+    tile_deposit_flat<LM>(tid, g, P, R, cells, cs);
     __syncthreads();
     PMPM_MARK(3);
     tile_fwd_x(tid, R);
@@ -71,19 +108,47 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(TileParams P) {
     __syncthreads();
     PMPM_MARK(5);
     tile_fwd_z(tid, C);
-    tile_component<0>(tid, g, P, gS, C, W, cells);
-    tile_component<1>(tid, g, P, gS, C, W, cells);
-    tile_component<2>(tid, g, P, gS, C, W, cells);
+    unsigned long long lo = 0, hi = 0;
+    tile_component<0, LM>(tid, g, P, gS, C, W, cells, cs, lo, hi);
+    tile_component<1, LM>(tid, g, P, gS, C, W, cells, cs, lo, hi);
+    tile_component<2, LM>(tid, g, P, gS, C, W, cells, cs, lo, hi);
+    if (LM && P.mode == 3) tile_sigma_flush(tid, P, W, lo, hi);
     __syncthreads();
     PMPM_MARK(19);
 }
 
+// One CTA per SM (the tile needs 231 KB of shared memory): one CTA per tile.
+__global__ void __launch_bounds__(kTileThreads, 1) k_tile(TileParams P) {
+    extern __shared__ __align__(16) unsigned char tile_smem[];
+    tile_body<false>((int)blockIdx.x, true, P, tile_smem, CtaScratch{nullptr, nullptr});
+}
+
+// Low-memory passes (modes 2-4): one resident CTA per SM takes tiles from
+// a counter (its first tile is blockIdx.x) and keeps its scratch slot.
+__global__ void __launch_bounds__(kTileThreads, 1) k_tile_lowmem(TileParams P, int* next_tile) {
+    extern __shared__ __align__(16) unsigned char tile_smem[];
+    __shared__ int next;
+    const CtaScratch cs{P.sp + (size_t)blockIdx.x * 3 * kLowmemCap,
+                        P.sq + (size_t)blockIdx.x * 2 * kLowmemCap};
+    const int ntiles = P.nt * P.nt * P.nt;
+    int tile = blockIdx.x;
+    bool first = true;
+    while (tile < ntiles) {
+        tile_body<true>(tile, first, P, tile_smem, cs);
+        first = false;
+        if (threadIdx.x == 0) next = (int)gridDim.x + atomicAdd(next_tile, 1);
+        __syncthreads();
+        tile = next;
+    }
+}
+
 void tile_setup() {
     cudaFuncSetAttribute(k_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemBytes);
+    cudaFuncSetAttribute(k_tile_lowmem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemBytes);
 }
 
 int tile_pass(Sim& s, int mode, float* G) {
-    TileParams P;
+    TileParams P{};
     P.nc = s.nc;
     P.nt = s.nt;
     P.n = s.n;
@@ -107,7 +172,25 @@ int tile_pass(Sim& s, int mode, float* G) {
     P.Pn = s.Pn;
     P.err = s.err;
     const int ntiles = s.nt * s.nt * s.nt;
-    k_tile<<<ntiles, kTileThreads, kTileSmemBytes, s.stream>>>(P);
+    int grid = ntiles;
+    if (mode >= 2) {
+        const int nxt = 1 - s.cur;
+        P.sp = s.lm_sp;
+        P.sq = s.lm_sq;
+        P.counts_new = s.counts[nxt];
+        P.S = s.S;
+        P.vc_new = s.vc[nxt];
+        P.d2 = s.d2;
+        P.offsets_new = s.offsets[nxt];
+        P.fill = s.fill;
+        P.sigma_new = s.sigma_d[nxt];
+        P.E = s.Eedge;
+        P.out = s.streams[nxt];
+        grid = ntiles < s.lm_grid ? ntiles : s.lm_grid;
+        cudaMemsetAsync(s.lm_next, 0, sizeof(int), s.stream);
+    }
+    if (mode >= 2) k_tile_lowmem<<<grid, kTileThreads, kTileSmemBytes, s.stream>>>(P, s.lm_next);
+    else k_tile<<<grid, kTileThreads, kTileSmemBytes, s.stream>>>(P);
     s.launches++;
     return check_launch(s, "tile pass");
 }

@@ -66,6 +66,26 @@ struct TileParams {
     int32_t* Qn;                  // [3][N] new codes (mode 1)
     float* Pn;                    // [3][N] new momenta (mode 1)
     uint32_t* err;
+    // low-memory passes: mode 2 counts the new cells and sums their momenta,
+    // mode 3 sums the squared deviations (Eq. 3), mode 4 re-encodes and
+    // scatters (Sec. III-A); per-CTA scratch of kLowmemCap own particles
+    float* sp;                    // [CTAs][3][kLowmemCap] parked long-range force, new momenta
+    int32_t* sq;                  // [CTAs][2][kLowmemCap] new codes of components 0 and 1
+    int32_t* counts_new;          // [nc^3] (mode 2)
+    unsigned long long* S;        // [3][nc^3] momentum sums in units of 2^-24 (mode 2)
+    const float* vc_new;          // [3][nc^3] (modes 3, 4)
+    unsigned long long* d2;       // [2] 128-bit dispersion sum (mode 3)
+    const int64_t* offsets_new;   // [nc^3 + 1] (mode 4)
+    int32_t* fill;                // [nc^3] slots taken per new cell (mode 4)
+    const float* sigma_new;       // device scalar (mode 4)
+    const float* E;               // [256] velocity bin edges (mode 4)
+    uint8_t* out;                 // [6][N] new store (mode 4)
+};
+
+// This CTA's part of the low-memory scratch.
+struct CtaScratch {
+    float* sp;       // [3][kLowmemCap]
+    int32_t* sq;     // [2][kLowmemCap]
 };
 
 struct TileGeom {
@@ -328,7 +348,7 @@ struct TileCells {
     int* ppre;         // [kOwnMax + 1] exclusive prefix over the tile's own cells (O)
     int* prel;         // [kOwnMax] storage offset of own cell p minus own_base (O)
     int* misc;         // [0..1] own_base (int64), [2] largest halo-cell count,
-                       // [4] sigma, [5] kick, [6] drift as float bits (O)
+                       // [4] sigma, [5] kick, [6] drift, [7] new sigma as float bits (O)
     int* tot;          // [kHaloChunks] particles per 32-cell chunk of the halo box (W)
     int* cmax;         // [kHaloChunks] largest cell count per chunk (W)
 };
@@ -380,7 +400,7 @@ PMPM_HD int own_to_halo(int p) {
 // the packed Green table, sigma and the step factors) is issued before the
 // first shared-memory store, so the tile waits for one memory round trip.
 PMPM_HD void tile_prologue(int tid, const TileGeom& g, const TileParams& P, TileCells c,
-                           uint32_t* R, float* gS) {
+                           uint32_t* R, float* gS, bool load_green) {
     const int hx = g.c1[0] - g.c0[0] + 4, hy = g.c1[1] - g.c0[1] + 4, hz = g.c1[2] - g.c0[2] + 4;
     int64_t st[2] = {0, 0};
     int cnt[2] = {0, 0};
@@ -400,15 +420,16 @@ PMPM_HD void tile_prologue(int tid, const TileGeom& g, const TileParams& P, Tile
 #pragma unroll
     for (int u = 0; u < (kGreenPacked + kTileThreads - 1) / kTileThreads; ++u) {
         const int i = tid + u * kTileThreads;
-        gv[u] = i < kGreenPacked ? P.green[i] : 0.f;
+        gv[u] = (load_green && i < kGreenPacked) ? P.green[i] : 0.f;
     }
-    float sc[3] = {0.f, 0.f, 0.f};
+    float sc[4] = {0.f, 0.f, 0.f, 0.f};
     if (tid == 0) {
         sc[0] = *P.sigma;
-        if (P.mode == 1) {
+        if (P.mode >= 1) {
             sc[1] = P.kd[0];
             sc[2] = P.kd[1];
         }
+        if (P.mode == 4) sc[3] = *P.sigma_new;
     }
     tile_zero(tid, R);
 #pragma unroll
@@ -422,12 +443,13 @@ PMPM_HD void tile_prologue(int tid, const TileGeom& g, const TileParams& P, Tile
 #pragma unroll
     for (int u = 0; u < (kGreenPacked + kTileThreads - 1) / kTileThreads; ++u) {
         const int i = tid + u * kTileThreads;
-        if (i < kGreenPacked) gS[i] = gv[u];
+        if (load_green && i < kGreenPacked) gS[i] = gv[u];
     }
     if (tid == 0) {
         c.misc[4] = f32_to_bits(sc[0]);
         c.misc[5] = f32_to_bits(sc[1]);
         c.misc[6] = f32_to_bits(sc[2]);
+        c.misc[7] = f32_to_bits(sc[3]);
     }
 }
 
@@ -618,8 +640,9 @@ PMPM_HD int own_of(const TileCells& c, int v) {
 constexpr int kDepositIlp = 4;   // halo particles per thread per iteration
 constexpr int kGatherIlp = 2;    // own particles per thread per iteration
 
+template <bool LM>
 PMPM_HD void tile_deposit_flat(int tid, const TileGeom& g, const TileParams& P, uint32_t* R,
-                               TileCells c) {
+                               TileCells c, CtaScratch cs) {
     const int total = c.pre[kHaloMax];
     const bool check = c.misc[2] > 255;
     for (int v0 = tid; v0 < total; v0 += kDepositIlp * kTileThreads) {
@@ -668,6 +691,16 @@ PMPM_HD void tile_deposit_flat(int tid, const TileGeom& g, const TileParams& P, 
             if (j[u] < 0) continue;
             float gc[3];
             coarse_gather(P, Q[u], gc);
+            if (LM) {
+                const int v = v0 + u * kTileThreads;
+                if (v >= kLowmemCap) {
+                    flag_error(P.err, kErrScratch);
+                    continue;
+                }
+#pragma unroll
+                for (int e = 0; e < 3; ++e) cs.sp[e * kLowmemCap + v] = gc[e];
+                continue;
+            }
 #pragma unroll
             for (int e = 0; e < 3; ++e) slot[e * P.n + j[u]] = gc[e];
         }
@@ -834,15 +867,65 @@ PMPM_HD void tile_inv_x(int tid, const TileGeom& g, float2* W) {
 
 // --- phase 5d: interpolate component D to the tile's own particles, add the
 // parked long-range part, then (mode 1) kick and drift that component.
-template <int D>
+// Low-memory passes: the new cell of one particle from its three new codes,
+// then mode 2 (count and momentum sums, as the default step's histogram),
+// mode 3 (squared deviation from the new cell mean, exact 128-bit sum in
+// lo/hi), or mode 4 (slot in the new cell, Eq. 2-3 re-encode).
+PMPM_HD void lowmem_particle(const TileParams& P, const int32_t (&q)[3], const float (&p)[3],
+                             float sigma_new, unsigned long long& lo, unsigned long long& hi) {
+    const int64_t C = (int64_t)P.nc * P.nc * P.nc;
+    const int64_t key = (int64_t)(q[0] >> 8) + P.nc * ((int64_t)(q[1] >> 8) + (int64_t)P.nc * (q[2] >> 8));
+    if (P.mode == 2) {
+        gmem_add_i32(&P.counts_new[key], 1);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            long long fx = 0;
+            if (fabsf(p[d]) < 1048576.f) fx = f64_to_ll_rn((double)p[d] * 16777216.0);
+            else flag_error(P.err, p[d] == p[d] ? kErrMomentum : kErrNaN);
+            gmem_add_u64(&P.S[d * C + key], (unsigned long long)fx);
+        }
+    } else if (P.mode == 3) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const float dev = fsub_rn(p[d], P.vc_new[d * C + key]);
+            if (!(fabsf(dev) < 65536.f)) {
+                flag_error(P.err, kErrDeviation);
+                continue;
+            }
+            const unsigned long long t = sq_fix32(dev);
+            lo += t;
+            if (lo < t) ++hi;
+        }
+    } else {
+        // every pass recomputes the same codes, so a cell never receives more
+        // particles than the counting pass gave it; checked all the same
+        const int rank = fetch_add_i32(&P.fill[key], 1);
+        const int64_t slot = P.offsets_new[key] + rank;
+        if (slot >= P.offsets_new[key + 1]) {
+            flag_error(P.err, kErrCount);
+            return;
+        }
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            P.out[d * P.n + slot] = (uint8_t)(q[d] & 255);
+            P.out[(3 + d) * P.n + slot] =
+                (uint8_t)encode_momentum(p[d], P.vc_new[d * C + key], sigma_new, P.E, P.err);
+        }
+    }
+}
+
+// LM: the low-memory passes (modes 2-4); otherwise modes 0 and 1.
+template <int D, bool LM>
 PMPM_HD void tile_interp(int tid, const TileGeom& g, const TileParams& P, const float2* W,
-                         TileCells c) {
-    constexpr int U = 2;   // particles per thread per iteration, loads issued together
+                         TileCells c, CtaScratch cs, unsigned long long& lo, unsigned long long& hi) {
+    constexpr int U = LM ? 1 : 2;   // particles per thread per iteration, loads issued together
     const float* Wf = reinterpret_cast<const float*>(W);
     const int64_t ncells = (int64_t)P.nc * P.nc * P.nc;
     const int64_t n = P.n;
+    constexpr bool lm = LM;
     const float sigma = bits_to_f32(c.misc[4]);
     const float kick = bits_to_f32(c.misc[5]), drift = bits_to_f32(c.misc[6]);
+    const float sigma_new = bits_to_f32(c.misc[7]);
     const uint8_t* ud = D == 0 ? P.u0 : (D == 1 ? P.u1 : P.u2);
     float* slot = P.mode == 0 ? P.G : P.Pn;
     const int ptotal = c.ppre[kOwnMax];
@@ -855,7 +938,7 @@ PMPM_HD void tile_interp(int tid, const TileGeom& g, const TileParams& P, const 
         for (int u = 0; u < U; ++u) {
             const int v = v0 + u * kTileThreads;
             const int p = v < ptotal ? prefix_find(c.ppre, kOwnMax, v) : 0;
-            j[u] = v < ptotal ? base + c.prel[p] + (v - c.ppre[p]) : -1;
+            j[u] = (v < ptotal && (!lm || v < kLowmemCap)) ? base + c.prel[p] + (v - c.ppre[p]) : -1;
             const int cx = g.c0[0] + p % kOwnDim, cy = g.c0[1] + (p / kOwnDim) % kOwnDim,
                       cz = g.c0[2] + p / (kOwnDim * kOwnDim);
             cell[u] = cx + (int64_t)P.nc * (cy + (int64_t)P.nc * cz);
@@ -863,8 +946,8 @@ PMPM_HD void tile_interp(int tid, const TileGeom& g, const TileParams& P, const 
                 Q[u][0] = (int64_t)cx * kBins + P.m0[j[u]];
                 Q[u][1] = (int64_t)cy * kBins + P.m1[j[u]];
                 Q[u][2] = (int64_t)cz * kBins + P.m2[j[u]];
-                gcd[u] = slot[D * n + j[u]];
-                if (P.mode == 1) {
+                gcd[u] = lm ? cs.sp[D * kLowmemCap + v] : slot[D * n + j[u]];
+                if (lm || P.mode >= 1) {
                     u8[u] = ud[j[u]];
                     vcd[u] = P.vc[D * ncells + cell[u]];
                 }
@@ -874,11 +957,11 @@ PMPM_HD void tile_interp(int tid, const TileGeom& g, const TileParams& P, const 
         for (int u = 0; u < U; ++u) {
             if (j[u] < 0) continue;
             // fine gather
-            int lo[3], w1[3];
+            int lo3[3], w1[3];
 #pragma unroll
             for (int e = 0; e < 3; ++e) {
                 const int s = (int)(2 * Q[u][e] + 1 - kCodesPerFine - 128 * (int64_t)g.o[e]);
-                lo[e] = (s >> 7) - (kBuffer - 1);
+                lo3[e] = (s >> 7) - (kBuffer - 1);
                 w1[e] = s & 127;
             }
             float gf = 0.f;
@@ -887,10 +970,10 @@ PMPM_HD void tile_interp(int tid, const TileGeom& g, const TileParams& P, const 
                 const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
                 const float w = (float)((dx ? w1[0] : 128 - w1[0]) * (dy ? w1[1] : 128 - w1[1]) *
                                         (dz ? w1[2] : 128 - w1[2]));
-                gf += w * Wf[wfidx(lo[0] + dx, lo[1] + dy, lo[2] + dz)];
+                gf += w * Wf[wfidx(lo3[0] + dx, lo3[1] + dy, lo3[2] + dz)];
             }
             const float gval = gf * 4.76837158203125e-07f + gcd[u];   // 2^-21
-            if (P.mode == 0) {
+            if (!lm && P.mode == 0) {
                 slot[D * n + j[u]] = gval;
                 continue;
             }
@@ -906,8 +989,20 @@ PMPM_HD void tile_interp(int tid, const TileGeom& g, const TileParams& P, const 
             const int64_t M = (int64_t)P.nc * kBins;
             int64_t qn = (Q[u][D] + dq) % M;
             if (qn < 0) qn += M;
-            P.Qn[D * n + j[u]] = (int32_t)qn;
-            P.Pn[D * n + j[u]] = pn;
+            if (!lm) {
+                P.Qn[D * n + j[u]] = (int32_t)qn;
+                P.Pn[D * n + j[u]] = pn;
+                continue;
+            }
+            const int v = v0 + u * kTileThreads;
+            if (D < 2) {
+                cs.sp[D * kLowmemCap + v] = pn;
+                cs.sq[D * kLowmemCap + v] = (int32_t)qn;
+                continue;
+            }
+            const int32_t qa[3] = {cs.sq[v], cs.sq[kLowmemCap + v], (int32_t)qn};
+            const float pa[3] = {cs.sp[v], cs.sp[kLowmemCap + v], pn};
+            lowmem_particle(P, qa, pa, sigma_new, lo, hi);
         }
     }
 }

@@ -25,11 +25,13 @@ class SimConfig:
     pos_bytes: int = 1
     vel_bytes: int = 1
     pk_mesh_max: int = 0
+    lowmem: bool = False    # three tile passes per step, no per-particle intermediate
 
     def to_c(self):
         c = _lib.Config()
         c.np, c.nc, c.tile_max, c.buffer = self.np, self.nc, self.tile_max, self.buffer
         c.pos_bytes, c.vel_bytes, c.pk_mesh_max = self.pos_bytes, self.vel_bytes, self.pk_mesh_max
+        c.flags = _lib.FLAG_LOWMEM if self.lowmem else 0
         c.a_init, c.a_final, c.n_steps = self.a_init, self.a_final, self.n_steps
         return c
 

@@ -67,3 +67,25 @@ def test_init_without_device_fails_cleanly(lib):
     h = ctypes.c_void_p()
     rc = lib.pmpm_init(ctypes.byref(c), ctypes.c_void_p(256), 1 << 30, None, ctypes.byref(h))
     assert rc != _lib.PMPM_OK
+
+
+def test_lowmem_workspace_fits_2048_cubed(lib):
+    # the low-memory step keeps no per-particle intermediate: 2048^3 particles
+    # (nc = 1024) need about 25 bytes per particle, inside one GB300's HBM
+    from paper_2003_03931_gb300.sim import SimConfig, workspace_bytes
+    from paper_2003_03931_gb300._lib import PmpmError
+    big = SimConfig(np=2048, nc=1024, n_steps=20, lowmem=True)
+    b = workspace_bytes(big)
+    assert b < 230e9
+    assert b / 2048 ** 3 < 26
+    assert workspace_bytes(SimConfig(np=2048, nc=1024, n_steps=20)) > 3 * b
+    # store (2 x 6 B), cell arrays and the float32 IC field must all be there
+    assert b > (12 + 12) * 2048 ** 3
+    with pytest.raises(PmpmError):
+        c = SimConfig(np=32, nc=16)
+        cc = c.to_c()
+        cc.flags = 6
+        import ctypes
+        from paper_2003_03931_gb300 import _lib
+        out = ctypes.c_size_t(0)
+        _lib.check(lib.pmpm_workspace_bytes(ctypes.byref(cc), ctypes.byref(out)))
