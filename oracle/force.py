@@ -23,7 +23,7 @@ tile plus a buffer of r_cut on each side.
 
 import numpy as np
 
-from . import cic, kernels
+from . import cic, codec, kernels
 
 
 class ForceOperator:
@@ -86,3 +86,82 @@ class ForceOperator:
         if parts:
             return gs, gl
         return gs + gl
+
+
+# ---------------------------------------------------------------- large boxes
+# For boxes whose fine mesh is too large for a float64 FFT here, the same
+# force at a few chosen particles.  Both follow the definitions above:
+# the coarse density in chunks of particles (integer, so the sum is the
+# same), and F_s at the chosen particles' CIC nodes by the direct sum
+# F_s(b) = sum_{0 < |d| < r_cut} K_s(d) rho_f(b - d), K_s vanishing beyond
+# r_cut (Sec. II), over the fine density of the particles near them.
+
+def coarse_density_chunked(Q, nc, pos_bytes=1, chunk=1 << 22):
+    """``cic.deposit`` on the coarse mesh, accumulated chunk by chunk."""
+    Q = np.asarray(Q)
+    n3 = nc ** 3
+    rho = np.zeros(n3, dtype=np.int64)
+    for s in range(0, Q.shape[0], chunk):
+        node, w = cic.corners(Q[s:s + chunk], nc, kernels.RATIO, pos_bytes)
+        # per-chunk node sums stay below 2^53, so float64 bincount is exact
+        rho += np.rint(np.bincount(node.ravel(), weights=w.ravel().astype(np.float64),
+                                   minlength=n3)).astype(np.int64)
+    return rho.reshape(nc, nc, nc)
+
+
+def coarse_field_from_density(rho_c, nc, pos_bytes=1):
+    """F_l on the coarse mesh from a given integer coarse density."""
+    U = cic.node_units(kernels.RATIO, pos_bytes)
+    rho = rho_c.astype(np.float64) / float((2 * U) ** 3)
+    rho_hat = np.fft.rfftn(rho)
+    K = kernels.coarse_kernel_table(nc)
+    return np.stack([np.fft.irfftn(rho_hat * np.fft.rfftn(K[c]), s=rho.shape, axes=(0, 1, 2))
+                     for c in range(3)])
+
+
+def sampled_fine_force(Q, counts, nc, idx, pos_bytes=1):
+    """F_s gathered at particles ``idx`` of a cell-ordered store (codes Q
+    [N, 3] in storage order, per-cell ``counts``), [len(idx), 3] float64.
+
+    Every fine node within r_cut of a chosen particle's CIC nodes only
+    receives mass from particles at most 8 fine cells (2 coarse cells) away,
+    so the 5^3 coarse cells around the particle's own cell hold all of it.
+    """
+    Q = np.asarray(Q, dtype=np.int64)
+    nf = kernels.RATIO * nc
+    B = codec.bins_per_cell(pos_bytes)
+    U = cic.node_units(1, pos_bytes)
+    unit = float((2 * U) ** 3)
+    d, Ks = kernels.fine_kernel_values(nc)
+    offsets = np.concatenate([[0], np.cumsum(np.asarray(counts, dtype=np.int64))])
+    r = np.arange(-2, 3)
+    out = np.zeros((len(idx), 3))
+    for k, i in enumerate(idx):
+        c = Q[i] // B
+        cz, cy, cx = np.meshgrid(r + c[2], r + c[1], r + c[0], indexing="ij")
+        cells = np.mod(cx, nc) + nc * (np.mod(cy, nc) + nc * np.mod(cz, nc))
+        near = np.concatenate([np.arange(offsets[j], offsets[j + 1]) for j in cells.ravel()])
+        node, w = cic.corners(Q[near], nf, 1, pos_bytes)
+        keys, inv = np.unique(node.ravel(), return_inverse=True)
+        mass = np.bincount(inv, weights=w.ravel().astype(np.float64)) / unit
+        bnode, bw = cic.corners(Q[i:i + 1], nf, 1, pos_bytes)
+        for b, wb in zip(bnode[0], bw[0]):
+            bx, by, bz = b % nf, (b // nf) % nf, b // (nf * nf)
+            src = (np.mod(bx - d[:, 0], nf) + nf * (np.mod(by - d[:, 1], nf) +
+                                                   nf * np.mod(bz - d[:, 2], nf)))
+            pos = np.searchsorted(keys, src)
+            pos[pos == len(keys)] = 0
+            rho = np.where(keys[pos] == src, mass[pos], 0.0)
+            out[k] += (wb / unit) * (Ks * rho[:, None]).sum(axis=0)
+    return out
+
+
+def sampled_force(Q, counts, nc, idx, Fl=None, pos_bytes=1):
+    """g = F_s + F_l gathered at particles ``idx``; ``Fl`` is the coarse
+    field (computed from the chunked coarse density when not given)."""
+    Q = np.asarray(Q, dtype=np.int64)
+    if Fl is None:
+        Fl = coarse_field_from_density(coarse_density_chunked(Q, nc, pos_bytes), nc, pos_bytes)
+    gl = np.stack([cic.interpolate(Fl[c], Q[idx], kernels.RATIO, pos_bytes) for c in range(3)], axis=1)
+    return sampled_fine_force(Q, counts, nc, idx, pos_bytes) + gl
+

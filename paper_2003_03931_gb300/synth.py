@@ -16,6 +16,8 @@ WORKLOADS = {
     "c4sub_256": dict(np=256, nc=128, a_init=0.02, a_final=1.0, n_steps=20),
     # small ragged-tile case: 7 tiles of 4/5 coarse cells per side
     "ragged_32": dict(np=32, nc=32, a_init=0.02, a_final=1.0, n_steps=10),
+    # 2048^3 particles (51.5 GB at 6 B/particle) on one GPU: low-memory step
+    "c4_2048": dict(np=2048, nc=1024, a_init=0.02, a_final=1.0, n_steps=20, lowmem=True),
 }
 
 IC_SPECTRUM = dict(slope=-1.5, k_c=np.pi / 2, rms_disp=0.3)
