@@ -155,23 +155,6 @@ def kick_drift(Q, p32, g, kick, drift, nc, pos_bytes=1):
     return Q_new, p_new
 
 
-def kick_drift_f32(Q, p32, g32, kick, drift, nc, pos_bytes=1):
-    """The same kick and drift with the kick also in float32 operations,
-    p' = fl32(p + fl32(fl32(kick) g)), the order a float32 kernel uses.  The
-    paper fixes no precision for the integrator; this variant lets a test
-    feed a float32 force field in and expect the kernel's integer codes and
-    float32 momenta exactly."""
-    U = codec.code_units_per_fine_cell(pos_bytes)
-    B = codec.bins_per_cell(pos_bytes)
-    k32 = np.float32(kick)
-    kg = (k32 * np.asarray(g32, dtype=np.float32)).astype(np.float32)
-    p_new = (np.asarray(p32, dtype=np.float32) + kg).astype(np.float32)
-    cd = np.float32(drift * U)
-    dq = np.floor((p_new * cd).astype(np.float32) + np.float32(0.5)).astype(np.int64)
-    Q_new = np.mod(np.asarray(Q, dtype=np.int64) + dq, nc * B)
-    return Q_new, p_new
-
-
 class Simulation:
     """Plain PM-PM evolution of a compressed state (oracle)."""
 

@@ -27,10 +27,10 @@ def nvcc():
     return path
 
 
-def _compile(unit, verbose):
+def _compile(unit, verbose, build_dir, defines):
     src = os.path.join(SRC, unit)
-    obj = os.path.join(BUILD, unit.replace(".cu", ".o"))
-    cmd = [nvcc(), *ARCH, *FLAGS, "-c", src, "-o", obj]
+    obj = os.path.join(build_dir, unit.replace(".cu", ".o"))
+    cmd = [nvcc(), *ARCH, *FLAGS, *["-D" + d for d in defines], "-c", src, "-o", obj]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -39,28 +39,32 @@ def _compile(unit, verbose):
     return obj, r.stderr
 
 
-def build(verbose=False, force=False):
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose=False, force=False, defines=(), lib=None, build_dir=None):
+    """Build libpmpm.so (or, with ``lib``/``build_dir``, a variant compiled
+    with extra preprocessor ``defines``); returns the library path."""
+    lib = lib or LIB
+    build_dir = build_dir or BUILD
+    os.makedirs(build_dir, exist_ok=True)
     sources = [os.path.join(SRC, u) for u in UNITS]
     headers = [os.path.join(SRC, f) for f in os.listdir(SRC) if f.endswith(".cuh")]
     headers.append(os.path.join(os.path.dirname(HERE), "include", "pmpm.h"))
-    if not force and os.path.exists(LIB):
+    if not force and os.path.exists(lib):
         newest = max(os.path.getmtime(p) for p in sources + headers + [__file__])
-        if os.path.getmtime(LIB) >= newest:
-            return LIB
+        if os.path.getmtime(lib) >= newest:
+            return lib
     with concurrent.futures.ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
-        results = list(ex.map(lambda u: _compile(u, verbose), UNITS))
+        results = list(ex.map(lambda u: _compile(u, verbose, build_dir, defines), UNITS))
     if verbose:
         for _, log in results:
             sys.stderr.write(log)
     objs = [o for o, _ in results]
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -225,26 +225,3 @@ def test_sampled_force_equals_whole_mesh_force():
     np.testing.assert_allclose(fs, gs[idx], rtol=1e-9, atol=1e-12 * np.abs(gs).max())
     g = force.sampled_force(Q, st.counts, 16, idx)
     np.testing.assert_allclose(g, (gs + gl)[idx], rtol=1e-9, atol=1e-12 * np.abs(gs + gl).max())
-
-
-def test_float32_kick_matches_float64_kick_to_rounding():
-    # the float32-operation kick differs from the float64 one by at most two
-    # float32 roundings; the drift codes differ only where fl32 products straddle .5
-    from oracle import dynamics
-    rng = np.random.default_rng(2)
-    n = 20000
-    Q = rng.integers(0, 16 * 256, size=(n, 3))
-    p = rng.normal(0, 3, size=(n, 3)).astype(np.float32)
-    g = rng.normal(0, 50, size=(n, 3)).astype(np.float32)
-    Q64, p64 = dynamics.kick_drift(Q, p, g, 0.01, 0.8, 16)
-    Q32, p32 = dynamics.kick_drift_f32(Q, p, g, 0.01, 0.8, 16)
-    # one rounding of the product and one of the sum, each within half an ulp
-    # of the larger operand
-    big = np.maximum(np.abs(p), np.abs(np.float32(0.01) * g)).astype(np.float32)
-    assert (np.abs(p32.astype(np.float64) - p64) <= 2 * np.spacing(big)).all()
-    assert (np.abs(Q32 - Q64) <= 1).all() and (Q32 != Q64).mean() < 1e-3
-    # exact where the kick adds exactly (g = 0)
-    Qz, pz = dynamics.kick_drift_f32(Q, p, np.zeros_like(g), 0.01, 0.8, 16)
-    Q0, p0 = dynamics.kick_drift(Q, p, np.zeros_like(g), 0.01, 0.8, 16)
-    np.testing.assert_array_equal(pz, p0)
-    np.testing.assert_array_equal(Qz, Q0)
