@@ -341,9 +341,11 @@ static int enqueue_step(Sim& s) {
     if (s.lowmem) {
         if ((rc = lowmem_passes(s))) return rc;
     } else {
+        cudaMemsetAsync(s.counts[1 - s.cur], 0, sizeof(int32_t) * s.ncells, s.stream);
+        cudaMemsetAsync(s.S, 0, sizeof(unsigned long long) * 3 * s.ncells, s.stream);
         if ((rc = tile_pass(s, 1, nullptr))) return rc;
         prof_mark(s, 2);
-        if ((rc = encode_from_qp(s, false))) return rc;
+        if ((rc = encode_from_qp(s, true))) return rc;
     }
     k_step_advance<<<1, 1, 0, s.stream>>>(s.d_step, s.d_kd, s.d_factors, s.cfg.n_steps);
     s.launches++;

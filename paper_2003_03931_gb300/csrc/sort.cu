@@ -164,48 +164,40 @@ __device__ __forceinline__ int64_t key3(const int32_t (&q)[3], int nc) {
     return (int64_t)(q[0] >> 8) + nc * ((int64_t)(q[1] >> 8) + (int64_t)nc * (q[2] >> 8));
 }
 
-// New-cell counts and fixed-point momentum sums.  Lanes of a warp whose
-// particles land in the same new cell (common: the input is in old cell
-// order) add their values with warp reductions first, so one lane per cell
-// issues the global atomics.  The sums are integers, so the result does not
-// depend on how particles are grouped.
+// New-cell counts and fixed-point momentum sums.  Each thread takes kHistIlp
+// particles at a time and issues all their loads before the atomics; the
+// sums are integers, so their order does not matter.  (Grouping the lanes of
+// a warp by cell before the atomics measured no faster: the kernel waits on
+// its loads, not on atomic throughput.)
+constexpr int kHistIlp = 4;
 template <class Src>
 __global__ void k_hist(Src src, int64_t n, int nc, int32_t* counts, unsigned long long* S,
                        uint32_t* err) {
     const int64_t ncells = (int64_t)nc * nc * nc;
-    const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); base < n;
-         base += stride) {
-        const int64_t i = base + lane;
-        const bool live = i < n;
-        int32_t q[3] = {0, 0, 0};
-        float p[3] = {0.f, 0.f, 0.f};
-        if (live) src.load(i, q, p);
-        const long long key = live ? key3(q, nc) : -1ll - lane;
-        long long fx[3] = {0, 0, 0};
-        if (live) {
+    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < n;
+         i0 += stride * kHistIlp) {
+        int32_t q[kHistIlp][3];
+        float p[kHistIlp][3];
+#pragma unroll
+        for (int u = 0; u < kHistIlp; ++u) {
+            const int64_t i = i0 + u * stride;
+            q[u][0] = q[u][1] = q[u][2] = 0;
+            p[u][0] = p[u][1] = p[u][2] = 0.f;
+            if (i < n) src.load(i, q[u], p[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < kHistIlp; ++u) {
+            if (i0 + u * stride >= n) continue;
+            const int64_t key = key3(q[u], nc);
+            atomicAdd(&counts[key], 1);
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                if (fabsf(p[d]) < 1048576.f) fx[d] = __double2ll_rn((double)p[d] * 16777216.0);
-                else atomicOr(err, p[d] == p[d] ? kErrMomentum : kErrNaN);
+                long long fx = 0;
+                if (fabsf(p[u][d]) < 1048576.f) fx = __double2ll_rn((double)p[u][d] * 16777216.0);
+                else atomicOr(err, p[u][d] == p[u][d] ? kErrMomentum : kErrNaN);
+                atomicAdd(&S[d * ncells + key], (unsigned long long)fx);
             }
-        }
-        const unsigned peers = __match_any_sync(0xffffffffu, key);
-        // |fx| < 2^44: sum the low 22 bits and the signed high part separately;
-        // 32 lanes keep both sums inside 32 bits
-        long long sum[3];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            const unsigned lo = __reduce_add_sync(peers, (unsigned)(fx[d] & 0x3fffffll));
-            const unsigned hi = __reduce_add_sync(peers, (unsigned)(int)(fx[d] >> 22));
-            sum[d] = (long long)(int)hi * 4194304ll + (long long)lo;
-        }
-        if (live && lane == __ffs(peers) - 1) {
-            atomicAdd(&counts[key], __popc(peers));
-#pragma unroll
-            for (int d = 0; d < 3; ++d)
-                atomicAdd(&S[d * ncells + key], (unsigned long long)sum[d]);
         }
     }
 }
@@ -402,8 +394,8 @@ int encode_from_qp(Sim& s, bool counts_ready) {
     if (!counts_ready) {
         cudaMemsetAsync(s.counts[nxt], 0, sizeof(int32_t) * s.ncells, st);
         cudaMemsetAsync(s.S, 0, sizeof(unsigned long long) * 3 * s.ncells, st);
-        k_hist<<<grid_for(s.n, 256), 256, 0, st>>>(QPArrays{s.Qn, s.Pn, s.n}, s.n, s.nc, s.counts[nxt],
-                                                   s.S, s.err);
+        k_hist<<<grid_for(s.n, 256, 152 * 8), 256, 0, st>>>(QPArrays{s.Qn, s.Pn, s.n}, s.n, s.nc,
+                                                             s.counts[nxt], s.S, s.err);
         s.launches++;
     }
     int rc = scan_and_means(s, nxt);
@@ -438,7 +430,7 @@ int encode_from_psi(Sim& s, const double* scale) {
     const int nxt = 0;
     cudaMemsetAsync(s.counts[nxt], 0, sizeof(int32_t) * s.ncells, st);
     cudaMemsetAsync(s.S, 0, sizeof(unsigned long long) * 3 * s.ncells, st);
-    k_hist<<<grid_for(s.n, 256), 256, 0, st>>>(src, s.n, s.nc, s.counts[nxt], s.S, s.err);
+    k_hist<<<grid_for(s.n, 256, 152 * 8), 256, 0, st>>>(src, s.n, s.nc, s.counts[nxt], s.S, s.err);
     s.launches++;
     int rc = scan_and_means(s, nxt);
     if (rc) return rc;

@@ -173,6 +173,10 @@ int tile_pass(Sim& s, int mode, float* G) {
     P.err = s.err;
     const int ntiles = s.nt * s.nt * s.nt;
     int grid = ntiles;
+    if (mode == 1) {
+        P.counts_new = s.counts[1 - s.cur];
+        P.S = s.S;
+    }
     if (mode >= 2) {
         const int nxt = 1 - s.cur;
         P.sp = s.lm_sp;

@@ -20,7 +20,8 @@
 //      symmetric in (b, c), so only b <= c is kept, and it vanishes for own-
 //      axis |k| = 0 and 16, so those rows are not stored;
 //   O  the tile's own-cell table (prefix counts and storage offsets), built
-//      during the deposit and used by every interpolation phase (1 KB).
+//      during the deposit and used by every interpolation phase, a few
+//      per-tile scalars, and the velocity decode table T of Eq. 3 (2 KB).
 // Index swizzles (x ^ y) make every pencil pass free of bank conflicts.
 //
 // Each phase is a per-thread function; the kernel calls them with a block
@@ -40,7 +41,7 @@ constexpr int kGreenRows = kGreenS - 2;                         // own-axis |k| 
 constexpr int kGreenPacked = kGreenRows * kGreenTri;            // 2295 floats
 constexpr int kOwnTail = 126 + 125 + 8;                         // own-cell table, ints
 constexpr size_t kTileSmemBytes = (size_t)kTileR * 4 + (size_t)kTileW * 8 +
-                                  (size_t)kGreenPacked * 4 + (size_t)kOwnTail * 4;
+                                  (size_t)kGreenPacked * 4 + (size_t)kOwnTail * 4 + 256 * 4;
 
 struct TileParams {
     int nc;                       // coarse cells per side
@@ -71,8 +72,8 @@ struct TileParams {
     // scatters (Sec. III-A); per-CTA scratch of kLowmemCap own particles
     float* sp;                    // [CTAs][3][kLowmemCap] parked long-range force, new momenta
     int32_t* sq;                  // [CTAs][2][kLowmemCap] new codes of components 0 and 1
-    int32_t* counts_new;          // [nc^3] (mode 2)
-    unsigned long long* S;        // [3][nc^3] momentum sums in units of 2^-24 (mode 2)
+    int32_t* counts_new;          // [nc^3] (modes 1 and 2)
+    unsigned long long* S;        // [3][nc^3] momentum sums in units of 2^-24 (modes 1 and 2)
     const float* vc_new;          // [3][nc^3] (modes 3, 4)
     unsigned long long* d2;       // [2] 128-bit dispersion sum (mode 3)
     const int64_t* offsets_new;   // [nc^3 + 1] (mode 4)
@@ -349,6 +350,7 @@ struct TileCells {
     int* prel;         // [kOwnMax] storage offset of own cell p minus own_base (O)
     int* misc;         // [0..1] own_base (int64), [2] largest halo-cell count,
                        // [4] sigma, [5] kick, [6] drift, [7] new sigma as float bits (O)
+    float* Td;         // [256] velocity decode table T of Eq. 3 (after O)
     int* tot;          // [kHaloChunks] particles per 32-cell chunk of the halo box (W)
     int* cmax;         // [kHaloChunks] largest cell count per chunk (W)
 };
@@ -363,6 +365,7 @@ PMPM_HD TileCells tile_cells(float2* W, int* O) {
     c.ppre = O;
     c.prel = O + 126;
     c.misc = O + 126 + 125;
+    c.Td = reinterpret_cast<float*>(O + kOwnTail);
     c.tot = reinterpret_cast<int*>(c.pmap + kPMapCap);
     c.cmax = c.tot + 32;
     return c;
@@ -422,6 +425,7 @@ PMPM_HD void tile_prologue(int tid, const TileGeom& g, const TileParams& P, Tile
         const int i = tid + u * kTileThreads;
         gv[u] = (load_green && i < kGreenPacked) ? P.green[i] : 0.f;
     }
+    const float td = (load_green && tid < 256) ? P.Tdec[tid] : 0.f;
     float sc[4] = {0.f, 0.f, 0.f, 0.f};
     if (tid == 0) {
         sc[0] = *P.sigma;
@@ -445,6 +449,7 @@ PMPM_HD void tile_prologue(int tid, const TileGeom& g, const TileParams& P, Tile
         const int i = tid + u * kTileThreads;
         if (load_green && i < kGreenPacked) gS[i] = gv[u];
     }
+    if (load_green && tid < 256) c.Td[tid] = td;
     if (tid == 0) {
         c.misc[4] = f32_to_bits(sc[0]);
         c.misc[5] = f32_to_bits(sc[1]);
@@ -934,6 +939,12 @@ PMPM_HD void tile_interp(int tid, const TileGeom& g, const TileParams& P, const 
         int64_t j[U], Q[U][3], cell[U];
         float gcd[U], vcd[U];
         int u8[U];
+        int32_t q01[U][2];
+        float p01[U][2];
+        // default step: the last component also adds each particle to its new
+        // cell's count and momentum sums (the re-encode's histogram, fused
+        // here so the codes and momenta are not read back by another pass)
+        const bool fuse = !lm && D == 2 && P.mode == 1 && P.counts_new != nullptr;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int v = v0 + u * kTileThreads;
@@ -950,6 +961,12 @@ PMPM_HD void tile_interp(int tid, const TileGeom& g, const TileParams& P, const 
                 if (lm || P.mode >= 1) {
                     u8[u] = ud[j[u]];
                     vcd[u] = P.vc[D * ncells + cell[u]];
+                }
+                if (fuse) {
+                    q01[u][0] = P.Qn[j[u]];
+                    q01[u][1] = P.Qn[n + j[u]];
+                    p01[u][0] = P.Pn[j[u]];
+                    p01[u][1] = P.Pn[n + j[u]];
                 }
             }
         }
@@ -978,7 +995,7 @@ PMPM_HD void tile_interp(int tid, const TileGeom& g, const TileParams& P, const 
                 continue;
             }
             // kick (Eq. 3 decode, then p += kick * g) and integer drift
-            const float pv = decode_momentum(vcd[u], sigma, P.Tdec[u8[u]]);
+            const float pv = decode_momentum(vcd[u], sigma, c.Td[u8[u]]);
             const float pn = fadd_rn(pv, fmul_rn(kick, gval));
             const float xq = fmul_rn(pn, drift);
             if (!(pn == pn) || !(gval == gval)) flag_error(P.err, kErrNaN);
@@ -992,6 +1009,20 @@ PMPM_HD void tile_interp(int tid, const TileGeom& g, const TileParams& P, const 
             if (!lm) {
                 P.Qn[D * n + j[u]] = (int32_t)qn;
                 P.Pn[D * n + j[u]] = pn;
+                if (fuse) {
+                    const int32_t qa[3] = {q01[u][0], q01[u][1], (int32_t)qn};
+                    const float pa[3] = {p01[u][0], p01[u][1], pn};
+                    const int64_t key = (int64_t)(qa[0] >> 8) +
+                                        P.nc * ((int64_t)(qa[1] >> 8) + (int64_t)P.nc * (qa[2] >> 8));
+                    gmem_add_i32(&P.counts_new[key], 1);
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        long long fx = 0;
+                        if (fabsf(pa[d]) < 1048576.f) fx = f64_to_ll_rn((double)pa[d] * 16777216.0);
+                        else flag_error(P.err, pa[d] == pa[d] ? kErrMomentum : kErrNaN);
+                        gmem_add_u64(&P.S[d * ncells + key], (unsigned long long)fx);
+                    }
+                }
                 continue;
             }
             const int v = v0 + u * kTileThreads;
