@@ -32,27 +32,41 @@ __global__ void k_ic_noise(int64_t n, unsigned long long seed, double2* w) {
     }
 }
 
-__global__ void k_ic_spectrum(int np, int nf, int d, double slope, double kc,
-                              const double2* __restrict__ w, double2* __restrict__ out) {
+// sqrt(P(k)) / k^2 of every mode (0 on the k = 0 and Nyquist planes), shared
+// by the three displacement components
+__global__ void k_ic_amplitude(int np, int nf, double slope, double kc, double* __restrict__ amp) {
     const int64_t n = (int64_t)np * np * np;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int ix = (int)(i % np), iy = (int)((i / np) % np), iz = (int)(i / ((int64_t)np * np));
         const int h = np / 2;
         const int nx = ix < h ? ix : ix - np, ny = iy < h ? iy : iy - np, nz = iz < h ? iz : iz - np;
-        double2 v = make_double2(0.0, 0.0);
+        double c = 0.0;
         if (!(nx == -h || ny == -h || nz == -h) && (nx | ny | nz)) {
             const double kf = 2.0 * kPi / nf;
             const double kx = kf * nx, ky = kf * ny, kz = kf * nz;
             const double k2 = kx * kx + ky * ky + kz * kz;
             const double k = sqrt(k2);
-            const double amp = sqrt(pow(k, slope) * exp(-(k / kc) * (k / kc)));
-            const double kd = d == 0 ? kx : (d == 1 ? ky : kz);
-            const double c = kd / k2 * amp;
-            const double2 a = w[i];
-            v = make_double2(-c * a.y, c * a.x);   // i c a
+            c = sqrt(pow(k, slope) * exp(-(k / kc) * (k / kc))) / k2;
         }
-        out[i] = v;
+        amp[i] = c;
+    }
+}
+
+// Psi~_d = i k_d amp w~
+__global__ void k_ic_component(int np, int nf, int d, const double* __restrict__ amp,
+                               const double2* __restrict__ w, double2* __restrict__ out) {
+    const int64_t n = (int64_t)np * np * np;
+    const double kf = 2.0 * kPi / nf;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int ix = (int)(i % np), iy = (int)((i / np) % np), iz = (int)(i / ((int64_t)np * np));
+        const int h = np / 2;
+        const int nd = d == 0 ? (ix < h ? ix : ix - np) : (d == 1 ? (iy < h ? iy : iy - np)
+                                                                  : (iz < h ? iz : iz - np));
+        const double c = kf * nd * amp[i];
+        const double2 a = w[i];
+        out[i] = make_double2(-c * a.y, c * a.x);   // i c a
     }
 }
 
@@ -122,26 +136,37 @@ __global__ void k_ic_noise_f(int64_t n, unsigned long long seed, float2* w) {
         w[i] = make_float2((float)(sqrt(-2.0 * log(u1)) * cos(2.0 * kPi * u2)), 0.f);
     }
 }
-__global__ void k_ic_spectrum_f(int np, int nf, int d, double slope, double kc, float2* w) {
+__global__ void k_ic_amplitude_f(int np, int nf, double slope, double kc, float* __restrict__ amp) {
     const int64_t n = (int64_t)np * np * np;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int ix = (int)(i % np), iy = (int)((i / np) % np), iz = (int)(i / ((int64_t)np * np));
         const int h = np / 2;
         const int nx = ix < h ? ix : ix - np, ny = iy < h ? iy : iy - np, nz = iz < h ? iz : iz - np;
-        float2 v = make_float2(0.f, 0.f);
+        double c = 0.0;
         if (!(nx == -h || ny == -h || nz == -h) && (nx | ny | nz)) {
             const double kf = 2.0 * kPi / nf;
             const double kx = kf * nx, ky = kf * ny, kz = kf * nz;
             const double k2 = kx * kx + ky * ky + kz * kz;
             const double k = sqrt(k2);
-            const double amp = sqrt(pow(k, slope) * exp(-(k / kc) * (k / kc)));
-            const double kd = d == 0 ? kx : (d == 1 ? ky : kz);
-            const double c = kd / k2 * amp;
-            const float2 a = w[i];
-            v = make_float2((float)(-c * a.y), (float)(c * a.x));   // i c a
+            c = sqrt(pow(k, slope) * exp(-(k / kc) * (k / kc))) / k2;
         }
-        w[i] = v;
+        amp[i] = (float)c;
+    }
+}
+// in place: w = i k_d amp w
+__global__ void k_ic_component_f(int np, int nf, int d, const float* __restrict__ amp, float2* w) {
+    const int64_t n = (int64_t)np * np * np;
+    const double kf = 2.0 * kPi / nf;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int ix = (int)(i % np), iy = (int)((i / np) % np), iz = (int)(i / ((int64_t)np * np));
+        const int h = np / 2;
+        const int nd = d == 0 ? (ix < h ? ix : ix - np) : (d == 1 ? (iy < h ? iy : iy - np)
+                                                                  : (iz < h ? iz : iz - np));
+        const double c = kf * nd * (double)amp[i];
+        const float2 a = w[i];
+        w[i] = make_float2((float)(-c * a.y), (float)(c * a.x));   // i c a
     }
 }
 __global__ void k_ic_store_f(int64_t n, int d, const float2* __restrict__ in, float* __restrict__ psi,
@@ -175,16 +200,19 @@ static int ic_zeldovich_lowmem(Sim& s, uint64_t seed, double slope, double kc, d
     const int nblk = 1024;
     cudaMemsetAsync(partial, 0, sizeof(double) * (3 * nblk + 1), st);
     int rc;
+    // the amplitude lives in psi's last component until that component is stored
+    float* amp = s.ic_psi + 2 * n;
+    k_ic_amplitude_f<<<grid_for(n, 256), 256, 0, st>>>(np, s.nf, slope, kc, amp);
     for (int d = 0; d < 3; ++d) {
         k_ic_noise_f<<<grid_for(n, 256), 256, 0, st>>>(n, (unsigned long long)seed, w);
         if ((rc = fft3d<float>(s, w, np, -1))) return rc;
-        k_ic_spectrum_f<<<grid_for(n, 256), 256, 0, st>>>(np, s.nf, d, slope, kc, w);
+        k_ic_component_f<<<grid_for(n, 256), 256, 0, st>>>(np, s.nf, d, amp, w);
         if ((rc = fft3d<float>(s, w, np, 1))) return rc;
         k_ic_store_f<<<nblk, 256, 0, st>>>(n, d, w, s.ic_psi, partial);
     }
     double* scale = partial + 3 * nblk;
     k_ic_scale<<<1, 1, 0, st>>>(nblk, n, s.cfg.a_init, rms, partial, scale);
-    s.launches += 3 * 3 + 1;
+    s.launches += 3 * 3 + 2;
     if ((rc = check_launch(s, "ic"))) return rc;
     s.a = s.cfg.a_init;
     s.step = 0;
@@ -207,15 +235,18 @@ int ic_zeldovich(Sim& s, uint64_t seed, double slope, double kc, double rms) {
     k_ic_noise<<<grid_for(n, 256), 256, 0, st>>>(n, (unsigned long long)seed, w);
     int rc = fft3d<double>(s, w, np, -1);
     if (rc) return rc;
+    // the amplitude lives in psi's last component until that component is stored
+    double* amp = psi + 2 * n;
+    k_ic_amplitude<<<grid_for(n, 256), 256, 0, st>>>(np, s.nf, slope, kc, amp);
     for (int d = 0; d < 3; ++d) {
-        k_ic_spectrum<<<grid_for(n, 256), 256, 0, st>>>(np, s.nf, d, slope, kc, w, work);
+        k_ic_component<<<grid_for(n, 256), 256, 0, st>>>(np, s.nf, d, amp, w, work);
         if ((rc = fft3d<double>(s, work, np, 1))) return rc;
         k_ic_store<<<nblk, 256, 0, st>>>(n, d, work, psi, partial);
     }
     double* scale = partial + 3 * nblk;
     k_ic_scale<<<1, 1, 0, st>>>(nblk, n, s.cfg.a_init, rms, partial, scale);
     k_ic_particles<<<grid_for(n, 256), 256, 0, st>>>(np, s.nc, s.cfg.a_init, psi, scale, s.Qn, s.Pn);
-    s.launches += 4 + 3 * 2;
+    s.launches += 5 + 3 * 2;
     if ((rc = check_launch(s, "ic"))) return rc;
     s.a = s.cfg.a_init;
     s.step = 0;
