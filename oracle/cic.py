@@ -12,6 +12,14 @@ weight is the product of the three 1-D weights, an exact integer in units of
 ``(2U)^-3``.  Fine mesh (h = 1, 1-byte): units 2^-21; coarse mesh (h = 4):
 units 2^-27.  Because the weights are integers, the mesh density is an exact
 integer and independent of summation order.
+
+Reading for 2-byte positions (Sec. III-A, B = 65536): the exact 3-D product
+is in units of 2^-45 (fine) and 2^-51 (coarse), too fine for the integer
+meshes of a clustered box, so each corner's product is rounded half-even to
+the 1-byte units (a factor 2^24 coarser: (256 / 65536 * ...)^3 = 2^-24 for
+every mesh spacing), and the same rounded weights serve assignment and
+interpolation.  A particle's mass is then 1 to within 4 units of 2^-21 (or
+2^-27), and its force on itself stays exactly zero.
 """
 
 import numpy as np
@@ -28,6 +36,21 @@ def node_units(h, pos_bytes=1):
     return U
 
 
+def weight_unit(h, pos_bytes=1):
+    """Mesh density units per particle, (2U)^3 of the 1-byte format, which
+    both formats use (see the module docstring)."""
+    return (2 * node_units(h, 1)) ** 3
+
+
+def round_half_even_shift(w, bits):
+    """round-half-even(w / 2^bits) for non-negative int64 w."""
+    w = np.asarray(w, dtype=np.int64)
+    q = w >> bits
+    r = w & ((1 << bits) - 1)
+    half = 1 << (bits - 1)
+    return q + ((r > half) | ((r == half) & ((q & 1) == 1))).astype(np.int64)
+
+
 def weights_1d(Q, h, pos_bytes=1):
     """Per-axis CIC: (i0, w0, w1) with integer weights summing to 2U."""
     U = node_units(h, pos_bytes)
@@ -42,7 +65,8 @@ def corners(Q, n, h, pos_bytes=1):
     """All 8 CIC corners of every particle.
 
     Returns (flat_node [N, 8] int64, weight [N, 8] int64); weights are in
-    units of (2U)^-3 and each particle's 8 weights sum to (2U)^3.
+    units of 1/weight_unit(h); for 1-byte positions each particle's 8
+    weights sum to weight_unit(h) exactly, for 2-byte positions to within 4.
     """
     Q = np.asarray(Q, dtype=np.int64)
     i0, w0, w1 = weights_1d(Q, h, pos_bytes)
@@ -59,7 +83,11 @@ def corners(Q, n, h, pos_bytes=1):
                 wz = w1[:, 2] if dz else w0[:, 2]
                 nodes.append(ix + n * (iy + n * iz))
                 weights.append(wx * wy * wz)
-    return np.stack(nodes, axis=1), np.stack(weights, axis=1)
+    w = np.stack(weights, axis=1)
+    if pos_bytes == 2:
+        # (2U_2 / 2U_1)^3 = 256^3 = 2^24 for every mesh spacing
+        w = round_half_even_shift(w, 24)
+    return np.stack(nodes, axis=1), w
 
 
 def deposit(Q, n, h, pos_bytes=1):
@@ -76,7 +104,6 @@ def deposit(Q, n, h, pos_bytes=1):
 def interpolate(field, Q, h, pos_bytes=1):
     """CIC gather of a scalar mesh field [z, y, x] at the particles (float64)."""
     n = field.shape[0]
-    U = node_units(h, pos_bytes)
     node, w = corners(Q, n, h, pos_bytes)
     flat = np.asarray(field, dtype=np.float64).ravel()
-    return (flat[node] * (w.astype(np.float64) / float((2 * U) ** 3))).sum(axis=1)
+    return (flat[node] * (w.astype(np.float64) / float(weight_unit(h, pos_bytes)))).sum(axis=1)

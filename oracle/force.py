@@ -59,16 +59,14 @@ class ForceOperator:
     # mesh forces (Eq. 1)
     def fine_field(self, Q):
         """F_s on the fine mesh, [3, z, y, x] float64."""
-        U = cic.node_units(1, self.pos_bytes)
-        rho = self.fine_density(Q).astype(np.float64) / float((2 * U) ** 3)
+        rho = self.fine_density(Q).astype(np.float64) / float(cic.weight_unit(1, self.pos_bytes))
         rho_hat = np.fft.rfftn(rho)
         Kh = self.Ks_hat()
         return np.stack([np.fft.irfftn(rho_hat * Kh[c], s=rho.shape, axes=(0, 1, 2)) for c in range(3)])
 
     def coarse_field(self, Q):
         """F_l on the coarse mesh, [3, z, y, x] float64."""
-        U = cic.node_units(kernels.RATIO, self.pos_bytes)
-        rho = self.coarse_density(Q).astype(np.float64) / float((2 * U) ** 3)
+        rho = self.coarse_density(Q).astype(np.float64) / float(cic.weight_unit(kernels.RATIO, self.pos_bytes))
         rho_hat = np.fft.rfftn(rho)
         Kh = self.Kl_hat()
         return np.stack([np.fft.irfftn(rho_hat * Kh[c], s=rho.shape, axes=(0, 1, 2)) for c in range(3)])
@@ -111,8 +109,7 @@ def coarse_density_chunked(Q, nc, pos_bytes=1, chunk=1 << 22):
 
 def coarse_field_from_density(rho_c, nc, pos_bytes=1):
     """F_l on the coarse mesh from a given integer coarse density."""
-    U = cic.node_units(kernels.RATIO, pos_bytes)
-    rho = rho_c.astype(np.float64) / float((2 * U) ** 3)
+    rho = rho_c.astype(np.float64) / float(cic.weight_unit(kernels.RATIO, pos_bytes))
     rho_hat = np.fft.rfftn(rho)
     K = kernels.coarse_kernel_table(nc)
     return np.stack([np.fft.irfftn(rho_hat * np.fft.rfftn(K[c]), s=rho.shape, axes=(0, 1, 2))
@@ -130,8 +127,7 @@ def sampled_fine_force(Q, counts, nc, idx, pos_bytes=1):
     Q = np.asarray(Q, dtype=np.int64)
     nf = kernels.RATIO * nc
     B = codec.bins_per_cell(pos_bytes)
-    U = cic.node_units(1, pos_bytes)
-    unit = float((2 * U) ** 3)
+    unit = float(cic.weight_unit(1, pos_bytes))
     d, Ks = kernels.fine_kernel_values(nc)
     offsets = np.concatenate([[0], np.cumsum(np.asarray(counts, dtype=np.int64))])
     r = np.arange(-2, 3)
