@@ -257,7 +257,9 @@ def run_ours(args):
     if E:
         n, C = cfg.n, cfg.ncells
         pin = lambda shape, dt: torch.empty(shape, dtype=dt, pin_memory=True).numpy()
-        host = {"streams": pin((6, n), torch.uint8), "counts": pin((C,), torch.int32),
+        pb = cfg.pos_bytes
+        shape = (6, n) if pb == 1 else ((3 * pb + 3) * n,)
+        host = {"streams": pin(shape, torch.uint8), "counts": pin((C,), torch.int32),
                 "vc": pin((3, C), torch.float32)}
         sim.fetch_into(host)
         host["scalars"] = sim.fetch_scalars()
@@ -270,7 +272,7 @@ def run_ours(args):
             host["scalars"] = sim.fetch_scalars()
         torch.cuda.synchronize()
         te = reduce_max(time.perf_counter() - t0, f"cuda:{local}")
-        per = 6 * n + 4 * C + 12 * C + 32
+        per = (3 * pb + 3) * n + 4 * C + 12 * C + 32
         e2e = {"value": job_rate(n * E, world, te), "unit": UNIT, "h2d_bytes_per_step": per,
                "d2h_bytes_per_step": per, "steps": E}
 
@@ -310,8 +312,9 @@ def run_ours(args):
                    "workspace_gb": sim.workspace.numel() / 1e9,
                    "nf": 4 * cfg.nc, "tile_fine": "16/20 + 6 buffer in 32^3",
                    "schedule": f"a 0.02->1 in {cfg.n_steps} steps, timed steps {W + 1}..{W + K}",
-                   "parallelism": f"replicas x{world}", "bytes_per_particle_store": 6,
-                   "l2": "inputs larger than L2 (%.0f MB particle store)" % (6 * n / 1e6)},
+                   "parallelism": f"replicas x{world}",
+                   "bytes_per_particle_store": 3 * cfg.pos_bytes + 3,
+                   "l2": "inputs larger than L2 (%.0f MB particle store)" % ((3 * cfg.pos_bytes + 3) * n / 1e6)},
         "e2e": e2e,
         "gpu_launches": launches,
         "roofline": roofline,

@@ -14,7 +14,8 @@
  *  - Lengths are in fine cells; the box is 4*nc fine cells per side (the
  *    coarse mesh is 4x coarser, Sec. II).  Cell indices are 0-based, flat
  *    index cx + nc*(cy + nc*cz) (x fastest).
- *  - Position code Q = c*256 + m; decoded position (Q + 1/2)/64 (Eq. 2).
+ *  - Position code Q = c*B + m with B = 256 bins per coarse cell (1-byte m,
+ *    Eq. 2) or 65536 (2-byte m, Sec. III-A); decoded position (Q + 1/2)/(B/4).
  *  - Velocity p = a^2 dx/dt; decoded p = v_c + sigma*T[u] in float32, T the
  *    tangent of the bin-centre angle of 256 equal angle bins (Eq. 3; the
  *    map f is the arctangent form of Sec. III-B.2).
@@ -51,7 +52,9 @@ extern "C" {
 #define PMPM_ETIMEOUT  -7   /* a host-side time limit ran out; the work goes on */
 
 /* what to fetch / load */
-#define PMPM_STREAMS          1  /* uint8 [6][N]: m0 m1 m2 u0 u1 u2 in storage order */
+#define PMPM_STREAMS          1  /* the store in storage order: m0 m1 m2 [N] of pos_bytes
+                                    each (little-endian), then u0 u1 u2 [N] uint8;
+                                    (3 pos_bytes + 3) N bytes */
 #define PMPM_COUNTS           2  /* int32 [nc^3] particles per coarse cell */
 #define PMPM_VC               3  /* float [3][nc^3] per-cell mean momentum v_c */
 #define PMPM_SCALARS          4  /* pmpm_scalars */
@@ -87,7 +90,8 @@ typedef struct pmpm_config {
     int32_t nc;              /* coarse cells per side (>= 8); fine mesh 4*nc */
     int32_t tile_max;        /* largest tile edge in coarse cells: 4 or 5 */
     int32_t buffer;          /* tile buffer in fine cells; must be 6 (Sec. IV-A.2) */
-    int32_t pos_bytes;       /* bytes per position coordinate; must be 1 (Eq. 2) */
+    int32_t pos_bytes;       /* bytes per position coordinate: 1 (Eq. 2) or 2 (Sec. III-A;
+                                CIC weight products rounded to the 1-byte units) */
     int32_t vel_bytes;       /* bytes per velocity coordinate; must be 1 (Eq. 3) */
     int32_t pk_mesh_max;     /* largest power-spectrum mesh; 0 = min(4*nc, 512) */
     int32_t flags;           /* PMPM_FLAG_* below; 0 = default */

@@ -47,8 +47,10 @@ static int validate(const pmpm_config* c, char* msg, size_t len) {
         return snprintf(msg, len, "tile_max=%d must be 4 or 5", c->tile_max), PMPM_EINVAL;
     if (c->buffer != kBuffer)
         return snprintf(msg, len, "buffer=%d: only %d is supported", c->buffer, kBuffer), PMPM_EINVAL;
-    if (c->pos_bytes != 1 || c->vel_bytes != 1)
-        return snprintf(msg, len, "only the 1-byte position/velocity format is built"), PMPM_EINVAL;
+    if ((c->pos_bytes != 1 && c->pos_bytes != 2) || c->vel_bytes != 1)
+        return snprintf(msg, len, "positions take 1 or 2 bytes, velocities 1 byte"), PMPM_EINVAL;
+    if (c->pos_bytes == 2 && (c->flags & PMPM_FLAG_LOWMEM))
+        return snprintf(msg, len, "the low-memory step stores 1-byte positions"), PMPM_EINVAL;
     const int nf = 4 * c->nc;
     if (c->pk_mesh_max && (!pow2(c->pk_mesh_max) || c->pk_mesh_max > nf || c->pk_mesh_max < 4))
         return snprintf(msg, len, "pk_mesh_max=%d must be a power of two <= %d", c->pk_mesh_max, nf),
@@ -75,6 +77,7 @@ static void derive(Sim& s, const pmpm_config* c) {
     if (s.pk_max > s.fft_max) s.fft_max = s.pk_max;
     s.nblocks_scan = (s.ncells + 4095) / 4096;
     s.lowmem = (c->flags & PMPM_FLAG_LOWMEM) != 0;
+    s.pb = c->pos_bytes == 2 ? 2 : 1;
     s.lm_ctas = s.lowmem ? kLowmemCtas : 0;
 }
 
@@ -122,7 +125,7 @@ static size_t layout_lowmem(Sim& s, uint8_t* base) {
     off = align_up(off);
     const size_t p1 = off;
     // P1
-    s.streams[0] = take(6 * (size_t)N);
+    s.streams[0] = take(6 * (size_t)N);   // low-memory sims store 1-byte positions
     s.counts[0] = reinterpret_cast<int32_t*>(take(4 * (size_t)C));
     s.offsets[0] = reinterpret_cast<int64_t*>(take(8 * (size_t)(C + 1)));
     s.vc[0] = reinterpret_cast<float*>(take(12 * (size_t)C));
@@ -183,7 +186,7 @@ size_t layout(Sim& s, uint8_t* base) {
     };
     const int64_t N = s.n, C = s.ncells;
     for (int b = 0; b < 2; ++b) {
-        s.streams[b] = take(6 * (size_t)N);
+        s.streams[b] = take((size_t)(3 * s.pb + 3) * N);
         s.counts[b] = reinterpret_cast<int32_t*>(take(4 * (size_t)C));
         s.offsets[b] = reinterpret_cast<int64_t*>(take(8 * (size_t)(C + 1)));
         s.vc[b] = reinterpret_cast<float*>(take(12 * (size_t)C));
@@ -319,7 +322,7 @@ static void fill_factors(Sim& s) {
                             (sqrt(a_hi) - sqrt(a_lo));
         const double drift = 2.0 * (1.0 / sqrt(an) - 1.0 / sqrt(an1));
         f[2 * n] = (float)kick;
-        f[2 * n + 1] = (float)(drift * kCodesPerFine);
+        f[2 * n + 1] = (float)(drift * (s.pb == 2 ? PosFmt<2>::kCodesPerFine : PosFmt<1>::kCodesPerFine));
     }
     cudaMemcpyAsync(s.d_factors, f, sizeof(float) * 2 * S, cudaMemcpyHostToDevice, s.stream);
     cudaStreamSynchronize(s.stream);
@@ -624,7 +627,7 @@ int pmpm_fetch(pmpm_sim* h, int32_t what, void* dst, size_t bytes) {
     const size_t N = (size_t)s.n, C = (size_t)s.ncells;
     size_t need = 0;
     switch (what) {
-        case PMPM_STREAMS: need = 6 * N; break;
+        case PMPM_STREAMS: need = store_bytes(s); break;
         case PMPM_COUNTS: need = 4 * C; break;
         case PMPM_VC: need = 12 * C; break;
         case PMPM_SCALARS: need = sizeof(pmpm_scalars); break;
@@ -687,7 +690,8 @@ int pmpm_load(pmpm_sim* h, int32_t what, const void* src, size_t bytes) {
     cudaError_t e = cudaSuccess;
     switch (what) {
         case PMPM_STREAMS:
-            if (bytes != 6 * N) return set_error(s, PMPM_EINVAL, "streams need %zu bytes", 6 * N);
+            if (bytes != store_bytes(s))
+                return set_error(s, PMPM_EINVAL, "streams need %zu bytes", store_bytes(s));
             e = cudaMemcpyAsync(s.streams[s.cur], src, bytes, cudaMemcpyHostToDevice, s.stream);
             s.loaded |= 1;
             break;
@@ -741,7 +745,7 @@ int pmpm_load(pmpm_sim* h, int32_t what, const void* src, size_t bytes) {
             if (e != cudaSuccess) break;
             // the codes index cells: check their range before any kernel uses them
             const int32_t* q = static_cast<const int32_t*>(src);
-            const int64_t M = (int64_t)s.nc * kBins;
+            const int64_t M = (int64_t)s.nc * (s.pb == 2 ? PosFmt<2>::kBins : PosFmt<1>::kBins);
             for (size_t i = 0; i < 3 * N; ++i)
                 if (q[i] < 0 || q[i] >= M) {
                     cudaStreamSynchronize(s.stream);

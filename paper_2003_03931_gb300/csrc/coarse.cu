@@ -20,6 +20,7 @@ constexpr int kNX = kBX + 2, kNY = kBY + 2, kNZ = kBZ + 2;
 // One thread per coarse cell: the cell's particles reach only the 3^3 nodes
 // around it, so their weights are summed in 27 registers and added to the
 // brick's shared accumulator once per cell.
+template <int PB>
 __global__ void __launch_bounds__(256) k_coarse_deposit(int nc, const int32_t* __restrict__ counts,
                                                         const int64_t* __restrict__ offsets,
                                                         const uint8_t* __restrict__ m0,
@@ -42,24 +43,30 @@ __global__ void __launch_bounds__(256) k_coarse_deposit(int nc, const int32_t* _
     for (int k = 0; k < 27; ++k) a[k] = 0ull;
     for (int q = 0; q < cnt; ++q) {
         const int64_t j = j0 + q;
-        // per axis: weights of nodes c-1, c, c+1 (in 1/512); the bin m < 128
-        // lies left of the cell centre
+        // per axis: weights of nodes c-1, c, c+1 (in 1/(2B)); the bins in the
+        // lower half lie left of the cell centre
+        constexpr int B = PosFmt<PB>::kBins;
         uint32_t w[3][3];
-        const int mm[3] = {m0[j], m1[j], m2[j]};
+        const int mm[3] = {load_bin<PB>(m0, j), load_bin<PB>(m1, j), load_bin<PB>(m2, j)};
 #pragma unroll
         for (int e = 0; e < 3; ++e) {
-            const int s = 2 * mm[e] + 1 - kBins;     // offset from the centre, 1/512
+            const int s = 2 * mm[e] + 1 - B;     // offset from the centre, 1/(2B)
             w[e][0] = s < 0 ? (uint32_t)(-s) : 0u;
-            w[e][1] = 512u - (uint32_t)(s < 0 ? -s : s);
+            w[e][1] = (uint32_t)(2 * B) - (uint32_t)(s < 0 ? -s : s);
             w[e][2] = s > 0 ? (uint32_t)s : 0u;
         }
 #pragma unroll
         for (int kz = 0; kz < 3; ++kz)
 #pragma unroll
             for (int ky = 0; ky < 3; ++ky) {
-                const unsigned long long wyz = (unsigned long long)(w[1][ky] * w[2][kz]);
+                const unsigned long long wyz = (unsigned long long)w[1][ky] * w[2][kz];
 #pragma unroll
-                for (int kx = 0; kx < 3; ++kx) a[kx + 3 * (ky + 3 * kz)] += wyz * w[0][kx];
+                for (int kx = 0; kx < 3; ++kx) {
+                    const unsigned long long w3 = wyz * w[0][kx];
+                    // 2-byte bins: the 2^-51 product rounded to the 2^-27 unit
+                    a[kx + 3 * (ky + 3 * kz)] +=
+                        PB == 1 ? w3 : round_half_even_shift(w3, PosFmt<PB>::kRoundBits);
+                }
             }
     }
 #pragma unroll
@@ -130,9 +137,10 @@ __global__ void k_coarse_extract(int64_t ncells, const float2* __restrict__ B1,
 int coarse_deposit(Sim& s) {
     cudaMemsetAsync(s.rho_c, 0, sizeof(long long) * s.ncells, s.stream);
     const int nb = (s.nc / kBX) * (s.nc / kBY) * (s.nc / kBZ);
-    k_coarse_deposit<<<nb, 256, 0, s.stream>>>(
-        s.nc, s.counts[s.cur], s.offsets[s.cur], cur_stream(s, 0), cur_stream(s, 1),
-        cur_stream(s, 2), reinterpret_cast<unsigned long long*>(s.rho_c));
+    auto k = s.pb == 2 ? k_coarse_deposit<2> : k_coarse_deposit<1>;
+    k<<<nb, 256, 0, s.stream>>>(s.nc, s.counts[s.cur], s.offsets[s.cur], m_stream(s, s.cur, 0),
+                                m_stream(s, s.cur, 1), m_stream(s, s.cur, 2),
+                                reinterpret_cast<unsigned long long*>(s.rho_c));
     s.launches++;
     return check_launch(s, "coarse deposit");
 }

@@ -115,6 +115,44 @@ PMPM_HD unsigned long long sq_fix32(float d) {
     return q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull);
 }
 
+// ---------------------------------------------------------------- position format
+// PB bytes per position coordinate (Sec. III-A): B = 256 (1 byte, Eq. 2) or
+// 65536 (2 bytes) bins per coarse cell.  The 3-D CIC weight products of
+// 2-byte codes (2^-45 fine, 2^-51 coarse) are rounded half-even to the
+// 1-byte units (2^-21, 2^-27) so both formats share the integer meshes.
+template <int PB>
+struct PosFmt {
+    static_assert(PB == 1 || PB == 2, "1- or 2-byte positions");
+    static constexpr int kBins = PB == 1 ? 256 : 65536;
+    static constexpr int kShift = PB == 1 ? 8 : 16;             // log2(kBins)
+    static constexpr int kCodesPerFine = kBins / kRatio;         // 64 or 16384
+    static constexpr int kFineW = 2 * kCodesPerFine;             // fine weight denominator
+    static constexpr int kFineWBits = PB == 1 ? 7 : 15;
+    static constexpr int kCoarseW = 2 * kBins;                   // coarse weight denominator
+    static constexpr int kCoarseWBits = PB == 1 ? 9 : 17;
+    static constexpr int kRoundBits = PB == 1 ? 0 : 24;          // product -> 1-byte units
+};
+
+// round-half-even(w / 2^bits), bits > 0
+PMPM_HD uint64_t round_half_even_shift(uint64_t w, int bits) {
+    const uint64_t q = w >> bits, r = w & ((1ull << bits) - 1ull), half = 1ull << (bits - 1);
+    return q + ((r > half || (r == half && (q & 1ull))) ? 1ull : 0ull);
+}
+
+// 3-D weight in the 1-byte units from three 1-D weights of format PB
+template <int PB>
+PMPM_HD uint32_t cic_weight3(uint32_t wx, uint32_t wy, uint32_t wz) {
+    if (PB == 1) return wx * wy * wz;
+    return (uint32_t)round_half_even_shift((uint64_t)wx * wy * wz, PosFmt<PB>::kRoundBits);
+}
+
+// position bin m of particle j from a stream of PB-byte entries
+template <int PB>
+PMPM_HD int load_bin(const uint8_t* stream, int64_t j) {
+    if (PB == 1) return stream[j];
+    return reinterpret_cast<const uint16_t*>(stream)[j];
+}
+
 // ---------------------------------------------------------------- CIC
 // Nodes at cell centres.  For a mesh whose node spacing holds U position
 // codes, s = 2Q + 1 - U is the particle's offset from node 0 in units of

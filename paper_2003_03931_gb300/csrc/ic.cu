@@ -100,6 +100,7 @@ __global__ void k_ic_scale(int nblk, int64_t n, double a_init, double rms_disp, 
     *scale = rms > 0.0 ? rms_disp / (a_init * rms) : 0.0;
 }
 
+template <int PB>
 __global__ void k_ic_particles(int np, int nc, double a_init, const double* __restrict__ psi,
                                const double* __restrict__ scale_p, int32_t* __restrict__ Qn,
                                float* __restrict__ Pn) {
@@ -107,7 +108,7 @@ __global__ void k_ic_particles(int np, int nc, double a_init, const double* __re
     const double scale = *scale_p;
     const double spacing = 4.0 * nc / (double)np;
     const double a15 = pow(a_init, 1.5);
-    const int64_t M = (int64_t)nc * kBins;
+    const int64_t M = (int64_t)nc * PosFmt<PB>::kBins;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int li[3] = {(int)(i % np), (int)((i / np) % np), (int)(i / ((int64_t)np * np))};
@@ -115,7 +116,7 @@ __global__ void k_ic_particles(int np, int nc, double a_init, const double* __re
             const double ps = psi[d * n + i] * scale;
             const double q = ((double)li[d] + 0.5) * spacing;
             const double x = q + a_init * ps;
-            int64_t Q = (int64_t)floor(x * (double)kCodesPerFine) % M;
+            int64_t Q = (int64_t)floor(x * (double)PosFmt<PB>::kCodesPerFine) % M;
             if (Q < 0) Q += M;
             Qn[d * n + i] = (int32_t)Q;
             Pn[d * n + i] = (float)(a15 * ps);
@@ -245,7 +246,8 @@ int ic_zeldovich(Sim& s, uint64_t seed, double slope, double kc, double rms) {
     }
     double* scale = partial + 3 * nblk;
     k_ic_scale<<<1, 1, 0, st>>>(nblk, n, s.cfg.a_init, rms, partial, scale);
-    k_ic_particles<<<grid_for(n, 256), 256, 0, st>>>(np, s.nc, s.cfg.a_init, psi, scale, s.Qn, s.Pn);
+    auto kp = s.pb == 2 ? k_ic_particles<2> : k_ic_particles<1>;
+    kp<<<grid_for(n, 256), 256, 0, st>>>(np, s.nc, s.cfg.a_init, psi, scale, s.Qn, s.Pn);
     s.launches += 5 + 3 * 2;
     if ((rc = check_launch(s, "ic"))) return rc;
     s.a = s.cfg.a_init;

@@ -19,13 +19,14 @@ struct Sim {
     pmpm_config cfg;
     int device = 0;
     int nc = 0, nf = 0, np = 0, nt = 0, tile_max = 0, pk_max = 0, fft_max = 0;
+    int pb = 1;                                 // bytes per position bin (1 or 2)
     int64_t n = 0, ncells = 0;
     cudaStream_t stream = nullptr;
     uint8_t* ws = nullptr;
     size_t ws_bytes = 0;
 
     // particle store, double-buffered (Sec. III-A)
-    uint8_t* streams[2] = {nullptr, nullptr};   // [6][N]
+    uint8_t* streams[2] = {nullptr, nullptr};   // m0 m1 m2 [N] (pb bytes each), u0 u1 u2 [N]
     int32_t* counts[2] = {nullptr, nullptr};    // [nc^3]
     int64_t* offsets[2] = {nullptr, nullptr};   // [nc^3 + 1]
     float* vc[2] = {nullptr, nullptr};          // [3][nc^3]
@@ -139,7 +140,13 @@ void power_spectrum_finish(const double* host_bins, int nbins, double* k, double
 void prof_mark(Sim& s, int stage);     // records an event closing `stage` (-1: opening)
 void set_device_step(Sim& s, int64_t step);
 
-inline uint8_t* cur_stream(Sim& s, int which) { return s.streams[s.cur] + (size_t)which * s.n; }
+// The store of buffer b: position bins m_d (pb bytes each) then velocity
+// bins u_d (1 byte each), every stream N entries long.
+inline uint8_t* m_stream(Sim& s, int b, int d) { return s.streams[b] + (size_t)d * s.pb * s.n; }
+inline uint8_t* u_stream(Sim& s, int b, int d) {
+    return s.streams[b] + (size_t)3 * s.pb * s.n + (size_t)d * s.n;
+}
+inline size_t store_bytes(const Sim& s) { return (size_t)(3 * s.pb + 3) * s.n; }
 
 }  // namespace pmpm
 

@@ -11,12 +11,14 @@ namespace {
 
 constexpr double kPi = 3.141592653589793238462643383279502884;
 
-// integer CIC at node spacing h = 2^lh fine cells: U = 64 h codes per node
+// integer CIC at node spacing h = 2^lh fine cells: U = (B/4) h codes per node;
+// 2-byte products are rounded to the 1-byte unit (2U_1)^-3
+template <int PB>
 __global__ void k_pk_deposit(int64_t n, int nc, int nmesh, int lh, const int64_t* __restrict__ offsets,
                              const uint8_t* __restrict__ st, unsigned long long* rho) {
     const int64_t ncells = (int64_t)nc * nc * nc;
-    const int lu2 = 7 + lh;          // log2(2U)
-    const int64_t U = (int64_t)kCodesPerFine << lh;
+    const int lu2 = PosFmt<PB>::kFineWBits + lh;   // log2(2U)
+    const int64_t U = (int64_t)PosFmt<PB>::kCodesPerFine << lh;
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
          j += (int64_t)gridDim.x * blockDim.x) {
         int64_t lo = 0, hi = ncells;
@@ -28,7 +30,7 @@ __global__ void k_pk_deposit(int64_t n, int nc, int nmesh, int lh, const int64_t
         int i0[3];
         int64_t w1[3];
         for (int d = 0; d < 3; ++d) {
-            const int64_t Q = (int64_t)cc[d] * kBins + st[d * n + j];
+            const int64_t Q = (int64_t)cc[d] * PosFmt<PB>::kBins + load_bin<PB>(st + (size_t)d * PB * n, j);
             const int64_t s = 2 * Q + 1 - U;
             i0[d] = (int)(s >> lu2);
             w1[d] = s & ((2 * U) - 1);
@@ -36,9 +38,10 @@ __global__ void k_pk_deposit(int64_t n, int nc, int nmesh, int lh, const int64_t
         const int64_t W = 2 * U;
         for (int k = 0; k < 8; ++k) {
             const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
-            const unsigned long long w = (unsigned long long)((dx ? w1[0] : W - w1[0]) *
-                                                              (dy ? w1[1] : W - w1[1]) *
-                                                              (dz ? w1[2] : W - w1[2]));
+            unsigned long long w = (unsigned long long)((dx ? w1[0] : W - w1[0]) *
+                                                        (dy ? w1[1] : W - w1[1]) *
+                                                        (dz ? w1[2] : W - w1[2]));
+            if (PB == 2) w = round_half_even_shift(w, PosFmt<PB>::kRoundBits);
             if (!w) continue;
             const int x = wrap(i0[0] + dx, nmesh), y = wrap(i0[1] + dy, nmesh), z = wrap(i0[2] + dz, nmesh);
             atomicAdd(&rho[x + (int64_t)nmesh * (y + (int64_t)nmesh * z)], w);
@@ -97,8 +100,8 @@ int power_spectrum_enqueue(Sim& s, int nmesh, int nbins, double* host_bins) {
     unsigned long long* rho = reinterpret_cast<unsigned long long*>(s.scratch);
     float2* dk = reinterpret_cast<float2*>(align_up(reinterpret_cast<uintptr_t>(rho + m3)));
     cudaMemsetAsync(rho, 0, sizeof(unsigned long long) * m3, st);
-    k_pk_deposit<<<grid_for(s.n, 256), 256, 0, st>>>(s.n, s.nc, nmesh, lh, s.offsets[s.cur],
-                                                      s.streams[s.cur], rho);
+    auto kd = s.pb == 2 ? k_pk_deposit<2> : k_pk_deposit<1>;
+    kd<<<grid_for(s.n, 256), 256, 0, st>>>(s.n, s.nc, nmesh, lh, s.offsets[s.cur], s.streams[s.cur], rho);
     const double U = (double)(kCodesPerFine << lh);
     const double mean = (double)s.n * (2 * U) * (2 * U) * (2 * U) / (double)m3;
     k_pk_delta<<<grid_for(m3, 256), 256, 0, st>>>(m3, 1.0 / mean, rho, dk);

@@ -160,8 +160,10 @@ struct QPFromPsi {
     }
 };
 
+template <int PB>
 __device__ __forceinline__ int64_t key3(const int32_t (&q)[3], int nc) {
-    return (int64_t)(q[0] >> 8) + nc * ((int64_t)(q[1] >> 8) + (int64_t)nc * (q[2] >> 8));
+    constexpr int sh = PosFmt<PB>::kShift;
+    return (int64_t)(q[0] >> sh) + nc * ((int64_t)(q[1] >> sh) + (int64_t)nc * (q[2] >> sh));
 }
 
 // New-cell counts and fixed-point momentum sums.  Each thread takes kHistIlp
@@ -170,7 +172,7 @@ __device__ __forceinline__ int64_t key3(const int32_t (&q)[3], int nc) {
 // a warp by cell before the atomics measured no faster: the kernel waits on
 // its loads, not on atomic throughput.)
 constexpr int kHistIlp = 4;
-template <class Src>
+template <int PB, class Src>
 __global__ void k_hist(Src src, int64_t n, int nc, int32_t* counts, unsigned long long* S,
                        uint32_t* err) {
     const int64_t ncells = (int64_t)nc * nc * nc;
@@ -189,7 +191,7 @@ __global__ void k_hist(Src src, int64_t n, int nc, int32_t* counts, unsigned lon
 #pragma unroll
         for (int u = 0; u < kHistIlp; ++u) {
             if (i0 + u * stride >= n) continue;
-            const int64_t key = key3(q[u], nc);
+            const int64_t key = key3<PB>(q[u], nc);
             atomicAdd(&counts[key], 1);
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
@@ -205,7 +207,7 @@ __global__ void k_hist(Src src, int64_t n, int nc, int32_t* counts, unsigned lon
 // 128-bit sum of round((p - v_c)^2 2^32).  Each thread takes kSigmaIlp
 // particles at a time and issues all their loads before using any.
 constexpr int kSigmaIlp = 4;
-template <class Src>
+template <int PB, class Src>
 __global__ void __launch_bounds__(256) k_sigma(Src src, int64_t n, int nc,
                                                const float* __restrict__ vc,
                                                unsigned long long* d2, uint32_t* err) {
@@ -222,7 +224,7 @@ __global__ void __launch_bounds__(256) k_sigma(Src src, int64_t n, int nc,
             int32_t q[3] = {0, 0, 0};
             p[u][0] = p[u][1] = p[u][2] = 0.f;
             if (i < n) src.load(i, q, p[u]);
-            key[u] = i < n ? key3(q, nc) : -1;
+            key[u] = i < n ? key3<PB>(q, nc) : -1;
         }
 #pragma unroll
         for (int u = 0; u < kSigmaIlp; ++u)
@@ -286,7 +288,7 @@ __global__ void k_sigma_final(const unsigned long long* d2, int64_t n, float* si
 // Lanes with the same new cell take consecutive ranks from one atomic.  Each
 // warp handles two particles per lane at a time, and the cell's offset and
 // mean momentum are loaded before the rank atomic returns.
-template <class Src>
+template <int PB, class Src>
 __global__ void k_scatter(Src src, int64_t n, int nc, const float* __restrict__ vc,
                           const int64_t* __restrict__ offsets, int32_t* fill,
                           const float* __restrict__ sigma_p, const float* __restrict__ E,
@@ -309,7 +311,7 @@ __global__ void k_scatter(Src src, int64_t n, int nc, const float* __restrict__ 
             q[u][0] = q[u][1] = q[u][2] = 0;
             p[u][0] = p[u][1] = p[u][2] = 0.f;
             if (live) src.load(i[u], q[u], p[u]);
-            key[u] = live ? key3(q[u], nc) : -1ll - lane;
+            key[u] = live ? key3<PB>(q[u], nc) : -1ll - lane;
         }
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
@@ -328,14 +330,16 @@ __global__ void k_scatter(Src src, int64_t n, int nc, const float* __restrict__ 
             const int64_t slot = off[u] + first[u] + __popc(peers[u] & ((1u << lane) - 1u));
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                out[d * n + slot] = (uint8_t)(q[u][d] & 255);
-                out[(3 + d) * n + slot] = (uint8_t)encode_momentum(p[u][d], v[u][d], sigma, E, err);
+                if (PB == 1) out[d * n + slot] = (uint8_t)(q[u][d] & 255);
+                else reinterpret_cast<uint16_t*>(out + 2 * d * n)[slot] = (uint16_t)(q[u][d] & 65535);
+                out[(3 * PB + d) * n + slot] = (uint8_t)encode_momentum(p[u][d], v[u][d], sigma, E, err);
             }
         }
     }
 }
 
 // decoded codes and momenta of the current store, storage order
+template <int PB>
 __global__ void k_decode(int64_t n, int nc, const int64_t* __restrict__ offsets,
                          const uint8_t* __restrict__ st, const float* __restrict__ vc,
                          const float* __restrict__ sigma_p, const float* __restrict__ T,
@@ -354,8 +358,8 @@ __global__ void k_decode(int64_t n, int nc, const int64_t* __restrict__ offsets,
         const int cx = (int)(c % nc), cy = (int)((c / nc) % nc), cz = (int)(c / ((int64_t)nc * nc));
         const int cc[3] = {cx, cy, cz};
         for (int d = 0; d < 3; ++d) {
-            Qn[d * n + j] = cc[d] * kBins + st[d * n + j];
-            Pn[d * n + j] = decode_momentum(vc[d * ncells + c], sigma, T[st[(3 + d) * n + j]]);
+            Qn[d * n + j] = cc[d] * PosFmt<PB>::kBins + load_bin<PB>(st + (size_t)d * PB * n, j);
+            Pn[d * n + j] = decode_momentum(vc[d * ncells + c], sigma, T[st[(3 * PB + d) * n + j]]);
         }
     }
 }
@@ -394,22 +398,25 @@ int encode_from_qp(Sim& s, bool counts_ready) {
     if (!counts_ready) {
         cudaMemsetAsync(s.counts[nxt], 0, sizeof(int32_t) * s.ncells, st);
         cudaMemsetAsync(s.S, 0, sizeof(unsigned long long) * 3 * s.ncells, st);
-        k_hist<<<grid_for(s.n, 256, 152 * 8), 256, 0, st>>>(QPArrays{s.Qn, s.Pn, s.n}, s.n, s.nc,
-                                                             s.counts[nxt], s.S, s.err);
+        auto kh = s.pb == 2 ? k_hist<2, QPArrays> : k_hist<1, QPArrays>;
+        kh<<<grid_for(s.n, 256, 152 * 8), 256, 0, st>>>(QPArrays{s.Qn, s.Pn, s.n}, s.n, s.nc,
+                                                         s.counts[nxt], s.S, s.err);
         s.launches++;
     }
     int rc = scan_and_means(s, nxt);
     if (rc) return rc;
     prof_mark(s, 3);
     cudaMemsetAsync(s.d2, 0, 16, st);
-    k_sigma<<<grid_for(s.n, 256, 152 * 8), 256, 0, st>>>(QPArrays{s.Qn, s.Pn, s.n}, s.n, s.nc,
-                                                         s.vc[nxt], s.d2, s.err);
+    auto ks = s.pb == 2 ? k_sigma<2, QPArrays> : k_sigma<1, QPArrays>;
+    ks<<<grid_for(s.n, 256, 152 * 8), 256, 0, st>>>(QPArrays{s.Qn, s.Pn, s.n}, s.n, s.nc, s.vc[nxt],
+                                                     s.d2, s.err);
     k_sigma_final<<<1, 1, 0, st>>>(s.d2, s.n, s.sigma_d[nxt]);
     s.launches += 2;
     prof_mark(s, 4);
-    k_scatter<<<grid_for(s.n, 256), 256, 0, st>>>(QPArrays{s.Qn, s.Pn, s.n}, s.n, s.nc, s.vc[nxt],
-                                                  s.offsets[nxt], s.fill, s.sigma_d[nxt], s.Eedge,
-                                                  s.streams[nxt], s.err);
+    auto kc = s.pb == 2 ? k_scatter<2, QPArrays> : k_scatter<1, QPArrays>;
+    kc<<<grid_for(s.n, 256), 256, 0, st>>>(QPArrays{s.Qn, s.Pn, s.n}, s.n, s.nc, s.vc[nxt],
+                                           s.offsets[nxt], s.fill, s.sigma_d[nxt], s.Eedge,
+                                           s.streams[nxt], s.err);
     s.launches++;
     prof_mark(s, 5);
     s.cur = nxt;
@@ -430,14 +437,14 @@ int encode_from_psi(Sim& s, const double* scale) {
     const int nxt = 0;
     cudaMemsetAsync(s.counts[nxt], 0, sizeof(int32_t) * s.ncells, st);
     cudaMemsetAsync(s.S, 0, sizeof(unsigned long long) * 3 * s.ncells, st);
-    k_hist<<<grid_for(s.n, 256, 152 * 8), 256, 0, st>>>(src, s.n, s.nc, s.counts[nxt], s.S, s.err);
+    k_hist<1><<<grid_for(s.n, 256, 152 * 8), 256, 0, st>>>(src, s.n, s.nc, s.counts[nxt], s.S, s.err);
     s.launches++;
     int rc = scan_and_means(s, nxt);
     if (rc) return rc;
     cudaMemsetAsync(s.d2, 0, 16, st);
-    k_sigma<<<grid_for(s.n, 256, 152 * 8), 256, 0, st>>>(src, s.n, s.nc, s.vc[nxt], s.d2, s.err);
+    k_sigma<1><<<grid_for(s.n, 256, 152 * 8), 256, 0, st>>>(src, s.n, s.nc, s.vc[nxt], s.d2, s.err);
     k_sigma_final<<<1, 1, 0, st>>>(s.d2, s.n, s.sigma_d[nxt]);
-    k_scatter<<<grid_for(s.n, 256), 256, 0, st>>>(src, s.n, s.nc, s.vc[nxt], s.offsets[nxt], s.fill,
+    k_scatter<1><<<grid_for(s.n, 256), 256, 0, st>>>(src, s.n, s.nc, s.vc[nxt], s.offsets[nxt], s.fill,
                                                   s.sigma_d[nxt], s.Eedge, s.streams[nxt], s.err);
     s.launches += 3;
     s.cur = nxt;
@@ -475,9 +482,9 @@ int lowmem_passes(Sim& s) {
 }
 
 int decode_state(Sim& s) {
-    k_decode<<<grid_for(s.n, 256), 256, 0, s.stream>>>(s.n, s.nc, s.offsets[s.cur], s.streams[s.cur],
-                                                       s.vc[s.cur], s.sigma_d[s.cur], s.Tdec, s.Qn,
-                                                       s.Pn);
+    auto k = s.pb == 2 ? k_decode<2> : k_decode<1>;
+    k<<<grid_for(s.n, 256), 256, 0, s.stream>>>(s.n, s.nc, s.offsets[s.cur], s.streams[s.cur],
+                                                s.vc[s.cur], s.sigma_d[s.cur], s.Tdec, s.Qn, s.Pn);
     s.launches++;
     return check_launch(s, "decode");
 }

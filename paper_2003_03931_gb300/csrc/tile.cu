@@ -23,7 +23,7 @@ __device__ unsigned long long g_phase[4096 * kMarks];
     } while (0)
 #endif
 
-template <int D, bool LM>
+template <int D, bool LM, int PB>
 __device__ __forceinline__ void tile_component(int tid, const TileGeom& g, const TileParams& P,
                                                const float* gS, const float2* C, float2* W,
                                                TileCells cells, CtaScratch cs,
@@ -39,7 +39,7 @@ __device__ __forceinline__ void tile_component(int tid, const TileGeom& g, const
     tile_inv_x(tid, g, W);
     __syncthreads();
     PMPM_MARK(10 + 4 * D);
-    tile_interp<D, LM>(tid, g, P, W, cells, cs, lo, hi);
+    tile_interp<D, LM, PB>(tid, g, P, W, cells, cs, lo, hi);
 }
 
 // 128-bit block sum of the dispersion terms (low-memory mode 3), staged in
@@ -78,7 +78,7 @@ __device__ __forceinline__ void tile_sigma_flush(int tid, const TileParams& P, f
 // The whole tile: prologue, cell tables, deposit, forward transform, then
 // per force component the Green multiply, inverse transform and
 // interpolation (phases of tile_core.cuh with a block barrier between).
-template <bool LM>
+template <bool LM, int PB>
 __device__ __forceinline__ void tile_body(int tile, bool first, const TileParams& P,
                                           unsigned char* tile_smem, CtaScratch cs) {
     uint32_t* R = reinterpret_cast<uint32_t*>(tile_smem);
@@ -98,7 +98,7 @@ __device__ __forceinline__ void tile_body(int tile, bool first, const TileParams
     tile_cells_map(tid, g, cells);
     __syncthreads();
     PMPM_MARK(2);
-    tile_deposit_flat<LM>(tid, g, P, R, cells, cs);
+    tile_deposit_flat<LM, PB>(tid, g, P, R, cells, cs);
     __syncthreads();
     PMPM_MARK(3);
     tile_fwd_x(tid, R);
@@ -109,18 +109,20 @@ __device__ __forceinline__ void tile_body(int tile, bool first, const TileParams
     PMPM_MARK(5);
     tile_fwd_z(tid, C);
     unsigned long long lo = 0, hi = 0;
-    tile_component<0, LM>(tid, g, P, gS, C, W, cells, cs, lo, hi);
-    tile_component<1, LM>(tid, g, P, gS, C, W, cells, cs, lo, hi);
-    tile_component<2, LM>(tid, g, P, gS, C, W, cells, cs, lo, hi);
+    tile_component<0, LM, PB>(tid, g, P, gS, C, W, cells, cs, lo, hi);
+    tile_component<1, LM, PB>(tid, g, P, gS, C, W, cells, cs, lo, hi);
+    tile_component<2, LM, PB>(tid, g, P, gS, C, W, cells, cs, lo, hi);
     if (LM && P.mode == 3) tile_sigma_flush(tid, P, W, lo, hi);
     __syncthreads();
     PMPM_MARK(19);
 }
 
 // One CTA per SM (the tile needs 231 KB of shared memory): one CTA per tile.
+// PB: bytes per position bin.
+template <int PB>
 __global__ void __launch_bounds__(kTileThreads, 1) k_tile(TileParams P) {
     extern __shared__ __align__(16) unsigned char tile_smem[];
-    tile_body<false>((int)blockIdx.x, true, P, tile_smem, CtaScratch{nullptr, nullptr});
+    tile_body<false, PB>((int)blockIdx.x, true, P, tile_smem, CtaScratch{nullptr, nullptr});
 }
 
 // Low-memory passes (modes 2-4): one resident CTA per SM takes tiles from
@@ -134,7 +136,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_lowmem(TileParams P, i
     int tile = blockIdx.x;
     bool first = true;
     while (tile < ntiles) {
-        tile_body<true>(tile, first, P, tile_smem, cs);
+        tile_body<true, 1>(tile, first, P, tile_smem, cs);
         first = false;
         if (threadIdx.x == 0) next = (int)gridDim.x + atomicAdd(next_tile, 1);
         __syncthreads();
@@ -143,7 +145,8 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_lowmem(TileParams P, i
 }
 
 void tile_setup() {
-    cudaFuncSetAttribute(k_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemBytes);
+    cudaFuncSetAttribute(k_tile<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemBytes);
+    cudaFuncSetAttribute(k_tile<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemBytes);
     cudaFuncSetAttribute(k_tile_lowmem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemBytes);
 }
 
@@ -154,12 +157,12 @@ int tile_pass(Sim& s, int mode, float* G) {
     P.n = s.n;
     P.counts = s.counts[s.cur];
     P.offsets = s.offsets[s.cur];
-    P.m0 = cur_stream(s, 0);
-    P.m1 = cur_stream(s, 1);
-    P.m2 = cur_stream(s, 2);
-    P.u0 = cur_stream(s, 3);
-    P.u1 = cur_stream(s, 4);
-    P.u2 = cur_stream(s, 5);
+    P.m0 = m_stream(s, s.cur, 0);
+    P.m1 = m_stream(s, s.cur, 1);
+    P.m2 = m_stream(s, s.cur, 2);
+    P.u0 = u_stream(s, s.cur, 0);
+    P.u1 = u_stream(s, s.cur, 1);
+    P.u2 = u_stream(s, s.cur, 2);
     P.vc = s.vc[s.cur];
     P.sigma = s.sigma_d[s.cur];
     P.Tdec = s.Tdec;
@@ -194,7 +197,8 @@ int tile_pass(Sim& s, int mode, float* G) {
         cudaMemsetAsync(s.lm_next, 0, sizeof(int), s.stream);
     }
     if (mode >= 2) k_tile_lowmem<<<grid, kTileThreads, kTileSmemBytes, s.stream>>>(P, s.lm_next);
-    else k_tile<<<grid, kTileThreads, kTileSmemBytes, s.stream>>>(P);
+    else if (s.pb == 2) k_tile<2><<<grid, kTileThreads, kTileSmemBytes, s.stream>>>(P);
+    else k_tile<1><<<grid, kTileThreads, kTileSmemBytes, s.stream>>>(P);
     s.launches++;
     return check_launch(s, "tile pass");
 }

@@ -49,7 +49,7 @@ struct TileParams {
     int64_t n;                    // particles
     const int32_t* counts;        // [nc^3]
     const int64_t* offsets;       // [nc^3 + 1]
-    const uint8_t* m0;            // position bins (Eq. 2), storage order
+    const uint8_t* m0;            // position bins (Eq. 2; 1 or 2 bytes each), storage order
     const uint8_t* m1;
     const uint8_t* m2;
     const uint8_t* u0;            // velocity bins (Eq. 3)
@@ -260,28 +260,33 @@ PMPM_HD void smem_red_u32(uint32_t* p, uint32_t v) {
 // at most 2^21; with at most 255 particles per cell no node can pass 2^32, so
 // CHECK (overflow detection on the returned old value) is needed only when
 // some halo cell holds more.
-template <bool CHECK>
+template <bool CHECK, int PB>
 PMPM_HD void deposit_one(const TileGeom& g, const int (&cu)[3], const int (&m)[3], uint32_t* R,
                          uint32_t* err) {
+    using F = PosFmt<PB>;
+    constexpr int W = F::kFineW;
     int li[3], w1[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        // s = 2Q + 1 - 64 relative to the mesh origin, units 1/128
-        const int s = 2 * (cu[d] * kBins + m[d]) + 1 - kCodesPerFine - 128 * g.o[d];
-        li[d] = s >> 7;
-        w1[d] = s & 127;
+        // s = 2Q + 1 - B/4 relative to the mesh origin, units 1/W (W = B/2)
+        const int s = 2 * (cu[d] * F::kBins + m[d]) + 1 - F::kCodesPerFine - W * g.o[d];
+        li[d] = s >> F::kFineWBits;
+        w1[d] = s & (W - 1);
     }
     // a cloud whose lower node is below -1 or above 31 on some axis misses the box
     if ((unsigned)(li[0] + 1) > 32u || (unsigned)(li[1] + 1) > 32u || (unsigned)(li[2] + 1) > 32u) return;
     const bool inside = (unsigned)li[0] < 31u && (unsigned)li[1] < 31u && (unsigned)li[2] < 31u;
-    const uint32_t wyz[4] = {(uint32_t)((128 - w1[1]) * (128 - w1[2])), (uint32_t)(w1[1] * (128 - w1[2])),
-                             (uint32_t)((128 - w1[1]) * w1[2]), (uint32_t)(w1[1] * w1[2])};
+    const uint32_t wyz[4] = {(uint32_t)((W - w1[1]) * (W - w1[2])), (uint32_t)(w1[1] * (W - w1[2])),
+                             (uint32_t)((W - w1[1]) * w1[2]), (uint32_t)(w1[1] * w1[2])};
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
         const int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
         const int x = li[0] + dx, y = li[1] + dy, z = li[2] + dz;
         if (!inside && ((unsigned)x >= 32u || (unsigned)y >= 32u || (unsigned)z >= 32u)) continue;
-        const uint32_t w = (uint32_t)(dx ? w1[0] : 128 - w1[0]) * wyz[dy + 2 * dz];
+        // 1-byte: exact in 2^-21; 2-byte: the 2^-45 product rounded to 2^-21
+        const uint32_t w = PB == 1 ? (uint32_t)(dx ? w1[0] : W - w1[0]) * wyz[dy + 2 * dz]
+                                   : cic_weight3<PB>(dx ? w1[0] : W - w1[0], dy ? w1[1] : W - w1[1],
+                                                     dz ? w1[2] : W - w1[2]);
         if (w == 0u) continue;
         if (CHECK) {
             const uint32_t old = smem_add_u32(&R[ridx(x, y, z)], w);
@@ -293,11 +298,18 @@ PMPM_HD void deposit_one(const TileGeom& g, const int (&cu)[3], const int (&m)[3
 }
 
 // Coarse-mesh force (all three components) at one particle, CIC gather
+template <int PB>
 PMPM_HD void coarse_gather(const TileParams& P, const int64_t (&Q)[3], float (&gc)[3]) {
+    using F = PosFmt<PB>;
+    constexpr int W = F::kCoarseW;
     const int64_t ncells = (int64_t)P.nc * P.nc * P.nc;
     Cic1 cc[3];
 #pragma unroll
-    for (int e = 0; e < 3; ++e) cc[e] = cic_coarse(Q[e]);
+    for (int e = 0; e < 3; ++e) {
+        const int64_t sc = 2 * Q[e] + 1 - F::kBins;     // units 1/(2B) of a coarse cell
+        cc[e].i0 = (int)(sc >> F::kCoarseWBits);
+        cc[e].w1 = (int)(sc & (W - 1));
+    }
     int ix[2], iy[2], iz[2];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
@@ -310,8 +322,11 @@ PMPM_HD void coarse_gather(const TileParams& P, const int64_t (&Q)[3], float (&g
     for (int c = 0; c < 8; ++c) {
         const int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
         const int64_t node = ix[dx] + (int64_t)P.nc * (iy[dy] + (int64_t)P.nc * iz[dz]);
-        const float w = (float)((dx ? cc[0].w1 : 512 - cc[0].w1) * (dy ? cc[1].w1 : 512 - cc[1].w1)) *
-                        (float)(dz ? cc[2].w1 : 512 - cc[2].w1);
+        const float w = PB == 1
+            ? (float)((dx ? cc[0].w1 : W - cc[0].w1) * (dy ? cc[1].w1 : W - cc[1].w1)) *
+                  (float)(dz ? cc[2].w1 : W - cc[2].w1)
+            : (float)cic_weight3<PB>(dx ? cc[0].w1 : W - cc[0].w1, dy ? cc[1].w1 : W - cc[1].w1,
+                                     dz ? cc[2].w1 : W - cc[2].w1);
 #pragma unroll
         for (int e = 0; e < 3; ++e) gc[e] += w * P.Fl[e * ncells + node];
     }
@@ -645,7 +660,7 @@ PMPM_HD int own_of(const TileCells& c, int v) {
 constexpr int kDepositIlp = 4;   // halo particles per thread per iteration
 constexpr int kGatherIlp = 2;    // own particles per thread per iteration
 
-template <bool LM>
+template <bool LM, int PB>
 PMPM_HD void tile_deposit_flat(int tid, const TileGeom& g, const TileParams& P, uint32_t* R,
                                TileCells c, CtaScratch cs) {
     const int total = c.pre[kHaloMax];
@@ -660,9 +675,9 @@ PMPM_HD void tile_deposit_flat(int tid, const TileGeom& g, const TileParams& P, 
             b[u] = ok[u] ? halo_of(c, v) : 0;
             const int64_t j = c.st[b[u]] + (v - c.pre[b[u]]);
             if (ok[u]) {
-                m[u][0] = P.m0[j];
-                m[u][1] = P.m1[j];
-                m[u][2] = P.m2[j];
+                m[u][0] = load_bin<PB>(P.m0, j);
+                m[u][1] = load_bin<PB>(P.m1, j);
+                m[u][2] = load_bin<PB>(P.m2, j);
             }
         }
 #pragma unroll
@@ -670,8 +685,8 @@ PMPM_HD void tile_deposit_flat(int tid, const TileGeom& g, const TileParams& P, 
             if (!ok[u]) continue;
             const int cu[3] = {g.c0[0] - 2 + b[u] % kHaloDim, g.c0[1] - 2 + (b[u] / kHaloDim) % kHaloDim,
                                g.c0[2] - 2 + b[u] / (kHaloDim * kHaloDim)};
-            if (check) deposit_one<true>(g, cu, m[u], R, P.err);
-            else deposit_one<false>(g, cu, m[u], R, P.err);
+            if (check) deposit_one<true, PB>(g, cu, m[u], R, P.err);
+            else deposit_one<false, PB>(g, cu, m[u], R, P.err);
         }
     }
     // long-range force of the tile's own particles
@@ -686,16 +701,17 @@ PMPM_HD void tile_deposit_flat(int tid, const TileGeom& g, const TileParams& P, 
             const int p = v < ptotal ? own_of(c, v) : 0;
             j[u] = v < ptotal ? obase + c.prel[p] + (v - c.ppre[p]) : -1;
             if (j[u] >= 0) {
-                Q[u][0] = (int64_t)(g.c0[0] + p % kOwnDim) * kBins + P.m0[j[u]];
-                Q[u][1] = (int64_t)(g.c0[1] + (p / kOwnDim) % kOwnDim) * kBins + P.m1[j[u]];
-                Q[u][2] = (int64_t)(g.c0[2] + p / (kOwnDim * kOwnDim)) * kBins + P.m2[j[u]];
+                constexpr int B = PosFmt<PB>::kBins;
+                Q[u][0] = (int64_t)(g.c0[0] + p % kOwnDim) * B + load_bin<PB>(P.m0, j[u]);
+                Q[u][1] = (int64_t)(g.c0[1] + (p / kOwnDim) % kOwnDim) * B + load_bin<PB>(P.m1, j[u]);
+                Q[u][2] = (int64_t)(g.c0[2] + p / (kOwnDim * kOwnDim)) * B + load_bin<PB>(P.m2, j[u]);
             }
         }
 #pragma unroll
         for (int u = 0; u < kGatherIlp; ++u) {
             if (j[u] < 0) continue;
             float gc[3];
-            coarse_gather(P, Q[u], gc);
+            coarse_gather<PB>(P, Q[u], gc);
             if (LM) {
                 const int v = v0 + u * kTileThreads;
                 if (v >= kLowmemCap) {
@@ -920,9 +936,10 @@ PMPM_HD void lowmem_particle(const TileParams& P, const int32_t (&q)[3], const f
 }
 
 // LM: the low-memory passes (modes 2-4); otherwise modes 0 and 1.
-template <int D, bool LM>
+template <int D, bool LM, int PB>
 PMPM_HD void tile_interp(int tid, const TileGeom& g, const TileParams& P, const float2* W,
                          TileCells c, CtaScratch cs, unsigned long long& lo, unsigned long long& hi) {
+    using F = PosFmt<PB>;
     constexpr int U = LM ? 1 : 2;   // particles per thread per iteration, loads issued together
     const float* Wf = reinterpret_cast<const float*>(W);
     const int64_t ncells = (int64_t)P.nc * P.nc * P.nc;
@@ -954,9 +971,9 @@ PMPM_HD void tile_interp(int tid, const TileGeom& g, const TileParams& P, const 
                       cz = g.c0[2] + p / (kOwnDim * kOwnDim);
             cell[u] = cx + (int64_t)P.nc * (cy + (int64_t)P.nc * cz);
             if (j[u] >= 0) {
-                Q[u][0] = (int64_t)cx * kBins + P.m0[j[u]];
-                Q[u][1] = (int64_t)cy * kBins + P.m1[j[u]];
-                Q[u][2] = (int64_t)cz * kBins + P.m2[j[u]];
+                Q[u][0] = (int64_t)cx * F::kBins + load_bin<PB>(P.m0, j[u]);
+                Q[u][1] = (int64_t)cy * F::kBins + load_bin<PB>(P.m1, j[u]);
+                Q[u][2] = (int64_t)cz * F::kBins + load_bin<PB>(P.m2, j[u]);
                 gcd[u] = lm ? cs.sp[D * kLowmemCap + v] : slot[D * n + j[u]];
                 if (lm || P.mode >= 1) {
                     u8[u] = ud[j[u]];
@@ -977,16 +994,17 @@ PMPM_HD void tile_interp(int tid, const TileGeom& g, const TileParams& P, const 
             int lo3[3], w1[3];
 #pragma unroll
             for (int e = 0; e < 3; ++e) {
-                const int s = (int)(2 * Q[u][e] + 1 - kCodesPerFine - 128 * (int64_t)g.o[e]);
-                lo3[e] = (s >> 7) - (kBuffer - 1);
-                w1[e] = s & 127;
+                const int s = (int)(2 * Q[u][e] + 1 - F::kCodesPerFine - (int64_t)F::kFineW * g.o[e]);
+                lo3[e] = (s >> F::kFineWBits) - (kBuffer - 1);
+                w1[e] = s & (F::kFineW - 1);
             }
             float gf = 0.f;
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
-                const float w = (float)((dx ? w1[0] : 128 - w1[0]) * (dy ? w1[1] : 128 - w1[1]) *
-                                        (dz ? w1[2] : 128 - w1[2]));
+                constexpr int W = F::kFineW;
+                const float w = (float)cic_weight3<PB>(dx ? w1[0] : W - w1[0], dy ? w1[1] : W - w1[1],
+                                                       dz ? w1[2] : W - w1[2]);
                 gf += w * Wf[wfidx(lo3[0] + dx, lo3[1] + dy, lo3[2] + dz)];
             }
             const float gval = gf * 4.76837158203125e-07f + gcd[u];   // 2^-21
@@ -1003,7 +1021,7 @@ PMPM_HD void tile_interp(int tid, const TileGeom& g, const TileParams& P, const 
             int64_t dq = 0;
             if (fabsf(xq) < 1.0e9f) dq = (int64_t)floorf(fadd_rn(xq, 0.5f));
             else flag_error(P.err, kErrDrift);
-            const int64_t M = (int64_t)P.nc * kBins;
+            const int64_t M = (int64_t)P.nc * F::kBins;
             int64_t qn = (Q[u][D] + dq) % M;
             if (qn < 0) qn += M;
             if (!lm) {
@@ -1012,8 +1030,8 @@ PMPM_HD void tile_interp(int tid, const TileGeom& g, const TileParams& P, const 
                 if (fuse) {
                     const int32_t qa[3] = {q01[u][0], q01[u][1], (int32_t)qn};
                     const float pa[3] = {p01[u][0], p01[u][1], pn};
-                    const int64_t key = (int64_t)(qa[0] >> 8) +
-                                        P.nc * ((int64_t)(qa[1] >> 8) + (int64_t)P.nc * (qa[2] >> 8));
+                    const int64_t key = (int64_t)(qa[0] >> F::kShift) +
+                                        P.nc * ((int64_t)(qa[1] >> F::kShift) + (int64_t)P.nc * (qa[2] >> F::kShift));
                     gmem_add_i32(&P.counts_new[key], 1);
 #pragma unroll
                     for (int d = 0; d < 3; ++d) {

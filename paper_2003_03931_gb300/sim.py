@@ -44,6 +44,21 @@ class SimConfig:
         return self.nc ** 3
 
 
+def split_store(raw, n, pos_bytes):
+    """Position and velocity bins of a raw PMPM_STREAMS buffer."""
+    raw = np.ascontiguousarray(raw).reshape(-1)
+    pb = pos_bytes
+    m = raw[:3 * pb * n].view(np.uint8 if pb == 1 else np.uint16).reshape(3, n)
+    u = raw[3 * pb * n:].reshape(3, n)
+    return m, u
+
+
+def join_store(m, u):
+    """The raw PMPM_STREAMS buffer of position bins m [3, N] and velocity bins u."""
+    return np.concatenate([np.ascontiguousarray(m).view(np.uint8).reshape(-1),
+                           np.ascontiguousarray(u, np.uint8).reshape(-1)])
+
+
 def workspace_bytes(cfg):
     lib = _lib.load()
     out = ctypes.c_size_t(0)
@@ -131,7 +146,15 @@ class Simulation:
         return arr
 
     def fetch_streams(self):
-        return self._fetch(_lib.STREAMS, np.empty((6, self.cfg.n), np.uint8))
+        """The raw store: uint8 [6, N] for 1-byte positions, otherwise the
+        (3 pos_bytes + 3) N bytes of include/pmpm.h's PMPM_STREAMS layout."""
+        if self.cfg.pos_bytes == 1:
+            return self._fetch(_lib.STREAMS, np.empty((6, self.cfg.n), np.uint8))
+        return self._fetch(_lib.STREAMS, np.empty((3 * self.cfg.pos_bytes + 3) * self.cfg.n, np.uint8))
+
+    def fetch_store(self):
+        """(m [3, N] uint8 or uint16 position bins, u [3, N] uint8 velocity bins)."""
+        return split_store(self.fetch_streams(), self.cfg.n, self.cfg.pos_bytes)
 
     def fetch_counts(self):
         return self._fetch(_lib.COUNTS, np.empty(self.cfg.ncells, np.int32))
@@ -178,7 +201,7 @@ class Simulation:
                                        ctypes.sizeof(sc)))
 
     def load_state(self, state):
-        self._load(_lib.STREAMS, np.asarray(state["streams"], np.uint8))
+        self._load(_lib.STREAMS, np.ascontiguousarray(state["streams"]).view(np.uint8))
         self._load(_lib.COUNTS, np.asarray(state["counts"], np.int32))
         self._load(_lib.VC, np.asarray(state["vc"], np.float32))
         sc = state["scalars"]

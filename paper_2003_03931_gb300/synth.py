@@ -14,6 +14,8 @@ WORKLOADS = {
     "c2_128": dict(np=128, nc=64, a_init=0.02, a_final=1.0, n_steps=20),
     "c3_512": dict(np=512, nc=256, a_init=0.02, a_final=1.0, n_steps=20),
     "c4sub_256": dict(np=256, nc=128, a_init=0.02, a_final=1.0, n_steps=20),
+    # the same box with 2-byte positions (Sec. III-A)
+    "c4sub_256_pos2": dict(np=256, nc=128, a_init=0.02, a_final=1.0, n_steps=20, pos_bytes=2),
     # small ragged-tile case: 7 tiles of 4/5 coarse cells per side
     "ragged_32": dict(np=32, nc=32, a_init=0.02, a_final=1.0, n_steps=10),
     # 2048^3 particles (51.5 GB at 6 B/particle) on one GPU: low-memory step
@@ -23,20 +25,21 @@ WORKLOADS = {
 IC_SPECTRUM = dict(slope=-1.5, k_c=np.pi / 2, rms_disp=0.3)
 
 
-def uniform_codes(rng, n, nc):
-    """Codes uniformly over the box, int32 [3, n]."""
-    return rng.integers(0, nc * 256, size=(3, n)).astype(np.int32)
+def uniform_codes(rng, n, nc, bins=256):
+    """Codes uniformly over the box, int32 [3, n] (bins per coarse cell: 256
+    for 1-byte, 65536 for 2-byte positions)."""
+    return rng.integers(0, nc * bins, size=(3, n)).astype(np.int32)
 
 
-def clustered_codes(rng, n, nc, n_clusters=12, frac=0.6, width_fine=3.0):
+def clustered_codes(rng, n, nc, n_clusters=12, frac=0.6, width_fine=3.0, bins=256):
     """A fraction of the particles in Gaussian clumps (width in fine cells),
     the rest uniform; int32 [3, n]."""
-    M = nc * 256
+    M = nc * bins
     Q = rng.integers(0, M, size=(3, n)).astype(np.int64)
     k = int(frac * n)
     centres = rng.integers(0, M, size=(3, n_clusters))
     which = rng.integers(0, n_clusters, size=k)
-    off = rng.normal(scale=width_fine * 64.0, size=(3, k))
+    off = rng.normal(scale=width_fine * bins / 4.0, size=(3, k))
     Q[:, :k] = np.mod(np.floor(centres[:, which] + off).astype(np.int64), M)
     return Q.astype(np.int32)
 

@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 from oracle import dynamics
+from paper_2003_03931_gb300.sim import join_store, split_store
 
 
 def need_gpu():
@@ -24,14 +25,19 @@ def make_sim(**kw):
 def oracle_state(sim):
     """The sim's current store as an oracle State (same storage order)."""
     st = sim.fetch_state()
-    return dynamics.State(sim.cfg.nc, st["counts"], st["streams"][:3].T, st["streams"][3:].T,
-                          st["vc"].T, np.float32(st["scalars"]["sigma"]), st["scalars"]["a"],
-                          st["scalars"]["step"])
+    pb = sim.cfg.pos_bytes
+    m, u = split_store(st["streams"], sim.cfg.n, pb)
+    return dynamics.State(sim.cfg.nc, st["counts"], m.T, u.T, st["vc"].T,
+                          np.float32(st["scalars"]["sigma"]), st["scalars"]["a"],
+                          st["scalars"]["step"], pos_bytes=pb)
 
 
 def load_oracle_state(sim, ost):
-    sim.load_state({"streams": np.concatenate([ost.m.T, ost.u.T]).astype(np.uint8),
-                    "counts": ost.counts, "vc": ost.vc.T,
+    m = np.ascontiguousarray(ost.m.T).astype(np.uint8 if sim.cfg.pos_bytes == 1 else np.uint16)
+    raw = join_store(m, ost.u.T)
+    if sim.cfg.pos_bytes == 1:
+        raw = raw.reshape(6, -1)
+    sim.load_state({"streams": raw, "counts": ost.counts, "vc": ost.vc.T,
                     "scalars": {"a": ost.a, "sigma": float(ost.sigma), "step": ost.step}})
 
 

@@ -37,8 +37,11 @@ def test_workspace_bytes_and_validation(lib):
     assert 0 < b1 < b2 < b3
     # the persistent particle store is 2 x 6 bytes per particle plus cell fields
     assert b3 > 2 * 6 * 512 ** 3
+    # 2-byte positions: 9 bytes per particle in each store buffer
+    assert workspace_bytes(SimConfig(np=512, nc=256, pos_bytes=2)) - b3 == 2 * 3 * 512 ** 3
     for bad in (dict(np=30, nc=16), dict(np=32, nc=12), dict(np=32, nc=16, tile_max=6),
-                dict(np=32, nc=16, buffer=4), dict(np=32, nc=16, pos_bytes=2),
+                dict(np=32, nc=16, buffer=4), dict(np=32, nc=16, pos_bytes=3),
+                dict(np=32, nc=16, pos_bytes=2, lowmem=True),
                 dict(np=32, nc=16, a_init=0.5, a_final=0.1)):
         with pytest.raises(PmpmError):
             workspace_bytes(SimConfig(**bad))
