@@ -59,13 +59,19 @@ __global__ void __launch_bounds__(256) k_coarse_deposit(int nc, const int32_t* _
         for (int kz = 0; kz < 3; ++kz)
 #pragma unroll
             for (int ky = 0; ky < 3; ++ky) {
-                const unsigned long long wyz = (unsigned long long)w[1][ky] * w[2][kz];
+                if (PB == 1) {
+                    // 1-byte bins: products below 2^27, 32-bit arithmetic
+                    const uint32_t wyz = w[1][ky] * w[2][kz];
 #pragma unroll
-                for (int kx = 0; kx < 3; ++kx) {
-                    const unsigned long long w3 = wyz * w[0][kx];
+                    for (int kx = 0; kx < 3; ++kx)
+                        a[kx + 3 * (ky + 3 * kz)] += (unsigned long long)(wyz * w[0][kx]);
+                } else {
                     // 2-byte bins: the 2^-51 product rounded to the 2^-27 unit
-                    a[kx + 3 * (ky + 3 * kz)] +=
-                        PB == 1 ? w3 : round_half_even_shift(w3, PosFmt<PB>::kRoundBits);
+                    const unsigned long long wyz = (unsigned long long)w[1][ky] * w[2][kz];
+#pragma unroll
+                    for (int kx = 0; kx < 3; ++kx)
+                        a[kx + 3 * (ky + 3 * kz)] +=
+                            round_half_even_shift(wyz * w[0][kx], PosFmt<PB>::kRoundBits);
                 }
             }
     }
