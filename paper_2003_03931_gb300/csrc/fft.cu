@@ -26,6 +26,7 @@ __device__ __forceinline__ C cmul(C a, C b) {
 // Each thread holds at most kPassElems elements of the group; it issues all
 // its global loads before storing any into shared memory.
 constexpr int kPassThreads = 256;
+constexpr int kPassSmem = 72 * 1024;   // two buffers of 4096 + P padded elements
 // P n / threads: 4096 / 256 (float), 2048 / 256 (double)
 template <typename R> constexpr int pass_elems() { return sizeof(R) == 4 ? 16 : 8; }
 
@@ -36,8 +37,11 @@ __global__ void __launch_bounds__(kPassThreads) k_fft_pass(typename Cplx<R>::T* 
                                                            int log2tw) {
     using C = typename Cplx<R>::T;
     extern __shared__ __align__(16) unsigned char fft_smem[];
+    // pencils sit n + 1 apart in shared memory: the pencils a warp touches
+    // together (adjacent in x for the y and z axes) fall in different banks
+    const int ps = n + 1;
     C* buf0 = reinterpret_cast<C*>(fft_smem);
-    C* buf1 = buf0 + (size_t)P * n;
+    C* buf1 = buf0 + (size_t)P * ps;
     const int64_t q0 = (int64_t)blockIdx.x * P;     // first pencil of the group
     const int tid = threadIdx.x;
     const int total = P * n;
@@ -74,7 +78,7 @@ __global__ void __launch_bounds__(kPassThreads) k_fft_pass(typename Cplx<R>::T* 
         if (e < total) {
             int p, j;
             coords(e, p, j);
-            buf0[(p << log2n) + j] = v[r];
+            buf0[p * ps + j] = v[r];
         }
     }
     __syncthreads();
@@ -88,7 +92,7 @@ __global__ void __launch_bounds__(kPassThreads) k_fft_pass(typename Cplx<R>::T* 
         for (int e = tid; e < P * half; e += kPassThreads) {
             const int p = e >> lhalf, j = e & (half - 1);
             const int k = j & (Ns - 1);
-            const int b = p << log2n;
+            const int b = p * ps;
             C v0 = src[b + j];
             C v1 = src[b + j + half];
             C w = tw[(int64_t)k << twsh];
@@ -111,7 +115,7 @@ __global__ void __launch_bounds__(kPassThreads) k_fft_pass(typename Cplx<R>::T* 
         if (e < total) {
             int p, j;
             coords(e, p, j);
-            data[base_of(p) + ((int64_t)j << sh)] = src[(p << log2n) + j];
+            data[base_of(p) + ((int64_t)j << sh)] = src[p * ps + j];
         }
     }
 }
@@ -141,7 +145,7 @@ int fft3d(Sim& s, void* data, int n, int sign) {
     const int P = pencils_per_block<R>(n);
     if (P * n > pass_elems<R>() * kPassThreads)
         return set_error(s, PMPM_EINVAL, "fft length %d too long for this precision", n);
-    const size_t smem = 2 * (size_t)P * n * sizeof(C);
+    const size_t smem = 2 * (size_t)P * (n + 1) * sizeof(C);
     const C* tw = sizeof(R) == 4 ? reinterpret_cast<const C*>(s.tw_f)
                                  : reinterpret_cast<const C*>(s.tw_d);
     const int64_t groups = (int64_t)n * n / P;
@@ -156,8 +160,8 @@ int fft3d(Sim& s, void* data, int n, int sign) {
 template int fft3d<float>(Sim&, void*, int, int);
 
 void fft_setup() {
-    cudaFuncSetAttribute(k_fft_pass<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536);
-    cudaFuncSetAttribute(k_fft_pass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536);
+    cudaFuncSetAttribute(k_fft_pass<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPassSmem);
+    cudaFuncSetAttribute(k_fft_pass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPassSmem);
 }
 
 // The same three float passes for a caller-supplied twiddle table of tw_n
@@ -168,8 +172,8 @@ cudaError_t fft3d_float_raw(cudaStream_t st, float2* data, int n, int sign, cons
     while ((1 << log2n) < n) ++log2n;
     const int P = pencils_per_block<float>(n);
     if (P * n > pass_elems<float>() * kPassThreads) return cudaErrorInvalidValue;
-    const size_t smem = 2 * (size_t)P * n * sizeof(float2);
-    cudaFuncSetAttribute(k_fft_pass<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536);
+    const size_t smem = 2 * (size_t)P * (n + 1) * sizeof(float2);
+    cudaFuncSetAttribute(k_fft_pass<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPassSmem);
     const int64_t groups = (int64_t)n * n / P;
     for (int axis = 0; axis < 3; ++axis)
         k_fft_pass<float><<<(unsigned)groups, kPassThreads, smem, st>>>(data, n, log2n, axis, sign, P,
