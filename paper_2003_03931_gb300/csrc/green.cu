@@ -86,15 +86,50 @@ __device__ void ewald_force(const Ewald& e, double x, double y, double z, double
     ewald_fourier(e, x, y, z, out);
 }
 
+// The x component of the same force, evaluated by one warp: lane l takes the
+// images and Fourier vectors with flat index l, l + 32, ...; the lane sums
+// are combined in a fixed order (every lane returns the total).
+__device__ double ewald_force_x_warp(const Ewald& e, double x, double y, double z, int lane) {
+    double fx = 0.0;
+    if (!(x == 0.0 && y == 0.0 && z == 0.0)) {
+        const double two_over_sqrt_pi = 1.1283791670955126;
+        const int ni = 2 * e.n_img + 1;
+        for (int t = lane; t < ni * ni * ni; t += 32) {
+            const int nx = t % ni - e.n_img, ny = (t / ni) % ni - e.n_img, nz = t / (ni * ni) - e.n_img;
+            const double rx = x + nx * e.L, ry = y + ny * e.L, rz = z + nz * e.L;
+            const double r2 = rx * rx + ry * ry + rz * rz;
+            if (r2 == 0.0 || r2 > e.rs * e.rs) continue;
+            const double r = sqrt(r2);
+            const double ar = e.alpha * r;
+            const double screen = erfc(ar) + two_over_sqrt_pi * ar * exp(-ar * ar);
+            fx -= rx * screen / (r2 * r);
+        }
+        const double pref = 4.0 * kPi / (e.L * e.L * e.L);
+        const double kf = 2.0 * kPi / e.L;
+        const int H = e.h_max, nh = 2 * H + 1;
+        for (int t = lane; t < nh * nh * nh; t += 32) {
+            const int hx = t % nh - H, hy = (t / nh) % nh - H, hz = t / (nh * nh) - H;
+            const int h2 = hx * hx + hy * hy + hz * hz;
+            if (h2 == 0 || h2 > H * H) continue;
+            const double kx = kf * hx, ky = kf * hy, kz = kf * hz;
+            const double k2 = kx * kx + ky * ky + kz * kz;
+            fx -= pref * exp(-k2 / (4.0 * e.alpha * e.alpha)) / k2 * sin(kx * x + ky * y + kz * z) * kx;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) fx += __shfl_xor_sync(0xffffffffu, fx, o);
+    return fx;
+}
+
 // x-component of the coarse kernel at coarse offsets D in [-3, 3]^3
+// one warp per entry
 __global__ void k_coarse_small(double L, double* Tsmall) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (i >= 343) return;
     const int Dx = i % 7 - 3, Dy = (i / 7) % 7 - 3, Dz = i / 49 - 3;
     const Ewald e = make_ewald(L, 8);
-    double f[3];
-    ewald_force(e, 4.0 * Dx, 4.0 * Dy, 4.0 * Dz, f);
-    Tsmall[i] = f[0];
+    const double fx = ewald_force_x_warp(e, 4.0 * Dx, 4.0 * Dy, 4.0 * Dz, lane);
+    if (lane == 0) Tsmall[i] = fx;
 }
 
 // coarse CIC weights of a point at pos (fine units, relative to the left edge
@@ -106,22 +141,22 @@ __device__ void cw1(double pos, int& a0, double& w0, double& w1) {
     w0 = 1.0 - w1;
 }
 
-// K_s^x(d) = K_per^x(d) - A^x(d) over d in [-5, 5]^3 (zero off the support)
+// K_s^x(d) = K_per^x(d) - A^x(d) over d in [-5, 5]^3 (zero off the support);
+// one warp per entry, the lanes splitting the Ewald sum and the 64 centres
 __global__ void k_fine_values(double L, const double* Tsmall, double* Ks) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (i >= 1331) return;
     const int dx = i % 11 - 5, dy = (i / 11) % 11 - 5, dz = i / 121 - 5;
     const int r2 = dx * dx + dy * dy + dz * dz;
     if (r2 == 0 || r2 >= kBuffer * kBuffer) {
-        Ks[i] = 0.0;
+        if (lane == 0) Ks[i] = 0.0;
         return;
     }
     const Ewald e = make_ewald(L, 8);
-    double f[3];
-    ewald_force(e, dx, dy, dz, f);
+    const double fx = ewald_force_x_warp(e, dx, dy, dz, lane);
     // A^x(d): average over the 64 fine-cell centres s of one coarse cell
     double A = 0.0;
-    for (int s = 0; s < 64; ++s) {
+    for (int s = lane; s < 64; s += 32) {
         const double sx = (s & 3) + 0.5, sy = ((s >> 2) & 3) + 0.5, sz = (s >> 4) + 0.5;
         int a0[3], b0[3];
         double aw[3][2], bw[3][2];
@@ -143,28 +178,33 @@ __global__ void k_fine_values(double L, const double* Tsmall, double* Ks) {
             }
         }
     }
-    Ks[i] = f[0] - A / 64.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) A += __shfl_xor_sync(0xffffffffu, A, o);
+    if (lane == 0) Ks[i] = fx - A / 64.0;
 }
 
 // S_s(a, b, c) = sum_d K_s^x(d) sin(2 pi a dx/32) cos(2 pi b dy/32) cos(2 pi c dz/32),
 // times 2^-21 (density units) and 2^-15 (unnormalised inverse 32^3 DFT)
+// one warp per entry, the lanes splitting the 1331 separations
 __global__ void k_fine_table(const double* Ks, float* table) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (i >= kGreenS * kGreenS * kGreenS) return;
     const int a = i / (kGreenS * kGreenS), b = (i / kGreenS) % kGreenS, c = i % kGreenS;
     if (a == 0 || a == 16) {
-        table[i] = 0.f;   // odd in its own axis: zero at k = 0 and at Nyquist
+        if (lane == 0) table[i] = 0.f;   // odd in its own axis: zero at k = 0 and at Nyquist
         return;
     }
     double acc = 0.0;
-    for (int j = 0; j < 1331; ++j) {
+    for (int j = lane; j < 1331; j += 32) {
         const double k = Ks[j];
         if (k == 0.0) continue;
         const int dx = j % 11 - 5, dy = (j / 11) % 11 - 5, dz = j / 121 - 5;
         acc += k * sinpi((double)(2 * a * dx) / 32.0) * cospi((double)(2 * b * dy) / 32.0) *
                cospi((double)(2 * c * dz) / 32.0);
     }
-    table[i] = (float)(acc * 0x1p-36);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) table[i] = (float)(acc * 0x1p-36);
 }
 
 // b <= c half of the 17^3 table for own-axis rows a = 1..15 (rows 0 and 16
@@ -230,9 +270,9 @@ int build_green_tables(Sim& s) {
     double* Tsmall = reinterpret_cast<double*>(s.scratch);
     double* Ks = Tsmall + 343;
     double2* mesh = reinterpret_cast<double2*>(align_up(reinterpret_cast<uintptr_t>(Ks + 1331)));
-    k_coarse_small<<<2, 256, 0, st>>>(L, Tsmall);
-    k_fine_values<<<6, 256, 0, st>>>(L, Tsmall, Ks);
-    k_fine_table<<<(kGreenS * kGreenS * kGreenS + 255) / 256, 256, 0, st>>>(Ks, s.green_fine);
+    k_coarse_small<<<(343 * 32 + 255) / 256, 256, 0, st>>>(L, Tsmall);
+    k_fine_values<<<(1331 * 32 + 255) / 256, 256, 0, st>>>(L, Tsmall, Ks);
+    k_fine_table<<<(kGreenS * kGreenS * kGreenS * 32 + 255) / 256, 256, 0, st>>>(Ks, s.green_fine);
     k_pack_fine<<<((kGreenS - 2) * kGreenS * (kGreenS + 1) / 2 + 255) / 256, 256, 0, st>>>(s.green_fine,
                                                                                    s.green_packed);
     const Ewald e = make_ewald(L, nc / 2 - 1);
