@@ -125,6 +125,14 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(TileParams P) {
     tile_body<false, PB>((int)blockIdx.x, true, P, tile_smem, CtaScratch{nullptr, nullptr});
 }
 
+// One tile of a low-memory pass, out of line: called from the persistent
+// loop, it gets its own register allocation without the loop's state
+// (inlined, the kernel spilled 372 bytes per thread; measured 10% slower).
+__device__ __noinline__ void tile_body_lowmem(int tile, bool first, const TileParams& P,
+                                              unsigned char* tile_smem, CtaScratch cs) {
+    tile_body<true, 1>(tile, first, P, tile_smem, cs);
+}
+
 // Low-memory passes (modes 2-4): one resident CTA per SM takes tiles from
 // a counter (its first tile is blockIdx.x) and keeps its scratch slot.
 __global__ void __launch_bounds__(kTileThreads, 1) k_tile_lowmem(TileParams P, int* next_tile) {
@@ -136,7 +144,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_lowmem(TileParams P, i
     int tile = blockIdx.x;
     bool first = true;
     while (tile < ntiles) {
-        tile_body<true, 1>(tile, first, P, tile_smem, cs);
+        tile_body_lowmem(tile, first, P, tile_smem, cs);
         first = false;
         if (threadIdx.x == 0) next = (int)gridDim.x + atomicAdd(next_tile, 1);
         __syncthreads();
