@@ -115,6 +115,28 @@ PMPM_HD unsigned long long sq_fix32(float d) {
     return q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull);
 }
 
+// round-half-even(p 2^24) for a float32 p with |p| < 2^20, in integers (the
+// fixed-point momentum of the cell sums): p = m 2^(E - 150) exactly, so
+// p 2^24 = m 2^(E - 126) with m < 2^24; no FP64 (slow on this part).
+PMPM_HD long long fix24_rn(float p) {
+    union { float f; uint32_t u; } bits;
+    bits.f = p;
+    const uint32_t E = (bits.u >> 23) & 255u, M = bits.u & 0x7fffffu;
+    const uint32_t m = E ? (M | 0x800000u) : M;
+    const int sh = (E ? (int)E : 1) - 126;
+    long long r;
+    if (sh >= 0) {
+        r = (long long)m << sh;
+    } else if (sh < -24) {
+        r = 0;                                       // below 1/2
+    } else {
+        const int k = -sh;
+        const uint32_t q = m >> k, rem = m & ((1u << k) - 1u), half = 1u << (k - 1);
+        r = (long long)(q + ((rem > half || (rem == half && (q & 1u))) ? 1u : 0u));
+    }
+    return (bits.u >> 31) ? -r : r;
+}
+
 // ---------------------------------------------------------------- position format
 // PB bytes per position coordinate (Sec. III-A): B = 256 (1 byte, Eq. 2) or
 // 65536 (2 bytes) bins per coarse cell.  The 3-D CIC weight products of

@@ -40,37 +40,59 @@ PMPM_HD float sin32(int j) { return cos32(8 - j); }
 PMPM_HD float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 PMPM_HD float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 
-// d * exp(S * 2 pi i j / 32), j a compile-time constant after unrolling;
-// S = -1 forward, +1 inverse.
+// Twiddle factor w = exp(S 2 pi i j / 32) (S = -1 forward, +1 inverse, j a
+// compile-time constant after unrolling) in factored form: returns u and m
+// with w d = m u.  Multiples of pi/2 are a swap and signs (m = +-1); other
+// angles divide through by the larger of |cos|, |sin| (ratio t with |t| <= 1),
+// u = d (1 + i t) or d (t + i), so that a later a + m u is one fused
+// multiply-add per component (the FMA butterfly of Linzer and Feig).
 template <int S>
-PMPM_HD float2 twiddle32(float2 d, int j) {
+PMPM_HD float2 twiddle_f(float2 d, int j, float& m) {
     j &= 31;
-    if (j == 0) return d;
-    if (j == 8) return S < 0 ? make_float2(d.y, -d.x) : make_float2(-d.y, d.x);
-    if (j == 16) return make_float2(-d.x, -d.y);
-    if (j == 24) return S < 0 ? make_float2(-d.y, d.x) : make_float2(d.y, -d.x);
-    float c = cos32(j), s = (S < 0 ? -1.f : 1.f) * sin32(j);
-    return make_float2(d.x * c - d.y * s, d.x * s + d.y * c);
+    if (j == 0 || j == 16) {
+        m = j == 0 ? 1.f : -1.f;
+        return d;
+    }
+    if (j == 8 || j == 24) {
+        m = 1.f;   // w = -i (forward 8, inverse 24) or +i
+        return ((j == 8) == (S < 0)) ? make_float2(d.y, -d.x) : make_float2(-d.y, d.x);
+    }
+    const float wr = cos32(j), wi = (S < 0 ? -1.f : 1.f) * sin32(j);
+    if (fabsf(wr) >= fabsf(wi)) {
+        const float t = wi / wr;
+        m = wr;
+        return make_float2(d.x - t * d.y, d.y + t * d.x);
+    }
+    const float t = wr / wi;
+    m = wi;
+    return make_float2(t * d.x - d.y, t * d.y + d.x);
 }
 
-// One radix-2 decimation-in-frequency stage of an N-point transform.
+// (a, b) <- (a + w b, a - w b)
+template <int S>
+PMPM_HD void butterfly(float2& a, float2& b, int j) {
+    float m;
+    const float2 u = twiddle_f<S>(b, j, m);
+    const float2 x = a;
+    a = make_float2(x.x + m * u.x, x.y + m * u.y);
+    b = make_float2(x.x - m * u.x, x.y - m * u.y);
+}
+
+// One radix-2 decimation-in-time stage (span 2 HALF) of an N-point transform,
+// then the next larger span.
 template <int N, int HALF, int S>
-struct DifStage {
+struct DitStage {
     static PMPM_HD void run(float2 (&a)[N]) {
 #pragma unroll
         for (int g = 0; g < N; g += 2 * HALF) {
 #pragma unroll
-            for (int k = 0; k < HALF; ++k) {
-                float2 x = a[g + k], y = a[g + k + HALF];
-                a[g + k] = cadd(x, y);
-                a[g + k + HALF] = twiddle32<S>(csub(x, y), k * (N / (2 * HALF)) * (32 / N));
-            }
+            for (int k = 0; k < HALF; ++k) butterfly<S>(a[g + k], a[g + k + HALF], k * (32 / (2 * HALF)));
         }
-        DifStage<N, HALF / 2, S>::run(a);
+        DitStage<N, 2 * HALF, S>::run(a);
     }
 };
 template <int N, int S>
-struct DifStage<N, 0, S> {
+struct DitStage<N, N, S> {
     static PMPM_HD void run(float2 (&)[N]) {}
 };
 
@@ -82,49 +104,52 @@ PMPM_HD int bitrev(int k) {
     return r;
 }
 
-// In-place unnormalised N-point DFT (N = 16 or 32): on return a[bitrev(k)]
-// holds X[k] = sum_n x[n] exp(S 2 pi i n k / N).
+// In-place unnormalised N-point DFT (N = 16 or 32) by radix-2 decimation in
+// time: on entry a[bitrev(n)] holds x[n]; on return a[k] holds
+// X[k] = sum_n x[n] exp(S 2 pi i n k / N).
 template <int N, int S>
-PMPM_HD void fft_bitrev_out(float2 (&a)[N]) {
-    DifStage<N, N / 2, S>::run(a);
+PMPM_HD void fft_dit(float2 (&a)[N]) {
+    DitStage<N, 1, S>::run(a);
 }
 
-// Real 32-point forward DFT through a 16-point complex one.
-// In: x[0..31] real.  Out: X[0..16] (X[0], X[16] real).
-PMPM_HD void rfft32(const float (&x)[32], float2 (&X)[17]) {
+// Real 32-point forward DFT through a 16-point complex one, scaled by 2.
+// In: x[0..31] real.  Out: X[0..16] = 2 DFT(x)[0..16] (X[0], X[16] real).
+PMPM_HD void rfft32x2(const float (&x)[32], float2 (&X)[17]) {
     float2 z[16];
 #pragma unroll
-    for (int m = 0; m < 16; ++m) z[m] = make_float2(x[2 * m], x[2 * m + 1]);
-    fft_bitrev_out<16, -1>(z);
+    for (int m = 0; m < 16; ++m) z[bitrev<4>(m)] = make_float2(x[2 * m], x[2 * m + 1]);
+    fft_dit<16, -1>(z);
 #pragma unroll
     for (int k = 0; k <= 16; ++k) {
-        float2 Zk = z[bitrev<4>(k & 15)];
-        float2 Zr = z[bitrev<4>((16 - k) & 15)];
-        // E = (Zk + conj Zr)/2, O = -i (Zk - conj Zr)/2
-        float2 E = make_float2(0.5f * (Zk.x + Zr.x), 0.5f * (Zk.y - Zr.y));
-        float2 O = make_float2(0.5f * (Zk.y + Zr.y), -0.5f * (Zk.x - Zr.x));
-        X[k] = cadd(E, twiddle32<-1>(O, k));
+        const float2 Zk = z[k & 15];
+        const float2 Zr = z[(16 - k) & 15];
+        // 2E = Zk + conj Zr, 2O = -i (Zk - conj Zr); 2X = 2E + w^k 2O
+        const float2 E = make_float2(Zk.x + Zr.x, Zk.y - Zr.y);
+        const float2 O = make_float2(Zk.y + Zr.y, Zr.x - Zk.x);
+        float m;
+        const float2 u = twiddle_f<-1>(O, k, m);
+        X[k] = make_float2(E.x + m * u.x, E.y + m * u.y);
     }
 }
 
-// Inverse of rfft32 without the 1/32: x[n] = sum_k X[k] exp(+2 pi i n k/32)
+// Inverse of the true DFT without the 1/32: x[n] = sum_k X[k] exp(+2 pi i n k/32)
 // over the Hermitian-extended spectrum.  In: X[0..16]; out: x[0..31].
 PMPM_HD void irfft32(const float2 (&X)[17], float (&x)[32]) {
     float2 z[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
-        float2 Xk = X[k];
-        float2 Xc = make_float2(X[16 - k].x, -X[16 - k].y);   // conj X[16-k]
-        float2 E = cadd(Xk, Xc);
-        float2 O = twiddle32<1>(csub(Xk, Xc), k);
-        z[k] = make_float2(E.x - O.y, E.y + O.x);             // E + i O
+        const float2 Xk = X[k];
+        const float2 Xc = make_float2(X[16 - k].x, -X[16 - k].y);   // conj X[16-k]
+        const float2 E = cadd(Xk, Xc);
+        float m;
+        const float2 u = twiddle_f<1>(csub(Xk, Xc), k, m);         // O = m u
+        z[bitrev<4>(k)] = make_float2(E.x - m * u.y, E.y + m * u.x); // E + i O
     }
-    fft_bitrev_out<16, 1>(z);
+    fft_dit<16, 1>(z);
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
-        float2 v = z[bitrev<4>(m)];
-        x[2 * m] = v.x;
-        x[2 * m + 1] = v.y;
+        x[2 * m] = z[m].x;
+        x[2 * m + 1] = z[m].y;
     }
 }
 

@@ -196,7 +196,7 @@ __global__ void k_hist(Src src, int64_t n, int nc, int32_t* counts, unsigned lon
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 long long fx = 0;
-                if (fabsf(p[u][d]) < 1048576.f) fx = __double2ll_rn((double)p[u][d] * 16777216.0);
+                if (fabsf(p[u][d]) < 1048576.f) fx = fix24_rn(p[u][d]);
                 else atomicOr(err, p[u][d] == p[u][d] ? kErrMomentum : kErrNaN);
                 atomicAdd(&S[d * ncells + key], (unsigned long long)fx);
             }

@@ -30,8 +30,10 @@ __device__ __forceinline__ void tile_component(int tid, const TileGeom& g, const
                                                unsigned long long& lo, unsigned long long& hi) {
     __syncthreads();
     PMPM_MARK(7 + 4 * D);
-    tile_inv_z<D>(tid, g, gS, C, W);
-    __syncthreads();
+    if (D > 0) {   // the x force's inverse z ran with the forward z pass
+        tile_inv_z<D>(tid, g, gS, C, W);
+        __syncthreads();
+    }
     PMPM_MARK(8 + 4 * D);
     tile_inv_y(tid, g, W);
     __syncthreads();
@@ -107,7 +109,7 @@ __device__ __forceinline__ void tile_body(int tile, bool first, const TileParams
     tile_fwd_y(tid, C);
     __syncthreads();
     PMPM_MARK(5);
-    tile_fwd_z(tid, C);
+    tile_fwd_z_inv_z0(tid, g, gS, C, W);
     unsigned long long lo = 0, hi = 0;
     tile_component<0, LM, PB>(tid, g, P, gS, C, W, cells, cs, lo, hi);
     tile_component<1, LM, PB>(tid, g, P, gS, C, W, cells, cs, lo, hi);

@@ -11,7 +11,7 @@
 //
 // Shared memory (one CTA per SM):
 //   R  32 KB x 4 B = 128 KB: integer density (uint32, units 2^-21 per
-//      particle), then its 3-D spectrum packed as 16 x 32 x 32 complex with
+//      particle), then twice its 3-D spectrum packed as 16 x 32 x 32 complex with
 //      the kx = 16 (Nyquist) plane folded into the imaginary part of kx = 0;
 //   W  22 x 32 x 16 complex = 88 KB: one force component on its way back,
 //      pruned to the 22 output planes that are needed (during the deposit it
@@ -120,13 +120,11 @@ PMPM_HD uint32_t smem_add_u32(uint32_t* p, uint32_t v) { return atomicAdd(p, v);
 PMPM_HD void gmem_add_i32(int32_t* p, int32_t v) { atomicAdd(p, v); }
 PMPM_HD void gmem_add_u64(unsigned long long* p, unsigned long long v) { atomicAdd(p, v); }
 PMPM_HD float u32_to_f32(uint32_t v) { return __uint2float_rn(v); }
-PMPM_HD long long f64_to_ll_rn(double v) { return __double2ll_rn(v); }
 #else
 PMPM_HD uint32_t smem_add_u32(uint32_t* p, uint32_t v) { uint32_t o = *p; *p = o + v; return o; }
 PMPM_HD void gmem_add_i32(int32_t* p, int32_t v) { *p += v; }
 PMPM_HD void gmem_add_u64(unsigned long long* p, unsigned long long v) { *p += v; }
 PMPM_HD float u32_to_f32(uint32_t v) { return (float)v; }
-PMPM_HD long long f64_to_ll_rn(double v) { return llrint(v); }
 #endif
 
 // --- phase 0: clear the density --------------------------------------------
@@ -640,8 +638,23 @@ PMPM_HD void tile_cells_map(int tid, const TileGeom& g, TileCells c) {
 #endif
 }
 
-// largest i in [0, n) with pre[i] <= v (pre non-decreasing, pre[0] = 0 <= v)
-PMPM_HD int prefix_find(const int* pre, int n, int v) {
+// largest i in [0, N) with pre[i] <= v (pre non-decreasing, pre[0] = 0 <= v):
+// a fixed number of halving steps with no branch, so that searches of
+// several particles interleave
+template <int N>
+PMPM_HD int prefix_find(const int* pre, int v) {
+    int pos = 0;
+#pragma unroll
+    for (int step = 1 << 10; step > 0; step >>= 1) {
+        if (step >= N) continue;
+        const int t = pos + step;
+        pos = (t < N && pre[t < N ? t : 0] <= v) ? t : pos;
+    }
+    return pos;
+}
+
+// the same search as a loop (compact code for the rare lookups past the maps)
+PMPM_HD int prefix_find_loop(const int* pre, int n, int v) {
     int lo = 0, hi = n;
     while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
@@ -651,10 +664,10 @@ PMPM_HD int prefix_find(const int* pre, int n, int v) {
 }
 
 PMPM_HD int halo_of(const TileCells& c, int v) {
-    return v < kMapCap ? (int)c.map[v] : prefix_find(c.pre, kHaloMax, v);
+    return v < kMapCap ? (int)c.map[v] : prefix_find_loop(c.pre, kHaloMax, v);
 }
 PMPM_HD int own_of(const TileCells& c, int v) {
-    return v < kPMapCap ? (int)c.pmap[v] : prefix_find(c.ppre, kOwnMax, v);
+    return v < kPMapCap ? (int)c.pmap[v] : prefix_find_loop(c.ppre, kOwnMax, v);
 }
 
 constexpr int kDepositIlp = 4;   // halo particles per thread per iteration
@@ -737,32 +750,22 @@ PMPM_HD void tile_fwd_x(int tid, uint32_t* R) {
 #pragma unroll
         for (int n = 0; n < 32; ++n) x[n] = u32_to_f32(R[ridx(n, y, z)]);
         float2 X[17];
-        rfft32(x, X);
+        rfft32x2(x, X);
         C[cidx(0, y, z)] = make_float2(X[0].x, X[16].x);   // pack Nyquist
 #pragma unroll
         for (int k = 1; k < 16; ++k) C[cidx(k, y, z)] = X[k];
     }
 }
 
-// --- phase 3/4: forward complex transforms along y and z (512 pencils) ------
+// --- phase 3: forward complex transform along y (512 pencils) --------------
 PMPM_HD void tile_fwd_y(int tid, float2* C) {
     const int kx = tid & 15, z = tid >> 4;
     float2 a[32];
 #pragma unroll
-    for (int k = 0; k < 32; ++k) a[k] = C[cidx(kx, k, z)];
-    fft_bitrev_out<32, -1>(a);
+    for (int k = 0; k < 32; ++k) a[bitrev<5>(k)] = C[cidx(kx, k, z)];
+    fft_dit<32, -1>(a);
 #pragma unroll
-    for (int k = 0; k < 32; ++k) C[cidx(kx, k, z)] = a[bitrev<5>(k)];
-}
-
-PMPM_HD void tile_fwd_z(int tid, float2* C) {
-    const int kx = tid & 15, ky = tid >> 4;
-    float2 a[32];
-#pragma unroll
-    for (int k = 0; k < 32; ++k) a[k] = C[cidx(kx, ky, k)];
-    fft_bitrev_out<32, -1>(a);
-#pragma unroll
-    for (int k = 0; k < 32; ++k) C[cidx(kx, ky, k)] = a[bitrev<5>(k)];
+    for (int k = 0; k < 32; ++k) C[cidx(kx, k, z)] = a[k];
 }
 
 // |signed frequency| and its sign for a 32-point index
@@ -789,11 +792,9 @@ PMPM_HD void tile_load_green(int tid, const float* Gp, float* gS) {
 // Thread mapping of the z passes: warp w owns kx = w and lane l owns ky = l,
 // so warp 0 alone carries the packed kx = 0 / 16 pencils and the other warps
 // run without divergence; every half-warp touches 16 distinct bank pairs.
-template <int D>
-PMPM_HD void tile_inv_z(int tid, const TileGeom& g, const float* gS, const float2* C,
-                        float2* W) {
-    const int kx = tid >> 5, ky = tid & 31;
-    const int nz = g.T[2] + 2;
+template <int D, typename Spec>
+PMPM_HD void inv_z_pencil(int kx, int ky, int nz, const float* gS, Spec spec, const float2* C,
+                          float2* W) {
     const int ay = kabs32(ky);
     float2 a[32];
     if (D == 0 && kx == 0) {
@@ -803,53 +804,84 @@ PMPM_HD void tile_inv_z(int tid, const TileGeom& g, const float* gS, const float
             if (zo < nz) W[widx(0, ky, zo)] = make_float2(0.f, 0.f);
         return;
     }
-    // per-thread parts of the table index (own-axis row a is stored at a - 1);
-    // the third index |kz| is a compile-time constant in the unrolled loop
-    const float sgy = (D == 1 && (ay == 0 || ay == 16)) ? 0.f : ksgn32(ky);
-    const int offA = green_off(D == 0 ? ay : kx);          // pair (b, c) with b fixed
-    const int bfix = D == 0 ? ay : kx;
-    const int rowA = D == 0 ? (kx - 1) * kGreenTri : (ay >= 1 && ay <= 15 ? ay - 1 : 0) * kGreenTri;
-    const int t0 = green_tri(0, ay), t16 = green_tri(16, ay), txy = green_tri(kx, ay);
+    // Each case has its own unrolled kz loop with no branch inside, so the
+    // loads of all 32 iterations can be scheduled ahead of their use.
+    // Per-thread parts of the table index (own-axis row a is stored at a - 1);
+    // the third index |kz| is a compile-time constant in the unrolled loop.
+    if (D == 0 || kx != 0) {
+        const float sgy = (D == 1 && (ay == 0 || ay == 16)) ? 0.f : ksgn32(ky);
+        const int bfix = D == 0 ? ay : kx;                   // pair (b, c) with b fixed
+        const int offA = green_off(bfix);
+        const int rowA = D == 0 ? (kx - 1) * kGreenTri : (ay >= 1 && ay <= 15 ? ay - 1 : 0) * kGreenTri;
+        const int txy = green_tri(kx, ay);
 #pragma unroll
-    for (int kz = 0; kz < 32; ++kz) {
-        const int az = kabs32(kz);
-        const float2 Z = C[cidx(kx, ky, kz)];
-        float cA, cB;
-        float2 Zp = make_float2(0.f, 0.f);
-        if (D == 2) {
-            const float sz = (az == 0 || az == 16) ? 0.f : ksgn32(kz);
-            const int rz = (az >= 1 && az <= 15 ? az - 1 : 0) * kGreenTri;
-            if (kx != 0) {
+        for (int kz = 0; kz < 32; ++kz) {
+            const int az = kabs32(kz);
+            const float2 Z = spec(kz);
+            float cA;
+            if (D == 2) {
+                const float sz = (az == 0 || az == 16) ? 0.f : ksgn32(kz);
+                const int rz = (az >= 1 && az <= 15 ? az - 1 : 0) * kGreenTri;
                 cA = sz * gS[rz + txy];
-                cB = 0.f;
             } else {
-                const float s0 = sz * gS[rz + t0];
-                const float s16 = sz * gS[rz + t16];
-                cA = 0.5f * (s0 + s16);
-                cB = 0.5f * (s0 - s16);
-                Zp = C[cidx(0, (32 - ky) & 31, (32 - kz) & 31)];
+                const int idx = bfix <= az ? offA + az : green_off(az) + bfix;
+                cA = (D == 0 ? 1.f : sgy) * gS[rowA + idx];
             }
-        } else if (kx != 0) {
-            const int idx = bfix <= az ? offA + az : green_off(az) + bfix;
-            cA = (D == 0 ? 1.f : sgy) * gS[rowA + idx];
-            cB = 0.f;
-        } else {
-            // D == 1, packed kx = 0 / 16 pencil: b = 0 and b = 16
-            const float s0 = sgy * gS[rowA + green_off(0) + az];
-            const float s16 = sgy * gS[rowA + green_off(az) + 16];
-            cA = 0.5f * (s0 + s16);
-            cB = 0.5f * (s0 - s16);
-            Zp = C[cidx(0, (32 - ky) & 31, (32 - kz) & 31)];
+            a[bitrev<5>(kz)] = make_float2(cA * Z.y, -(cA * Z.x));   // G = -i cA Z
         }
-        // V = cA Z + cB conj(Zp);  G = -i V
-        const float vx = cA * Z.x + cB * Zp.x;
-        const float vy = cA * Z.y - cB * Zp.y;
-        a[kz] = make_float2(vy, -vx);
+    } else {
+        // packed kx = 0 / 16 pencil (y and z forces): b = 0 and b = 16
+        const float sgy = (D == 1 && (ay == 0 || ay == 16)) ? 0.f : ksgn32(ky);
+        const int rowA = (ay >= 1 && ay <= 15 ? ay - 1 : 0) * kGreenTri;
+        const int t0 = green_tri(0, ay), t16 = green_tri(16, ay);
+#pragma unroll
+        for (int kz = 0; kz < 32; ++kz) {
+            const int az = kabs32(kz);
+            const float2 Z = spec(kz);
+            const float2 Zp = C[cidx(0, (32 - ky) & 31, (32 - kz) & 31)];
+            float s0, s16;
+            if (D == 2) {
+                const float sz = (az == 0 || az == 16) ? 0.f : ksgn32(kz);
+                const int rz = (az >= 1 && az <= 15 ? az - 1 : 0) * kGreenTri;
+                s0 = sz * gS[rz + t0];
+                s16 = sz * gS[rz + t16];
+            } else {
+                s0 = sgy * gS[rowA + green_off(0) + az];
+                s16 = sgy * gS[rowA + green_off(az) + 16];
+            }
+            const float cA = 0.5f * (s0 + s16), cB = 0.5f * (s0 - s16);
+            // V = cA Z + cB conj(Zp);  G = -i V
+            const float vx = cA * Z.x + cB * Zp.x;
+            const float vy = cA * Z.y - cB * Zp.y;
+            a[bitrev<5>(kz)] = make_float2(vy, -vx);
+        }
     }
-    fft_bitrev_out<32, 1>(a);
+    fft_dit<32, 1>(a);
 #pragma unroll
     for (int zo = 0; zo < kTileOut; ++zo)
-        if (zo < nz) W[widx(kx, ky, zo)] = a[bitrev<5>(zo + kBuffer - 1)];
+        if (zo < nz) W[widx(kx, ky, zo)] = a[zo + kBuffer - 1];
+}
+
+template <int D>
+PMPM_HD void tile_inv_z(int tid, const TileGeom& g, const float* gS, const float2* C, float2* W) {
+    const int kx = tid >> 5, ky = tid & 31;
+    inv_z_pencil<D>(kx, ky, g.T[2] + 2, gS, [&](int kz) { return C[cidx(kx, ky, kz)]; }, C, W);
+}
+
+// --- phase 4 + 5a of the x force: forward transform along z, then at once
+// the x-force Green multiply and inverse z of the same pencil from the
+// registers (the stored spectrum serves the y and z forces).  Same thread
+// mapping as the inverse z passes; every half-warp touches 16 distinct bank
+// pairs of the (kx ^ ky) swizzle.
+PMPM_HD void tile_fwd_z_inv_z0(int tid, const TileGeom& g, const float* gS, float2* C, float2* W) {
+    const int kx = tid >> 5, ky = tid & 31;
+    float2 a[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) a[bitrev<5>(k)] = C[cidx(kx, ky, k)];
+    fft_dit<32, -1>(a);
+#pragma unroll
+    for (int k = 0; k < 32; ++k) C[cidx(kx, ky, k)] = a[k];
+    inv_z_pencil<0>(kx, ky, g.T[2] + 2, gS, [&](int kz) { return a[kz]; }, C, W);
 }
 
 // --- phase 5b: inverse transform along y, pruned to T + 2 output rows -----
@@ -862,11 +894,11 @@ __host__ __device__ __noinline__ void tile_inv_y(int tid, const TileGeom& g, flo
     const int kx = tid & 15, zo = tid >> 4;
     float2 a[32];
 #pragma unroll
-    for (int k = 0; k < 32; ++k) a[k] = W[widx(kx, k, zo)];
-    fft_bitrev_out<32, 1>(a);
+    for (int k = 0; k < 32; ++k) a[bitrev<5>(k)] = W[widx(kx, k, zo)];
+    fft_dit<32, 1>(a);
 #pragma unroll
     for (int yo = 0; yo < kTileOut; ++yo)
-        if (yo < ny) W[widx(kx, yo, zo)] = a[bitrev<5>(yo + kBuffer - 1)];
+        if (yo < ny) W[widx(kx, yo, zo)] = a[yo + kBuffer - 1];
 }
 
 // --- phase 5c: inverse real transform along x, pruned to T + 2 columns ----
@@ -904,7 +936,7 @@ PMPM_HD void lowmem_particle(const TileParams& P, const int32_t (&q)[3], const f
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             long long fx = 0;
-            if (fabsf(p[d]) < 1048576.f) fx = f64_to_ll_rn((double)p[d] * 16777216.0);
+            if (fabsf(p[d]) < 1048576.f) fx = fix24_rn(p[d]);
             else flag_error(P.err, p[d] == p[d] ? kErrMomentum : kErrNaN);
             gmem_add_u64(&P.S[d * C + key], (unsigned long long)fx);
         }
@@ -968,7 +1000,7 @@ PMPM_HD void tile_interp(int tid, const TileGeom& g, const TileParams& P, const 
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int v = v0 + u * kTileThreads;
-            const int p = v < ptotal ? prefix_find(c.ppre, kOwnMax, v) : 0;
+            const int p = prefix_find<kOwnMax>(c.ppre, v < ptotal ? v : 0);
             j[u] = (v < ptotal && (!lm || v < kLowmemCap)) ? base + c.prel[p] + (v - c.ppre[p]) : -1;
             const int cx = g.c0[0] + p % kOwnDim, cy = g.c0[1] + (p / kOwnDim) % kOwnDim,
                       cz = g.c0[2] + p / (kOwnDim * kOwnDim);
@@ -1010,7 +1042,9 @@ PMPM_HD void tile_interp(int tid, const TileGeom& g, const TileParams& P, const 
                                                        dz ? w1[2] : W - w1[2]);
                 gf += w * Wf[wfidx(lo3[0] + dx, lo3[1] + dy, lo3[2] + dz)];
             }
-            const float gval = gf * 4.76837158203125e-07f + gcd[u];   // 2^-21
+            // weights in units of 2^-21, and the forward x transform (rfft32x2)
+            // leaves the whole spectrum doubled: 2^-22
+            const float gval = gf * 2.384185791015625e-07f + gcd[u];
             if (!lm && P.mode == 0) {
                 slot[D * n + j[u]] = gval;
                 continue;
@@ -1025,8 +1059,13 @@ PMPM_HD void tile_interp(int tid, const TileGeom& g, const TileParams& P, const 
             if (fabsf(xq) < 1.0e9f) dq = (int64_t)floorf(fadd_rn(xq, 0.5f));
             else flag_error(P.err, kErrDrift);
             const int64_t M = (int64_t)P.nc * F::kBins;
-            int64_t qn = (Q[u][D] + dq) % M;
-            if (qn < 0) qn += M;
+            // periodic wrap; a 64-bit division only for the rare particle
+            // that crosses the box boundary
+            int64_t qn = Q[u][D] + dq;
+            if (qn < 0 || qn >= M) {
+                qn %= M;
+                if (qn < 0) qn += M;
+            }
             if (!lm) {
                 P.Qn[D * n + j[u]] = (int32_t)qn;
                 P.Pn[D * n + j[u]] = pn;
@@ -1039,7 +1078,7 @@ PMPM_HD void tile_interp(int tid, const TileGeom& g, const TileParams& P, const 
 #pragma unroll
                     for (int d = 0; d < 3; ++d) {
                         long long fx = 0;
-                        if (fabsf(pa[d]) < 1048576.f) fx = f64_to_ll_rn((double)pa[d] * 16777216.0);
+                        if (fabsf(pa[d]) < 1048576.f) fx = fix24_rn(pa[d]);
                         else flag_error(P.err, pa[d] == pa[d] ? kErrMomentum : kErrNaN);
                         gmem_add_u64(&P.S[d * ncells + key], (unsigned long long)fx);
                     }
