@@ -276,6 +276,19 @@ PMPM_HD void deposit_one(const TileGeom& g, const int (&cu)[3], const int (&m)[3
     const bool inside = (unsigned)li[0] < 31u && (unsigned)li[1] < 31u && (unsigned)li[2] < 31u;
     const uint32_t wyz[4] = {(uint32_t)((W - w1[1]) * (W - w1[2])), (uint32_t)(w1[1] * (W - w1[2])),
                              (uint32_t)((W - w1[1]) * w1[2]), (uint32_t)(w1[1] * w1[2])};
+    if (!CHECK && inside) {
+        // the common case, all eight nodes in the box: straight-line adds
+        // (a zero weight adds nothing)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
+            const uint32_t w = PB == 1 ? (uint32_t)(dx ? w1[0] : W - w1[0]) * wyz[dy + 2 * dz]
+                                       : cic_weight3<PB>(dx ? w1[0] : W - w1[0], dy ? w1[1] : W - w1[1],
+                                                         dz ? w1[2] : W - w1[2]);
+            smem_red_u32(&R[ridx(li[0] + dx, li[1] + dy, li[2] + dz)], w);
+        }
+        return;
+    }
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
         const int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
@@ -903,8 +916,7 @@ __host__ __device__ __noinline__ void tile_inv_y(int tid, const TileGeom& g, flo
 
 // --- phase 5c: inverse real transform along x, pruned to T + 2 columns ----
 __host__ __device__ __noinline__ void tile_inv_x(int tid, const TileGeom& g, float2* W) {
-    const int ny = g.T[1] + 2, nz = g.T[2] + 2, nx = g.T[0] + 2;
-    float* Wf = reinterpret_cast<float*>(W);
+    const int ny = g.T[1] + 2, nz = g.T[2] + 2, nx = g.T[0] + 2;   // all even
     for (int r = tid; r < ny * nz; r += kTileThreads) {
         const int yo = r % ny, zo = r / ny;
         float2 X[17];
@@ -915,9 +927,10 @@ __host__ __device__ __noinline__ void tile_inv_x(int tid, const TileGeom& g, flo
         for (int k = 1; k < 16; ++k) X[k] = W[widx(k, yo, zo)];
         float x[32];
         irfft32(X, x);
+        // outputs xo, xo + 1 as one 8-byte store (the pair wfidx(xo), wfidx(xo + 1))
 #pragma unroll
-        for (int xo = 0; xo < kTileOut; ++xo)
-            if (xo < nx) Wf[wfidx(xo, yo, zo)] = x[xo + kBuffer - 1];
+        for (int xo = 0; xo < kTileOut; xo += 2)
+            if (xo < nx) W[widx(xo >> 1, yo, zo)] = make_float2(x[xo + kBuffer - 1], x[xo + kBuffer]);
     }
 }
 
