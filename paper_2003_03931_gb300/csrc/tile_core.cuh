@@ -329,17 +329,19 @@ PMPM_HD void coarse_gather(const TileParams& P, const int64_t (&Q)[3], float (&g
         iz[k] = wrap1(cc[2].i0 + k, P.nc);
     }
     gc[0] = gc[1] = gc[2] = 0.f;
+    // nc <= 1024 (config limit), so node indices fit in 32 bits
+    const float* Fe[3] = {P.Fl, P.Fl + ncells, P.Fl + 2 * ncells};
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
         const int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
-        const int64_t node = ix[dx] + (int64_t)P.nc * (iy[dy] + (int64_t)P.nc * iz[dz]);
+        const int node = ix[dx] + P.nc * (iy[dy] + P.nc * iz[dz]);
         const float w = PB == 1
             ? (float)((dx ? cc[0].w1 : W - cc[0].w1) * (dy ? cc[1].w1 : W - cc[1].w1)) *
                   (float)(dz ? cc[2].w1 : W - cc[2].w1)
             : (float)cic_weight3<PB>(dx ? cc[0].w1 : W - cc[0].w1, dy ? cc[1].w1 : W - cc[1].w1,
                                      dz ? cc[2].w1 : W - cc[2].w1);
 #pragma unroll
-        for (int e = 0; e < 3; ++e) gc[e] += w * P.Fl[e * ncells + node];
+        for (int e = 0; e < 3; ++e) gc[e] += w * Fe[e][node];
     }
 #pragma unroll
     for (int e = 0; e < 3; ++e) gc[e] *= 7.450580596923828e-09f;   // 2^-27
@@ -1047,12 +1049,17 @@ PMPM_HD void tile_interp(int tid, const TileGeom& g, const TileParams& P, const 
                 w1[e] = s & (F::kFineW - 1);
             }
             float gf = 0.f;
+            constexpr int W = F::kFineW;
+            // 1-byte weights: products of integers <= 128, exact in float
+            const float fx[2] = {(float)(W - w1[0]), (float)w1[0]};
+            const float fy[2] = {(float)(W - w1[1]), (float)w1[1]};
+            const float fz[2] = {(float)(W - w1[2]), (float)w1[2]};
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
-                constexpr int W = F::kFineW;
-                const float w = (float)cic_weight3<PB>(dx ? w1[0] : W - w1[0], dy ? w1[1] : W - w1[1],
-                                                       dz ? w1[2] : W - w1[2]);
+                const float w = PB == 1 ? fx[dx] * (fy[dy] * fz[dz])
+                                        : (float)cic_weight3<PB>(dx ? w1[0] : W - w1[0], dy ? w1[1] : W - w1[1],
+                                                                 dz ? w1[2] : W - w1[2]);
                 gf += w * Wf[wfidx(lo3[0] + dx, lo3[1] + dy, lo3[2] + dz)];
             }
             // weights in units of 2^-21, and the forward x transform (rfft32x2)
