@@ -3,8 +3,9 @@
 //
 //  1. integer CIC of all particles on the nc^3 coarse mesh (int64, units
 //     2^-27 per particle): one thread per cell sums its particles' weights on
-//     the 27 surrounding nodes in registers, an 8x8x4-cell brick collects
-//     them in shared memory and flushes one global atomic per touched node;
+//     the 27 surrounding nodes in 32-bit registers, an 8x8x4-cell brick
+//     collects them in shared memory and flushes one global atomic per
+//     touched node;
 //  2. delta = rho - mean (float64 subtraction, float32 storage), 3-D FFT;
 //  3. Green multiply: B1 = rho~ (K~_x + i K~_y), B2 = rho~ K~_z (K~ = -i S);
 //  4. two inverse FFTs give F_x + i F_y and F_z.
@@ -38,48 +39,55 @@ __global__ void __launch_bounds__(256) k_coarse_deposit(int nc, const int32_t* _
     const int64_t cell = cx + (int64_t)nc * (cy + (int64_t)nc * cz);
     const int64_t j0 = offsets[cell];
     const int cnt = counts[cell];
-    unsigned long long a[27];
+    // A particle's weight on one node is at most its whole mass, 2^27 units,
+    // so 31 particles sum below 2^32: 32-bit accumulators (one multiply-add
+    // per node), added to the brick every kChunk particles.
+    constexpr int kChunk = 31;
+    for (int q0 = 0; q0 < cnt; q0 += kChunk) {
+        uint32_t a[27];
 #pragma unroll
-    for (int k = 0; k < 27; ++k) a[k] = 0ull;
-    for (int q = 0; q < cnt; ++q) {
-        const int64_t j = j0 + q;
-        // per axis: weights of nodes c-1, c, c+1 (in 1/(2B)); the bins in the
-        // lower half lie left of the cell centre
-        constexpr int B = PosFmt<PB>::kBins;
-        uint32_t w[3][3];
-        const int mm[3] = {load_bin<PB>(m0, j), load_bin<PB>(m1, j), load_bin<PB>(m2, j)};
+        for (int k = 0; k < 27; ++k) a[k] = 0u;
+        const int qe = min(cnt, q0 + kChunk);
+#pragma unroll 2
+        for (int q = q0; q < qe; ++q) {
+            const int64_t j = j0 + q;
+            // per axis: weights of nodes c-1, c, c+1 (in 1/(2B)); the bins in the
+            // lower half lie left of the cell centre
+            constexpr int B = PosFmt<PB>::kBins;
+            uint32_t w[3][3];
+            const int mm[3] = {load_bin<PB>(m0, j), load_bin<PB>(m1, j), load_bin<PB>(m2, j)};
 #pragma unroll
-        for (int e = 0; e < 3; ++e) {
-            const int s = 2 * mm[e] + 1 - B;     // offset from the centre, 1/(2B)
-            w[e][0] = s < 0 ? (uint32_t)(-s) : 0u;
-            w[e][1] = (uint32_t)(2 * B) - (uint32_t)(s < 0 ? -s : s);
-            w[e][2] = s > 0 ? (uint32_t)s : 0u;
+            for (int e = 0; e < 3; ++e) {
+                const int s = 2 * mm[e] + 1 - B;     // offset from the centre, 1/(2B)
+                w[e][0] = s < 0 ? (uint32_t)(-s) : 0u;
+                w[e][1] = (uint32_t)(2 * B) - (uint32_t)(s < 0 ? -s : s);
+                w[e][2] = s > 0 ? (uint32_t)s : 0u;
+            }
+#pragma unroll
+            for (int kz = 0; kz < 3; ++kz)
+#pragma unroll
+                for (int ky = 0; ky < 3; ++ky) {
+                    if (PB == 1) {
+                        // 1-byte bins: products below 2^27
+                        const uint32_t wyz = w[1][ky] * w[2][kz];
+#pragma unroll
+                        for (int kx = 0; kx < 3; ++kx) a[kx + 3 * (ky + 3 * kz)] += wyz * w[0][kx];
+                    } else {
+                        // 2-byte bins: the 2^-51 product rounded to the 2^-27 unit
+                        const unsigned long long wyz = (unsigned long long)w[1][ky] * w[2][kz];
+#pragma unroll
+                        for (int kx = 0; kx < 3; ++kx)
+                            a[kx + 3 * (ky + 3 * kz)] +=
+                                (uint32_t)round_half_even_shift(wyz * w[0][kx], PosFmt<PB>::kRoundBits);
+                    }
+                }
         }
 #pragma unroll
-        for (int kz = 0; kz < 3; ++kz)
-#pragma unroll
-            for (int ky = 0; ky < 3; ++ky) {
-                if (PB == 1) {
-                    // 1-byte bins: products below 2^27, 32-bit arithmetic
-                    const uint32_t wyz = w[1][ky] * w[2][kz];
-#pragma unroll
-                    for (int kx = 0; kx < 3; ++kx)
-                        a[kx + 3 * (ky + 3 * kz)] += (unsigned long long)(wyz * w[0][kx]);
-                } else {
-                    // 2-byte bins: the 2^-51 product rounded to the 2^-27 unit
-                    const unsigned long long wyz = (unsigned long long)w[1][ky] * w[2][kz];
-#pragma unroll
-                    for (int kx = 0; kx < 3; ++kx)
-                        a[kx + 3 * (ky + 3 * kz)] +=
-                            round_half_even_shift(wyz * w[0][kx], PosFmt<PB>::kRoundBits);
-                }
-            }
-    }
-#pragma unroll
-    for (int k = 0; k < 27; ++k) {
-        if (!a[k]) continue;
-        const int dx = k % 3, dy = (k / 3) % 3, dz = k / 9;
-        atomicAdd(&acc[(lx + dx) + kNX * ((ly + dy) + kNY * (lz + dz))], a[k]);
+        for (int k = 0; k < 27; ++k) {
+            if (!a[k]) continue;
+            const int dx = k % 3, dy = (k / 3) % 3, dz = k / 9;
+            atomicAdd(&acc[(lx + dx) + kNX * ((ly + dy) + kNY * (lz + dz))], (unsigned long long)a[k]);
+        }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < kNX * kNY * kNZ; i += blockDim.x) {

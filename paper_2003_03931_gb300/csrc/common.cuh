@@ -97,22 +97,22 @@ PMPM_HD uint32_t encode_momentum(float p, float vc, float sigma, const float* E,
 }
 
 // round-half-even(d^2 2^32) for a float32 d with |d| < 2^16, in integers:
-// d = m 2^e exactly, so d^2 2^32 = m^2 2^(2e + 32) with m^2 < 2^48.  The
-// dispersion of Eq. 3 is the exact sum of these terms.
+// d = m 2^(E - 150) exactly, so d^2 2^32 = m^2 2^(2E - 268) with m^2 < 2^48.
+// A right shift by r rounds half to even as (x + 2^(r-1) - 1 + bit r of x)
+// >> r (checked against the plain remainder test for every float below
+// 2^16).  The dispersion of Eq. 3 is the exact sum of these terms.
 PMPM_HD unsigned long long sq_fix32(float d) {
     union { float f; uint32_t u; } bits;
     bits.f = d;
     const uint32_t b = bits.u & 0x7fffffffu;
     const uint32_t E = b >> 23, M = b & 0x7fffffu;
-    const unsigned long long m = E ? (unsigned long long)(M | 0x800000u) : (unsigned long long)M;
-    const int e = E ? (int)E - 150 : -149;
-    const unsigned long long m2 = m * m;
-    const int sh = 2 * e + 32;
+    const uint32_t m = E ? (M | 0x800000u) : M;
+    const unsigned long long m2 = (unsigned long long)m * m;
+    const int sh = 2 * (E ? (int)E : 1) - 268;
     if (sh >= 0) return m2 << sh;
     const int r = -sh;
     if (r > 49) return 0ull;                       // value below 1/4
-    const unsigned long long q = m2 >> r, rem = m2 & ((1ull << r) - 1ull), half = 1ull << (r - 1);
-    return q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull);
+    return (m2 + ((1ull << (r - 1)) - 1ull) + ((m2 >> r) & 1ull)) >> r;
 }
 
 // round-half-even(p 2^24) for a float32 p with |p| < 2^20, in integers (the

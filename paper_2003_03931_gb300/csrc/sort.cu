@@ -81,6 +81,10 @@ __global__ void __launch_bounds__(1024) k_scan_top(int64_t nb, long long* blocks
     }
 }
 
+// One tile of kScanTile cells per block.  Global loads and stores are
+// striped (consecutive threads, consecutive cells); the scan runs over each
+// thread's kScanItems consecutive cells, and shared memory, padded by one
+// word in 16 against bank conflicts, transposes between the two orders.
 __global__ void __launch_bounds__(kScanThreads) k_scan_apply(int64_t ncells, const int32_t* __restrict__ counts,
                                                              const long long* __restrict__ blocksums,
                                                              int64_t* __restrict__ offsets,
@@ -88,36 +92,60 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(int64_t ncells, con
                                                              float* __restrict__ vc,
                                                              int32_t* __restrict__ fill) {
     __shared__ long long sh[32];
+    __shared__ long long buf[kScanTile + kScanTile / 16];
+    int* cbuf = reinterpret_cast<int*>(buf);
     const int64_t b0 = (int64_t)blockIdx.x * kScanTile;
-    // each thread owns kScanItems consecutive cells
-    const int64_t t0 = b0 + (int64_t)threadIdx.x * kScanItems;
-    int32_t c[kScanItems];
-    long long acc = 0;
+    const int t = threadIdx.x;
+    int cst[kScanItems];
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
-        const int64_t i = t0 + k;
-        c[k] = i < ncells ? counts[i] : 0;
-        acc += c[k];
+        const int p = k * kScanThreads + t;
+        const int64_t i = b0 + p;
+        cst[k] = i < ncells ? counts[i] : 0;
+        cbuf[p + (p >> 4)] = cst[k];
     }
-    long long total;
-    long long run = blocksums[blockIdx.x] + block_exclusive_scan(acc, sh, total);
+    // slot counters and cell means, in the striped order
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
-        const int64_t i = t0 + k;
+        const int64_t i = b0 + k * kScanThreads + t;
         if (i >= ncells) break;
-        offsets[i] = run;
-        run += c[k];
         if (fill) fill[i] = 0;
         if (S) {
+#pragma unroll
             for (int d = 0; d < 3; ++d) {
                 float v = 0.f;
-                if (c[k] > 0) {
+                if (cst[k] > 0) {
                     const float sum = __fmul_rn(__ll2float_rn((long long)S[d * ncells + i]), 0x1p-24f);
-                    v = __fdiv_rn(sum, (float)c[k]);
+                    v = __fdiv_rn(sum, (float)cst[k]);
                 }
                 vc[d * ncells + i] = v;
             }
         }
+    }
+    __syncthreads();
+    int c[kScanItems];
+    long long acc = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const int p = t * kScanItems + k;
+        c[k] = cbuf[p + (p >> 4)];
+        acc += c[k];
+    }
+    long long total;
+    // (its barriers also order the reads of cbuf before the writes to buf)
+    long long run = blocksums[blockIdx.x] + block_exclusive_scan(acc, sh, total);
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const int p = t * kScanItems + k;
+        buf[p + (p >> 4)] = run;
+        run += c[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const int p = k * kScanThreads + t;
+        const int64_t i = b0 + p;
+        if (i < ncells) offsets[i] = buf[p + (p >> 4)];
     }
 }
 

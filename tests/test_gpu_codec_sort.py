@@ -81,3 +81,18 @@ def test_coarse_density_bit_exact(nc, np_):
     np.testing.assert_array_equal(rho, ref.ravel())
     assert rho.sum() == sim.cfg.n * 2 ** 27
     sim.close()
+
+
+def test_coarse_density_crowded_cell():
+    # every particle in one coarse cell: the deposit's 32-bit per-cell sums
+    # are flushed every 31 particles
+    need_gpu()
+    sim = make_sim(np=16, nc=8, a_init=0.1, a_final=0.5, n_steps=4)
+    rng = np.random.default_rng(8)
+    Q = synth.single_cell_codes(sim.cfg.n, 8)
+    sim.load_qp(Q, synth.momenta(rng, sim.cfg.n), 0.3)
+    rho = sim.fetch_coarse_density()
+    ref = cic.deposit(Q.T.astype(np.int64), 8, 4)
+    np.testing.assert_array_equal(rho, ref.ravel())
+    assert rho.sum() == sim.cfg.n * 2 ** 27
+    sim.close()
