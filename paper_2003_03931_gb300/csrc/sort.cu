@@ -188,10 +188,11 @@ struct QPFromPsi {
     }
 };
 
+// flat cell index of codes q (nc^3 <= 2^30: 32-bit)
 template <int PB>
-__device__ __forceinline__ int64_t key3(const int32_t (&q)[3], int nc) {
+__device__ __forceinline__ int key3(const int32_t (&q)[3], int nc) {
     constexpr int sh = PosFmt<PB>::kShift;
-    return (int64_t)(q[0] >> sh) + nc * ((int64_t)(q[1] >> sh) + (int64_t)nc * (q[2] >> sh));
+    return (q[0] >> sh) + nc * ((q[1] >> sh) + nc * (q[2] >> sh));
 }
 
 // New-cell counts and fixed-point momentum sums.  Each thread takes kHistIlp
@@ -240,11 +241,12 @@ __global__ void __launch_bounds__(256) k_sigma(Src src, int64_t n, int nc,
                                                const float* __restrict__ vc,
                                                unsigned long long* d2, uint32_t* err) {
     const int64_t ncells = (int64_t)nc * nc * nc;
+    const float* vcd[3] = {vc, vc + ncells, vc + 2 * ncells};
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     unsigned long long lo = 0, hi = 0;
     for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < n;
          i0 += stride * kSigmaIlp) {
-        int64_t key[kSigmaIlp];
+        int key[kSigmaIlp];
         float p[kSigmaIlp][3], v[kSigmaIlp][3];
 #pragma unroll
         for (int u = 0; u < kSigmaIlp; ++u) {
@@ -257,7 +259,7 @@ __global__ void __launch_bounds__(256) k_sigma(Src src, int64_t n, int nc,
 #pragma unroll
         for (int u = 0; u < kSigmaIlp; ++u)
 #pragma unroll
-            for (int d = 0; d < 3; ++d) v[u][d] = key[u] >= 0 ? vc[d * ncells + key[u]] : 0.f;
+            for (int d = 0; d < 3; ++d) v[u][d] = key[u] >= 0 ? vcd[d][key[u]] : 0.f;
 #pragma unroll
         for (int u = 0; u < kSigmaIlp; ++u) {
             if (key[u] < 0) continue;
@@ -325,9 +327,15 @@ __global__ void k_scatter(Src src, int64_t n, int nc, const float* __restrict__ 
     const float sigma = *sigma_p;
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const float* vcd[3] = {vc, vc + ncells, vc + 2 * ncells};
+    // the Eq. 3 bin edges, looked up once or twice per component
+    __shared__ float Es[256];
+    for (int k = threadIdx.x; k < 256; k += blockDim.x) Es[k] = E[k];
+    __syncthreads();
     for (int64_t base = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); base < n;
          base += 2 * stride) {
-        int64_t i[2], key[2], off[2];
+        int64_t i[2], off[2];
+        int key[2];
         int32_t q[2][3];
         float p[2][3], v[2][3];
         int first[2];
@@ -339,14 +347,14 @@ __global__ void k_scatter(Src src, int64_t n, int nc, const float* __restrict__ 
             q[u][0] = q[u][1] = q[u][2] = 0;
             p[u][0] = p[u][1] = p[u][2] = 0.f;
             if (live) src.load(i[u], q[u], p[u]);
-            key[u] = live ? key3<PB>(q[u], nc) : -1ll - lane;
+            key[u] = live ? key3<PB>(q[u], nc) : -1 - lane;
         }
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
             const bool live = key[u] >= 0;
             off[u] = live ? offsets[key[u]] : 0;
 #pragma unroll
-            for (int d = 0; d < 3; ++d) v[u][d] = live ? vc[d * ncells + key[u]] : 0.f;
+            for (int d = 0; d < 3; ++d) v[u][d] = live ? vcd[d][key[u]] : 0.f;
             peers[u] = __match_any_sync(0xffffffffu, key[u]);
             first[u] = 0;
             if (live && lane == __ffs(peers[u]) - 1) first[u] = atomicAdd(&fill[key[u]], __popc(peers[u]));
@@ -360,7 +368,7 @@ __global__ void k_scatter(Src src, int64_t n, int nc, const float* __restrict__ 
             for (int d = 0; d < 3; ++d) {
                 if (PB == 1) out[d * n + slot] = (uint8_t)(q[u][d] & 255);
                 else reinterpret_cast<uint16_t*>(out + 2 * d * n)[slot] = (uint16_t)(q[u][d] & 65535);
-                out[(3 * PB + d) * n + slot] = (uint8_t)encode_momentum(p[u][d], v[u][d], sigma, E, err);
+                out[(3 * PB + d) * n + slot] = (uint8_t)encode_momentum(p[u][d], v[u][d], sigma, Es, err);
             }
         }
     }

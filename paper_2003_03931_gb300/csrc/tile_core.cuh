@@ -310,14 +310,14 @@ PMPM_HD void deposit_one(const TileGeom& g, const int (&cu)[3], const int (&m)[3
 
 // Coarse-mesh force (all three components) at one particle, CIC gather
 template <int PB>
-PMPM_HD void coarse_gather(const TileParams& P, const int64_t (&Q)[3], float (&gc)[3]) {
+PMPM_HD void coarse_gather(const TileParams& P, const int (&Q)[3], float (&gc)[3]) {
     using F = PosFmt<PB>;
     constexpr int W = F::kCoarseW;
     const int64_t ncells = (int64_t)P.nc * P.nc * P.nc;
     Cic1 cc[3];
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
-        const int64_t sc = 2 * Q[e] + 1 - F::kBins;     // units 1/(2B) of a coarse cell
+        const int sc = 2 * Q[e] + 1 - F::kBins;     // units 1/(2B) of a coarse cell (< 2^28)
         cc[e].i0 = (int)(sc >> F::kCoarseWBits);
         cc[e].w1 = (int)(sc & (W - 1));
     }
@@ -722,7 +722,8 @@ PMPM_HD void tile_deposit_flat(int tid, const TileGeom& g, const TileParams& P, 
     const int ptotal = c.ppre[kOwnMax];
     const int64_t obase = own_base(c);
     for (int v0 = tid; v0 < ptotal; v0 += kGatherIlp * kTileThreads) {
-        int64_t Q[kGatherIlp][3], j[kGatherIlp];
+        int64_t j[kGatherIlp];
+        int Q[kGatherIlp][3];   // codes, below nc 65536 <= 2^26
 #pragma unroll
         for (int u = 0; u < kGatherIlp; ++u) {
             const int v = v0 + u * kTileThreads;
@@ -730,9 +731,9 @@ PMPM_HD void tile_deposit_flat(int tid, const TileGeom& g, const TileParams& P, 
             j[u] = v < ptotal ? obase + c.prel[p] + (v - c.ppre[p]) : -1;
             if (j[u] >= 0) {
                 constexpr int B = PosFmt<PB>::kBins;
-                Q[u][0] = (int64_t)(g.c0[0] + p % kOwnDim) * B + load_bin<PB>(P.m0, j[u]);
-                Q[u][1] = (int64_t)(g.c0[1] + (p / kOwnDim) % kOwnDim) * B + load_bin<PB>(P.m1, j[u]);
-                Q[u][2] = (int64_t)(g.c0[2] + p / (kOwnDim * kOwnDim)) * B + load_bin<PB>(P.m2, j[u]);
+                Q[u][0] = (g.c0[0] + p % kOwnDim) * B + load_bin<PB>(P.m0, j[u]);
+                Q[u][1] = (g.c0[1] + (p / kOwnDim) % kOwnDim) * B + load_bin<PB>(P.m1, j[u]);
+                Q[u][2] = (g.c0[2] + p / (kOwnDim * kOwnDim)) * B + load_bin<PB>(P.m2, j[u]);
             }
         }
 #pragma unroll
@@ -1002,8 +1003,10 @@ PMPM_HD void tile_interp(int tid, const TileGeom& g, const TileParams& P, const 
     float* slot = P.mode == 0 ? P.G : P.Pn;
     const int ptotal = c.ppre[kOwnMax];
     const int64_t base = own_base(c);
+    const float* vcD = P.vc + D * ncells;
     for (int v0 = tid; v0 < ptotal; v0 += U * kTileThreads) {
-        int64_t j[U], Q[U][3], cell[U];
+        int64_t j[U];
+        int Q[U][3], cell[U];   // codes below nc 65536 <= 2^26, cells below 2^30
         float gcd[U], vcd[U];
         int u8[U];
         int32_t q01[U][2];
@@ -1019,15 +1022,15 @@ PMPM_HD void tile_interp(int tid, const TileGeom& g, const TileParams& P, const 
             j[u] = (v < ptotal && (!lm || v < kLowmemCap)) ? base + c.prel[p] + (v - c.ppre[p]) : -1;
             const int cx = g.c0[0] + p % kOwnDim, cy = g.c0[1] + (p / kOwnDim) % kOwnDim,
                       cz = g.c0[2] + p / (kOwnDim * kOwnDim);
-            cell[u] = cx + (int64_t)P.nc * (cy + (int64_t)P.nc * cz);
+            cell[u] = cx + P.nc * (cy + P.nc * cz);
             if (j[u] >= 0) {
-                Q[u][0] = (int64_t)cx * F::kBins + load_bin<PB>(P.m0, j[u]);
-                Q[u][1] = (int64_t)cy * F::kBins + load_bin<PB>(P.m1, j[u]);
-                Q[u][2] = (int64_t)cz * F::kBins + load_bin<PB>(P.m2, j[u]);
+                Q[u][0] = cx * F::kBins + load_bin<PB>(P.m0, j[u]);
+                Q[u][1] = cy * F::kBins + load_bin<PB>(P.m1, j[u]);
+                Q[u][2] = cz * F::kBins + load_bin<PB>(P.m2, j[u]);
                 gcd[u] = lm ? cs.sp[D * kLowmemCap + v] : slot[D * n + j[u]];
                 if (lm || P.mode >= 1) {
                     u8[u] = ud[j[u]];
-                    vcd[u] = P.vc[D * ncells + cell[u]];
+                    vcd[u] = vcD[cell[u]];
                 }
                 if (fuse) {
                     q01[u][0] = P.Qn[j[u]];
@@ -1044,7 +1047,7 @@ PMPM_HD void tile_interp(int tid, const TileGeom& g, const TileParams& P, const 
             int lo3[3], w1[3];
 #pragma unroll
             for (int e = 0; e < 3; ++e) {
-                const int s = (int)(2 * Q[u][e] + 1 - F::kCodesPerFine - (int64_t)F::kFineW * g.o[e]);
+                const int s = 2 * Q[u][e] + 1 - F::kCodesPerFine - F::kFineW * g.o[e];
                 lo3[e] = (s >> F::kFineWBits) - (kBuffer - 1);
                 w1[e] = s & (F::kFineW - 1);
             }
