@@ -111,9 +111,9 @@ PMPM_HD TileGeom tile_geom(int b, int nc, int nt) {
 PMPM_HD int ridx(int x, int y, int z) { return ((z << 5) + y) * 32 + (x ^ y); }
 PMPM_HD int cidx(int kx, int ky, int kz) { return ((kz << 5) + ky) * 16 + (kx ^ (ky & 15)); }
 PMPM_HD int widx(int kx, int ky, int zo) { return ((zo << 5) + ky) * 16 + (kx ^ (ky & 15)); }
-PMPM_HD int wfidx(int xo, int yo, int zo) {
-    return 2 * (((zo << 5) + yo) * 16 + ((xo >> 1) ^ (yo & 15))) + (xo & 1);
-}
+// the float view of widx: word xo of the pair (xo >> 1) ^ (yo & 15), i.e.
+// xo ^ 2 (yo & 15) (an even XOR keeps the low bit)
+PMPM_HD int wfidx(int xo, int yo, int zo) { return ((zo << 5) + yo) * 32 + (xo ^ ((yo & 15) << 1)); }
 
 #ifdef __CUDA_ARCH__
 PMPM_HD uint32_t smem_add_u32(uint32_t* p, uint32_t v) { return atomicAdd(p, v); }
@@ -1078,13 +1078,14 @@ PMPM_HD void tile_interp(int tid, const TileGeom& g, const TileParams& P, const 
             const float xq = fmul_rn(pn, drift);
             if (!(pn == pn) || !(gval == gval)) flag_error(P.err, kErrNaN);
             if (fabsf(pn) >= 1048576.f) flag_error(P.err, kErrMomentum);
-            int64_t dq = 0;
-            if (fabsf(xq) < 1.0e9f) dq = (int64_t)floorf(fadd_rn(xq, 0.5f));
+            // |dq| < 1e9 and codes below 2^26: the sum fits in 32 bits
+            int dq = 0;
+            if (fabsf(xq) < 1.0e9f) dq = (int)floorf(fadd_rn(xq, 0.5f));
             else flag_error(P.err, kErrDrift);
-            const int64_t M = (int64_t)P.nc * F::kBins;
-            // periodic wrap; a 64-bit division only for the rare particle
-            // that crosses the box boundary
-            int64_t qn = Q[u][D] + dq;
+            const int M = P.nc * F::kBins;
+            // periodic wrap; a division only for the rare particle that
+            // crosses the box boundary
+            int qn = Q[u][D] + dq;
             if (qn < 0 || qn >= M) {
                 qn %= M;
                 if (qn < 0) qn += M;
@@ -1093,10 +1094,9 @@ PMPM_HD void tile_interp(int tid, const TileGeom& g, const TileParams& P, const 
                 P.Qn[D * n + j[u]] = (int32_t)qn;
                 P.Pn[D * n + j[u]] = pn;
                 if (fuse) {
-                    const int32_t qa[3] = {q01[u][0], q01[u][1], (int32_t)qn};
+                    const int32_t qa[3] = {q01[u][0], q01[u][1], qn};
                     const float pa[3] = {p01[u][0], p01[u][1], pn};
-                    const int64_t key = (int64_t)(qa[0] >> F::kShift) +
-                                        P.nc * ((int64_t)(qa[1] >> F::kShift) + (int64_t)P.nc * (qa[2] >> F::kShift));
+                    const int key = (qa[0] >> F::kShift) + P.nc * ((qa[1] >> F::kShift) + P.nc * (qa[2] >> F::kShift));
                     gmem_add_i32(&P.counts_new[key], 1);
 #pragma unroll
                     for (int d = 0; d < 3; ++d) {
