@@ -65,13 +65,19 @@ PMPM_HD float decode_momentum(float vc, float sigma, float tu) {
 }
 
 // Eq. 4: the paper's fast arctangent, |x| <= 1 branch and its reflection
-// atan(x) = +-pi/2 - atan(1/x) for |x| > 1.
+// atan(x) = +-pi/2 - atan(1/x) for |x| > 1.  It only guesses the Eq. 3 bin
+// (the edge comparisons after it decide), so the reciprocal may be the
+// hardware approximation (a few ulp against a margin of 0.008 rad).
 PMPM_HD float atan_eq4(float x) {
     const float q = 0.78539816339744831f;   // pi/4
     const float c = 0.273f;
     float ax = x < 0.f ? -x : x;
     if (ax <= 1.f) return q * x + c * x * (1.f - ax);
+#ifdef __CUDA_ARCH__
+    float inv = __fdividef(1.f, x);
+#else
     float inv = 1.f / x;
+#endif
     float ainv = inv < 0.f ? -inv : inv;
     float half_pi = x > 0.f ? 1.5707963267948966f : -1.5707963267948966f;
     return half_pi - q * inv - c * inv * (1.f - ainv);
