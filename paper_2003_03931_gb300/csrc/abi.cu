@@ -121,7 +121,6 @@ static size_t layout_lowmem(Sim& s, uint8_t* base) {
     for (int b = 0; b < 2; ++b) s.sigma_d[b] = reinterpret_cast<float*>(take(4));
     s.lm_sp = reinterpret_cast<float*>(take(4 * 3 * (size_t)kLowmemCap * s.lm_ctas));
     s.lm_sq = reinterpret_cast<int32_t*>(take(4 * 2 * (size_t)kLowmemCap * s.lm_ctas));
-    s.lm_next = reinterpret_cast<int*>(take(4));
     off = align_up(off);
     const size_t p1 = off;
     // P1
@@ -285,7 +284,8 @@ static int sync_and_check(Sim& s) {
         return set_error(s, PMPM_EOVERFLOW,
                          "device range check failed (flags 0x%x: 1 fine density, 2 momentum, "
                          "4 velocity deviation, 16 non-finite, 32 drift, 64 more than %d own "
-                         "particles in a tile)", flags, kLowmemCap);
+                         "particles in a tile, 128 an SM id of %d or more)", flags, kLowmemCap,
+                         kLowmemCtas);
     }
     return PMPM_OK;
 }
@@ -439,11 +439,6 @@ static pmpm_sim* init_common(const pmpm_config* cfg, void* d_workspace, size_t b
     s.stream = static_cast<cudaStream_t>(cuda_stream);
     layout(s, s.ws);
     cudaGetDevice(&s.device);
-    if (s.lowmem) {
-        int sms = 0;
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s.device);
-        s.lm_grid = sms < 1 ? 1 : (sms < s.lm_ctas ? sms : s.lm_ctas);
-    }
     tile_setup();
     fft_setup();
     cudaMemsetAsync(s.err, 0, 4, s.stream);

@@ -36,6 +36,7 @@ enum : uint32_t {
     kErrNaN = 16u,            // non-finite momentum or force
     kErrDrift = 32u,          // drift larger than the int32 code range
     kErrScratch = 64u,        // a tile has more own particles than the low-memory scratch holds
+    kErrSlot = 128u,          // an SM id beyond the low-memory scratch slots
 };
 
 #ifdef __CUDA_ARCH__

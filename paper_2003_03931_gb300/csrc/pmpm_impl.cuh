@@ -12,7 +12,7 @@
 namespace pmpm {
 
 constexpr int kStages = 6;          // see pmpm_stage_times
-constexpr int kLowmemCtas = 160;    // persistent tile CTAs of the low-memory step (>= SMs)
+constexpr int kLowmemCtas = 160;    // low-memory scratch slots, one per SM id (%smid)
 constexpr int kEventRing = 4096;
 
 struct Sim {
@@ -72,8 +72,6 @@ struct Sim {
     // low-memory step (PMPM_FLAG_LOWMEM)
     bool lowmem = false;
     int lm_ctas = 0;                            // scratch slots (kLowmemCtas)
-    int lm_grid = 0;                            // persistent tile CTAs: min(SMs, slots)
-    int* lm_next = nullptr;                     // tile counter of a low-memory pass
     float* lm_sp = nullptr;                     // [ctas][3][kLowmemCap] per-CTA momenta
     int32_t* lm_sq = nullptr;                   // [ctas][2][kLowmemCap] per-CTA codes
     float2* ic_work = nullptr;                  // [N] float32 IC transform (overlays the store)

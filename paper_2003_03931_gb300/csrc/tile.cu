@@ -81,7 +81,7 @@ __device__ __forceinline__ void tile_sigma_flush(int tid, const TileParams& P, f
 // per force component the Green multiply, inverse transform and
 // interpolation (phases of tile_core.cuh with a block barrier between).
 template <bool LM, int PB>
-__device__ __forceinline__ void tile_body(int tile, bool first, const TileParams& P,
+__device__ __forceinline__ void tile_body(int tile, const TileParams& P,
                                           unsigned char* tile_smem, CtaScratch cs) {
     uint32_t* R = reinterpret_cast<uint32_t*>(tile_smem);
     float2* C = reinterpret_cast<float2*>(tile_smem);
@@ -92,7 +92,7 @@ __device__ __forceinline__ void tile_body(int tile, bool first, const TileParams
     const TileGeom g = tile_geom(tile, P.nc, P.nt);
     const TileCells cells = tile_cells(W, O);   // W is free until phase 5
     PMPM_MARK(0);
-    tile_prologue(tid, g, P, cells, R, gS, first);
+    tile_prologue(tid, g, P, cells, R, gS);
     __syncthreads();
     PMPM_MARK(1);
     tile_cells_scan(tid, g, cells);
@@ -124,34 +124,24 @@ __device__ __forceinline__ void tile_body(int tile, bool first, const TileParams
 template <int PB>
 __global__ void __launch_bounds__(kTileThreads, 1) k_tile(TileParams P) {
     extern __shared__ __align__(16) unsigned char tile_smem[];
-    tile_body<false, PB>((int)blockIdx.x, true, P, tile_smem, CtaScratch{nullptr, nullptr});
+    tile_body<false, PB>((int)blockIdx.x, P, tile_smem, CtaScratch{nullptr, nullptr});
 }
 
-// One tile of a low-memory pass, out of line: called from the persistent
-// loop, it gets its own register allocation without the loop's state
-// (inlined, the kernel spilled 372 bytes per thread; measured 10% slower).
-__device__ __noinline__ void tile_body_lowmem(int tile, bool first, const TileParams& P,
-                                              unsigned char* tile_smem, CtaScratch cs) {
-    tile_body<true, 1>(tile, first, P, tile_smem, cs);
-}
-
-// Low-memory passes (modes 2-4): one resident CTA per SM takes tiles from
-// a counter (its first tile is blockIdx.x) and keeps its scratch slot.
-__global__ void __launch_bounds__(kTileThreads, 1) k_tile_lowmem(TileParams P, int* next_tile) {
+// Low-memory passes (modes 2-4): one CTA per tile, like k_tile.  A tile's
+// scratch slot is its SM's (one tile CTA fits an SM at a time, so no two
+// running CTAs share a slot).  (A persistent loop over tiles with the body
+// out of line was 10% slower: the out-of-line body reads the parameters
+// through memory instead of the constant bank.)
+__global__ void __launch_bounds__(kTileThreads, 1) k_tile_lowmem(TileParams P) {
     extern __shared__ __align__(16) unsigned char tile_smem[];
-    __shared__ int next;
-    const CtaScratch cs{P.sp + (size_t)blockIdx.x * 3 * kLowmemCap,
-                        P.sq + (size_t)blockIdx.x * 2 * kLowmemCap};
-    const int ntiles = P.nt * P.nt * P.nt;
-    int tile = blockIdx.x;
-    bool first = true;
-    while (tile < ntiles) {
-        tile_body_lowmem(tile, first, P, tile_smem, cs);
-        first = false;
-        if (threadIdx.x == 0) next = (int)gridDim.x + atomicAdd(next_tile, 1);
-        __syncthreads();
-        tile = next;
+    unsigned smid;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+    if (smid >= (unsigned)kLowmemCtas) {
+        if (threadIdx.x == 0) flag_error(P.err, kErrSlot);
+        return;
     }
+    const CtaScratch cs{P.sp + (size_t)smid * 3 * kLowmemCap, P.sq + (size_t)smid * 2 * kLowmemCap};
+    tile_body<true, 1>((int)blockIdx.x, P, tile_smem, cs);
 }
 
 void tile_setup() {
@@ -203,10 +193,8 @@ int tile_pass(Sim& s, int mode, float* G) {
         P.sigma_new = s.sigma_d[nxt];
         P.E = s.Eedge;
         P.out = s.streams[nxt];
-        grid = ntiles < s.lm_grid ? ntiles : s.lm_grid;
-        cudaMemsetAsync(s.lm_next, 0, sizeof(int), s.stream);
     }
-    if (mode >= 2) k_tile_lowmem<<<grid, kTileThreads, kTileSmemBytes, s.stream>>>(P, s.lm_next);
+    if (mode >= 2) k_tile_lowmem<<<grid, kTileThreads, kTileSmemBytes, s.stream>>>(P);
     else if (s.pb == 2) k_tile<2><<<grid, kTileThreads, kTileSmemBytes, s.stream>>>(P);
     else k_tile<1><<<grid, kTileThreads, kTileSmemBytes, s.stream>>>(P);
     s.launches++;

@@ -133,116 +133,6 @@ PMPM_HD void tile_zero(int tid, uint32_t* R) {
     for (int i = tid; i < kTileR / 4; i += kTileThreads) R4[i] = make_uint4(0u, 0u, 0u, 0u);
 }
 
-// Per-lane table of up to 9 consecutive cells of one row: prefix counts and
-// storage offsets, held in registers (fixed-size, fully unrolled).
-struct RowCells {
-    int pc[10];          // pc[i] = particles in cells before i; pc[n] = total
-    int64_t st[9];       // storage offset of cell i
-    int n;
-};
-
-PMPM_HD void row_cells(RowCells& rc, const TileParams& P, int base, int x_first, int ncell) {
-    rc.n = ncell;
-    int acc = 0;
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        rc.pc[i] = acc;
-        rc.st[i] = 0;
-        if (i < ncell) {
-            int cell = base + wrap(x_first + i, P.nc);
-            rc.st[i] = P.offsets[cell];
-            acc += P.counts[cell];
-        }
-    }
-    rc.pc[9] = acc;
-    if (ncell < 9) {
-#pragma unroll
-        for (int i = 0; i < 10; ++i)
-            if (i > ncell) rc.pc[i] = acc;
-    }
-}
-
-// Cell of the v-th particle of the row: returns its index i and, through
-// start, the storage offset of particle v.  Only compile-time array indices
-// are used, so the table stays in registers.
-PMPM_HD int row_find(const RowCells& rc, int v, int64_t& start) {
-    int c = 0;
-    int64_t st = rc.st[0];
-    int pc = rc.pc[0];
-#pragma unroll
-    for (int i = 1; i < 9; ++i)
-        if (i < rc.n && rc.pc[i] <= v) {
-            c = i;
-            st = rc.st[i];
-            pc = rc.pc[i];
-        }
-    start = st + (v - pc);
-    return c;
-}
-
-// One row of up to 9 consecutive coarse cells (periodic in x) as a warp
-// sees it.  On the device lane i < n holds cell i's storage offset and the
-// number of the row's particles before it, and lookups are shuffles; on the
-// host every lane keeps the whole table.
-struct RowTable {
-#ifdef __CUDA_ARCH__
-    int64_t st;
-    int ex;
-#else
-    RowCells rc;
-#endif
-    int n, total;
-};
-
-PMPM_HD void row_build(RowTable& t, const TileParams& P, int base, int x_first, int ncell,
-                       int lane) {
-    t.n = ncell;
-#ifdef __CUDA_ARCH__
-    int cnt = 0;
-    int64_t st = 0;
-    if (lane < ncell) {
-        const int cell = base + wrap(x_first + lane, P.nc);
-        st = P.offsets[cell];
-        cnt = P.counts[cell];
-    }
-    int incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 16; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    t.st = st;
-    t.ex = incl - cnt;
-    t.total = __shfl_sync(0xffffffffu, incl, 15);
-#else
-    (void)lane;
-    row_cells(t.rc, P, base, x_first, ncell);
-    t.total = t.rc.pc[9];
-#endif
-}
-
-// Storage offset of the row's v-th particle and its cell index i.  On the
-// device all 32 lanes must call it together (v may be past the end).
-PMPM_HD int64_t row_locate(const RowTable& t, int v, int& i) {
-#ifdef __CUDA_ARCH__
-    int c = 0;
-#pragma unroll
-    for (int step = 8; step > 0; step >>= 1) {
-        const int cand = c + step;
-        const int e = __shfl_sync(0xffffffffu, t.ex, cand & 31);
-        if (cand < t.n && e <= v) c = cand;
-    }
-    i = c;
-    const int64_t st = __shfl_sync(0xffffffffu, t.st, c);
-    const int ex = __shfl_sync(0xffffffffu, t.ex, c);
-    return st + (v - ex);
-#else
-    int64_t j;
-    i = row_find(t.rc, v, j);
-    return j;
-#endif
-}
-
 // shared-memory add without a returned value
 PMPM_HD void smem_red_u32(uint32_t* p, uint32_t v) {
 #ifdef __CUDA_ARCH__
@@ -431,7 +321,7 @@ PMPM_HD int own_to_halo(int p) {
 // the packed Green table, sigma and the step factors) is issued before the
 // first shared-memory store, so the tile waits for one memory round trip.
 PMPM_HD void tile_prologue(int tid, const TileGeom& g, const TileParams& P, TileCells c,
-                           uint32_t* R, float* gS, bool load_green) {
+                           uint32_t* R, float* gS) {
     const int hx = g.c1[0] - g.c0[0] + 4, hy = g.c1[1] - g.c0[1] + 4, hz = g.c1[2] - g.c0[2] + 4;
     int64_t st[2] = {0, 0};
     int cnt[2] = {0, 0};
@@ -451,9 +341,9 @@ PMPM_HD void tile_prologue(int tid, const TileGeom& g, const TileParams& P, Tile
 #pragma unroll
     for (int u = 0; u < (kGreenPacked + kTileThreads - 1) / kTileThreads; ++u) {
         const int i = tid + u * kTileThreads;
-        gv[u] = (load_green && i < kGreenPacked) ? P.green[i] : 0.f;
+        gv[u] = i < kGreenPacked ? P.green[i] : 0.f;
     }
-    const float td = (load_green && tid < 256) ? P.Tdec[tid] : 0.f;
+    const float td = tid < 256 ? P.Tdec[tid] : 0.f;
     float sc[4] = {0.f, 0.f, 0.f, 0.f};
     if (tid == 0) {
         sc[0] = *P.sigma;
@@ -475,9 +365,9 @@ PMPM_HD void tile_prologue(int tid, const TileGeom& g, const TileParams& P, Tile
 #pragma unroll
     for (int u = 0; u < (kGreenPacked + kTileThreads - 1) / kTileThreads; ++u) {
         const int i = tid + u * kTileThreads;
-        if (load_green && i < kGreenPacked) gS[i] = gv[u];
+        if (i < kGreenPacked) gS[i] = gv[u];
     }
-    if (load_green && tid < 256) c.Td[tid] = td;
+    if (tid < 256) c.Td[tid] = td;
     if (tid == 0) {
         c.misc[4] = f32_to_bits(sc[0]);
         c.misc[5] = f32_to_bits(sc[1]);
@@ -794,11 +684,6 @@ PMPM_HD int green_tri(int b, int c) {
     return b <= c ? green_off(b) + c : green_off(c) + b;
 }
 
-// Copy the packed Green table (15 x 153 floats: own-axis |k| = 1..15, b <= c)
-// into shared memory.
-PMPM_HD void tile_load_green(int tid, const float* Gp, float* gS) {
-    for (int i = tid; i < kGreenPacked; i += kTileThreads) gS[i] = Gp[i];
-}
 
 // --- phase 5a: Green multiply (Eq. 1) and inverse transform along z -------
 // For kx = 1..15: G = rho~ K~_d = -i S rho~.  For the packed kx = 0 pencil,
