@@ -79,7 +79,9 @@ extern "C" {
                                 About 24.5 bytes per particle of workspace instead
                                 of 83 (2048^3 particles fit in one GB300), for about
                                 three times the tile work.  A tile may hold at most
-                                65,536 of its own particles (PMPM_EOVERFLOW above).
+                                65,536 of its own particles, and the device at most
+                                160 SM ids (each SM keeps a scratch slot; both
+                                PMPM_EOVERFLOW above).
                                 Initial conditions use float32 transforms and a
                                 float32 displacement field (the default uses
                                 float64).  PMPM_DECODED_Q/P, PMPM_FORCE and loading
