@@ -163,9 +163,10 @@ struct PosFmt {
 };
 
 // round-half-even(w / 2^bits), bits > 0
+// (w + 2^(bits-1) - 1 + bit `bits` of w) >> bits: the same as comparing the
+// remainder with one half, with ties to the even quotient (w < 2^63)
 PMPM_HD uint64_t round_half_even_shift(uint64_t w, int bits) {
-    const uint64_t q = w >> bits, r = w & ((1ull << bits) - 1ull), half = 1ull << (bits - 1);
-    return q + ((r > half || (r == half && (q & 1ull))) ? 1ull : 0ull);
+    return (w + ((1ull << (bits - 1)) - 1ull) + ((w >> bits) & 1ull)) >> bits;
 }
 
 // 3-D weight in the 1-byte units from three 1-D weights of format PB

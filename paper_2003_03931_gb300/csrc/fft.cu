@@ -7,6 +7,7 @@
 // z axes the P pencils are adjacent in x, so every global access reads P
 // consecutive complex numbers.
 #include "pmpm_impl.cuh"
+#include "regfft.cuh"
 
 namespace pmpm {
 
@@ -120,6 +121,84 @@ __global__ void __launch_bounds__(kPassThreads) k_fft_pass(typename Cplx<R>::T* 
     }
 }
 
+// Float pencils of n = N1 N2 points (N1, N2 in {16, 32}) in two register
+// steps, one shared-memory transpose between (the "four-step" split of the
+// DFT): with j = N2 n1 + n2 and k = k1 + N1 k2,
+//   X[k] = sum_n2 W_N2^(n2 k2) [ W_n^(n2 k1) sum_n1 W_N1^(n1 k1) x[j] ].
+// Step A: one thread per (pencil, n2) does the N1-point transform and the
+// twiddle; step B: one thread per (pencil, k1) does the N2-point transform.
+// Each element crosses shared memory once and the block waits at one
+// barrier, against log2 n sweeps and barriers in k_fft_pass.  Rows of the
+// transpose buffer are N2 + 1 long and pencils N1 (N2 + 1) + 1 (odd), so
+// lanes over n2, k1 or the pencil all touch distinct banks.  Loads and
+// stores are coalesced as in k_fft_pass: lanes run along the pencil for the
+// x axis and across adjacent pencils for y and z.
+template <int N1, int N2, int S>
+__global__ void __launch_bounds__(kPassThreads) k_fft_pass_r(float2* data, int axis, int P, int log2P,
+                                                             const float2* tw, int twsh) {
+    constexpr int n = N1 * N2;
+    constexpr int L1 = N1 == 16 ? 4 : 5, L2 = N2 == 16 ? 4 : 5, LN = L1 + L2;
+    constexpr int RS = N2 + 1, PS = N1 * RS + 1;
+    extern __shared__ __align__(16) unsigned char fft_smem[];
+    float2* Y = reinterpret_cast<float2*>(fft_smem);
+    const int64_t q0 = (int64_t)blockIdx.x * P;
+    auto base_of = [&](int p) -> int64_t {
+        const int64_t q = q0 + p;
+        if (axis == 0) return q << LN;
+        const int64_t hi = q >> LN, lo = q & (n - 1);
+        if (axis == 1) return (hi << (2 * LN)) + lo;
+        return (hi << LN) + lo;
+    };
+    const int sh = axis * LN;
+    for (int it = threadIdx.x; it < P * N2; it += kPassThreads) {
+        const int p = axis == 0 ? it >> L2 : (it & (P - 1));
+        const int n2 = axis == 0 ? (it & (N2 - 1)) : (it >> log2P);
+        const int64_t b = base_of(p);
+        float2 a[N1];
+#pragma unroll
+        for (int n1 = 0; n1 < N1; ++n1) a[bitrev<L1>(n1)] = data[b + ((int64_t)(N2 * n1 + n2) << sh)];
+        fft_dit<N1, S>(a);
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) {
+            float2 w = tw[(n2 * k1) << twsh];
+            if (S > 0) w.y = -w.y;
+            Y[p * PS + k1 * RS + n2] = make_float2(a[k1].x * w.x - a[k1].y * w.y, a[k1].x * w.y + a[k1].y * w.x);
+        }
+    }
+    __syncthreads();
+    for (int it = threadIdx.x; it < P * N1; it += kPassThreads) {
+        const int p = axis == 0 ? it >> L1 : (it & (P - 1));
+        const int k1 = axis == 0 ? (it & (N1 - 1)) : (it >> log2P);
+        float2 a[N2];
+#pragma unroll
+        for (int n2 = 0; n2 < N2; ++n2) a[bitrev<L2>(n2)] = Y[p * PS + k1 * RS + n2];
+        fft_dit<N2, S>(a);
+        const int64_t b = base_of(p);
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) data[b + ((int64_t)(k1 + N1 * k2) << sh)] = a[k2];
+    }
+}
+
+template <int N1, int N2>
+static void launch_pass_r(float2* data, int n, int sign, const float2* tw, int tw_n, cudaStream_t st) {
+    constexpr int P = 4096 / (N1 * N2) < 8 ? 8 : 4096 / (N1 * N2);   // 16 at 256, 8 at 512 and 1024
+    constexpr int PS = N1 * (N2 + 1) + 1;
+    const size_t smem = (size_t)P * PS * sizeof(float2);
+    int lt = 0, lp = 0;
+    while ((1 << lt) < tw_n) ++lt;
+    while ((1 << lp) < P) ++lp;
+    int ln = 0;
+    while ((1 << ln) < n) ++ln;
+    const int twsh = lt - ln;                       // W_n^e = tw[e << twsh]
+    const int64_t groups = (int64_t)n * n / P;
+    for (int axis = 0; axis < 3; ++axis) {
+        if (sign < 0)
+            k_fft_pass_r<N1, N2, -1><<<(unsigned)groups, kPassThreads, smem, st>>>(data, axis, P, lp, tw, twsh);
+        else
+            k_fft_pass_r<N1, N2, 1><<<(unsigned)groups, kPassThreads, smem, st>>>(data, axis, P, lp, tw, twsh);
+    }
+}
+
 static int ilog2(int v) {
     int l = 0;
     while ((1 << l) < v) ++l;
@@ -140,6 +219,14 @@ int fft3d(Sim& s, void* data, int n, int sign) {
     using C = typename Cplx<R>::T;
     if (n < 2 || (n & (n - 1)) || n > s.fft_max)
         return set_error(s, PMPM_EINVAL, "fft length %d not supported", n);
+    if (sizeof(R) == 4 && (n == 256 || n == 512 || n == 1024)) {
+        float2* d = reinterpret_cast<float2*>(data);
+        if (n == 256) launch_pass_r<16, 16>(d, n, sign, s.tw_f, s.fft_max, s.stream);
+        else if (n == 512) launch_pass_r<16, 32>(d, n, sign, s.tw_f, s.fft_max, s.stream);
+        else launch_pass_r<32, 32>(d, n, sign, s.tw_f, s.fft_max, s.stream);
+        s.launches += 3;
+        return check_launch(s, "fft");
+    }
     int log2n = 0;
     while ((1 << log2n) < n) ++log2n;
     const int P = pencils_per_block<R>(n);
@@ -162,6 +249,10 @@ template int fft3d<float>(Sim&, void*, int, int);
 void fft_setup() {
     cudaFuncSetAttribute(k_fft_pass<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPassSmem);
     cudaFuncSetAttribute(k_fft_pass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPassSmem);
+    cudaFuncSetAttribute(k_fft_pass_r<32, 32, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPassSmem);
+    cudaFuncSetAttribute(k_fft_pass_r<32, 32, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPassSmem);
+    cudaFuncSetAttribute(k_fft_pass_r<16, 32, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPassSmem);
+    cudaFuncSetAttribute(k_fft_pass_r<16, 32, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPassSmem);
 }
 
 // The same three float passes for a caller-supplied twiddle table of tw_n
