@@ -121,7 +121,9 @@ __global__ void __launch_bounds__(kPassThreads) k_fft_pass(typename Cplx<R>::T* 
     }
 }
 
-// Float pencils of n = N1 N2 points (N1, N2 in {16, 32}) in two register
+constexpr int clog2(int v) { return v <= 1 ? 0 : 1 + clog2(v / 2); }
+
+// Float pencils of n = N1 N2 points (N1, N2 in {8, 16, 32}) in two register
 // steps, one shared-memory transpose between (the "four-step" split of the
 // DFT): with j = N2 n1 + n2 and k = k1 + N1 k2,
 //   X[k] = sum_n2 W_N2^(n2 k2) [ W_n^(n2 k1) sum_n1 W_N1^(n1 k1) x[j] ].
@@ -137,7 +139,7 @@ template <int N1, int N2, int S>
 __global__ void __launch_bounds__(kPassThreads) k_fft_pass_r(float2* data, int axis, int P, int log2P,
                                                              const float2* tw, int twsh) {
     constexpr int n = N1 * N2;
-    constexpr int L1 = N1 == 16 ? 4 : 5, L2 = N2 == 16 ? 4 : 5, LN = L1 + L2;
+    constexpr int L1 = clog2(N1), L2 = clog2(N2), LN = L1 + L2;
     constexpr int RS = N2 + 1, PS = N1 * RS + 1;
     extern __shared__ __align__(16) unsigned char fft_smem[];
     float2* Y = reinterpret_cast<float2*>(fft_smem);
@@ -181,7 +183,7 @@ __global__ void __launch_bounds__(kPassThreads) k_fft_pass_r(float2* data, int a
 
 template <int N1, int N2>
 static void launch_pass_r(float2* data, int n, int sign, const float2* tw, int tw_n, cudaStream_t st) {
-    constexpr int P = 4096 / (N1 * N2) < 8 ? 8 : 4096 / (N1 * N2);   // 16 at 256, 8 at 512 and 1024
+    constexpr int P = 4096 / (N1 * N2) < 8 ? 8 : 4096 / (N1 * N2);   // 64 at n = 64 ... 8 at 512, 1024
     constexpr int PS = N1 * (N2 + 1) + 1;
     const size_t smem = (size_t)P * PS * sizeof(float2);
     int lt = 0, lp = 0;
@@ -219,9 +221,11 @@ int fft3d(Sim& s, void* data, int n, int sign) {
     using C = typename Cplx<R>::T;
     if (n < 2 || (n & (n - 1)) || n > s.fft_max)
         return set_error(s, PMPM_EINVAL, "fft length %d not supported", n);
-    if (sizeof(R) == 4 && (n == 256 || n == 512 || n == 1024)) {
+    if (sizeof(R) == 4 && n >= 64 && n <= 1024) {
         float2* d = reinterpret_cast<float2*>(data);
-        if (n == 256) launch_pass_r<16, 16>(d, n, sign, s.tw_f, s.fft_max, s.stream);
+        if (n == 64) launch_pass_r<8, 8>(d, n, sign, s.tw_f, s.fft_max, s.stream);
+        else if (n == 128) launch_pass_r<8, 16>(d, n, sign, s.tw_f, s.fft_max, s.stream);
+        else if (n == 256) launch_pass_r<16, 16>(d, n, sign, s.tw_f, s.fft_max, s.stream);
         else if (n == 512) launch_pass_r<16, 32>(d, n, sign, s.tw_f, s.fft_max, s.stream);
         else launch_pass_r<32, 32>(d, n, sign, s.tw_f, s.fft_max, s.stream);
         s.launches += 3;
@@ -259,6 +263,15 @@ void fft_setup() {
 // entries (n divides tw_n); used where no Sim exists.
 cudaError_t fft3d_float_raw(cudaStream_t st, float2* data, int n, int sign, const float2* tw,
                             int tw_n) {
+    if (n >= 64 && n <= 1024 && n <= tw_n) {   // the same passes as fft3d<float>
+        if (n > 512) fft_setup();                // more than 48 KB of shared memory
+        if (n == 64) launch_pass_r<8, 8>(data, n, sign, tw, tw_n, st);
+        else if (n == 128) launch_pass_r<8, 16>(data, n, sign, tw, tw_n, st);
+        else if (n == 256) launch_pass_r<16, 16>(data, n, sign, tw, tw_n, st);
+        else if (n == 512) launch_pass_r<16, 32>(data, n, sign, tw, tw_n, st);
+        else launch_pass_r<32, 32>(data, n, sign, tw, tw_n, st);
+        return cudaGetLastError();
+    }
     int log2n = 0;
     while ((1 << log2n) < n) ++log2n;
     const int P = pencils_per_block<float>(n);

@@ -14,10 +14,11 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-4
 
 
-@pytest.mark.parametrize("np_,nc,evolve", [(32, 16, 0), (32, 16, 6), (32, 32, 4), (64, 32, 3)])
+@pytest.mark.parametrize("np_,nc,evolve", [(32, 16, 0), (32, 16, 6), (32, 32, 4), (64, 32, 3), (64, 64, 1)])
 def test_force_matches_oracle(np_, nc, evolve):
     # (32, 16): 4 tiles of 16 per side; (32, 32) and (64, 32): 7 ragged tiles
-    # of 16/20; evolved states are clustered
+    # of 16/20; evolved states are clustered; (64, 64): the coarse mesh goes
+    # through the two-step register FFT (64 = 8 x 8 points)
     need_gpu()
     sim = make_sim(np=np_, nc=nc, a_init=0.02, a_final=1.0, n_steps=10)
     sim.ic_zeldovich(11)
