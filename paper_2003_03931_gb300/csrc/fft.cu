@@ -2,10 +2,12 @@
 // (n a power of two), float or double.  Used for the coarse-mesh force of
 // Eq. 1, the Zel'dovich displacement field and the power spectrum.
 //
-// One block transforms P neighbouring pencils in shared memory with a
-// Stockham autosort radix-2 sweep (natural order in and out).  For the y and
-// z axes the P pencils are adjacent in x, so every global access reads P
-// consecutive complex numbers.
+// One block transforms P neighbouring pencils.  Float pencils of 64 to 1024
+// points take two register steps with one shared-memory transpose
+// (k_fft_pass_r); other sizes and float64 take a Stockham autosort radix-2
+// sweep in shared memory (k_fft_pass; natural order in and out).  For the y
+// and z axes the P pencils are adjacent in x, so every global access reads
+// P consecutive complex numbers.
 #include "pmpm_impl.cuh"
 #include "regfft.cuh"
 
