@@ -1,6 +1,6 @@
 """GPU checks of the low-memory step (PMPM_FLAG_LOWMEM): from the same state
 it writes the same store as the default step (cell-sorted records, counts,
-v_c, sigma bit for bit), also when each persistent CTA walks many tiles; its
+v_c, sigma bit for bit), also when many tiles share each SM's scratch slot; its
 float32 initial conditions match the oracle's like the default ones; and the
 per-particle fetches it cannot serve fail cleanly."""
 
