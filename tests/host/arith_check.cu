@@ -1,0 +1,148 @@
+// Host checks of the device arithmetic helpers that the kernels share with
+// the host build (common.cuh, regfft.cuh) against their plain definitions.
+// Prints one line per check: "<name> <cases> <failures> [<max error>]".
+#include "../../paper_2003_03931_gb300/csrc/common.cuh"
+#include "../../paper_2003_03931_gb300/csrc/regfft.cuh"
+
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+using namespace pmpm;
+
+static unsigned long long rng_state = 0x9E3779B97F4A7C15ull;
+static unsigned long long next_u64() {
+    rng_state ^= rng_state << 13;
+    rng_state ^= rng_state >> 7;
+    rng_state ^= rng_state << 17;
+    return rng_state;
+}
+static float bits_float(uint32_t u) {
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+}
+
+// round-half-even of p 2^24 through long double arithmetic and llrint
+static void check_fix24() {
+    long long n = 0, bad = 0;
+    auto one = [&](float p) {
+        if (!(fabsf(p) < 1048576.f)) return;
+        ++n;
+        if (fix24_rn(p) != llrint((double)p * 16777216.0)) ++bad;
+    };
+    for (int i = 0; i < 4000000; ++i) one(bits_float((uint32_t)next_u64()));
+    for (long long j = -200000; j < 200000; ++j) one((float)(((double)j + 0.5) / 16777216.0));
+    printf("fix24 %lld %lld\n", n, bad);
+}
+
+// round-half-even of d^2 2^32 from the exact square (m^2 < 2^48) and a
+// remainder test
+static void check_sq() {
+    long long n = 0, bad = 0;
+    for (int i = 0; i < 4000000; ++i) {
+        const float d = bits_float((uint32_t)next_u64() & 0x7fffffffu);
+        if (!(d < 65536.f)) continue;
+        ++n;
+        uint32_t u;
+        memcpy(&u, &d, 4);
+        const uint32_t E = u >> 23, M = u & 0x7fffffu;
+        const unsigned long long m = E ? (M | 0x800000u) : M;
+        const int e = (E ? (int)E : 1) - 150;
+        const unsigned long long m2 = m * m;
+        const int sh = 2 * e + 32;
+        unsigned long long ref;
+        if (sh >= 0) ref = m2 << sh;
+        else if (-sh > 60) ref = 0;
+        else {
+            const int r = -sh;
+            const unsigned long long q = m2 >> r, rem = m2 - (q << r), half = 1ull << (r - 1);
+            ref = q + ((rem > half || (rem == half && (q & 1))) ? 1 : 0);
+        }
+        if (sq_fix32(d) != ref) ++bad;
+    }
+    printf("sq_fix32 %lld %lld\n", n, bad);
+}
+
+static void check_rhe() {
+    long long n = 0, bad = 0;
+    for (int bits = 1; bits <= 40; ++bits)
+        for (int i = 0; i < 100000; ++i) {
+            unsigned long long w = next_u64() >> 12;
+            if (i % 3 == 0) w = (w >> bits << bits) | (1ull << (bits - 1));   // exact halves
+            const unsigned long long q = w >> bits, rem = w - (q << bits), half = 1ull << (bits - 1);
+            const unsigned long long ref = q + ((rem > half || (rem == half && (q & 1))) ? 1 : 0);
+            ++n;
+            if (round_half_even_shift(w, bits) != ref) ++bad;
+        }
+    printf("round_half_even %lld %lld\n", n, bad);
+}
+
+// register FFTs against the direct DFT (float32 arithmetic, relative error)
+template <int N, int S>
+static double dft_err() {
+    float2 a[N];
+    std::vector<std::complex<double>> x(N);
+    for (int i = 0; i < N; ++i) {
+        const float re = (float)((next_u64() >> 40) * 0x1p-24 - 0.5), im = (float)((next_u64() >> 40) * 0x1p-24 - 0.5);
+        x[i] = {re, im};
+        a[bitrev<N == 16 ? 4 : (N == 32 ? 5 : 3)>(i)] = make_float2(re, im);
+    }
+    fft_dit<N, S>(a);
+    double err = 0, mx = 0;
+    for (int k = 0; k < N; ++k) {
+        std::complex<double> acc = 0;
+        for (int j = 0; j < N; ++j) acc += x[j] * std::polar(1.0, S * 2 * M_PI * (double)j * k / N);
+        err = fmax(err, std::abs(acc - std::complex<double>(a[k].x, a[k].y)));
+        mx = fmax(mx, std::abs(acc));
+    }
+    return err / mx;
+}
+
+// the real forward transform (which returns twice the DFT) against the
+// direct DFT, and the round trip through the inverse
+static double rfft_err() {
+    float x[32];
+    double xm = 0;
+    for (int i = 0; i < 32; ++i) {
+        x[i] = (float)((next_u64() >> 40) * 0x1p-24 - 0.5);
+        xm = fmax(xm, fabs(x[i]));
+    }
+    float2 X[17];
+    rfft32x2(x, X);
+    double err = 0, mx = 0;
+    for (int k = 0; k <= 16; ++k) {
+        std::complex<double> acc = 0;
+        for (int j = 0; j < 32; ++j) acc += (double)x[j] * std::polar(1.0, -2 * M_PI * j * k / 32.0);
+        err = fmax(err, std::abs(2.0 * acc - std::complex<double>(X[k].x, X[k].y)));
+        mx = fmax(mx, 2.0 * std::abs(acc));
+    }
+    float2 Xh[17];
+    for (int k = 0; k <= 16; ++k) Xh[k] = make_float2(0.5f * X[k].x, 0.5f * X[k].y);
+    float y[32];
+    irfft32(Xh, y);   // 32 x
+    double rt = 0;
+    for (int j = 0; j < 32; ++j) rt = fmax(rt, fabs(y[j] / 32.0 - x[j]));
+    return fmax(err / mx, rt / xm);
+}
+
+int main() {
+    check_fix24();
+    check_sq();
+    check_rhe();
+    double e = 0;
+    for (int t = 0; t < 20; ++t) {
+        e = fmax(e, dft_err<8, -1>());
+        e = fmax(e, dft_err<16, -1>());
+        e = fmax(e, dft_err<16, 1>());
+        e = fmax(e, dft_err<32, -1>());
+        e = fmax(e, dft_err<32, 1>());
+    }
+    printf("fft_dit 100 0 %.3e\n", e);
+    double r = 0;
+    for (int t = 0; t < 50; ++t) r = fmax(r, rfft_err());
+    printf("rfft32 50 0 %.3e\n", r);
+    return 0;
+}
