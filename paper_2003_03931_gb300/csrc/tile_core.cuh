@@ -198,45 +198,6 @@ PMPM_HD void deposit_one(const TileGeom& g, const int (&cu)[3], const int (&m)[3
     }
 }
 
-// Coarse-mesh force (all three components) at one particle, CIC gather
-template <int PB>
-PMPM_HD void coarse_gather(const TileParams& P, const int (&Q)[3], float (&gc)[3]) {
-    using F = PosFmt<PB>;
-    constexpr int W = F::kCoarseW;
-    const int64_t ncells = (int64_t)P.nc * P.nc * P.nc;
-    Cic1 cc[3];
-#pragma unroll
-    for (int e = 0; e < 3; ++e) {
-        const int sc = 2 * Q[e] + 1 - F::kBins;     // units 1/(2B) of a coarse cell (< 2^28)
-        cc[e].i0 = (int)(sc >> F::kCoarseWBits);
-        cc[e].w1 = (int)(sc & (W - 1));
-    }
-    int ix[2], iy[2], iz[2];
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        ix[k] = wrap1(cc[0].i0 + k, P.nc);
-        iy[k] = wrap1(cc[1].i0 + k, P.nc);
-        iz[k] = wrap1(cc[2].i0 + k, P.nc);
-    }
-    gc[0] = gc[1] = gc[2] = 0.f;
-    // nc <= 1024 (config limit), so node indices fit in 32 bits
-    const float* Fe[3] = {P.Fl, P.Fl + ncells, P.Fl + 2 * ncells};
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
-        const int node = ix[dx] + P.nc * (iy[dy] + P.nc * iz[dz]);
-        const float w = PB == 1
-            ? (float)((dx ? cc[0].w1 : W - cc[0].w1) * (dy ? cc[1].w1 : W - cc[1].w1)) *
-                  (float)(dz ? cc[2].w1 : W - cc[2].w1)
-            : (float)cic_weight3<PB>(dx ? cc[0].w1 : W - cc[0].w1, dy ? cc[1].w1 : W - cc[1].w1,
-                                     dz ? cc[2].w1 : W - cc[2].w1);
-#pragma unroll
-        for (int e = 0; e < 3; ++e) gc[e] += w * Fe[e][node];
-    }
-#pragma unroll
-    for (int e = 0; e < 3; ++e) gc[e] *= 7.450580596923828e-09f;   // 2^-27
-}
-
 // --- phase 1: integer CIC of the tile and its 2-coarse-cell halo ------------
 // Particles in coarse cells [c0 - 2, c1 + 2) can reach the mesh nodes
 // [-6, T + 5]; their contributions outside the 32^3 box are clipped.
@@ -254,7 +215,13 @@ constexpr int kHaloDim = kTileMaxCoarse + 4;                  // 9
 constexpr int kHaloMax = kHaloDim * kHaloDim * kHaloDim;       // 729
 constexpr int kOwnDim = kTileMaxCoarse;                       // 5
 constexpr int kOwnMax = kOwnDim * kOwnDim * kOwnDim;           // 125
-constexpr int kMapCap = 32768;    // particles whose cell is looked up by table
+// The long-range force on the 7^3 coarse nodes the tile's own particles
+// gather from (own cells [c0, c1) reach nodes [c0 - 1, c1]) is staged in
+// shared memory by the prologue, behind the map, which gives up that room.
+constexpr int kFlWin = kTileMaxCoarse + 2;                           // 7
+constexpr int kFlWinNodes = kFlWin * kFlWin * kFlWin;                // 343
+constexpr int kFlWinEntries = (3 * kFlWinNodes * 4 + 15) / 16 * 8;   // in map entries (4128 B)
+constexpr int kMapCap = 32768 - kFlWinEntries;   // particles whose cell is looked up by table
 constexpr int kPMapCap = 8192;
 constexpr int kHaloChunks = (kHaloMax + 31) / 32;               // 23
 
@@ -279,7 +246,7 @@ PMPM_HD TileCells tile_cells(float2* W, int* O) {
     c.cnt = reinterpret_cast<int*>(c.st + kHaloMax);
     c.pre = c.cnt + kHaloMax;
     c.map = reinterpret_cast<uint16_t*>(c.pre + kHaloMax + 1 + 1);
-    c.pmap = reinterpret_cast<uint8_t*>(c.map + kMapCap);
+    c.pmap = reinterpret_cast<uint8_t*>(c.map + kMapCap + kFlWinEntries);
     c.ppre = O;
     c.prel = O + 126;
     c.misc = O + 126 + 125;
@@ -288,8 +255,43 @@ PMPM_HD TileCells tile_cells(float2* W, int* O) {
     c.cmax = c.tot + 32;
     return c;
 }
-static_assert(kHaloMax * 8 + (2 * kHaloMax + 2) * 4 + kMapCap * 2 + kPMapCap + 64 * 4 <= kTileW * 8,
+static_assert(kHaloMax * 8 + (2 * kHaloMax + 2) * 4 + (kMapCap + kFlWinEntries) * 2 + kPMapCap + 64 * 4 <=
+                  kTileW * 8,
               "tile cell tables must fit in W");
+
+// the staged F_l window, [3][kFlWin^3], x fastest (derived, holds no register)
+PMPM_HD float* fl_window(const TileCells& c) { return reinterpret_cast<float*>(c.map + kMapCap); }
+
+// Coarse-mesh force (all three components) at one of the tile's own
+// particles from the staged window: the same nodes, weights and order of
+// accumulation as a gather from global memory
+template <int PB>
+PMPM_HD void coarse_gather_win(const float* flw, const TileGeom& g, const int (&Q)[3], float (&gc)[3]) {
+    using F = PosFmt<PB>;
+    constexpr int W = F::kCoarseW;
+    Cic1 cc[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        const int sc = 2 * Q[e] + 1 - F::kBins;     // units 1/(2B) of a coarse cell (< 2^28)
+        cc[e].i0 = (int)(sc >> F::kCoarseWBits) - (g.c0[e] - 1);   // window node, 0..5
+        cc[e].w1 = (int)(sc & (W - 1));
+    }
+    gc[0] = gc[1] = gc[2] = 0.f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
+        const int node = (cc[0].i0 + dx) + kFlWin * ((cc[1].i0 + dy) + kFlWin * (cc[2].i0 + dz));
+        const float w = PB == 1
+            ? (float)((dx ? cc[0].w1 : W - cc[0].w1) * (dy ? cc[1].w1 : W - cc[1].w1)) *
+                  (float)(dz ? cc[2].w1 : W - cc[2].w1)
+            : (float)cic_weight3<PB>(dx ? cc[0].w1 : W - cc[0].w1, dy ? cc[1].w1 : W - cc[1].w1,
+                                     dz ? cc[2].w1 : W - cc[2].w1);
+#pragma unroll
+        for (int e = 0; e < 3; ++e) gc[e] += w * flw[e * kFlWinNodes + node];
+    }
+#pragma unroll
+    for (int e = 0; e < 3; ++e) gc[e] *= 7.450580596923828e-09f;   // 2^-27
+}
 static_assert(kHaloChunks <= 32, "one lane per halo chunk");
 
 PMPM_HD float bits_to_f32(int v) {
@@ -337,6 +339,24 @@ PMPM_HD void tile_prologue(int tid, const TileGeom& g, const TileParams& P, Tile
             cnt[u] = P.counts[cell];
         }
     }
+    // the F_l window (three values per thread at most)
+    constexpr int kWinPer = (3 * kFlWinNodes + kTileThreads - 1) / kTileThreads;
+    float fw[kWinPer];
+    {
+        const int64_t ncells = (int64_t)P.nc * P.nc * P.nc;
+#pragma unroll
+        for (int k = 0; k < kWinPer; ++k) {
+            const int i = tid + k * kTileThreads;
+            fw[k] = 0.f;
+            if (i < 3 * kFlWinNodes) {
+                const int e = i / kFlWinNodes, w = i % kFlWinNodes;
+                const int x = wrap1(g.c0[0] - 1 + w % kFlWin, P.nc);
+                const int y = wrap1(g.c0[1] - 1 + (w / kFlWin) % kFlWin, P.nc);
+                const int z = wrap1(g.c0[2] - 1 + w / (kFlWin * kFlWin), P.nc);
+                fw[k] = P.Fl[e * ncells + x + P.nc * (y + P.nc * z)];
+            }
+        }
+    }
     float gv[(kGreenPacked + kTileThreads - 1) / kTileThreads];
 #pragma unroll
     for (int u = 0; u < (kGreenPacked + kTileThreads - 1) / kTileThreads; ++u) {
@@ -368,6 +388,12 @@ PMPM_HD void tile_prologue(int tid, const TileGeom& g, const TileParams& P, Tile
         if (i < kGreenPacked) gS[i] = gv[u];
     }
     if (tid < 256) c.Td[tid] = td;
+    float* flw = fl_window(c);
+#pragma unroll
+    for (int k = 0; k < kWinPer; ++k) {
+        const int i = tid + k * kTileThreads;
+        if (i < 3 * kFlWinNodes) flw[i] = fw[k];
+    }
     if (tid == 0) {
         c.misc[4] = f32_to_bits(sc[0]);
         c.misc[5] = f32_to_bits(sc[1]);
@@ -630,7 +656,7 @@ PMPM_HD void tile_deposit_flat(int tid, const TileGeom& g, const TileParams& P, 
         for (int u = 0; u < kGatherIlp; ++u) {
             if (j[u] < 0) continue;
             float gc[3];
-            coarse_gather<PB>(P, Q[u], gc);
+            coarse_gather_win<PB>(fl_window(c), g, Q[u], gc);
             if (LM) {
                 const int v = v0 + u * kTileThreads;
                 if (v >= kLowmemCap) {
