@@ -16,6 +16,7 @@ time.  --impl reference times the FP64 oracle on the host cores instead.
 """
 
 import os
+import re
 
 # separate hardware queues for the serving engine's per-box streams; must be
 # set before the CUDA context exists
@@ -77,11 +78,19 @@ def fp32_peak_tflops(sm_mhz):
     return SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
 
 
+def _code_only(text):
+    """C/C++ source without comments and blank space: what the compiler sees."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def source_hash(paths):
+    """Hash of the kernel sources' code (comment edits do not change it)."""
     h = hashlib.sha256()
     for p in paths:
-        with open(os.path.join(ROOT, p), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, p), encoding="utf-8") as f:
+            h.update(_code_only(f.read()).encode())
     return h.hexdigest()[:16]
 
 

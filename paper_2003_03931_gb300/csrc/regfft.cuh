@@ -1,6 +1,7 @@
-// regfft.cuh -- small FFTs held in one thread's registers (16 and 32 points),
-// and the real-to-complex / complex-to-real wrappers built on them.  Used by
-// the tile fine-mesh solver (Sec. II: F_s = IDFT(rho~ K~_s), Eq. 1).
+// regfft.cuh -- small FFTs held in one thread's registers (8, 16 and 32
+// points), and the real-to-complex / complex-to-real wrappers built on them.
+// Used by the tile fine-mesh solver (Sec. II: F_s = IDFT(rho~ K~_s), Eq. 1)
+// and by the two-step passes of the coarse-mesh transforms.
 //
 // Twiddles exp(-+2 pi i j / 32) are written as exact symmetric constants; all
 // loops have compile-time bounds so every twiddle index folds to a constant.

@@ -15,14 +15,17 @@
 //      the kx = 16 (Nyquist) plane folded into the imaginary part of kx = 0;
 //   W  22 x 32 x 16 complex = 88 KB: one force component on its way back,
 //      pruned to the 22 output planes that are needed (during the deposit it
-//      holds the table of the halo box's cells);
+//      holds the table of the halo box's cells and the coarse force on the
+//      7^3 coarse nodes around the tile);
 //   G  the short-range Green table, 15 x 153 floats (9 KB): S(a, b, c) is
 //      symmetric in (b, c), so only b <= c is kept, and it vanishes for own-
 //      axis |k| = 0 and 16, so those rows are not stored;
 //   O  the tile's own-cell table (prefix counts and storage offsets), built
 //      during the deposit and used by every interpolation phase, a few
 //      per-tile scalars, and the velocity decode table T of Eq. 3 (2 KB).
-// Index swizzles (x ^ y) make every pencil pass free of bank conflicts.
+// Index swizzles (x ^ y) make every pencil pass free of bank conflicts.  The
+// transforms are the register FFTs of regfft.cuh (decimation in time with
+// fused multiply-add butterflies).
 //
 // Each phase is a per-thread function; the kernel calls them with a block
 // barrier between phases.
