@@ -119,7 +119,8 @@ __device__ __forceinline__ void tile_body(int tile, const TileParams& P,
     PMPM_MARK(19);
 }
 
-// One CTA per SM (the tile needs 231 KB of shared memory): one CTA per tile.
+// One CTA per tile; one fits an SM at a time (the tile needs 232 KB of shared
+// memory).
 // PB: bytes per position bin.
 template <int PB>
 __global__ void __launch_bounds__(kTileThreads, 1) k_tile(TileParams P) {
