@@ -1,0 +1,348 @@
+// Host checks of the tile kernel's index arithmetic (tile_core.cuh, built for
+// the host): the shared-memory swizzles, the tiling of the coarse mesh, the
+// own-cell and halo-cell maps, the carving of shared memory into the cell
+// tables, and the prologue's staging of the halo table and of the
+// long-range force window, which the interpolation then reads.  Nothing here
+// needs a GPU.  Prints one line per check: "<name> <cases> <failures> [<max
+// error>]".
+#include "../../paper_2003_03931_gb300/csrc/tile_core.cuh"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+using namespace pmpm;
+
+static unsigned long long rng_state = 0x2545F4914F6CDD1Dull;
+static unsigned long long next_u64() {
+    rng_state ^= rng_state << 13;
+    rng_state ^= rng_state >> 7;
+    rng_state ^= rng_state << 17;
+    return rng_state;
+}
+static int pmod(long long a, long long n) { return (int)(((a % n) + n) % n); }
+
+// Every index map is a bijection onto its array, and 32 consecutive words
+// (16 consecutive float2) along the axes the pencil passes walk fall in
+// distinct banks.
+static void check_swizzles() {
+    long long n = 0, bad = 0;
+    std::vector<int> hit(2 * kTileR);
+    auto bijective = [&](int range, auto f, int nx, int ny, int nz) {
+        std::fill(hit.begin(), hit.end(), 0);
+        for (int z = 0; z < nz; ++z)
+            for (int y = 0; y < ny; ++y)
+                for (int x = 0; x < nx; ++x) {
+                    const int i = f(x, y, z);
+                    ++n;
+                    if (i < 0 || i >= range) ++bad;
+                    else ++hit[i];
+                }
+        for (int i = 0; i < range; ++i) bad += hit[i] != 1;
+    };
+    bijective(kTileR, [](int x, int y, int z) { return ridx(x, y, z); }, 32, 32, 32);
+    bijective(kTileR / 2, [](int x, int y, int z) { return cidx(x, y, z); }, 16, 32, 32);
+    bijective(kTileW, [](int x, int y, int z) { return widx(x, y, z); }, 16, 32, kTileOut);
+    bijective(2 * kTileW, [](int x, int y, int z) { return wfidx(x, y, z); }, 32, 32, kTileOut);
+    // the float view addresses the same pair as the complex view
+    for (int zo = 0; zo < kTileOut; ++zo)
+        for (int yo = 0; yo < 32; ++yo)
+            for (int xo = 0; xo < 32; ++xo, ++n)
+                bad += wfidx(xo, yo, zo) != 2 * widx(xo >> 1, yo, zo) + (xo & 1);
+    // banks: word maps mod 32 along x and y, float2 maps mod 16 along kx and
+    // along each half of ky
+    auto distinct = [&](int mod, auto idx, int len) {
+        unsigned long long seen = 0;
+        for (int t = 0; t < len; ++t) seen |= 1ull << (idx(t) % mod);
+        ++n;
+        bad += __builtin_popcountll(seen) != len;
+    };
+    for (int z = 0; z < 32; ++z)
+        for (int a = 0; a < 32; ++a) {
+            distinct(32, [&](int t) { return ridx(t, a, z); }, 32);
+            distinct(32, [&](int t) { return ridx(a, t, z); }, 32);
+        }
+    for (int z = 0; z < 32; ++z)
+        for (int a = 0; a < 32; ++a) {
+            distinct(16, [&](int t) { return cidx(t, a, z); }, 16);
+            if (a < 16)
+                for (int h = 0; h < 2; ++h) {
+                    distinct(16, [&](int t) { return cidx(a, 16 * h + t, z); }, 16);
+                    if (z < kTileOut) distinct(16, [&](int t) { return widx(a, 16 * h + t, z); }, 16);
+                }
+        }
+    printf("swizzles %lld %lld\n", n, bad);
+}
+
+// Every allowed mesh (nc a power of two from 8 to 1024, tiles of at most 4
+// or 5 cells): the tiles partition each axis into runs of 4 or 5 cells; a
+// tile's halo box (two cells each side) never holds a cell twice; the tile
+// and its buffer fit the FFT box; each coarse cell belongs to one tile.
+static void check_tiling() {
+    long long n = 0, bad = 0;
+    for (int nc = 8; nc <= 1024; nc *= 2)
+        for (int tm = 4; tm <= 5; ++tm) {
+            const int nt = tile_count(nc, tm);
+            ++n;
+            bad += (long long)nt * nt * nt > 2147483647ll;   // grid.x limit
+            bad += tile_bound(0, nc, nt) != 0 || tile_bound(nt, nc, nt) != nc;
+            for (int t = 0; t < nt; ++t) {
+                const int s = tile_bound(t + 1, nc, nt) - tile_bound(t, nc, nt);
+                ++n;
+                bad += s < 4 || s > kTileMaxCoarse || s + 4 > nc || kRatio * s + 2 * kBuffer > kTileFFT ||
+                       kRatio * s + 2 > kTileOut;
+            }
+            if (nc > 64) continue;
+            std::vector<int> owner(nc * nc * nc, 0);
+            for (int b = 0; b < nt * nt * nt; ++b) {
+                const TileGeom g = tile_geom(b, nc, nt);
+                for (int z = g.c0[2]; z < g.c1[2]; ++z)
+                    for (int y = g.c0[1]; y < g.c1[1]; ++y)
+                        for (int x = g.c0[0]; x < g.c1[0]; ++x) ++owner[x + nc * (y + nc * z)];
+                for (int d = 0; d < 3; ++d) {
+                    ++n;
+                    bad += g.T[d] != kRatio * (g.c1[d] - g.c0[d]) || g.o[d] != kRatio * g.c0[d] - kBuffer;
+                }
+            }
+            for (int c : owner) {
+                ++n;
+                bad += c != 1;
+            }
+        }
+    printf("tiling %lld %lld\n", n, bad);
+}
+
+// The 32^3 box's circular convolution equals the linear one on the output
+// nodes [-1, T] for any density on the box's nodes [-6, T + 5] and a kernel
+// that vanishes beyond 5 nodes per axis: no pair aliases into the support.
+static void check_no_alias() {
+    long long n = 0, bad = 0;
+    for (int T = 16; T <= 20; T += 4)
+        for (int y = kBuffer - 1; y <= kBuffer + T; ++y)
+            for (int x = 0; x < T + 2 * kBuffer; ++x) {
+                int c = pmod(y - x, kTileFFT);
+                if (c >= kTileFFT / 2) c -= kTileFFT;
+                ++n;
+                if (std::abs(c) <= kBuffer - 1) bad += c != y - x;
+            }
+    printf("no_alias %lld %lld\n", n, bad);
+}
+
+// Own cells: for each tile shape, own_valid accepts exactly the tile's cells
+// and own_to_halo sends them to distinct halo cells two cells in from the
+// halo box's corner.
+static void check_own_cells() {
+    long long n = 0, bad = 0;
+    for (int sz = 4; sz <= 5; ++sz)
+        for (int sy = 4; sy <= 5; ++sy)
+            for (int sx = 4; sx <= 5; ++sx) {
+                TileGeom g{};
+                g.c0[0] = 8; g.c1[0] = 8 + sx;
+                g.c0[1] = 4; g.c1[1] = 4 + sy;
+                g.c0[2] = 0; g.c1[2] = sz;
+                std::vector<int> seen(kHaloMax, 0);
+                int valid = 0;
+                for (int p = 0; p < kOwnMax; ++p) {
+                    const int px = p % kOwnDim, py = (p / kOwnDim) % kOwnDim, pz = p / (kOwnDim * kOwnDim);
+                    const bool inside = px < sx && py < sy && pz < sz;
+                    ++n;
+                    bad += own_valid(g, p) != inside;
+                    if (!inside) continue;
+                    ++valid;
+                    const int h = own_to_halo(p);
+                    if (h < 0 || h >= kHaloMax) { ++bad; continue; }
+                    const int hx = h % kHaloDim, hy = (h / kHaloDim) % kHaloDim, hz = h / (kHaloDim * kHaloDim);
+                    bad += hx != px + 2 || hy != py + 2 || hz != pz + 2 || seen[h]++ != 0;
+                    // inside the halo box that the prologue fills (sides s + 4)
+                    bad += hx >= sx + 4 || hy >= sy + 4 || hz >= sz + 4;
+                }
+                bad += valid != sx * sy * sz;
+            }
+    printf("own_cells %lld %lld\n", n, bad);
+}
+
+// The carving of shared memory: R, W, the Green table, the own-cell table and
+// the decode table end at kTileSmemBytes (at most 227 KB per CTA); inside W
+// the cell tables, the map, the long-range window, the own-particle map and
+// the chunk sums neither overlap nor leave W, each aligned for its type.
+static void check_smem_layout() {
+    long long n = 0, bad = 0;
+    std::vector<unsigned char> smem(kTileSmemBytes + 64);
+    unsigned char* base = smem.data();
+    float2* W = reinterpret_cast<float2*>(base + (size_t)kTileR * 4);
+    float* gS = reinterpret_cast<float*>(base + (size_t)kTileR * 4 + (size_t)kTileW * 8);
+    int* O = reinterpret_cast<int*>(gS + kGreenPacked);
+    const TileCells c = tile_cells(W, O);
+    const float* flw = fl_window(c);
+    struct Region { const char* name; const void* p; size_t bytes; size_t align; };
+    const Region w[] = {
+        {"st", c.st, kHaloMax * 8, 8},
+        {"cnt", c.cnt, kHaloMax * 4, 4},
+        {"pre", c.pre, (kHaloMax + 1) * 4, 4},
+        {"map", c.map, (size_t)kMapCap * 2, 2},
+        {"flw", flw, 3 * kFlWinNodes * 4, 4},
+        {"pmap", c.pmap, kPMapCap, 1},
+        {"tot", c.tot, kHaloChunks * 4, 4},
+        {"cmax", c.cmax, kHaloChunks * 4, 4},
+    };
+    const Region o[] = {
+        {"ppre", c.ppre, (kOwnMax + 1) * 4, 4},
+        {"prel", c.prel, kOwnMax * 4, 4},
+        {"misc", c.misc, 8 * 4, 4},
+        {"Td", c.Td, 256 * 4, 4},
+    };
+    auto inside = [&](const Region* r, int k, const unsigned char* lo, const unsigned char* hi) {
+        for (int i = 0; i < k; ++i) {
+            const unsigned char* p = static_cast<const unsigned char*>(r[i].p);
+            ++n;
+            bad += p < lo || p + r[i].bytes > hi || ((size_t)(p - base) % r[i].align) != 0;
+            for (int j = 0; j < i; ++j) {
+                const unsigned char* q = static_cast<const unsigned char*>(r[j].p);
+                ++n;
+                bad += p < q + r[j].bytes && q < p + r[i].bytes;
+            }
+        }
+    };
+    inside(w, 8, reinterpret_cast<unsigned char*>(W), reinterpret_cast<unsigned char*>(W + kTileW));
+    inside(o, 4, reinterpret_cast<unsigned char*>(O), base + kTileSmemBytes);
+    ++n;
+    bad += reinterpret_cast<unsigned char*>(c.Td + 256) != base + kTileSmemBytes;
+    ++n;
+    bad += kTileSmemBytes > 227u * 1024u;
+    // the float2 spectrum view of R and the uint4 clear stay inside R
+    ++n;
+    bad += (size_t)kTileR * 4 % 16 != 0 || (size_t)(kTileR / 2) * 8 != (size_t)kTileR * 4;
+    printf("smem_layout %lld %lld\n", n, bad);
+}
+
+// The prologue, run for all 512 threads of one tile on host arrays: the halo
+// table holds the offsets and counts of the wrapped cells around the tile
+// (zero count outside a smaller tile's box), and the staged window gives, for
+// particles anywhere in the tile's own cells, the same long-range force as a
+// plain periodic CIC gather from the whole coarse mesh.
+template <int PB>
+static void check_prologue(long long& n, long long& bad, double& err, int nc, int tm) {
+    using F = PosFmt<PB>;
+    const int nt = tile_count(nc, tm);
+    const int64_t nc3 = (int64_t)nc * nc * nc;
+    std::vector<int32_t> counts(nc3);
+    std::vector<int64_t> offsets(nc3 + 1);
+    std::vector<float> Fl(3 * nc3), green(kGreenPacked), Td(256);
+    for (int64_t i = 0; i < nc3; ++i) {
+        counts[i] = (int32_t)(1 + i % 13);
+        offsets[i] = 7 * i + 3;
+    }
+    float fmax = 0.f;
+    for (auto& v : Fl) {
+        v = (float)((double)(next_u64() >> 11) * 0x1p-53 * 2.0 - 1.0);
+        fmax = std::fmax(fmax, std::fabs(v));
+    }
+    for (int i = 0; i < kGreenPacked; ++i) green[i] = (float)i;
+    for (int i = 0; i < 256; ++i) Td[i] = (float)(i - 128);
+    const float sigma = 0.25f;
+    TileParams P{};
+    P.nc = nc;
+    P.nt = nt;
+    P.counts = counts.data();
+    P.offsets = offsets.data();
+    P.Fl = Fl.data();
+    P.green = green.data();
+    P.Tdec = Td.data();
+    P.sigma = &sigma;
+    P.mode = 0;
+    constexpr size_t kGuard = 256;
+    std::vector<unsigned char> smem(kTileSmemBytes + kGuard);
+    unsigned char* base = smem.data();
+    uint32_t* R = reinterpret_cast<uint32_t*>(base);
+    float2* W = reinterpret_cast<float2*>(base + (size_t)kTileR * 4);
+    float* gS = reinterpret_cast<float*>(base + (size_t)kTileR * 4 + (size_t)kTileW * 8);
+    int* O = reinterpret_cast<int*>(gS + kGreenPacked);
+    const int ntiles = nt * nt * nt;
+    for (int b = 0; b < ntiles; b += 1 + ntiles / 40) {
+        memset(base, 0xA5, smem.size());
+        const TileGeom g = tile_geom(b, nc, nt);
+        const TileCells c = tile_cells(W, O);
+        for (int t = 0; t < kTileThreads; ++t) tile_prologue(t, g, P, c, R, gS);
+        for (size_t i = kTileSmemBytes; i < smem.size(); ++i) {
+            ++n;
+            bad += base[i] != 0xA5;   // nothing written past the end
+        }
+        // halo table
+        const int hx = g.c1[0] - g.c0[0] + 4, hy = g.c1[1] - g.c0[1] + 4, hz = g.c1[2] - g.c0[2] + 4;
+        for (int h = 0; h < kHaloMax; ++h) {
+            const int bx = h % kHaloDim, by = (h / kHaloDim) % kHaloDim, bz = h / (kHaloDim * kHaloDim);
+            ++n;
+            if (bx < hx && by < hy && bz < hz) {
+                const int64_t cell = pmod(g.c0[0] - 2 + bx, nc) +
+                                     (int64_t)nc * (pmod(g.c0[1] - 2 + by, nc) + (int64_t)nc * pmod(g.c0[2] - 2 + bz, nc));
+                bad += c.st[h] != offsets[cell] || c.cnt[h] != counts[cell];
+            } else {
+                bad += c.cnt[h] != 0;
+            }
+        }
+        for (int i = 0; i < kGreenPacked; ++i) bad += gS[i] != green[i];
+        for (int i = 0; i < 256; ++i) bad += c.Td[i] != Td[i];
+        for (int i = 0; i < kTileR; ++i) bad += R[i] != 0u;
+        n += kGreenPacked + 256 + kTileR;
+        // the window against a plain periodic gather, at random particles of
+        // the own cells and at the extreme codes of the first and last cells
+        const float* flw = fl_window(c);
+        for (int k = 0; k < 400; ++k) {
+            int Q[3];
+            for (int e = 0; e < 3; ++e) {
+                const int s = g.c1[e] - g.c0[e];
+                int cell = g.c0[e] + (int)(next_u64() % s), m = (int)(next_u64() % F::kBins);
+                if (k < 8) {
+                    cell = (k >> e) & 1 ? g.c1[e] - 1 : g.c0[e];
+                    m = (k >> e) & 1 ? F::kBins - 1 : 0;
+                }
+                Q[e] = cell * F::kBins + m;
+            }
+            float gc[3];
+            coarse_gather_win<PB>(flw, g, Q, gc);
+            int i0[3];
+            double f[3];
+            for (int e = 0; e < 3; ++e) {
+                const double d = ((double)Q[e] + 0.5) / F::kBins - 0.5;   // from node 0, in cells
+                i0[e] = (int)std::floor(d);
+                f[e] = d - i0[e];
+            }
+            for (int e = 0; e < 3; ++e) {
+                double ref = 0.0;
+                for (int cn = 0; cn < 8; ++cn) {
+                    const int dx = cn & 1, dy = (cn >> 1) & 1, dz = cn >> 2;
+                    const double w = (dx ? f[0] : 1 - f[0]) * (dy ? f[1] : 1 - f[1]) * (dz ? f[2] : 1 - f[2]);
+                    const int64_t node = pmod(i0[0] + dx, nc) +
+                                         (int64_t)nc * (pmod(i0[1] + dy, nc) + (int64_t)nc * pmod(i0[2] + dz, nc));
+                    ref += w * Fl[e * nc3 + node];
+                }
+                const double d = std::fabs((double)gc[e] - ref) / fmax;
+                ++n;
+                if (!(d <= 2e-6)) ++bad;
+                if (d > err || d != d) err = d;
+            }
+        }
+    }
+}
+
+static void run_prologue_checks() {
+    long long n = 0, bad = 0;
+    double err = 0.0;
+    for (int nc = 8; nc <= 64; nc *= 2)
+        for (int tm = 4; tm <= 5; ++tm) {
+            check_prologue<1>(n, bad, err, nc, tm);
+            check_prologue<2>(n, bad, err, nc, tm);
+        }
+    printf("prologue %lld %lld %.3e\n", n, bad, err);
+}
+
+int main() {
+    check_swizzles();
+    check_tiling();
+    check_no_alias();
+    check_own_cells();
+    check_smem_layout();
+    run_prologue_checks();
+    return 0;
+}

@@ -1,7 +1,14 @@
-"""The device arithmetic helpers that compile for the host too (fixed-point
-rounding of the cell sums and the dispersion, the 2-byte weight rounding,
-the register FFTs) against their plain definitions, in a small host program
-built with nvcc (no GPU needed)."""
+"""Device code that compiles for the host too, checked without a GPU in small
+host programs built with nvcc:
+
+- the arithmetic helpers (fixed-point rounding of the cell sums and the
+  dispersion, the 2-byte weight rounding, the register FFTs) against their
+  plain definitions (host/arith_check.cu);
+- the tile kernel's index arithmetic (shared-memory swizzles, the tiling of
+  the coarse mesh, own and halo cells, the carving of shared memory) and its
+  prologue run thread by thread on host arrays: the staged halo table and
+  long-range force window against a plain periodic CIC gather
+  (host/tile_layout_check.cu)."""
 
 import os
 import shutil
@@ -12,21 +19,30 @@ import pytest
 HERE = os.path.dirname(os.path.abspath(__file__))
 
 
-@pytest.fixture(scope="module")
-def results(tmp_path_factory):
+def _run_host_check(tmp_path_factory, name):
     nvcc = shutil.which("nvcc") or ("/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else None)
     if nvcc is None:
         pytest.skip("nvcc not found")
-    exe = str(tmp_path_factory.mktemp("arith") / "arith_check")
+    exe = str(tmp_path_factory.mktemp(name) / name)
     subprocess.run([nvcc, "-O2", "-std=c++17", "--expt-relaxed-constexpr", "-x", "cu",
                     "-gencode", "arch=compute_103a,code=sm_103a",
-                    os.path.join(HERE, "host", "arith_check.cu"), "-o", exe], check=True)
+                    os.path.join(HERE, "host", name + ".cu"), "-o", exe], check=True)
     out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout
     res = {}
     for line in out.splitlines():
-        name, cases, fails, *rest = line.split()
-        res[name] = (int(cases), int(fails), float(rest[0]) if rest else 0.0)
+        key, cases, fails, *rest = line.split()
+        res[key] = (int(cases), int(fails), float(rest[0]) if rest else 0.0)
     return res
+
+
+@pytest.fixture(scope="module")
+def results(tmp_path_factory):
+    return _run_host_check(tmp_path_factory, "arith_check")
+
+
+@pytest.fixture(scope="module")
+def layout(tmp_path_factory):
+    return _run_host_check(tmp_path_factory, "tile_layout_check")
 
 
 @pytest.mark.parametrize("name", ["fix24", "sq_fix32", "round_half_even"])
@@ -39,3 +55,15 @@ def test_integer_rounding_matches_definition(results, name):
 def test_register_ffts_match_the_dft(results, name):
     _, _, err = results[name]
     assert err < 1e-6, err
+
+
+@pytest.mark.parametrize("name", ["swizzles", "tiling", "no_alias", "own_cells", "smem_layout"])
+def test_tile_index_arithmetic(layout, name):
+    cases, fails, _ = layout[name]
+    assert cases > 0 and fails == 0, (cases, fails)
+
+
+def test_tile_prologue_stages_halo_and_force_window(layout):
+    # float32 CIC gather of values in [-1, 1] against the float64 gather
+    cases, fails, err = layout["prologue"]
+    assert cases > 1_000_000 and fails == 0 and err < 2e-6, (cases, fails, err)
