@@ -1,9 +1,10 @@
 // Host checks of the tile kernel's index arithmetic (tile_core.cuh, built for
 // the host): the shared-memory swizzles, the tiling of the coarse mesh, the
 // own-cell and halo-cell maps, the carving of shared memory into the cell
-// tables, and the prologue's staging of the halo table and of the
-// long-range force window, which the interpolation then reads.  Nothing here
-// needs a GPU.  Prints one line per check: "<name> <cases> <failures> [<max
+// tables, the prologue's staging of the halo table and of the long-range
+// force window, and the deposit phases (cell prefix sums, particle maps,
+// integer CIC, parked long-range force) against a plain deposit and gather
+// of a clustered box.  Nothing here needs a GPU.  Prints one line per check: "<name> <cases> <failures> [<max
 // error>]".
 #include "../../paper_2003_03931_gb300/csrc/tile_core.cuh"
 
@@ -337,6 +338,181 @@ static void run_prologue_checks() {
     printf("prologue %lld %lld %.3e\n", n, bad, err);
 }
 
+// A clustered periodic box (cell-ordered store, counts, offsets) for the
+// deposit check: a few particles in every cell, a crowded block of cells
+// around one tile (more halo particles than the cell map holds, more own
+// particles than the own-particle map holds) and one cell above 255 particles
+// (the checked deposit path).
+template <int PB>
+struct Box {
+    int nc;
+    int64_t n = 0;
+    std::vector<int32_t> counts;
+    std::vector<int64_t> offsets;
+    std::vector<uint16_t> m[3];   // bins, PB bytes used
+    std::vector<uint8_t> s[3];    // the same bins as PB-byte streams
+    Box(int nc_, int crowd_x, int crowd_y, int crowd_z) : nc(nc_) {
+        const int64_t nc3 = (int64_t)nc * nc * nc;
+        counts.resize(nc3);
+        offsets.resize(nc3 + 1);
+        for (int z = 0; z < nc; ++z)
+            for (int y = 0; y < nc; ++y)
+                for (int x = 0; x < nc; ++x) {
+                    int k = (int)(next_u64() % 5);
+                    if (std::abs(x - crowd_x) <= 4 && std::abs(y - crowd_y) <= 4 && std::abs(z - crowd_z) <= 4)
+                        k = 130 + (int)(next_u64() % 9);
+                    if (x == crowd_x + 1 && y == crowd_y && z == crowd_z) k = 400;
+                    counts[x + (int64_t)nc * (y + (int64_t)nc * z)] = k;
+                }
+        for (int64_t i = 0; i < nc3; ++i) {
+            offsets[i] = n;
+            n += counts[i];
+        }
+        offsets[nc3] = n;
+        for (int e = 0; e < 3; ++e) {
+            m[e].resize(n);
+            for (int64_t j = 0; j < n; ++j) m[e][j] = (uint16_t)(next_u64() % PosFmt<PB>::kBins);
+            s[e].resize(n * PB);
+            for (int64_t j = 0; j < n; ++j) memcpy(&s[e][j * PB], &m[e][j], PB);   // little endian
+        }
+    }
+};
+
+// 3-D CIC weight in units of 2^-21 from per-axis weights in units of 1/(2U)
+// of a fine cell (U position codes per fine cell): exact for 1-byte codes,
+// rounded half to even from the exact product for 2-byte codes
+template <int PB>
+static uint32_t weight_ref(uint64_t wx, uint64_t wy, uint64_t wz) {
+    const uint64_t prod = wx * wy * wz;
+    if (PB == 1) return (uint32_t)prod;
+    const uint64_t unit = 1ull << 24, q = prod / unit, r = prod % unit;
+    return (uint32_t)(r * 2 > unit || (r * 2 == unit && (q & 1)) ? q + 1 : q);
+}
+
+// Phases 1a-1c of the tile kernel run thread by thread on host arrays: the
+// fine density in shared memory equals a plain integer CIC deposit of every
+// particle of the 5^3-cell halo box, clipped to the 32^3 box, node by node;
+// every own particle's long-range force slot holds the plain periodic gather.
+template <int PB>
+static void check_deposit(long long& n, long long& bad, double& err) {
+    using F = PosFmt<PB>;
+    const int nc = 32, tm = 5, nt = tile_count(nc, tm);
+    const int crowd = 11;   // tile 2 spans cells 9..13 along each axis
+    Box<PB> box(nc, crowd, crowd, crowd);
+    const int64_t nc3 = (int64_t)nc * nc * nc;
+    std::vector<float> Fl(3 * nc3), green(kGreenPacked, 0.f), Td(256, 0.f);
+    for (auto& v : Fl) v = (float)((double)(next_u64() >> 11) * 0x1p-53 * 2.0 - 1.0);
+    std::vector<float> G(3 * box.n);
+    const float sigma = 1.f;
+    uint32_t errw = 0;
+    TileParams P{};
+    P.nc = nc;
+    P.nt = nt;
+    P.n = box.n;
+    P.counts = box.counts.data();
+    P.offsets = box.offsets.data();
+    P.m0 = box.s[0].data();
+    P.m1 = box.s[1].data();
+    P.m2 = box.s[2].data();
+    P.Fl = Fl.data();
+    P.green = green.data();
+    P.Tdec = Td.data();
+    P.sigma = &sigma;
+    P.mode = 0;
+    P.G = G.data();
+    P.err = &errw;
+    std::vector<unsigned char> smem(kTileSmemBytes);
+    unsigned char* base = smem.data();
+    uint32_t* R = reinterpret_cast<uint32_t*>(base);
+    float2* W = reinterpret_cast<float2*>(base + (size_t)kTileR * 4);
+    float* gS = reinterpret_cast<float*>(base + (size_t)kTileR * 4 + (size_t)kTileW * 8);
+    int* O = reinterpret_cast<int*>(gS + kGreenPacked);
+    // the crowded tile, a neighbour, a ragged tile and the corner tile (wrap)
+    const int tiles[4][3] = {{2, 2, 2}, {3, 2, 2}, {1, 4, 6}, {nt - 1, 0, nt - 1}};
+    for (const auto& tt : tiles) {
+        const int b = tt[0] + nt * (tt[1] + nt * tt[2]);
+        const TileGeom g = tile_geom(b, nc, nt);
+        const TileCells c = tile_cells(W, O);
+        std::fill(G.begin(), G.end(), NAN);
+        for (int t = 0; t < kTileThreads; ++t) tile_prologue(t, g, P, c, R, gS);
+        for (int t = 0; t < kTileThreads; ++t) tile_cells_scan(t, g, c);
+        for (int t = 0; t < kTileThreads; ++t) tile_cells_map(t, g, c);
+        for (int t = 0; t < kTileThreads; ++t)
+            tile_deposit_flat<false, PB>(t, g, P, R, c, CtaScratch{nullptr, nullptr});
+        // plain deposit of the halo box's particles
+        std::vector<uint32_t> ref(kTileR, 0u);
+        int64_t halo_particles = 0, own_particles = 0;
+        for (int hz = g.c0[2] - 2; hz < g.c1[2] + 2; ++hz)
+            for (int hy = g.c0[1] - 2; hy < g.c1[1] + 2; ++hy)
+                for (int hx = g.c0[0] - 2; hx < g.c1[0] + 2; ++hx) {
+                    const int64_t cell = pmod(hx, nc) + (int64_t)nc * (pmod(hy, nc) + (int64_t)nc * pmod(hz, nc));
+                    const bool own = hx >= g.c0[0] && hx < g.c1[0] && hy >= g.c0[1] && hy < g.c1[1] &&
+                                     hz >= g.c0[2] && hz < g.c1[2];
+                    const int hc[3] = {hx, hy, hz};
+                    for (int64_t j = box.offsets[cell]; j < box.offsets[cell + 1]; ++j) {
+                        ++halo_particles;
+                        // fine position (unwrapped, in fine cells) of the bin
+                        // centre, and its offset from box node 0's centre
+                        int lo[3];
+                        uint64_t w1[3];
+                        for (int e = 0; e < 3; ++e) {
+                            const double x = ((double)hc[e] * F::kBins + box.m[e][j] + 0.5) / F::kCodesPerFine;
+                            const double d = x - 0.5 - g.o[e];
+                            lo[e] = (int)std::floor(d);
+                            w1[e] = (uint64_t)((d - lo[e]) * F::kFineW);   // exact
+                        }
+                        for (int cn = 0; cn < 8; ++cn) {
+                            const int dx = cn & 1, dy = (cn >> 1) & 1, dz = cn >> 2;
+                            const int x = lo[0] + dx, y = lo[1] + dy, z = lo[2] + dz;
+                            if (x < 0 || x >= 32 || y < 0 || y >= 32 || z < 0 || z >= 32) continue;
+                            ref[(z * 32 + y) * 32 + x] +=
+                                weight_ref<PB>(dx ? w1[0] : F::kFineW - w1[0], dy ? w1[1] : F::kFineW - w1[1],
+                                               dz ? w1[2] : F::kFineW - w1[2]);
+                        }
+                        if (!own) continue;
+                        ++own_particles;
+                        // its parked long-range force against a plain gather
+                        int i0[3];
+                        double f[3];
+                        for (int e = 0; e < 3; ++e) {
+                            const double d = ((double)hc[e] * F::kBins + box.m[e][j] + 0.5) / F::kBins - 0.5;
+                            i0[e] = (int)std::floor(d);
+                            f[e] = d - i0[e];
+                        }
+                        for (int e = 0; e < 3; ++e) {
+                            double r = 0.0;
+                            for (int cn = 0; cn < 8; ++cn) {
+                                const int dx = cn & 1, dy = (cn >> 1) & 1, dz = cn >> 2;
+                                const double w = (dx ? f[0] : 1 - f[0]) * (dy ? f[1] : 1 - f[1]) * (dz ? f[2] : 1 - f[2]);
+                                r += w * Fl[e * nc3 + pmod(i0[0] + dx, nc) +
+                                            (int64_t)nc * (pmod(i0[1] + dy, nc) + (int64_t)nc * pmod(i0[2] + dz, nc))];
+                            }
+                            const double d = std::fabs((double)G[e * box.n + j] - r);
+                            ++n;
+                            if (!(d <= 2e-6)) ++bad;
+                            if (d > err || d != d) err = d;
+                        }
+                    }
+                }
+        for (int z = 0; z < 32; ++z)
+            for (int y = 0; y < 32; ++y)
+                for (int x = 0; x < 32; ++x) {
+                    ++n;
+                    bad += R[ridx(x, y, z)] != ref[(z * 32 + y) * 32 + x];
+                }
+        // the crowded tile must take the paths past both maps and the
+        // checked deposit
+        ++n;
+        bad += c.pre[kHaloMax] != halo_particles || c.ppre[kOwnMax] != own_particles;
+        if (tt[0] == 2 && tt[1] == 2 && tt[2] == 2) {
+            ++n;
+            bad += !(halo_particles > kMapCap && own_particles > kPMapCap && c.misc[2] > 255);
+        }
+    }
+    ++n;
+    bad += errw != 0u;
+}
+
 int main() {
     check_swizzles();
     check_tiling();
@@ -344,5 +520,12 @@ int main() {
     check_own_cells();
     check_smem_layout();
     run_prologue_checks();
+    {
+        long long n = 0, bad = 0;
+        double err = 0.0;
+        check_deposit<1>(n, bad, err);
+        check_deposit<2>(n, bad, err);
+        printf("deposit %lld %lld %.3e\n", n, bad, err);
+    }
     return 0;
 }

@@ -6,9 +6,10 @@ host programs built with nvcc:
   plain definitions (host/arith_check.cu);
 - the tile kernel's index arithmetic (shared-memory swizzles, the tiling of
   the coarse mesh, own and halo cells, the carving of shared memory) and its
-  prologue run thread by thread on host arrays: the staged halo table and
-  long-range force window against a plain periodic CIC gather
-  (host/tile_layout_check.cu)."""
+  prologue and deposit phases run thread by thread on host arrays: the staged
+  halo table and long-range force window against a plain periodic CIC
+  gather, the fine density bit for bit against a plain integer CIC deposit
+  of a clustered box (host/tile_layout_check.cu)."""
 
 import os
 import shutil
@@ -67,3 +68,10 @@ def test_tile_prologue_stages_halo_and_force_window(layout):
     # float32 CIC gather of values in [-1, 1] against the float64 gather
     cases, fails, err = layout["prologue"]
     assert cases > 1_000_000 and fails == 0 and err < 2e-6, (cases, fails, err)
+
+
+def test_tile_deposit_matches_plain_cic(layout):
+    # fine density bit-exact (1- and 2-byte positions, crowded cells past
+    # both particle maps); parked long-range force within float32 rounding
+    cases, fails, err = layout["deposit"]
+    assert cases > 100_000 and fails == 0 and err < 2e-6, (cases, fails, err)
