@@ -2,13 +2,16 @@
 // the host): the shared-memory swizzles, the tiling of the coarse mesh, the
 // own-cell and halo-cell maps, the carving of shared memory into the cell
 // tables, the prologue's staging of the halo table and of the long-range
-// force window, and the deposit phases (cell prefix sums, particle maps,
-// integer CIC, parked long-range force) against a plain deposit and gather
-// of a clustered box.  Nothing here needs a GPU.  Prints one line per check: "<name> <cases> <failures> [<max
+// force window, the deposit phases (cell prefix sums, particle maps, integer
+// CIC, parked long-range force) against a plain deposit and gather of a
+// clustered box, and the transform phases (forward x, y, z, Green multiply
+// with the packed table, pruned inverse z, y, x) against a plain DFT
+// convolution.  Nothing here needs a GPU.  Prints one line per check: "<name> <cases> <failures> [<max
 // error>]".
 #include "../../paper_2003_03931_gb300/csrc/tile_core.cuh"
 
 #include <cmath>
+#include <complex>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -513,6 +516,114 @@ static void check_deposit(long long& n, long long& bad, double& err) {
     bad += errw != 0u;
 }
 
+// A short-range table S(a; b, c) for the spectral check: any values serve
+// (the transforms are linear in them); symmetric in the pair (b, c) as the
+// packed table requires, and unlike in a and the pair.
+static double s_table(int a, int b, int c) {
+    return (1.0 + 0.3 * a - 0.02 * a * a) / (1.0 + 0.05 * (b * b + c * c) + 0.013 * b * c + 0.11 * a * (b + c));
+}
+
+// Phases 2-5c of the tile kernel (forward real x, complex y, z, then per
+// force component the Green multiply with the packed table and the pruned
+// inverse z, y, x) run thread by thread on a random density, against a plain
+// float64 DFT convolution on the output nodes: F_d = 2 IDFT(K_d DFT(rho))
+// (the factor 2 is the forward x transform's doubling, and the inverse
+// transforms carry no 1/32), K_d(k) = -i sgn(k_d) S(|k_d|; |k_e|, |k_f|),
+// zero where |k_d| is 0 or 16.  Output node o of an axis is box node
+// o + 5 (fine node -1 of the tile).
+static void check_spectral() {
+    long long n = 0, bad = 0;
+    double err = 0.0;
+    std::vector<unsigned char> smem(kTileSmemBytes);
+    unsigned char* base = smem.data();
+    uint32_t* R = reinterpret_cast<uint32_t*>(base);
+    float2* C = reinterpret_cast<float2*>(base);
+    float2* W = reinterpret_cast<float2*>(base + (size_t)kTileR * 4);
+    float* gS = reinterpret_cast<float*>(base + (size_t)kTileR * 4 + (size_t)kTileW * 8);
+    // the packed table: rows a = 1..15, each the pairs b <= c in order
+    // (row b holds c = b..16)
+    {
+        int i = 0;
+        for (int a = 1; a <= 15; ++a)
+            for (int b = 0; b <= 16; ++b)
+                for (int c = b; c <= 16; ++c) gS[i++] = (float)s_table(a, b, c);
+        ++n;
+        bad += i != kGreenPacked;
+    }
+    typedef std::complex<double> cd;
+    std::vector<cd> tw(32);
+    for (int j = 0; j < 32; ++j) tw[j] = std::polar(1.0, -2.0 * M_PI * j / 32.0);
+    // separable 32^3 DFT along one axis, sign -1 (forward) or +1
+    auto dft_axis = [&](std::vector<cd>& a, int axis, int sign) {
+        std::vector<cd> line(32);
+        const int st = axis == 0 ? 1 : (axis == 1 ? 32 : 1024);
+        for (int u = 0; u < 32; ++u)
+            for (int v = 0; v < 32; ++v) {
+                const int b0 = axis == 0 ? 32 * u + 1024 * v : (axis == 1 ? u + 1024 * v : u + 32 * v);
+                for (int k = 0; k < 32; ++k) {
+                    cd acc = 0.0;
+                    for (int x = 0; x < 32; ++x) {
+                        const cd w = tw[(k * x) & 31];
+                        acc += a[b0 + st * x] * (sign < 0 ? w : std::conj(w));
+                    }
+                    line[k] = acc;
+                }
+                for (int k = 0; k < 32; ++k) a[b0 + st * k] = line[k];
+            }
+    };
+    auto kabs = [](int k) { return k <= 16 ? k : 32 - k; };
+    const int shapes[2][3] = {{0, 1, 2}, {1, 0, 6}};   // tiles (4,5,4) and (5,4,5) cells of nc = 32
+    for (const auto& sh : shapes) {
+        const int nc = 32, nt = tile_count(nc, 5);
+        const TileGeom g = tile_geom(sh[0] + nt * (sh[1] + nt * sh[2]), nc, nt);
+        std::vector<cd> rho(kTileR);
+        for (int z = 0; z < 32; ++z)
+            for (int y = 0; y < 32; ++y)
+                for (int x = 0; x < 32; ++x) {
+                    const uint32_t v = (uint32_t)(next_u64() % (1u << 22));
+                    R[ridx(x, y, z)] = v;
+                    rho[(z * 32 + y) * 32 + x] = (double)v;
+                }
+        for (int ax = 0; ax < 3; ++ax) dft_axis(rho, ax, -1);
+        for (int t = 0; t < kTileThreads; ++t) tile_fwd_x(t, R);
+        for (int t = 0; t < kTileThreads; ++t) tile_fwd_y(t, C);
+        for (int t = 0; t < kTileThreads; ++t) tile_fwd_z_inv_z0(t, g, gS, C, W);
+        for (int D = 0; D < 3; ++D) {
+            if (D == 1)
+                for (int t = 0; t < kTileThreads; ++t) tile_inv_z<1>(t, g, gS, C, W);
+            if (D == 2)
+                for (int t = 0; t < kTileThreads; ++t) tile_inv_z<2>(t, g, gS, C, W);
+            for (int t = 0; t < kTileThreads; ++t) tile_inv_y(t, g, W);
+            for (int t = 0; t < kTileThreads; ++t) tile_inv_x(t, g, W);
+            std::vector<cd> f(kTileR);
+            for (int kz = 0; kz < 32; ++kz)
+                for (int ky = 0; ky < 32; ++ky)
+                    for (int kx = 0; kx < 32; ++kx) {
+                        const int k[3] = {kx, ky, kz};
+                        const int a = kabs(k[D]), b = kabs(k[(D + 1) % 3]), c = kabs(k[(D + 2) % 3]);
+                        const double sg = k[D] == 0 || k[D] == 16 ? 0.0 : (k[D] < 16 ? 1.0 : -1.0);
+                        const double S = sg == 0.0 ? 0.0 : s_table(a, b < c ? b : c, b < c ? c : b);
+                        const int i = (kz * 32 + ky) * 32 + kx;
+                        f[i] = cd(0.0, -sg * S) * rho[i];
+                    }
+            for (int ax = 0; ax < 3; ++ax) dft_axis(f, ax, +1);
+            const float* Wf = reinterpret_cast<const float*>(W);
+            double fmax = 0.0;
+            for (const cd& v : f) fmax = std::fmax(fmax, std::abs(v.real()));
+            for (int zo = 0; zo < g.T[2] + 2; ++zo)
+                for (int yo = 0; yo < g.T[1] + 2; ++yo)
+                    for (int xo = 0; xo < g.T[0] + 2; ++xo) {
+                        const cd ref = 2.0 * f[((zo + 5) * 32 + yo + 5) * 32 + xo + 5];
+                        const double d = std::fabs((double)Wf[wfidx(xo, yo, zo)] - ref.real()) / (2.0 * fmax);
+                        ++n;
+                        if (!(d <= 1e-5)) ++bad;
+                        if (d > err || d != d) err = d;
+                    }
+        }
+    }
+    printf("spectral %lld %lld %.3e\n", n, bad, err);
+}
+
 int main() {
     check_swizzles();
     check_tiling();
@@ -527,5 +638,6 @@ int main() {
         check_deposit<2>(n, bad, err);
         printf("deposit %lld %lld %.3e\n", n, bad, err);
     }
+    check_spectral();
     return 0;
 }

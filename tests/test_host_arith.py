@@ -9,7 +9,8 @@ host programs built with nvcc:
   prologue and deposit phases run thread by thread on host arrays: the staged
   halo table and long-range force window against a plain periodic CIC
   gather, the fine density bit for bit against a plain integer CIC deposit
-  of a clustered box (host/tile_layout_check.cu)."""
+  of a clustered box, and the force on the output nodes against a plain
+  float64 DFT convolution with a packed symmetric table (host/tile_check.cu)."""
 
 import os
 import shutil
@@ -43,7 +44,7 @@ def results(tmp_path_factory):
 
 @pytest.fixture(scope="module")
 def layout(tmp_path_factory):
-    return _run_host_check(tmp_path_factory, "tile_layout_check")
+    return _run_host_check(tmp_path_factory, "tile_check")
 
 
 @pytest.mark.parametrize("name", ["fix24", "sq_fix32", "round_half_even"])
@@ -75,3 +76,11 @@ def test_tile_deposit_matches_plain_cic(layout):
     # both particle maps); parked long-range force within float32 rounding
     cases, fails, err = layout["deposit"]
     assert cases > 100_000 and fails == 0 and err < 2e-6, (cases, fails, err)
+
+
+def test_tile_transforms_match_dft_convolution(layout):
+    # forward transforms, packed Green multiply (including the kx = 0 / 16
+    # pencil) and pruned inverse transforms, three force components, tiles of
+    # 16 and 20 fine cells; error relative to the largest force value
+    cases, fails, err = layout["spectral"]
+    assert cases > 40_000 and fails == 0 and err < 1e-5, (cases, fails, err)
