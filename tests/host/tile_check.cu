@@ -6,7 +6,9 @@
 // CIC, parked long-range force) against a plain deposit and gather of a
 // clustered box, and the transform phases (forward x, y, z, Green multiply
 // with the packed table, pruned inverse z, y, x) against a plain DFT
-// convolution.  Nothing here needs a GPU.  Prints one line per check: "<name> <cases> <failures> [<max
+// convolution, and the interpolation with kick, drift and the fused
+// new-cell histogram against a plain gather and the Eq. 3 decode.  Nothing
+// here needs a GPU.  Prints one line per check: "<name> <cases> <failures> [<max
 // error>]".
 #include "../../paper_2003_03931_gb300/csrc/tile_core.cuh"
 
@@ -624,6 +626,182 @@ static void check_spectral() {
     printf("spectral %lld %lld %.3e\n", n, bad, err);
 }
 
+// Phase 5d (interpolation) run thread by thread after the deposit phases,
+// with W holding a random force field on the output nodes [0, T + 2) of
+// each axis and NaN everywhere else (a read outside the pruned output would
+// show).  Mode 0: each own particle's slot holds half the plain CIC gather
+// of the field (the transforms leave the field doubled) plus its parked
+// long-range force.  Mode 1: the momentum is the Eq. 3 decode plus the kick
+// times that force, the new code is the old one plus the rounded drift,
+// wrapped into the box, and the fused histogram's counts and momentum sums
+// match the tile's new codes and momenta.
+template <int D, int PB>
+static void run_interp(const TileGeom& g, const TileParams& P, const float2* W, TileCells c) {
+    unsigned long long lo = 0, hi = 0;
+    for (int t = 0; t < kTileThreads; ++t)
+        tile_interp<D, false, PB>(t, g, P, W, c, CtaScratch{nullptr, nullptr}, lo, hi);
+}
+
+template <int PB>
+static void check_interp(long long& n, long long& bad, double& err, int mode) {
+    using F = PosFmt<PB>;
+    const int nc = 32, nt = tile_count(nc, 5);
+    Box<PB> box(nc, 11, 11, 11);
+    const int64_t nc3 = (int64_t)nc * nc * nc, np = box.n;
+    std::vector<float> Fl(3 * nc3), green(kGreenPacked, 0.f), Td(256), vc(3 * nc3);
+    for (auto& v : Fl) v = (float)((double)(next_u64() >> 11) * 0x1p-53 * 2.0 - 1.0);
+    for (auto& v : vc) v = (float)((double)(next_u64() >> 11) * 0x1p-53 * 40.0 - 20.0);
+    for (int i = 0; i < 256; ++i) Td[i] = (float)(std::tan(M_PI * ((i + 0.5) / 256.0 - 0.5)) * 0.25);
+    std::vector<uint8_t> u[3];
+    for (int e = 0; e < 3; ++e) {
+        u[e].resize(np);
+        for (auto& x : u[e]) x = (uint8_t)(next_u64() & 255);
+    }
+    std::vector<float> G(3 * np), Pn(3 * np);
+    std::vector<int32_t> Qn(3 * np), cnew(nc3);
+    std::vector<unsigned long long> S(3 * nc3);
+    const float sigma = 2.0f, kd[2] = {0.75f, 3.3f};
+    uint32_t errw = 0;
+    TileParams P{};
+    P.nc = nc;
+    P.nt = nt;
+    P.n = np;
+    P.counts = box.counts.data();
+    P.offsets = box.offsets.data();
+    P.m0 = box.s[0].data();
+    P.m1 = box.s[1].data();
+    P.m2 = box.s[2].data();
+    P.u0 = u[0].data();
+    P.u1 = u[1].data();
+    P.u2 = u[2].data();
+    P.vc = vc.data();
+    P.sigma = &sigma;
+    P.Tdec = Td.data();
+    P.green = green.data();
+    P.Fl = Fl.data();
+    P.mode = mode;
+    P.kd = kd;
+    P.G = G.data();
+    P.Qn = Qn.data();
+    P.Pn = Pn.data();
+    P.err = &errw;
+    if (mode == 1) {
+        P.counts_new = cnew.data();
+        P.S = S.data();
+    }
+    std::vector<unsigned char> smem(kTileSmemBytes);
+    unsigned char* base = smem.data();
+    uint32_t* R = reinterpret_cast<uint32_t*>(base);
+    float2* W = reinterpret_cast<float2*>(base + (size_t)kTileR * 4);
+    float* Wf = reinterpret_cast<float*>(W);
+    float* gS = reinterpret_cast<float*>(base + (size_t)kTileR * 4 + (size_t)kTileW * 8);
+    int* O = reinterpret_cast<int*>(gS + kGreenPacked);
+    float* slot = mode == 0 ? G.data() : Pn.data();
+    const int M = nc * F::kBins;
+    const int tiles[3][3] = {{2, 2, 2}, {1, 4, 6}, {nt - 1, 0, nt - 1}};
+    for (const auto& tt : tiles) {
+        const TileGeom g = tile_geom(tt[0] + nt * (tt[1] + nt * tt[2]), nc, nt);
+        const TileCells c = tile_cells(W, O);
+        std::fill(cnew.begin(), cnew.end(), 0);
+        std::fill(S.begin(), S.end(), 0ull);
+        for (int t = 0; t < kTileThreads; ++t) tile_prologue(t, g, P, c, R, gS);
+        for (int t = 0; t < kTileThreads; ++t) tile_cells_scan(t, g, c);
+        for (int t = 0; t < kTileThreads; ++t) tile_cells_map(t, g, c);
+        for (int t = 0; t < kTileThreads; ++t)
+            tile_deposit_flat<false, PB>(t, g, P, R, c, CtaScratch{nullptr, nullptr});
+        // the tile's own particles and their cells
+        std::vector<int64_t> own;
+        std::vector<int> ocell;
+        for (int z = g.c0[2]; z < g.c1[2]; ++z)
+            for (int y = g.c0[1]; y < g.c1[1]; ++y)
+                for (int x = g.c0[0]; x < g.c1[0]; ++x) {
+                    const int cell = x + nc * (y + nc * z);
+                    for (int64_t j = box.offsets[cell]; j < box.offsets[cell + 1]; ++j) {
+                        own.push_back(j);
+                        ocell.push_back(cell);
+                    }
+                }
+        std::vector<float> field(32 * 32 * 32);
+        for (int D = 0; D < 3; ++D) {
+            std::fill(Wf, Wf + 2 * kTileW, NAN);
+            for (int zo = 0; zo < g.T[2] + 2; ++zo)
+                for (int yo = 0; yo < g.T[1] + 2; ++yo)
+                    for (int xo = 0; xo < g.T[0] + 2; ++xo) {
+                        const float v = (float)((double)(next_u64() >> 11) * 0x1p-53 * 2e3 - 1e3);
+                        field[(zo * 32 + yo) * 32 + xo] = v;
+                        Wf[wfidx(xo, yo, zo)] = v;
+                    }
+            std::vector<float> parked(own.size());
+            for (size_t i = 0; i < own.size(); ++i) parked[i] = slot[D * np + own[i]];
+            if (D == 0) run_interp<0, PB>(g, P, W, c);
+            if (D == 1) run_interp<1, PB>(g, P, W, c);
+            if (D == 2) run_interp<2, PB>(g, P, W, c);
+            for (size_t i = 0; i < own.size(); ++i) {
+                const int64_t j = own[i];
+                const int cc[3] = {ocell[i] % nc, (ocell[i] / nc) % nc, ocell[i] / (nc * nc)};
+                // fine position of the bin centre from output node 0 (fine
+                // node -1 of the tile, centre at fine 4 c0 - 0.5)
+                int lo[3], q[3];
+                double f[3];
+                for (int e = 0; e < 3; ++e) {
+                    q[e] = cc[e] * F::kBins + box.m[e][j];
+                    const double d = ((double)q[e] + 0.5) / F::kCodesPerFine - (kRatio * g.c0[e] - 0.5);
+                    lo[e] = (int)std::floor(d);
+                    f[e] = d - lo[e];
+                }
+                double gf = 0.0;
+                for (int cn = 0; cn < 8; ++cn) {
+                    const int dx = cn & 1, dy = (cn >> 1) & 1, dz = cn >> 2;
+                    const double w = (dx ? f[0] : 1 - f[0]) * (dy ? f[1] : 1 - f[1]) * (dz ? f[2] : 1 - f[2]);
+                    const int x = lo[0] + dx, y = lo[1] + dy, z = lo[2] + dz;
+                    gf += w * (x < 0 || y < 0 || z < 0 || x >= 32 || y >= 32 || z >= 32
+                                   ? NAN : (double)field[(z * 32 + y) * 32 + x]);
+                }
+                const double gref = 0.5 * gf + parked[i];
+                if (mode == 0) {
+                    const double d = std::fabs((double)G[D * np + j] - gref) / 1e3;
+                    ++n;
+                    if (!(d <= 1e-6)) ++bad;
+                    if (d > err || d != d) err = d;
+                    continue;
+                }
+                // mode 1: Eq. 3 decode, kick (float32 operations), drift
+                const float pv = vc[D * nc3 + ocell[i]] + sigma * Td[u[D][j]];
+                const double pref = (double)pv + (double)kd[0] * gref;
+                const float pn = Pn[D * np + j];
+                const double d = std::fabs((double)pn - pref) / 1e3;
+                ++n;
+                if (!(d <= 1e-6)) ++bad;
+                if (d > err || d != d) err = d;
+                // the new code from the kernel's own momentum: exact
+                const float xq = pn * kd[1];
+                const long long dq = (long long)std::floor((double)(xq + 0.5f));
+                const int qn = pmod((long long)q[D] + dq, M);
+                ++n;
+                bad += Qn[D * np + j] != qn;
+            }
+        }
+        if (mode == 1) {
+            // the fused histogram of the tile's particles in their new cells
+            std::vector<int32_t> cref(nc3, 0);
+            std::vector<unsigned long long> sref(3 * nc3, 0ull);
+            for (int64_t j : own) {
+                const int key = Qn[j] / F::kBins + nc * (Qn[np + j] / F::kBins + nc * (Qn[2 * np + j] / F::kBins));
+                ++cref[key];
+                for (int d = 0; d < 3; ++d)
+                    sref[d * nc3 + key] += (unsigned long long)std::llrint((double)Pn[d * np + j] * 16777216.0);
+            }
+            for (int64_t i = 0; i < nc3; ++i) {
+                ++n;
+                bad += cnew[i] != cref[i] || S[i] != sref[i] || S[nc3 + i] != sref[nc3 + i] ||
+                       S[2 * nc3 + i] != sref[2 * nc3 + i];
+            }
+        }
+    }
+    ++n;
+    bad += errw != 0u;
+}
+
 int main() {
     check_swizzles();
     check_tiling();
@@ -639,5 +817,12 @@ int main() {
         printf("deposit %lld %lld %.3e\n", n, bad, err);
     }
     check_spectral();
+    for (int mode = 0; mode <= 1; ++mode) {
+        long long n = 0, bad = 0;
+        double err = 0.0;
+        check_interp<1>(n, bad, err, mode);
+        check_interp<2>(n, bad, err, mode);
+        printf("interp_mode%d %lld %lld %.3e\n", mode, n, bad, err);
+    }
     return 0;
 }

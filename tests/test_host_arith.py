@@ -9,8 +9,10 @@ host programs built with nvcc:
   prologue and deposit phases run thread by thread on host arrays: the staged
   halo table and long-range force window against a plain periodic CIC
   gather, the fine density bit for bit against a plain integer CIC deposit
-  of a clustered box, and the force on the output nodes against a plain
-  float64 DFT convolution with a packed symmetric table (host/tile_check.cu)."""
+  of a clustered box, the force on the output nodes against a plain
+  float64 DFT convolution with a packed symmetric table, and the
+  interpolation, kick, drift and fused new-cell sums against a plain gather
+  (host/tile_check.cu)."""
 
 import os
 import shutil
@@ -84,3 +86,12 @@ def test_tile_transforms_match_dft_convolution(layout):
     # 16 and 20 fine cells; error relative to the largest force value
     cases, fails, err = layout["spectral"]
     assert cases > 40_000 and fails == 0 and err < 1e-5, (cases, fails, err)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_tile_interpolation_kick_drift(layout, mode):
+    # mode 0: gathered force; mode 1: kicked momentum, drifted code (exact)
+    # and the fused counts and momentum sums (exact); errors relative to the
+    # field scale
+    cases, fails, err = layout["interp_mode%d" % mode]
+    assert cases > 50_000 and fails == 0 and err < 1e-6, (cases, fails, err)
