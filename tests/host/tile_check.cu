@@ -6,12 +6,14 @@
 // CIC, parked long-range force) against a plain deposit and gather of a
 // clustered box, and the transform phases (forward x, y, z, Green multiply
 // with the packed table, pruned inverse z, y, x) against a plain DFT
-// convolution, and the interpolation with kick, drift and the fused
-// new-cell histogram against a plain gather and the Eq. 3 decode.  Nothing
-// here needs a GPU.  Prints one line per check: "<name> <cases> <failures> [<max
+// convolution, the interpolation with kick, drift and the fused new-cell
+// histogram against a plain gather and the Eq. 3 decode, and the
+// low-memory passes (counts, dispersion, scatter) against the default
+// pass.  Nothing here needs a GPU.  Prints one line per check: "<name> <cases> <failures> [<max
 // error>]".
 #include "../../paper_2003_03931_gb300/csrc/tile_core.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <complex>
 #include <cstdio>
@@ -802,6 +804,207 @@ static void check_interp(long long& n, long long& bad, double& err, int mode) {
     bad += errw != 0u;
 }
 
+// The low-memory passes (modes 2-4, one tile body each, own particles in a
+// CTA scratch slot instead of global arrays) against the default pass (mode
+// 1) of the same tile with the same force fields: mode 2's new-cell counts
+// and momentum sums equal mode 1's fused sums exactly; mode 3's 128-bit
+// dispersion sum equals the exact sum of round-half-even((p - v_c)^2 2^32)
+// over mode 1's momenta; mode 4 writes into each new cell's slots exactly
+// the records that mode 1's codes and momenta give (position byte, and the
+// Eq. 3 bin by the definition: the number of edges at or below t).
+template <int D, bool LM>
+static void run_interp_lm(const TileGeom& g, const TileParams& P, const float2* W, TileCells c,
+                          CtaScratch cs, unsigned long long& lo, unsigned long long& hi) {
+    for (int t = 0; t < kTileThreads; ++t) tile_interp<D, LM, 1>(t, g, P, W, c, cs, lo, hi);
+}
+
+static void check_lowmem(long long& n, long long& bad) {
+    const int nc = 32, nt = tile_count(nc, 5);
+    Box<1> box(nc, 20, 4, 27);
+    const int64_t nc3 = (int64_t)nc * nc * nc, np = box.n;
+    std::vector<float> Fl(3 * nc3), green(kGreenPacked, 0.f), Td(256), vc(3 * nc3), vcn(3 * nc3), E(256);
+    for (auto& v : Fl) v = (float)((double)(next_u64() >> 11) * 0x1p-53 * 2.0 - 1.0);
+    for (auto& v : vc) v = (float)((double)(next_u64() >> 11) * 0x1p-53 * 40.0 - 20.0);
+    // new cell means far from the momenta: the dispersion sum passes 2^64
+    // (the 128-bit carry is exercised), and a wide sigma_new keeps the Eq. 3
+    // bins spread
+    for (auto& v : vcn) v = (float)((double)(next_u64() >> 11) * 0x1p-53 * 4000.0 - 2000.0);
+    for (int i = 0; i < 256; ++i) Td[i] = (float)(std::tan(M_PI * ((i + 0.5) / 256.0 - 0.5)) * 0.25);
+    E[0] = -INFINITY;
+    for (int k = 1; k < 256; ++k) E[k] = (float)std::tan(M_PI * (k / 256.0 - 0.5));
+    std::vector<uint8_t> u[3];
+    for (int e = 0; e < 3; ++e) {
+        u[e].resize(np);
+        for (auto& x : u[e]) x = (uint8_t)(next_u64() & 255);
+    }
+    std::vector<float> Pn(3 * np), sp(3 * kLowmemCap);
+    std::vector<int32_t> Qn(3 * np), sq(2 * kLowmemCap), cnew(nc3), cnew2(nc3), fill(nc3);
+    std::vector<int64_t> offn(nc3 + 1);
+    std::vector<unsigned long long> S(3 * nc3), S2(3 * nc3);
+    std::vector<uint8_t> out(6 * np);
+    const float sigma = 2.0f, sigma_new = 300.0f, kd[2] = {0.75f, 3.3f};
+    uint32_t errw = 0;
+    TileParams P{};
+    P.nc = nc;
+    P.nt = nt;
+    P.n = np;
+    P.counts = box.counts.data();
+    P.offsets = box.offsets.data();
+    P.m0 = box.s[0].data();
+    P.m1 = box.s[1].data();
+    P.m2 = box.s[2].data();
+    P.u0 = u[0].data();
+    P.u1 = u[1].data();
+    P.u2 = u[2].data();
+    P.vc = vc.data();
+    P.sigma = &sigma;
+    P.Tdec = Td.data();
+    P.green = green.data();
+    P.Fl = Fl.data();
+    P.kd = kd;
+    P.Qn = Qn.data();
+    P.Pn = Pn.data();
+    P.err = &errw;
+    P.vc_new = vcn.data();
+    P.offsets_new = offn.data();
+    P.fill = fill.data();
+    P.sigma_new = &sigma_new;
+    P.E = E.data();
+    P.out = out.data();
+    std::vector<unsigned char> smem(kTileSmemBytes);
+    unsigned char* base = smem.data();
+    uint32_t* R = reinterpret_cast<uint32_t*>(base);
+    float2* W = reinterpret_cast<float2*>(base + (size_t)kTileR * 4);
+    float* Wf = reinterpret_cast<float*>(W);
+    float* gS = reinterpret_cast<float*>(base + (size_t)kTileR * 4 + (size_t)kTileW * 8);
+    int* O = reinterpret_cast<int*>(gS + kGreenPacked);
+    const CtaScratch cs{sp.data(), sq.data()};
+    // one tile body in the given mode, the force fields drawn from seed
+    auto run = [&](const TileGeom& g, int mode, unsigned long long seed, unsigned long long& lo,
+                   unsigned long long& hi) {
+        P.mode = mode;
+        const bool lm = mode >= 2;
+        const TileCells c = tile_cells(W, O);
+        for (int t = 0; t < kTileThreads; ++t) tile_prologue(t, g, P, c, R, gS);
+        for (int t = 0; t < kTileThreads; ++t) tile_cells_scan(t, g, c);
+        for (int t = 0; t < kTileThreads; ++t) tile_cells_map(t, g, c);
+        for (int t = 0; t < kTileThreads; ++t) {
+            if (lm) tile_deposit_flat<true, 1>(t, g, P, R, c, cs);
+            else tile_deposit_flat<false, 1>(t, g, P, R, c, cs);
+        }
+        const unsigned long long saved = rng_state;
+        rng_state = seed;
+        for (int D = 0; D < 3; ++D) {
+            std::fill(Wf, Wf + 2 * kTileW, NAN);
+            for (int zo = 0; zo < g.T[2] + 2; ++zo)
+                for (int yo = 0; yo < g.T[1] + 2; ++yo)
+                    for (int xo = 0; xo < g.T[0] + 2; ++xo)
+                        Wf[wfidx(xo, yo, zo)] = (float)((double)(next_u64() >> 11) * 0x1p-53 * 2e3 - 1e3);
+            if (D == 0) lm ? run_interp_lm<0, true>(g, P, W, c, cs, lo, hi) : run_interp_lm<0, false>(g, P, W, c, cs, lo, hi);
+            if (D == 1) lm ? run_interp_lm<1, true>(g, P, W, c, cs, lo, hi) : run_interp_lm<1, false>(g, P, W, c, cs, lo, hi);
+            if (D == 2) lm ? run_interp_lm<2, true>(g, P, W, c, cs, lo, hi) : run_interp_lm<2, false>(g, P, W, c, cs, lo, hi);
+        }
+        rng_state = saved;
+    };
+    const int tiles[3][3] = {{4, 0, 5}, {0, 3, 1}, {nt - 1, nt - 1, 0}};
+    for (const auto& tt : tiles) {
+        const TileGeom g = tile_geom(tt[0] + nt * (tt[1] + nt * tt[2]), nc, nt);
+        const unsigned long long seed = next_u64() | 1ull;
+        unsigned long long lo = 0, hi = 0;
+        // default pass: new codes, momenta and fused sums
+        P.counts_new = cnew.data();
+        P.S = S.data();
+        std::fill(cnew.begin(), cnew.end(), 0);
+        std::fill(S.begin(), S.end(), 0ull);
+        run(g, 1, seed, lo, hi);
+        // mode 2: the same sums
+        P.counts_new = cnew2.data();
+        P.S = S2.data();
+        std::fill(cnew2.begin(), cnew2.end(), 0);
+        std::fill(S2.begin(), S2.end(), 0ull);
+        run(g, 2, seed, lo, hi);
+        for (int64_t i = 0; i < nc3; ++i) {
+            ++n;
+            bad += cnew2[i] != cnew[i] || S2[i] != S[i] || S2[nc3 + i] != S[nc3 + i] || S2[2 * nc3 + i] != S[2 * nc3 + i];
+        }
+        // the tile's own particles (mode 1 wrote their new codes and momenta)
+        std::vector<int64_t> own;
+        for (int z = g.c0[2]; z < g.c1[2]; ++z)
+            for (int y = g.c0[1]; y < g.c1[1]; ++y)
+                for (int x = g.c0[0]; x < g.c1[0]; ++x) {
+                    const int cell = x + nc * (y + nc * z);
+                    for (int64_t j = box.offsets[cell]; j < box.offsets[cell + 1]; ++j) own.push_back(j);
+                }
+        auto key_of = [&](int64_t j) {
+            return Qn[j] / 256 + nc * (Qn[np + j] / 256 + nc * (Qn[2 * np + j] / 256));
+        };
+        // mode 3: exact dispersion sum
+        unsigned __int128 ref = 0;
+        for (int64_t j : own)
+            for (int d = 0; d < 3; ++d) {
+                const float dev = Pn[d * np + j] - vcn[d * nc3 + key_of(j)];
+                int ex;
+                const double fr = std::frexp((double)dev, &ex);              // dev = fr 2^ex
+                const unsigned long long m = (unsigned long long)std::fabs(std::ldexp(fr, 24));   // 24-bit
+                const unsigned long long m2 = m * m;                         // dev^2 = m2 2^(2 ex - 48)
+                const int sh = 2 * ex - 48 + 32;
+                unsigned long long t;
+                if (sh >= 0) t = m2 << sh;
+                else if (-sh >= 64) t = 0;
+                else {
+                    const int r = -sh;
+                    const unsigned long long q = m2 >> r, rem = m2 - (q << r), half = 1ull << (r - 1);
+                    t = rem > half || (rem == half && (q & 1)) ? q + 1 : q;
+                }
+                ref += t;
+            }
+        lo = hi = 0;
+        run(g, 3, seed, lo, hi);
+        ++n;
+        bad += lo != (unsigned long long)ref || hi != (unsigned long long)(ref >> 64);
+        if (&tt == &tiles[0]) {   // the crowded tile's sum passes 2^64
+            ++n;
+            bad += hi == 0;
+        }
+        // mode 4: slots of each new cell, records against the definition
+        int64_t acc = 0;
+        for (int64_t i = 0; i < nc3; ++i) {
+            offn[i] = acc;
+            acc += cnew[i];
+        }
+        offn[nc3] = acc;
+        std::fill(fill.begin(), fill.end(), 0);
+        std::fill(out.begin(), out.end(), (uint8_t)0);
+        run(g, 4, seed, lo, hi);
+        std::vector<std::vector<unsigned long long>> want(nc3), got(nc3);
+        for (int64_t j : own) {
+            const int key = key_of(j);
+            unsigned long long rec = 0;
+            for (int d = 0; d < 3; ++d) rec = rec << 8 | (unsigned long long)(Qn[d * np + j] & 255);
+            for (int d = 0; d < 3; ++d) {
+                const float t = (Pn[d * np + j] - vcn[d * nc3 + key]) / sigma_new;
+                int ub = 0;
+                for (int k = 1; k < 256; ++k) ub += E[k] <= t;
+                rec = rec << 8 | (unsigned long long)ub;
+            }
+            want[key].push_back(rec);
+        }
+        for (int64_t i = 0; i < nc3; ++i) {
+            for (int64_t sl = offn[i]; sl < offn[i + 1]; ++sl) {
+                unsigned long long rec = 0;
+                for (int f = 0; f < 6; ++f) rec = rec << 8 | out[f * np + sl];
+                got[i].push_back(rec);
+            }
+            std::sort(want[i].begin(), want[i].end());
+            std::sort(got[i].begin(), got[i].end());
+            ++n;
+            bad += want[i] != got[i] || fill[i] != cnew[i];
+        }
+    }
+    ++n;
+    bad += errw != 0u;
+}
+
 int main() {
     check_swizzles();
     check_tiling();
@@ -823,6 +1026,11 @@ int main() {
         check_interp<1>(n, bad, err, mode);
         check_interp<2>(n, bad, err, mode);
         printf("interp_mode%d %lld %lld %.3e\n", mode, n, bad, err);
+    }
+    {
+        long long n = 0, bad = 0;
+        check_lowmem(n, bad);
+        printf("lowmem %lld %lld\n", n, bad);
     }
     return 0;
 }

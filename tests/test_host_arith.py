@@ -11,8 +11,8 @@ host programs built with nvcc:
   gather, the fine density bit for bit against a plain integer CIC deposit
   of a clustered box, the force on the output nodes against a plain
   float64 DFT convolution with a packed symmetric table, and the
-  interpolation, kick, drift and fused new-cell sums against a plain gather
-  (host/tile_check.cu)."""
+  interpolation, kick, drift and fused new-cell sums against a plain gather,
+  and the low-memory passes against the default pass (host/tile_check.cu)."""
 
 import os
 import shutil
@@ -95,3 +95,10 @@ def test_tile_interpolation_kick_drift(layout, mode):
     # field scale
     cases, fails, err = layout["interp_mode%d" % mode]
     assert cases > 50_000 and fails == 0 and err < 1e-6, (cases, fails, err)
+
+
+def test_tile_lowmem_passes_match_default_pass(layout):
+    # counts and momentum sums, the 128-bit dispersion sum (past 2^64) and the
+    # scattered records of every new cell, all exact
+    cases, fails, _ = layout["lowmem"]
+    assert cases > 100_000 and fails == 0, (cases, fails)
