@@ -349,7 +349,7 @@ static void run_prologue_checks() {
 // deposit check: a few particles in every cell, a crowded block of cells
 // around one tile (more halo particles than the cell map holds, more own
 // particles than the own-particle map holds) and one cell above 255 particles
-// (the checked deposit path).
+// (the checked deposit path); optionally an empty block of 9^3 cells.
 template <int PB>
 struct Box {
     int nc;
@@ -358,7 +358,7 @@ struct Box {
     std::vector<int64_t> offsets;
     std::vector<uint16_t> m[3];   // bins, PB bytes used
     std::vector<uint8_t> s[3];    // the same bins as PB-byte streams
-    Box(int nc_, int crowd_x, int crowd_y, int crowd_z) : nc(nc_) {
+    Box(int nc_, int crowd_x, int crowd_y, int crowd_z, int empty = -100) : nc(nc_) {
         const int64_t nc3 = (int64_t)nc * nc * nc;
         counts.resize(nc3);
         offsets.resize(nc3 + 1);
@@ -369,6 +369,7 @@ struct Box {
                     if (std::abs(x - crowd_x) <= 4 && std::abs(y - crowd_y) <= 4 && std::abs(z - crowd_z) <= 4)
                         k = 130 + (int)(next_u64() % 9);
                     if (x == crowd_x + 1 && y == crowd_y && z == crowd_z) k = 400;
+                    if (std::abs(x - empty) <= 4 && std::abs(y - empty) <= 4 && std::abs(z - empty) <= 4) k = 0;
                     counts[x + (int64_t)nc * (y + (int64_t)nc * z)] = k;
                 }
         for (int64_t i = 0; i < nc3; ++i) {
@@ -404,8 +405,8 @@ template <int PB>
 static void check_deposit(long long& n, long long& bad, double& err) {
     using F = PosFmt<PB>;
     const int nc = 32, tm = 5, nt = tile_count(nc, tm);
-    const int crowd = 11;   // tile 2 spans cells 9..13 along each axis
-    Box<PB> box(nc, crowd, crowd, crowd);
+    const int crowd = 11;   // tile 2 spans cells 9..12 along each axis
+    Box<PB> box(nc, crowd, crowd, crowd, 24);   // tile 5's halo box (cells 20..28) is empty
     const int64_t nc3 = (int64_t)nc * nc * nc;
     std::vector<float> Fl(3 * nc3), green(kGreenPacked, 0.f), Td(256, 0.f);
     for (auto& v : Fl) v = (float)((double)(next_u64() >> 11) * 0x1p-53 * 2.0 - 1.0);
@@ -434,8 +435,9 @@ static void check_deposit(long long& n, long long& bad, double& err) {
     float2* W = reinterpret_cast<float2*>(base + (size_t)kTileR * 4);
     float* gS = reinterpret_cast<float*>(base + (size_t)kTileR * 4 + (size_t)kTileW * 8);
     int* O = reinterpret_cast<int*>(gS + kGreenPacked);
-    // the crowded tile, a neighbour, a ragged tile and the corner tile (wrap)
-    const int tiles[4][3] = {{2, 2, 2}, {3, 2, 2}, {1, 4, 6}, {nt - 1, 0, nt - 1}};
+    // the crowded tile, a neighbour, a ragged tile, the corner tile (wrap)
+    // and a tile with no particle in its halo box
+    const int tiles[5][3] = {{2, 2, 2}, {3, 2, 2}, {1, 4, 6}, {nt - 1, 0, nt - 1}, {5, 5, 5}};
     for (const auto& tt : tiles) {
         const int b = tt[0] + nt * (tt[1] + nt * tt[2]);
         const TileGeom g = tile_geom(b, nc, nt);
@@ -514,6 +516,10 @@ static void check_deposit(long long& n, long long& bad, double& err) {
         if (tt[0] == 2 && tt[1] == 2 && tt[2] == 2) {
             ++n;
             bad += !(halo_particles > kMapCap && own_particles > kPMapCap && c.misc[2] > 255);
+        }
+        if (tt[0] == 5) {
+            ++n;
+            bad += halo_particles != 0;
         }
     }
     ++n;
