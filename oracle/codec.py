@@ -14,8 +14,8 @@ Conventions (readings of the paper, stated once here):
   mentions in Sec. III-A).  The global position code is ``Q = c * B + m`` and
   the decoded position is ``x = (Q + 1/2) * q`` with quantum ``q = 4 / B``
   fine cells (the bin centre of Eq. 2).
-* Eq. 3 leaves the nonlinear map ``f`` open ("similar to the inverse error
-  function"; the arctangent form is the one Sec. III-B.2 refers to).  Reading:
+* Eq. 3 leaves the nonlinear map ``f`` open (the paper likens it to an
+  inverse error function, and Sec. III-B.2 works with an arctangent form).  Reading:
   a Cauchy-quantile map of scale sigma.  Bin ``u`` of 256 covers the angle
   interval [pi(u/256 - 1/2), pi((u+1)/256 - 1/2)); its decoded value is the
   tangent of the bin-centre angle, ``T[u] = tan(pi((u + 1/2)/256 - 1/2))``;

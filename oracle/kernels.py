@@ -32,7 +32,7 @@ import functools
 
 import numpy as np
 
-R_CUT = 6  # fine cells; the tile buffer width of Sec. IV-A.2 ("2 x 6")
+R_CUT = 6  # fine cells; the tile buffer width of Sec. IV-A.2 (6 cells on each side)
 RATIO = 4  # coarse / fine cell size, Sec. II
 
 

@@ -1,5 +1,6 @@
-// coarse.cu -- long-range force on the coarse mesh (Sec. II: "F_l is usually
-// computed on a 4-times-coarser mesh"; Eq. 1 with K~_l).
+// coarse.cu -- long-range force on the coarse mesh (Sec. II: the long-range
+// part lives on a mesh four times coarser than the fine one; Eq. 1 with
+// K~_l).
 //
 //  1. integer CIC of all particles on the nc^3 coarse mesh (int64, units
 //     2^-27 per particle): one thread per cell sums its particles' weights on

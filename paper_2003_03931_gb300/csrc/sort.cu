@@ -1,6 +1,6 @@
-// sort.cu -- cell-ordered re-encode of the particles (Sec. III-A): "particles'
-// m^i must be stored in memory in a cell-ordered way", with the per-cell
-// counts and the cell-mean velocity v_c of Eq. 3.
+// sort.cu -- cell-ordered re-encode of the particles (Sec. III-A: the bins
+// m^i only locate a particle once the store is ordered by cell), with the
+// per-cell counts and the cell-mean velocity v_c of Eq. 3.
 //
 // Input: new codes Q [3][N] and momenta p [3][N] (float32), any order.
 //   hist    counts[c] and fixed-point momentum sums S[d][c] (int64, p rounded

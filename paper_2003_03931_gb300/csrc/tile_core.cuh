@@ -1,6 +1,7 @@
 // tile_core.cuh -- the fine-mesh (short-range) PM of one tile, Sec. II:
-// "F_s on each V_tile is computed by a fine-mesh PM on a slightly enlarged
-// volume (L/N_tile + 2 r_cutoff)^3".  One CTA of 512 threads owns one tile.
+// each tile's short-range force comes from a fine-mesh PM over the tile
+// grown by the cutoff radius on every side.  One CTA of 512 threads owns one
+// tile.
 //
 // Tile geometry.  A tile is a box of whole coarse cells, 4 or 5 per side
 // (T = 16 or 20 fine cells).  Its FFT box is 32^3 fine nodes starting at

@@ -1,5 +1,7 @@
 """Pins of the oracle's Zel'dovich initial conditions and power spectrum."""
 
+import os
+
 import numpy as np
 
 from oracle import cic, codec, ic, power
@@ -20,6 +22,18 @@ def test_splitmix64_vectorised_matches_integer_arithmetic():
         got = ic.splitmix64(seed, j)
         for a, b in zip(got, j):
             assert int(a) == _splitmix64_bigint(seed, int(b))
+
+
+def test_splitmix64_published_outputs():
+    """The generator's own published outputs from state 0 pin its increment
+    and mixing constants (a mistyped constant in both the vectorised and the
+    integer form would pass the test above)."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "splitmix64_vectors.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 3
+    for seed, j, out in rows:
+        got = ic.splitmix64(int(seed), np.array([int(j)], dtype=np.uint64))[0]
+        assert int(got) == int(out, 16)
 
 
 def test_white_noise_is_unit_gaussian():
