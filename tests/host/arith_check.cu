@@ -128,8 +128,56 @@ static double rfft_err() {
     return fmax(err / mx, rt / xm);
 }
 
+// Eq. 3 encode (Eq. 4 first guess plus one edge comparison each side)
+// against the definition u = #{k in 1..255 : E[k] <= t}, E[k] the float32
+// rounding of tan(pi (k/256 - 1/2)): every edge and its float neighbours,
+// signed zeros, infinities, the largest and smallest floats, and random
+// values over the whole float range and around the edges.
+static void check_encode() {
+    float E[256];
+    E[0] = -INFINITY;
+    for (int k = 1; k < 256; ++k) E[k] = (float)tan(M_PI * (k / 256.0 - 0.5));
+    auto def = [&](float t) {
+        int u = 0;
+        for (int k = 1; k < 256; ++k) u += E[k] <= t;
+        return u;
+    };
+    long long n = 0, bad = 0;
+    uint32_t err = 0;
+    auto one = [&](float t) {
+        ++n;
+        bad += (int)encode_momentum(t, 0.f, 1.f, E, &err) != def(t);
+    };
+    for (int k = 1; k < 256; ++k) {
+        float t = E[k];
+        for (int s = 0; s < 4; ++s) t = nextafterf(t, -INFINITY);
+        for (int s = 0; s < 9; ++s, t = nextafterf(t, INFINITY)) one(t);
+    }
+    const float special[] = {0.f, -0.f, INFINITY, -INFINITY, 3.4028235e38f, -3.4028235e38f,
+                             1e-45f, -1e-45f, 1.f, -1.f, 1e30f, -1e30f};
+    for (float t : special) one(t);
+    for (int i = 0; i < 2000000; ++i) {
+        uint32_t b = (uint32_t)next_u64();
+        float t = bits_float(b);
+        if (!(t == t) || std::isinf(t)) continue;
+        one(t);
+        // near an edge: a few hundred ulps either side
+        const float e = E[1 + (int)(next_u64() % 255)];
+        memcpy(&b, &e, 4);
+        b = (uint32_t)((int32_t)b + (int32_t)(next_u64() % 601) - 300);
+        const float v = bits_float(b);
+        if (v == v && !std::isinf(v)) one(v);
+    }
+    // a NaN is flagged and gets the middle bin
+    err = 0;
+    ++n;
+    bad += encode_momentum(NAN, 0.f, 1.f, E, &err) != 128u || err == 0u;
+    printf("encode %lld %lld\n", n, bad);
+}
+
 int main() {
     check_fix24();
+    check_encode();
     check_sq();
     check_rhe();
     double e = 0;

@@ -2,8 +2,8 @@
 host programs built with nvcc:
 
 - the arithmetic helpers (fixed-point rounding of the cell sums and the
-  dispersion, the 2-byte weight rounding, the register FFTs) against their
-  plain definitions (host/arith_check.cu);
+  dispersion, the 2-byte weight rounding, the Eq. 3/4 velocity encoder, the
+  register FFTs) against their plain definitions (host/arith_check.cu);
 - the tile kernel's index arithmetic (shared-memory swizzles, the tiling of
   the coarse mesh, own and halo cells, the carving of shared memory) and its
   prologue and deposit phases run thread by thread on host arrays: the staged
@@ -52,6 +52,13 @@ def layout(tmp_path_factory):
 @pytest.mark.parametrize("name", ["fix24", "sq_fix32", "round_half_even"])
 def test_integer_rounding_matches_definition(results, name):
     cases, fails, _ = results[name]
+    assert cases > 1_000_000 and fails == 0
+
+
+def test_encode_matches_definition(results):
+    # Eq. 4 guess + one edge comparison each side = the bin count of Eq. 3,
+    # at every edge and its float neighbours, specials and random floats
+    cases, fails, _ = results["encode"]
     assert cases > 1_000_000 and fails == 0
 
 
