@@ -46,3 +46,21 @@ def test_single_particle_has_no_self_force():
     g = sim.fetch_force()
     assert np.abs(g).max() < 1e-4
     sim.close()
+
+
+@pytest.mark.parametrize("np_,nc,evolve", [(32, 32, 2), (64, 32, 0)])
+def test_force_with_four_cell_tiles(np_, nc, evolve):
+    # tile_max = 4: eight tiles of 16 fine cells per side where tile_max = 5
+    # gives seven ragged ones; the force must not depend on the tiling
+    need_gpu()
+    sim = make_sim(np=np_, nc=nc, a_init=0.02, a_final=1.0, n_steps=10, tile_max=4)
+    sim.ic_zeldovich(5)
+    ost = oracle_state(sim)
+    if evolve:
+        ost = dynamics.Simulation(nc, 0.02, 1.0, 10).run(ost, evolve)
+        load_oracle_state(sim, ost)
+    g = sim.fetch_force()
+    ref = force.ForceOperator(nc).particle_force(ost.codes()).T
+    err = vector_rel_err(g, ref)
+    assert err <= TOL, err
+    sim.close()
