@@ -59,6 +59,8 @@ def parse_args(argv=None):
                     help="Poisson arrival rates for the latency runs, as fractions of the "
                          "sequential capacity (comma list; empty: skip)")
     ap.add_argument("--serving-only", action="store_true")
+    ap.add_argument("--plain-pm", type=int, default=0, metavar="STEPS",
+                    help="also time STEPS steps of the plain float32 full-mesh PM comparator")
     return ap.parse_args(argv)
 
 
@@ -337,10 +339,122 @@ def run_ours(args):
                                "sample": "one FP64 oracle step of a 128^3-particle box "
                                          "(64^3 coarse, 256^3 fine: the same 8 particles per "
                                          "coarse cell and 8 fine cells per particle), %.1f s" % dt}
+    if world == 1 and args.plain_pm:
+        out["plain_gpu_pm"] = run_plain_pm(cfg, sim, args.plain_pm, 1)
+        out["plain_gpu_pm"]["ours_over_plain"] = value / out["plain_gpu_pm"]["value"]
     sim.close()
     if world == 1 and args.serving:
         out["serving"] = run_serving(args, f"cuda:{local}")
     return out
+
+
+class PlainPM:
+    """The plain particle-mesh step that the compressed PM-PM step is measured
+    against: float32 positions (fine cells) and momenta, 24 bytes per
+    particle; CIC deposit on the whole fine mesh (4 nc per side); one
+    real-to-complex FFT; the potential 4 pi / k^2 (the transform of 1/r,
+    unit masses) and, per component, its two-point central difference
+    (i sin k_d) through one complex-to-real FFT;
+    CIC gather; the library's kick-drift schedule (equal steps in log a,
+    momenta at the geometric mid-steps).  torch.fft is cuFFT on the GPU.
+    The same code runs on CPU tensors, so its arithmetic is tested there.
+    Measurement only: not the library's method (no force split, no
+    compression)."""
+
+    def __init__(self, x, p, nf, a_init, a_final, n_steps, step=0):
+        import torch
+        self.torch = torch
+        self.x, self.p, self.L, self.N = x, p, nf, x.shape[1]
+        self.a = [a_init * (a_final / a_init) ** (i / n_steps) for i in range(n_steps + 1)]
+        self.step_i = step
+        dev = x.device
+        two_pi = 2.0 * math.pi
+        k = torch.fft.fftfreq(nf, device=dev) * two_pi       # rad per fine cell
+        kr = torch.fft.rfftfreq(nf, device=dev) * two_pi
+        k2 = kr.view(1, 1, -1) ** 2 + k.view(1, -1, 1) ** 2 + k.view(-1, 1, 1) ** 2
+        k2[0, 0, 0] = 1.0
+        self.inv_k2 = (4.0 * math.pi) / k2
+        self.inv_k2[0, 0, 0] = 0.0
+        del k2
+        # two-point central difference of the potential: i sin(k_d)
+        kg, kgr = torch.sin(k), torch.sin(kr)
+        kg[nf // 2] = 0.0
+        kgr[-1] = 0.0
+        self.k = (kgr.view(1, 1, -1), kg.view(1, -1, 1), kg.view(-1, 1, 1))   # x, y, z
+
+    def _corners(self):
+        torch = self.torch
+        s = self.x - 0.5
+        i0 = torch.floor(s)
+        f = s - i0
+        i0 = i0.to(torch.int64)
+        L = self.L
+        for c in range(8):
+            d = [(c >> e) & 1 for e in range(3)]
+            w = torch.ones_like(f[0])
+            idx = torch.zeros_like(i0[0])
+            for e in (2, 1, 0):
+                w = w * (f[e] if d[e] else 1.0 - f[e])
+                idx = idx * L + torch.remainder(i0[e] + d[e], L)
+            yield idx, w
+
+    def force(self):
+        """g at every particle, float32 [3, N]."""
+        torch, L = self.torch, self.L
+        rho = torch.zeros(L * L * L, dtype=torch.float32, device=self.x.device)
+        for idx, w in self._corners():
+            rho.index_add_(0, idx, w)
+        rho_k = torch.fft.rfftn(rho.view(L, L, L))
+        del rho
+        g = torch.empty_like(self.x)
+        for d in range(3):
+            gd = torch.fft.irfftn(rho_k * (1j * self.k[d] * self.inv_k2), s=(L, L, L)).reshape(-1)
+            acc = torch.zeros_like(self.x[0])
+            for idx, w in self._corners():
+                acc += w * gd[idx]
+            g[d] = acc
+        return g
+
+    def step(self):
+        a, n = self.a, self.step_i
+        a_lo = a[0] if n == 0 else math.sqrt(a[n - 1] * a[n])
+        a_hi = math.sqrt(a[n] * a[n + 1])
+        rho_bar = self.N / float(self.L) ** 3
+        kick = 3.0 / (8.0 * math.pi * rho_bar) * 2.0 * (math.sqrt(a_hi) - math.sqrt(a_lo))
+        drift = 2.0 * (1.0 / math.sqrt(a[n]) - 1.0 / math.sqrt(a[n + 1]))
+        self.p += kick * self.force()
+        self.x = self.torch.remainder(self.x + drift * self.p, float(self.L))
+        self.step_i += 1
+
+
+def run_plain_pm(cfg, sim, steps, warmup):
+    """Time the plain PM comparator on the sim's current particles (decoded
+    to float32) for `steps` steps after `warmup`; CUDA events on torch's
+    current stream."""
+    import torch
+    Q, P = sim.fetch_decoded()
+    dev = sim.device
+    per_fine = (256 if cfg.pos_bytes == 1 else 65536) // 4
+    x = (torch.from_numpy(Q).to(dev).to(torch.float64) + 0.5).div_(per_fine).to(torch.float32)
+    p = torch.from_numpy(P).to(dev)
+    sc = sim.fetch_scalars()
+    pm = PlainPM(x, p, 4 * cfg.nc, cfg.a_init, cfg.a_final, cfg.n_steps, step=int(sc["step"]))
+    for _ in range(warmup):
+        pm.step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        pm.step()
+    e1.record()
+    e1.synchronize()
+    t = e0.elapsed_time(e1) / 1000.0
+    return {"value": cfg.n * steps / t, "unit": UNIT, "ms_per_step": t / steps * 1000.0,
+            "steps": steps, "warmup": warmup, "bytes_per_particle": 24,
+            "method": "float32 x, p; CIC on the whole (4 nc)^3 fine mesh; torch.fft (cuFFT) R2C + "
+                      "3 C2R of the potential 4 pi / k^2 differenced by i sin k; CIC gather; "
+                      "same kick-drift"}
 
 
 SERVING_ARENA = 48 << 30

@@ -1,0 +1,68 @@
+"""The plain float32 PM comparator that bench.py times beside the library
+(bench.PlainPM), run on CPU tensors: the pair force follows the periodic
+1/r^2 force of the oracle beyond a few cells, the net force vanishes, and a
+uniform lattice streams freely under the library's kick-drift schedule."""
+
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import bench
+from oracle import dynamics, kernels
+
+
+def _pm(x, p=None, nf=64, n_steps=4):
+    x = torch.tensor(np.asarray(x, np.float32))
+    p = torch.zeros_like(x) if p is None else torch.tensor(np.asarray(p, np.float32))
+    return bench.PlainPM(x, p, nf, 0.1, 1.0, n_steps)
+
+
+def test_pair_force_is_the_periodic_newtonian_force():
+    # a textbook PM (CIC both ways, central-difference gradient) reaches the
+    # periodic 1/r^2 force to a few per cent beyond 4 cells
+    rng = np.random.default_rng(5)
+    nf = 64
+    rs, errs = [], []
+    for _ in range(60):
+        x0 = rng.uniform(0, nf, 3)
+        r = rng.uniform(4.0, 16.0)
+        n = rng.normal(size=3)
+        n /= np.linalg.norm(n)
+        x1 = np.mod(x0 + r * n, nf)
+        g = _pm(np.stack([x0, x1], axis=1), nf=nf).force().numpy().astype(np.float64)
+        dx = x1 - x0
+        dx -= nf * np.round(dx / nf)
+        ref = kernels.periodic_pair_kernel(dx[None, :], float(nf))[0]
+        rs.append(r)
+        errs.append(np.linalg.norm(g[:, 1] - ref) / np.linalg.norm(ref))
+        # the source feels the opposite force
+        assert np.allclose(g[:, 0], -g[:, 1], rtol=1e-3, atol=1e-6 * np.abs(g).max())
+    rs, errs = np.array(rs), np.array(errs)
+    assert errs[rs >= 8].max() < 0.03, errs[rs >= 8].max()
+    assert errs[rs < 8].max() < 0.08, errs[rs < 8].max()
+
+
+def test_net_force_vanishes():
+    rng = np.random.default_rng(6)
+    g = _pm(rng.uniform(0, 64, (3, 2000))).force().numpy().astype(np.float64)
+    assert np.abs(g.sum(axis=1)).max() < 1e-5 * np.abs(g).sum(axis=1).max()
+
+
+def test_uniform_lattice_streams_freely():
+    nf, n_steps = 32, 4
+    q = (np.arange(nf) + 0.5).astype(np.float32)
+    x = np.stack(np.meshgrid(q, q, q, indexing="ij")).reshape(3, -1)
+    v = np.array([0.3, -0.2, 0.1], np.float32)
+    pm = _pm(x, np.repeat(v[:, None], x.shape[1], axis=1), nf=nf, n_steps=n_steps)
+    assert np.abs(pm.force().numpy()).max() < 1e-4
+    xs = x.astype(np.float64)
+    for n in range(n_steps):
+        pm.step()
+        kick, drift = dynamics.step_factors(0.1, 1.0, n_steps, n, x.shape[1], nf)
+        xs = np.mod(xs + drift * v[:, None].astype(np.float64), nf)
+    d = pm.x.numpy() - xs
+    d -= nf * np.round(d / nf)
+    assert np.abs(d).max() < 1e-3
