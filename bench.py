@@ -59,6 +59,8 @@ def parse_args(argv=None):
                     help="Poisson arrival rates for the latency runs, as fractions of the "
                          "sequential capacity (comma list; empty: skip)")
     ap.add_argument("--serving-only", action="store_true")
+    ap.add_argument("--fma-probe", action="store_true",
+                    help="measure the FP32 FMA peak with the library's probe and use it as the peak")
     ap.add_argument("--plain-pm", type=int, default=0, metavar="STEPS",
                     help="also time STEPS steps of the plain float32 full-mesh PM comparator")
     return ap.parse_args(argv)
@@ -308,6 +310,11 @@ def run_ours(args):
                 "peak_basis": "FP32 FMA: 152 SMs x 128 lanes x 2 x %d MHz (max SM clock)" % sm_max,
                 "flops_per_launch": flops, "avg_launch_ms": tile_s * 1000.0,
                 "launches_per_step": tile_launches}
+    if args.fma_probe:
+        measured = probe_fp32_tflops(torch.device(f"cuda:{local}"))
+        roofline.update({"peak": measured, "frac": achieved / measured if achieved else None,
+                         "peak_derived": peak,
+                         "peak_basis": "measured: FP32 FMA probe (pmpm_probe_fma), best of 5"})
     hbm = measured_peaks().get("hbm_gbs")
     stage_names = ["coarse_deposit", "coarse_fft_green", "tile_pm_kick_drift", "hist_scan_cell_means",
                    "dispersion", "encode_scatter"]
@@ -425,6 +432,30 @@ class PlainPM:
         self.p += kick * self.force()
         self.x = self.torch.remainder(self.x + drift * self.p, float(self.L))
         self.step_i += 1
+
+
+def probe_fp32_tflops(device, repeats=5, iters=1 << 15):
+    """Best of `repeats` runs of pmpm_probe_fma over 8 blocks of 256 threads
+    per SM (full occupancy), TFLOP/s."""
+    import ctypes
+
+    import torch
+
+    from paper_2003_03931_gb300 import _lib
+    lib = _lib.load()
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    out = torch.empty(sms * 8 * 256, dtype=torch.float32, device=device)
+    stream = torch.cuda.current_stream(device)
+    best = 0.0
+    for _ in range(repeats):
+        flops, ms = ctypes.c_double(), ctypes.c_float()
+        rc = lib.pmpm_probe_fma(ctypes.c_void_p(out.data_ptr()), out.numel(),
+                                ctypes.c_void_p(stream.cuda_stream), iters, ctypes.byref(flops),
+                                ctypes.byref(ms))
+        if rc != _lib.PMPM_OK:
+            raise RuntimeError(f"pmpm_probe_fma failed ({rc})")
+        best = max(best, flops.value / (ms.value * 1e-3) / 1e12)
+    return best
 
 
 def run_plain_pm(cfg, sim, steps, warmup):

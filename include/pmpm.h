@@ -321,6 +321,17 @@ const char* pmpm_batch_last_error(const pmpm_batch* batch);
  * pmpm_batch_config, pmpm_batch_stats, for binding checks.  Host only. */
 int pmpm_abi_sizes(int64_t* sizes, int32_t n);
 
+/* Measurement only: FP32 fused multiply-add throughput of the current
+ * device.  Launches out_len / 256 blocks of 256 threads on `stream` (a
+ * cudaStream_t, NULL for the default stream); each thread runs 8
+ * independent chains of `iters` FMAs and writes one float to d_out
+ * (caller-owned device memory, out_len floats, out_len a multiple of 256).
+ * Waits for the kernel; *flops receives 2 * 8 * iters * out_len and *ms the
+ * kernel's duration between two events on the stream.  PMPM_EINVAL for bad
+ * arguments, PMPM_ECUDA if a CUDA call fails. */
+int pmpm_probe_fma(float* d_out, int64_t out_len, void* stream, int32_t iters, double* flops,
+                   float* ms);
+
 /* Host copies of the float32 velocity tables the library uses: T[256]
  * bin-centre values and E[256] bin edges (E[0] = -inf), Eq. 3.  Host only. */
 int pmpm_codec_tables(float* T, float* E);

@@ -51,7 +51,7 @@ EXPORTS = [
     "pmpm_arena_create", "pmpm_arena_alloc", "pmpm_arena_free", "pmpm_arena_stats",
     "pmpm_arena_destroy", "pmpm_batch_create", "pmpm_batch_submit", "pmpm_batch_progress",
     "pmpm_batch_run", "pmpm_batch_poll", "pmpm_batch_clock", "pmpm_batch_get_stats",
-    "pmpm_batch_destroy", "pmpm_batch_last_error", "pmpm_abi_sizes",
+    "pmpm_batch_destroy", "pmpm_batch_last_error", "pmpm_abi_sizes", "pmpm_probe_fma",
 ]
 NO_RC = ("pmpm_destroy", "pmpm_last_error", "pmpm_noalloc_last_error", "pmpm_arena_destroy",
          "pmpm_batch_destroy", "pmpm_batch_last_error", "pmpm_batch_clock")
@@ -175,6 +175,8 @@ def load():
     lib.pmpm_arena_destroy.argtypes = [P]
     lib.pmpm_arena_destroy.restype = None
     lib.pmpm_batch_create.argtypes = [ctypes.POINTER(BatchConfig), P, S, ctypes.POINTER(P)]
+    lib.pmpm_probe_fma.argtypes = [P, ctypes.c_int64, P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_float)]
     lib.pmpm_batch_submit.argtypes = [P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_int64)]
     lib.pmpm_batch_progress.argtypes = [P, ctypes.POINTER(ctypes.c_int32)]
     lib.pmpm_batch_run.argtypes = [P, ctypes.c_double]

@@ -15,7 +15,7 @@ SRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpmpm.so")
 UNITS = ["abi.cu", "green.cu", "fft.cu", "coarse.cu", "tile.cu", "sort.cu", "ic.cu", "power.cu", "serve.cu",
-         "noalloc.cu"]
+         "noalloc.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -92,3 +92,12 @@ def test_lowmem_workspace_fits_2048_cubed(lib):
         from paper_2003_03931_gb300 import _lib
         out = ctypes.c_size_t(0)
         _lib.check(lib.pmpm_workspace_bytes(ctypes.byref(cc), ctypes.byref(out)))
+
+
+def test_fma_probe_rejects_bad_arguments(lib):
+    # argument checks come before any CUDA call, so they run without a GPU
+    f, ms = ctypes.c_double(), ctypes.c_float()
+    buf = ctypes.c_void_p(4096)   # never dereferenced on these paths
+    for args in ((None, 256, None, 10), (buf, 255, None, 10), (buf, 0, None, 10), (buf, 256, None, 0)):
+        assert lib.pmpm_probe_fma(*args, ctypes.byref(f), ctypes.byref(ms)) == -1
+    assert lib.pmpm_probe_fma(buf, 256, None, 10, None, ctypes.byref(ms)) == -1
