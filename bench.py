@@ -61,6 +61,8 @@ def parse_args(argv=None):
     ap.add_argument("--serving-only", action="store_true")
     ap.add_argument("--fma-probe", action="store_true",
                     help="measure the FP32 FMA peak with the library's probe and use it as the peak")
+    ap.add_argument("--library-fft", action="store_true",
+                    help="also time the tile transforms with torch.fft (cuFFT) for comparison")
     ap.add_argument("--plain-pm", type=int, default=0, metavar="STEPS",
                     help="also time STEPS steps of the plain float32 full-mesh PM comparator")
     return ap.parse_args(argv)
@@ -346,6 +348,15 @@ def run_ours(args):
                                "sample": "one FP64 oracle step of a 128^3-particle box "
                                          "(64^3 coarse, 256^3 fine: the same 8 particles per "
                                          "coarse cell and 8 fine cells per particle), %.1f s" % dt}
+    if world == 1 and args.library_fft:
+        nt = -(-cfg.nc // cfg.tile_max)
+        s_lib = time_library_tile_transforms(nt ** 3, f"cuda:{local}")
+        out["library_fft_tiles"] = {
+            "ms_per_step": s_lib * 1000.0 * tile_launches, "tiles": nt ** 3,
+            "ours_tile_pass_ms_per_step": tile_ms / K,
+            "what": "torch.fft (cuFFT) over batched 32^3 boxes in device memory: 1 R2C + 3 "
+                    "(complex multiply, C2R) per tile, the transforms alone; the tile pass also "
+                    "deposits, interpolates, kicks and drifts"}
     if world == 1 and args.plain_pm:
         out["plain_gpu_pm"] = run_plain_pm(cfg, sim, args.plain_pm, 1)
         out["plain_gpu_pm"]["ours_over_plain"] = value / out["plain_gpu_pm"]["value"]
@@ -456,6 +467,45 @@ def probe_fp32_tflops(device, repeats=5, iters=1 << 15):
             raise RuntimeError(f"pmpm_probe_fma failed ({rc})")
         best = max(best, flops.value / (ms.value * 1e-3) / 1e12)
     return best
+
+
+def time_library_tile_transforms(ntiles, device, batch=2048, reps=3):
+    """The tile pass's transforms done by the FFT library instead (torch.fft,
+    cuFFT on the GPU): per 32^3 tile box one real-to-complex transform and,
+    per force component, one complex multiply by a spectrum and one
+    complex-to-real transform, over batches of `batch` boxes in device
+    memory.  Returns seconds for `ntiles` tiles (scaled from the best of
+    `reps` batches).  No deposit, interpolation or output pruning: the
+    transforms alone."""
+    import torch
+    gen = torch.Generator(device="cpu").manual_seed(7)
+    x = torch.randn(batch, 32, 32, 32, generator=gen).to(device)
+    spec = torch.randn(3, 32, 32, 17, generator=gen, dtype=torch.complex64).to(device)
+    cuda = torch.device(device).type == "cuda"
+
+    def once():
+        xk = torch.fft.rfftn(x, dim=(1, 2, 3))
+        for d in range(3):
+            y = torch.fft.irfftn(xk * spec[d], s=(32, 32, 32), dim=(1, 2, 3))
+        return y
+
+    once()
+    best = float("inf")
+    for _ in range(reps):
+        if cuda:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            once()
+            e1.record()
+            e1.synchronize()
+            t = e0.elapsed_time(e1) / 1000.0
+        else:
+            t0 = time.perf_counter()
+            once()
+            t = time.perf_counter() - t0
+        best = min(best, t)
+    return best * ntiles / batch
 
 
 def run_plain_pm(cfg, sim, steps, warmup):

@@ -66,3 +66,11 @@ def test_uniform_lattice_streams_freely():
     d = pm.x.numpy() - xs
     d -= nf * np.round(d / nf)
     assert np.abs(d).max() < 1e-3
+
+
+def test_library_tile_transform_timer_runs_on_cpu():
+    # the cuFFT comparator of the tile transforms, on CPU tensors: a time
+    # that scales with the number of tiles
+    t1 = bench.time_library_tile_transforms(64, "cpu", batch=8, reps=1)
+    t2 = bench.time_library_tile_transforms(128, "cpu", batch=8, reps=1)
+    assert t1 > 0 and t2 > 0 and math.isfinite(t1)
