@@ -448,6 +448,18 @@ static void check_deposit(long long& n, long long& bad, double& err) {
         for (int t = 0; t < kTileThreads; ++t) tile_cells_map(t, g, c);
         for (int t = 0; t < kTileThreads; ++t)
             tile_deposit_flat<false, PB>(t, g, P, R, c, CtaScratch{nullptr, nullptr});
+        // the same phases with the threads in reverse order (another order
+        // of the integer adds) leave the same density, word for word
+        {
+            const std::vector<uint32_t> first(R, R + kTileR);
+            for (int t = kTileThreads - 1; t >= 0; --t) tile_prologue(t, g, P, c, R, gS);
+            for (int t = kTileThreads - 1; t >= 0; --t) tile_cells_scan(t, g, c);
+            for (int t = kTileThreads - 1; t >= 0; --t) tile_cells_map(t, g, c);
+            for (int t = kTileThreads - 1; t >= 0; --t)
+                tile_deposit_flat<false, PB>(t, g, P, R, c, CtaScratch{nullptr, nullptr});
+            ++n;
+            bad += memcmp(first.data(), R, sizeof(uint32_t) * kTileR) != 0;
+        }
         // plain deposit of the halo box's particles
         std::vector<uint32_t> ref(kTileR, 0u);
         int64_t halo_particles = 0, own_particles = 0;
