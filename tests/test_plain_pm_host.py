@@ -74,3 +74,28 @@ def test_library_tile_transform_timer_runs_on_cpu():
     t1 = bench.time_library_tile_transforms(64, "cpu", batch=8, reps=1)
     t2 = bench.time_library_tile_transforms(128, "cpu", batch=8, reps=1)
     assert t1 > 0 and t2 > 0 and math.isfinite(t1)
+
+
+def test_zeldovich_plane_wave_grows_linearly():
+    # Einstein-de Sitter: x = q + a Psi(q) is exact until shell crossing.  A
+    # box-scale plane wave from a = 0.05 to 0.4 (a A 2 pi / L = 0.5 at the
+    # end) must grow by a_final / a_init; a wrong force constant or time
+    # factor misses by more than 10%.
+    n_p, nf = 32, 64
+    ai, af, S = 0.05, 0.4, 16
+    A = 0.5 * nf / (2 * np.pi * af)
+    g1 = (np.arange(n_p) + 0.5) * (nf / n_p)
+    q = np.stack(np.meshgrid(g1, g1, g1, indexing="ij")).reshape(3, -1)
+    psi = np.zeros_like(q)
+    psi[0] = A * np.sin(2 * np.pi * q[0] / nf)
+    x = np.mod(q + ai * psi, nf)
+    pm = bench.PlainPM(torch.tensor(x.astype(np.float32)), torch.tensor((ai ** 1.5 * psi).astype(np.float32)),
+                       nf, ai, af, S)
+    for _ in range(S):
+        pm.step()
+    disp = pm.x.numpy().astype(np.float64)[0] - q[0]
+    disp -= nf * np.round(disp / nf)
+    shape = np.sin(2 * np.pi * q[0] / nf)
+    amp = disp @ shape / (shape @ shape)
+    assert 0.97 < amp / (af * A) < 1.01, amp / (af * A)
+    assert np.abs(disp - af * A * shape).max() < 0.03 * af * A
