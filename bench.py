@@ -518,8 +518,11 @@ def run_plain_pm(cfg, sim, steps, warmup):
     per_fine = (256 if cfg.pos_bytes == 1 else 65536) // 4
     x = (torch.from_numpy(Q).to(dev).to(torch.float64) + 0.5).div_(per_fine).to(torch.float32)
     p = torch.from_numpy(P).to(dev)
-    sc = sim.fetch_scalars()
-    pm = PlainPM(x, p, 4 * cfg.nc, cfg.a_init, cfg.a_final, cfg.n_steps, step=int(sc["step"]))
+    # continue the library's equal-log-a schedule from the current a for
+    # as many steps as run here
+    a_now = float(sim.fetch_scalars()["a"])
+    ratio = (cfg.a_final / cfg.a_init) ** (1.0 / cfg.n_steps)
+    pm = PlainPM(x, p, 4 * cfg.nc, a_now, a_now * ratio ** (warmup + steps), warmup + steps)
     for _ in range(warmup):
         pm.step()
     torch.cuda.synchronize()

@@ -99,3 +99,40 @@ def test_zeldovich_plane_wave_grows_linearly():
     amp = disp @ shape / (shape @ shape)
     assert 0.97 < amp / (af * A) < 1.01, amp / (af * A)
     assert np.abs(disp - af * A * shape).max() < 0.03 * af * A
+
+
+def test_run_plain_pm_continues_the_schedule(monkeypatch):
+    # bench's hook on CPU: a stand-in sim at the end of its own schedule;
+    # the comparator continues from the current a without running off it
+    class FakeSim:
+        device = "cpu"
+
+        def fetch_decoded(self):
+            rng = np.random.default_rng(1)
+            return (rng.integers(0, 16 * 256, size=(3, 512)).astype(np.int32),
+                    rng.normal(size=(3, 512)).astype(np.float32))
+
+        def fetch_scalars(self):
+            return {"a": 1.0, "step": 10}
+
+    class Cfg:
+        nc, n, pos_bytes, a_init, a_final, n_steps = 16, 512, 1, 0.02, 1.0, 10
+
+    class FakeEvent:
+        def __init__(self, enable_timing=True):
+            self.t = 0.0
+
+        def record(self):
+            import time
+            self.t = time.perf_counter()
+
+        def synchronize(self):
+            pass
+
+        def elapsed_time(self, other):
+            return (other.t - self.t) * 1000.0 + 1e-3
+
+    monkeypatch.setattr(torch.cuda, "Event", FakeEvent)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a: None)
+    out = bench.run_plain_pm(Cfg(), FakeSim(), 3, 1)
+    assert out["value"] > 0 and out["steps"] == 3 and out["bytes_per_particle"] == 24
