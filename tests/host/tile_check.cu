@@ -1023,6 +1023,94 @@ static void check_lowmem(long long& n, long long& bad) {
     bad += errw != 0u;
 }
 
+// Error paths of the tile body that real inputs rarely reach.
+// (1) A tile with more own particles than the low-memory scratch holds
+//     (kLowmemCap): the deposit parks the first kLowmemCap forces, flags
+//     kErrScratch for the rest and writes nothing past the slot.
+// (2) A fine node whose weight passes 2^32 - 1 units (over 2048 particles
+//     on one node): the checked deposit path, taken when a cell holds more
+//     than 255 particles, flags kErrFineOverflow.
+static void check_error_paths(long long& n, long long& bad) {
+    const int nc = 16, nt = tile_count(nc, 5);
+    const int64_t nc3 = (int64_t)nc * nc * nc;
+    std::vector<int32_t> counts(nc3, 0);
+    std::vector<int64_t> offsets(nc3 + 1);
+    // tile 0 owns cells 0..3 per axis: 64 cells of 1100 particles (70,400
+    // own particles, past the scratch); cell (1,1,1) holds 2,600 particles
+    // in one bin, whose nodes pass 2^32 units
+    for (int z = 0; z < 4; ++z)
+        for (int y = 0; y < 4; ++y)
+            for (int x = 0; x < 4; ++x) counts[x + nc * (y + nc * z)] = 1100;
+    counts[1 + nc * (1 + nc)] = 2600;
+    int64_t np = 0;
+    for (int64_t i = 0; i < nc3; ++i) {
+        offsets[i] = np;
+        np += counts[i];
+    }
+    offsets[nc3] = np;
+    std::vector<uint8_t> m[3];
+    for (int e = 0; e < 3; ++e) {
+        m[e].resize(np);
+        for (int64_t j = 0; j < np; ++j) m[e][j] = (uint8_t)(next_u64() & 255);
+        for (int64_t j = offsets[1 + nc * (1 + nc)]; j < offsets[2 + nc * (1 + nc)]; ++j) m[e][j] = 100;
+    }
+    std::vector<float> Fl(3 * nc3, 0.5f), green(kGreenPacked, 0.f), Td(256, 0.f);
+    const float sigma = 1.f, kd[2] = {0.f, 0.f};
+    // scratch with a guard zone after each component's slot
+    constexpr int kGuard = 1024;
+    std::vector<float> sp(3 * (size_t)kLowmemCap + kGuard, -7.f);
+    std::vector<int32_t> sq(2 * (size_t)kLowmemCap + kGuard, -7);
+    std::vector<int32_t> cnew(nc3, 0);
+    std::vector<unsigned long long> S(3 * nc3, 0ull);
+    uint32_t errw = 0;
+    TileParams P{};
+    P.nc = nc;
+    P.nt = nt;
+    P.n = np;
+    P.counts = counts.data();
+    P.offsets = offsets.data();
+    P.m0 = m[0].data();
+    P.m1 = m[1].data();
+    P.m2 = m[2].data();
+    P.Fl = Fl.data();
+    P.green = green.data();
+    P.Tdec = Td.data();
+    P.sigma = &sigma;
+    P.kd = kd;
+    P.mode = 2;
+    P.counts_new = cnew.data();
+    P.S = S.data();
+    P.err = &errw;
+    std::vector<unsigned char> smem(kTileSmemBytes);
+    unsigned char* base = smem.data();
+    uint32_t* R = reinterpret_cast<uint32_t*>(base);
+    float2* W = reinterpret_cast<float2*>(base + (size_t)kTileR * 4);
+    float* gS = reinterpret_cast<float*>(base + (size_t)kTileR * 4 + (size_t)kTileW * 8);
+    int* O = reinterpret_cast<int*>(gS + kGreenPacked);
+    const TileGeom g = tile_geom(0, nc, nt);
+    const TileCells c = tile_cells(W, O);
+    const CtaScratch cs{sp.data(), sq.data()};
+    for (int t = 0; t < kTileThreads; ++t) tile_prologue(t, g, P, c, R, gS);
+    for (int t = 0; t < kTileThreads; ++t) tile_cells_scan(t, g, c);
+    for (int t = 0; t < kTileThreads; ++t) tile_cells_map(t, g, c);
+    for (int t = 0; t < kTileThreads; ++t) tile_deposit_flat<true, 1>(t, g, P, R, c, cs);
+    ++n;
+    bad += c.ppre[kOwnMax] <= kLowmemCap || c.misc[2] <= 255;   // the case is what it claims
+    ++n;
+    bad += (errw & kErrScratch) == 0u || (errw & kErrFineOverflow) == 0u;
+    // parked forces: slots 0..cap-1 of each component written (F_l = 0.5
+    // everywhere gathers to 0.5), the guard after the last untouched
+    for (int e = 0; e < 3; ++e)
+        for (int v = 0; v < kLowmemCap; v += 97) {
+            ++n;
+            bad += std::fabs(sp[(size_t)e * kLowmemCap + v] - 0.5f) > 1e-6f;
+        }
+    for (int i = 0; i < kGuard; ++i) {
+        ++n;
+        bad += sp[3 * (size_t)kLowmemCap + i] != -7.f;
+    }
+}
+
 int main() {
     check_swizzles();
     check_tiling();
@@ -1049,6 +1137,11 @@ int main() {
         long long n = 0, bad = 0;
         check_lowmem(n, bad);
         printf("lowmem %lld %lld\n", n, bad);
+    }
+    {
+        long long n = 0, bad = 0;
+        check_error_paths(n, bad);
+        printf("error_paths %lld %lld\n", n, bad);
     }
     return 0;
 }

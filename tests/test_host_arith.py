@@ -109,3 +109,10 @@ def test_tile_lowmem_passes_match_default_pass(layout):
     # scattered records of every new cell, all exact
     cases, fails, _ = layout["lowmem"]
     assert cases > 100_000 and fails == 0, (cases, fails)
+
+
+def test_tile_error_paths_flag_and_stay_in_bounds(layout):
+    # a tile past the low-memory scratch flags it and writes nothing past
+    # its slot; a fine node past 2^32 units flags the overflow
+    cases, fails, _ = layout["error_paths"]
+    assert cases > 1000 and fails == 0, (cases, fails)
