@@ -101,3 +101,13 @@ def test_fma_probe_rejects_bad_arguments(lib):
     for args in ((None, 256, None, 10), (buf, 255, None, 10), (buf, 0, None, 10), (buf, 256, None, 0)):
         assert lib.pmpm_probe_fma(*args, ctypes.byref(f), ctypes.byref(ms)) == -1
     assert lib.pmpm_probe_fma(buf, 256, None, 10, None, ctypes.byref(ms)) == -1
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    # no fallback: without libpmpm.so the binding raises instead of running
+    # anything else
+    from paper_2003_03931_gb300 import _lib
+    monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "missing" / "libpmpm.so"))
+    monkeypatch.setattr(_lib, "_lib", None)
+    with pytest.raises(ImportError):
+        _lib.load()
