@@ -13,6 +13,11 @@ sequential plain stepping (--serving, --serving-rates, --serving-only).
 Under torchrun each rank evolves its own box (independent replicas, weak
 scaling); value is the particle-steps of all ranks over the slowest rank's
 time.  --impl reference times the FP64 oracle on the host cores instead.
+
+Optional objects on the line (one GPU): --fma-probe measures the FP32 FMA
+peak and uses it as the roofline's denominator; --library-fft times the
+tile transforms done by torch.fft (cuFFT) instead; --plain-pm STEPS times
+the plain float32 full-mesh PM step (class PlainPM) on the same particles.
 """
 
 import os
