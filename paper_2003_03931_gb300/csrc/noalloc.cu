@@ -221,10 +221,19 @@ extern "C" int pmpm_power_spectrum_noalloc(int32_t nc, int64_t n, const uint8_t*
     k_na_bin<<<grid_for(m3, 256, 152 * 4), 256, sizeof(double) * 3 * nbins, st>>>(
         nmesh, nbins, (double)nf, static_cast<const float2*>(mesh), bins);
     double hb[3 * kNaMaxBins];
+    long long total = -1;
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(hb, bins, sizeof(double) * 3 * nbins, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&total, offsets + ncells, sizeof(total), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return na_fail(PMPM_ECUDA, cudaGetErrorString(e));
+    // counts that do not add up to n put particles in the wrong cells and the
+    // mean density is wrong: refuse the result
+    if (total != n) {
+        char m[160];
+        snprintf(m, sizeof(m), "the counts add up to %lld, not n = %lld", total, (long long)n);
+        return na_fail(PMPM_EINVAL, m);
+    }
     for (int j = 0; j < nbins; ++j) {
         const double c = hb[2 * nbins + j];
         nmodes[j] = (int64_t)c;

@@ -44,7 +44,7 @@ def test_noalloc_power_spectrum_matches_and_repeats():
            "counts": torch.from_numpy(st["counts"]).cuda()}
     stream = torch.cuda.current_stream().cuda_stream
     torch.cuda.synchronize()
-    for nmesh in (64, 32, 64):   # consecutive calls share the scratch array
+    for nmesh in (64, 32, 16, 64):   # consecutive calls share the scratch array
         nbins = nmesh // 2
         kr, pr, nr = sim.power_spectrum(nmesh, nbins)
         for _ in range(2):
@@ -53,6 +53,37 @@ def test_noalloc_power_spectrum_matches_and_repeats():
             np.testing.assert_array_equal(nm, nr)
             np.testing.assert_allclose(k, kr, rtol=1e-12)
             np.testing.assert_allclose(pk, pr, rtol=1e-9)
+    # counts that do not add up to n are refused, not binned into wrong cells
+    bad = dict(dev, counts=dev["counts"].clone())
+    bad["counts"][0] += 1
+    rc, *_ = _noalloc(lib, w["nc"], bad, 32, 16, stream)
+    assert rc == _lib.PMPM_EINVAL
+    assert b"add up" in lib.pmpm_noalloc_last_error()
+    sim.close()
+
+
+def test_noalloc_at_its_largest_box():
+    # nc = 64 at nmesh = 64: the whole offsets and mesh regions of the array
+    need_gpu()
+    import torch
+    from paper_2003_03931_gb300 import _lib
+    lib = _lib.load()
+    sim = make_sim(np=64, nc=64, a_init=0.02, a_final=1.0, n_steps=4)
+    sim.ic_zeldovich(6, **synth.IC_SPECTRUM)
+    sim.step(2)
+    st = sim.fetch_state()
+    dev = {"n": sim.cfg.n,
+           "m": [torch.from_numpy(np.ascontiguousarray(st["streams"][d])).cuda() for d in range(3)],
+           "counts": torch.from_numpy(st["counts"]).cuda()}
+    stream = torch.cuda.current_stream().cuda_stream
+    torch.cuda.synchronize()
+    kr, pr, nr = sim.power_spectrum(64, 32)
+    for _ in range(2):
+        rc, k, pk, nm = _noalloc(lib, 64, dev, 64, 32, stream)
+        assert rc == 0, lib.pmpm_noalloc_last_error()
+        np.testing.assert_array_equal(nm, nr)
+        np.testing.assert_allclose(k, kr, rtol=1e-12)
+        np.testing.assert_allclose(pk, pr, rtol=1e-9)
     sim.close()
 
 
