@@ -66,6 +66,18 @@ extern "C" {
                                     per particle (fetch only) */
 #define PMPM_QP               9  /* load only: int32 Q[3][N] then float p[3][N];
                                     encodes them into the store (Sec. III-A) */
+#define PMPM_STEP_QP         10  /* fetch only: int32 Q'[3][N] then float p'[3][N], the
+                                    drifted position codes and kicked momenta of the
+                                    last step (Sec. II), in the storage order of the
+                                    state that step started from; 24 N bytes.
+                                    Available after pmpm_step on a default sim until
+                                    the next call that loads, initialises, fetches
+                                    DECODED_Q/P or FORCE, or computes a power spectrum
+                                    (they reuse the buffer): PMPM_ESTATE otherwise */
+#define PMPM_FINE_TILE_DENSITY 11 /* fetch only (pmpm_fetch_tile_density): uint32
+                                    [32][32][32], x fastest, the integer CIC density
+                                    of one tile's fine-mesh box, units 2^-21 per
+                                    particle (Sec. II) */
 
 /* pmpm_config.flags */
 #define PMPM_FLAG_LOWMEM 1   /* Low-memory step for the largest boxes.  The step
@@ -158,6 +170,24 @@ int pmpm_power_spectrum(pmpm_sim* sim, int32_t nmesh, int32_t nbins,
  * the listed size.  Synchronises. */
 int pmpm_fetch(pmpm_sim* sim, int32_t what, void* host_dst, size_t bytes);
 
+/* The fine-mesh box of one tile (Sec. II) as the tile pass deposits it,
+ * for checking the integer CIC density node by node.  tile: flat tile index,
+ * tx + nt (ty + nt tz), nt = ceil(nc / tile_max) tiles per side (tile t of
+ * an axis spans coarse cells [floor(t nc / nt), floor((t + 1) nc / nt))).
+ * host_dst: uint32 [32][32][32] (x fastest, 131072 bytes); box node i of an
+ * axis is fine node o + i (periodic), o = 4 c0 - 6 with c0 the tile's first
+ * coarse cell; origin (may be NULL) receives o for x, y, z and tile_edge
+ * (may be NULL) the tile's edge in fine cells per axis.  The box holds the
+ * deposit of the particles of coarse cells [c0 - 2, c1 + 2) clipped to the
+ * box, so nodes i <= T + 12 (T the tile edge) carry the whole density and
+ * the last nodes of a 16-cell tile only part of it.  Runs the deposit of
+ * the current state (default and low-memory sims alike; the step's buffers
+ * are reused, see PMPM_STEP_QP); synchronises.  PMPM_EINVAL for a tile out
+ * of range, a buffer of another size, or a workspace whose scratch is
+ * smaller than one box (tiny boxes with a small pk_mesh_max). */
+int pmpm_fetch_tile_density(pmpm_sim* sim, int32_t tile, uint32_t* host_dst, size_t bytes,
+                            int32_t* origin, int32_t* tile_edge);
+
 /* Replace part of the state from a host buffer (PMPM_STREAMS, PMPM_COUNTS,
  * PMPM_VC, PMPM_SCALARS, or PMPM_QP which encodes raw codes and momenta).
  * Synchronises. */
@@ -189,8 +219,10 @@ const char* pmpm_last_error(const pmpm_sim* sim);
  * has no counterpart; it computes the same P(k) as pmpm_power_spectrum for
  * a cell-ordered store the caller already holds on the device:
  *   nc         coarse cells per side, a power of two in [8, 64]
- *   n          particles; d_m0..d_m2 their position bins (Eq. 2), n bytes
- *              each, and d_counts the nc^3 per-cell counts (device pointers)
+ *   n          particles; d_m0..d_m2 their 1-byte position bins (Eq. 2; stores
+ *              with 2-byte bins are not accepted), n bytes each, and d_counts
+ *              the nc^3 per-cell counts (device pointers); counts that do not
+ *              add up to n return PMPM_EINVAL
  *   nmesh      power of two dividing 4*nc, 4*nc/4 <= nmesh <= 64
  *   nbins      in [1, nmesh/2]; k, pk, nmodes are host arrays of nbins
  *   cuda_stream the stream to run on (NULL: legacy default stream)
@@ -198,16 +230,20 @@ const char* pmpm_last_error(const pmpm_sim* sim);
  * memory, held by every GPU that loads the library until the process exits.
  * The first call on a device looks up that array's address and fills a
  * twiddle table there, synchronising the stream; make that first call before
- * any stream capture.  All calls share the array: calls whose GPU work
- * overlaps (other streams, other host threads) race and give wrong results.
- * Larger sizes return PMPM_EINVAL; pmpm_noalloc_last_error() explains. */
+ * any stream capture.  Every call copies its result to the host arrays and
+ * waits for the stream before it returns.  All calls share the array: calls
+ * whose GPU work overlaps (other streams, other host threads) race and give
+ * wrong results.  Larger sizes return PMPM_EINVAL; pmpm_noalloc_last_error()
+ * explains. */
 int pmpm_power_spectrum_noalloc(int32_t nc, int64_t n, const uint8_t* d_m0,
                                 const uint8_t* d_m1, const uint8_t* d_m2,
                                 const int32_t* d_counts, int32_t nmesh, int32_t nbins,
                                 double* k, double* pk, int64_t* nmodes,
                                 void* cuda_stream);
 
-/* Text of the last failure of pmpm_power_spectrum_noalloc. */
+/* Text of the last failure of pmpm_power_spectrum_noalloc.  One buffer for
+ * the whole process, written without a lock: with calls failing on several
+ * host threads at once the text may belong to any of them. */
 const char* pmpm_noalloc_last_error(void);
 
 /* ------------------------------------------------------------------------
@@ -237,7 +273,7 @@ typedef struct pmpm_request {
     int32_t n_steps;         /* steps of the equal-log-a schedule a_init -> a_final */
     int32_t pk_nmesh;        /* final P(k) mesh: power of two in [nc, 4*nc]; 0 = min(np, 4*nc) */
     int32_t pk_nbins;        /* 1..pk_nmesh/2; 0 = pk_nmesh/2 */
-    int32_t reserved;
+    int32_t flags;           /* 0 or PMPM_FLAG_LOWMEM (the low-memory step) */
     double  a_init, a_final;
     uint64_t seed;           /* initial conditions as pmpm_ic_zeldovich */
     double  slope, k_c, rms_disp;

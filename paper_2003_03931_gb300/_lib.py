@@ -28,6 +28,7 @@ DECODED_P = 6
 FORCE = 7
 COARSE_DENSITY = 8
 QP = 9
+STEP_QP = 10
 
 FLAG_LOWMEM = 1
 
@@ -45,7 +46,8 @@ ERROR_NAMES = {
 EXPORTS = [
     "pmpm_workspace_bytes", "pmpm_init", "pmpm_init_like", "pmpm_graph_mode",
     "pmpm_ic_zeldovich", "pmpm_step",
-    "pmpm_power_spectrum", "pmpm_fetch", "pmpm_load", "pmpm_sync", "pmpm_stage_times",
+    "pmpm_power_spectrum", "pmpm_fetch", "pmpm_fetch_tile_density", "pmpm_load", "pmpm_sync",
+    "pmpm_stage_times",
     "pmpm_destroy", "pmpm_last_error", "pmpm_codec_tables", "pmpm_power_spectrum_noalloc",
     "pmpm_noalloc_last_error",
     "pmpm_arena_create", "pmpm_arena_alloc", "pmpm_arena_free", "pmpm_arena_stats",
@@ -86,7 +88,7 @@ class Scalars(ctypes.Structure):
 class Request(ctypes.Structure):
     _fields_ = [
         ("np", ctypes.c_int32), ("nc", ctypes.c_int32), ("n_steps", ctypes.c_int32),
-        ("pk_nmesh", ctypes.c_int32), ("pk_nbins", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("pk_nmesh", ctypes.c_int32), ("pk_nbins", ctypes.c_int32), ("flags", ctypes.c_int32),
         ("a_init", ctypes.c_double), ("a_final", ctypes.c_double), ("seed", ctypes.c_uint64),
         ("slope", ctypes.c_double), ("k_c", ctypes.c_double), ("rms_disp", ctypes.c_double),
         ("arrival", ctypes.c_double),
@@ -155,6 +157,7 @@ def load():
     lib.pmpm_power_spectrum.argtypes = [P, ctypes.c_int32, ctypes.c_int32, P, P, P]
     lib.pmpm_fetch.argtypes = [P, ctypes.c_int32, P, ctypes.c_size_t]
     lib.pmpm_load.argtypes = [P, ctypes.c_int32, P, ctypes.c_size_t]
+    lib.pmpm_fetch_tile_density.argtypes = [P, ctypes.c_int32, P, ctypes.c_size_t, P, P]
     lib.pmpm_sync.argtypes = [P]
     lib.pmpm_stage_times.argtypes = [P, ctypes.c_int32, P, ctypes.c_int32, P]
     lib.pmpm_destroy.argtypes = [P]

@@ -577,6 +577,7 @@ int pmpm_ic_zeldovich(pmpm_sim* h, uint64_t seed, double slope, double k_c, doub
     if (!h) return PMPM_EINVAL;
     Sim& s = h->s;
     if (!(k_c > 0.0) || !(rms_disp >= 0.0)) return set_error(s, PMPM_EINVAL, "bad spectrum");
+    s.qp_step = false;
     return ic_zeldovich(s, seed, slope, k_c, rms_disp);
 }
 
@@ -588,9 +589,11 @@ int pmpm_step(pmpm_sim* h, int32_t nsteps) {
         return set_error(s, PMPM_EINVAL, "%d steps exceed the schedule (%lld of %d taken)", nsteps,
                          (long long)s.step, s.cfg.n_steps);
     for (int i = 0; i < nsteps; ++i) {
+        s.qp_step = false;
         const int rc = one_step(s);
         if (rc) return rc;
         if (s.prof && s.ev_count > kEventRing - 16) prof_fold(s);
+        s.qp_step = !s.lowmem;
     }
     return PMPM_OK;
 }
@@ -605,6 +608,7 @@ int pmpm_power_spectrum(pmpm_sim* h, int32_t nmesh, int32_t nbins, double* k, do
         if (rc) return rc;
         s.offsets_valid = true;
     }
+    s.qp_step = false;
     int rc = power_spectrum(s, nmesh, nbins, k, pk, nmodes);
     if (rc) return rc;
     return sync_and_check(s);
@@ -628,13 +632,18 @@ int pmpm_fetch(pmpm_sim* h, int32_t what, void* dst, size_t bytes) {
         case PMPM_SCALARS: need = sizeof(pmpm_scalars); break;
         case PMPM_DECODED_Q: case PMPM_DECODED_P: case PMPM_FORCE: need = 12 * N; break;
         case PMPM_COARSE_DENSITY: need = 8 * C; break;
+        case PMPM_STEP_QP: need = 24 * N; break;
         default: return set_error(s, PMPM_EINVAL, "unknown fetch item %d", what);
     }
-    if (s.lowmem && (what == PMPM_DECODED_Q || what == PMPM_DECODED_P || what == PMPM_FORCE))
+    if (s.lowmem && (what == PMPM_DECODED_Q || what == PMPM_DECODED_P || what == PMPM_FORCE ||
+                     what == PMPM_STEP_QP))
         return set_error(s, PMPM_EINVAL, "fetch %d needs the per-particle buffers a low-memory sim "
                          "does not have", what);
     if (bytes != need) return set_error(s, PMPM_EINVAL, "fetch %d needs %zu bytes, got %zu", what, need, bytes);
     if (!s.have_state) return set_error(s, PMPM_ESTATE, "no particle state");
+    if (what == PMPM_STEP_QP && !s.qp_step)
+        return set_error(s, PMPM_ESTATE, "no step result: fetch STEP_QP right after pmpm_step");
+    if (what == PMPM_DECODED_Q || what == PMPM_DECODED_P || what == PMPM_FORCE) s.qp_step = false;
     int rc = PMPM_OK;
     if (!s.offsets_valid && what != PMPM_STREAMS && what != PMPM_COUNTS && what != PMPM_VC &&
         what != PMPM_SCALARS) {
@@ -673,14 +682,50 @@ int pmpm_fetch(pmpm_sim* h, int32_t what, void* dst, size_t bytes) {
             if ((rc = coarse_deposit(s))) return rc;
             rc = copy_out(s, dst, s.rho_c, need);
             break;
+        case PMPM_STEP_QP:
+            rc = copy_out(s, dst, s.Qn, 12 * N);
+            if (!rc) rc = copy_out(s, static_cast<uint8_t*>(dst) + 12 * N, s.Pn, 12 * N);
+            break;
     }
     if (rc) return rc;
+    return sync_and_check(s);
+}
+
+int pmpm_fetch_tile_density(pmpm_sim* h, int32_t tile, uint32_t* dst, size_t bytes, int32_t* origin,
+                            int32_t* tile_edge) {
+    if (!h || !dst) return PMPM_EINVAL;
+    Sim& s = h->s;
+    const int64_t ntiles = (int64_t)s.nt * s.nt * s.nt;
+    if (tile < 0 || tile >= ntiles)
+        return set_error(s, PMPM_EINVAL, "tile %d outside [0, %lld)", tile, (long long)ntiles);
+    const size_t need = sizeof(uint32_t) * kTileFFT * kTileFFT * kTileFFT;
+    if (bytes != need) return set_error(s, PMPM_EINVAL, "a tile box needs %zu bytes, got %zu", need, bytes);
+    if (s.scratch_bytes < need)
+        return set_error(s, PMPM_EINVAL, "the workspace scratch (%zu bytes) cannot hold a tile box",
+                         s.scratch_bytes);
+    if (!s.have_state) return set_error(s, PMPM_ESTATE, "no particle state");
+    int rc = PMPM_OK;
+    if (!s.offsets_valid) {
+        if ((rc = scan_counts(s, s.counts[s.cur], s.offsets[s.cur]))) return rc;
+        s.offsets_valid = true;
+    }
+    s.qp_step = false;
+    uint32_t* d = reinterpret_cast<uint32_t*>(s.scratch);
+    if ((rc = tile_density(s, tile, d))) return rc;
+    if ((rc = copy_out(s, dst, d, need))) return rc;
+    const int t[3] = {tile % s.nt, (tile / s.nt) % s.nt, tile / (s.nt * s.nt)};
+    for (int d3 = 0; d3 < 3; ++d3) {
+        const int c0 = tile_bound(t[d3], s.nc, s.nt), c1 = tile_bound(t[d3] + 1, s.nc, s.nt);
+        if (origin) origin[d3] = kRatio * c0 - kBuffer;
+        if (tile_edge) tile_edge[d3] = kRatio * (c1 - c0);
+    }
     return sync_and_check(s);
 }
 
 int pmpm_load(pmpm_sim* h, int32_t what, const void* src, size_t bytes) {
     if (!h || !src) return PMPM_EINVAL;
     Sim& s = h->s;
+    s.qp_step = false;
     const size_t N = (size_t)s.n, C = (size_t)s.ncells;
     cudaError_t e = cudaSuccess;
     switch (what) {

@@ -35,6 +35,7 @@ struct Sim {
     bool have_state = false;
     int loaded = 0;                              // bits: streams, counts, v_c, scalars
     bool offsets_valid = false;
+    bool qp_step = false;                        // Qn/Pn hold the last step's new codes/momenta
     double a = 0.0;
     int64_t step = 0;
 
@@ -120,6 +121,7 @@ int fft_pass_count(int n);
 int coarse_force(Sim& s);             // deposit + FFT + Green -> s.Fl
 int coarse_deposit(Sim& s);           // -> s.rho_c
 int tile_pass(Sim& s, int mode, float* G);
+int tile_density(Sim& s, int tile, uint32_t* d_out);   // one tile's fine box after the deposit
 void tile_setup();
 void fft_setup();
 int scan_counts(Sim& s, const int32_t* counts, int64_t* offsets);

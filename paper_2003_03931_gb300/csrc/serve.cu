@@ -162,6 +162,8 @@ int request_config(const pmpm_request& r, pmpm_config* c, int* nmesh, int* nbins
     c->a_init = r.a_init;
     c->a_final = r.a_final;
     c->n_steps = r.n_steps;
+    if (r.flags & ~PMPM_FLAG_LOWMEM) return snprintf(msg, len, "unknown flags 0x%x", r.flags), PMPM_EINVAL;
+    c->flags = r.flags;
     const int nf = 4 * r.nc;
     int m = r.pk_nmesh ? r.pk_nmesh : std::min(r.np, nf);
     if (!pow2(m) || m > nf || m < 4 || nf % m || nf / m > 4)

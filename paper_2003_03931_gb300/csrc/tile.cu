@@ -145,13 +145,40 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_lowmem(TileParams P) {
     tile_body<true, 1>((int)blockIdx.x, P, tile_smem, cs);
 }
 
+// One tile's fine-mesh box right after the deposit, written out in x-fastest
+// node order (a check of the integer CIC; not part of a step).
+template <int PB>
+__global__ void __launch_bounds__(kTileThreads, 1) k_tile_density(TileParams P, int tile,
+                                                                   uint32_t* out) {
+    extern __shared__ __align__(16) unsigned char tile_smem[];
+    uint32_t* R = reinterpret_cast<uint32_t*>(tile_smem);
+    float2* W = reinterpret_cast<float2*>(tile_smem + (size_t)kTileR * 4);
+    float* gS = reinterpret_cast<float*>(tile_smem + (size_t)kTileR * 4 + (size_t)kTileW * 8);
+    int* O = reinterpret_cast<int*>(gS + kGreenPacked);
+    const int tid = threadIdx.x;
+    const TileGeom g = tile_geom(tile, P.nc, P.nt);
+    const TileCells cells = tile_cells(W, O);
+    tile_prologue(tid, g, P, cells, R, gS);
+    __syncthreads();
+    tile_cells_scan(tid, g, cells);
+    __syncthreads();
+    tile_cells_map(tid, g, cells);
+    __syncthreads();
+    tile_deposit_halo<PB>(tid, g, P, R, cells);
+    __syncthreads();
+    for (int i = tid; i < kTileR; i += kTileThreads) out[i] = R[ridx(i & 31, (i >> 5) & 31, i >> 10)];
+}
+
 void tile_setup() {
     cudaFuncSetAttribute(k_tile<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemBytes);
     cudaFuncSetAttribute(k_tile<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemBytes);
     cudaFuncSetAttribute(k_tile_lowmem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemBytes);
+    cudaFuncSetAttribute(k_tile_density<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemBytes);
+    cudaFuncSetAttribute(k_tile_density<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemBytes);
 }
 
-int tile_pass(Sim& s, int mode, float* G) {
+// the parameters every tile kernel reads: the current store, the tables and F_l
+static TileParams base_params(Sim& s) {
     TileParams P{};
     P.nc = s.nc;
     P.nt = s.nt;
@@ -169,12 +196,17 @@ int tile_pass(Sim& s, int mode, float* G) {
     P.Tdec = s.Tdec;
     P.green = s.green_packed;
     P.Fl = s.Fl;
-    P.mode = mode;
     P.kd = s.d_kd;
-    P.G = G;
     P.Qn = s.Qn;
     P.Pn = s.Pn;
     P.err = s.err;
+    return P;
+}
+
+int tile_pass(Sim& s, int mode, float* G) {
+    TileParams P = base_params(s);
+    P.mode = mode;
+    P.G = G;
     const int ntiles = s.nt * s.nt * s.nt;
     int grid = ntiles;
     if (mode == 1) {
@@ -200,6 +232,15 @@ int tile_pass(Sim& s, int mode, float* G) {
     else k_tile<1><<<grid, kTileThreads, kTileSmemBytes, s.stream>>>(P);
     s.launches++;
     return check_launch(s, "tile pass");
+}
+
+int tile_density(Sim& s, int tile, uint32_t* d_out) {
+    TileParams P = base_params(s);
+    P.mode = 0;
+    if (s.pb == 2) k_tile_density<2><<<1, kTileThreads, kTileSmemBytes, s.stream>>>(P, tile, d_out);
+    else k_tile_density<1><<<1, kTileThreads, kTileSmemBytes, s.stream>>>(P, tile, d_out);
+    s.launches++;
+    return check_launch(s, "tile density");
 }
 
 }  // namespace pmpm

@@ -608,9 +608,10 @@ PMPM_HD int own_of(const TileCells& c, int v) {
 constexpr int kDepositIlp = 4;   // halo particles per thread per iteration
 constexpr int kGatherIlp = 2;    // own particles per thread per iteration
 
-template <bool LM, int PB>
-PMPM_HD void tile_deposit_flat(int tid, const TileGeom& g, const TileParams& P, uint32_t* R,
-                               TileCells c, CtaScratch cs) {
+// the integer CIC of the halo box's particles into R
+template <int PB>
+PMPM_HD void tile_deposit_halo(int tid, const TileGeom& g, const TileParams& P, uint32_t* R,
+                               TileCells c) {
     const int total = c.pre[kHaloMax];
     const bool check = c.misc[2] > 255;
     for (int v0 = tid; v0 < total; v0 += kDepositIlp * kTileThreads) {
@@ -637,7 +638,13 @@ PMPM_HD void tile_deposit_flat(int tid, const TileGeom& g, const TileParams& P, 
             else deposit_one<false, PB>(g, cu, m[u], R, P.err);
         }
     }
-    // long-range force of the tile's own particles
+}
+
+// the long-range force of the tile's own particles, parked in their output
+// slots (low-memory passes: the CTA's scratch)
+template <bool LM, int PB>
+PMPM_HD void tile_gather_coarse(int tid, const TileGeom& g, const TileParams& P, TileCells c,
+                                CtaScratch cs) {
     float* slot = P.mode == 0 ? P.G : P.Pn;
     const int ptotal = c.ppre[kOwnMax];
     const int64_t obase = own_base(c);
@@ -675,6 +682,13 @@ PMPM_HD void tile_deposit_flat(int tid, const TileGeom& g, const TileParams& P, 
             for (int e = 0; e < 3; ++e) slot[e * P.n + j[u]] = gc[e];
         }
     }
+}
+
+template <bool LM, int PB>
+PMPM_HD void tile_deposit_flat(int tid, const TileGeom& g, const TileParams& P, uint32_t* R,
+                               TileCells c, CtaScratch cs) {
+    tile_deposit_halo<PB>(tid, g, P, R, c);
+    tile_gather_coarse<LM, PB>(tid, g, P, c, cs);
 }
 
 // --- phase 2: forward real transform along x (1024 rows, 2 per thread) -----

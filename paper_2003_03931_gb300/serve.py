@@ -31,6 +31,7 @@ class Request:
     pk_nmesh: int = 0            # 0: min(np, 4 nc)
     pk_nbins: int = 0            # 0: pk_nmesh / 2
     want_state: bool = False     # also return the final store (streams, counts)
+    lowmem: bool = False         # the low-memory step (PMPM_FLAG_LOWMEM)
 
     @property
     def n(self):
@@ -96,7 +97,8 @@ class Engine:
         if req.want_state:
             out["streams"] = np.zeros((6, req.n), np.uint8)
             out["counts"] = np.zeros(req.nc ** 3, np.int32)
-        r = _lib.Request(req.np, req.nc, req.n_steps, req.pk_nmesh, req.pk_nbins, 0,
+        r = _lib.Request(req.np, req.nc, req.n_steps, req.pk_nmesh, req.pk_nbins,
+                         _lib.FLAG_LOWMEM if req.lowmem else 0,
                          req.a_init, req.a_final, req.seed, req.slope, req.k_c, req.rms_disp,
                          req.arrival, out["k"].ctypes.data, out["pk"].ctypes.data,
                          out["nmodes"].ctypes.data,

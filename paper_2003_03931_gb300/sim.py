@@ -176,6 +176,23 @@ class Simulation:
     def fetch_force(self):
         return self._fetch(_lib.FORCE, np.empty((3, self.cfg.n), np.float32))
 
+    def fetch_step_qp(self):
+        """New codes Q' [3, N] int32 and kicked momenta p' [3, N] float32 of
+        the last step, in the storage order that step started from."""
+        n = self.cfg.n
+        buf = self._fetch(_lib.STEP_QP, np.empty(24 * n, np.uint8))
+        return buf[:12 * n].view(np.int32).reshape(3, n), buf[12 * n:].view(np.float32).reshape(3, n)
+
+    def fetch_tile_density(self, tile):
+        """(uint32 [32, 32, 32] fine box indexed [z, y, x], origin (3,) in fine
+        nodes, tile edge (3,) in fine cells) of one tile after its deposit."""
+        box = np.empty((32, 32, 32), np.uint32)
+        org = np.zeros(3, np.int32)
+        edge = np.zeros(3, np.int32)
+        self._check(self.lib.pmpm_fetch_tile_density(self.h, tile, box.ctypes.data, box.nbytes,
+                                                     org.ctypes.data, edge.ctypes.data))
+        return box, org, edge
+
     def fetch_coarse_density(self):
         return self._fetch(_lib.COARSE_DENSITY, np.empty(self.cfg.ncells, np.int64))
 

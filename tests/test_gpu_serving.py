@@ -16,7 +16,8 @@ def _solo(req):
     from paper_2003_03931_gb300.sim import SimConfig, Simulation
     m, nb = req.mesh()
     sim = Simulation(SimConfig(np=req.np, nc=req.nc, a_init=req.a_init, a_final=req.a_final,
-                               n_steps=req.n_steps, pk_mesh_max=m), device="cuda:0")
+                               n_steps=req.n_steps, pk_mesh_max=m, lowmem=req.lowmem),
+                     device="cuda:0")
     sim.ic_zeldovich(req.seed, req.slope, req.k_c, req.rms_disp)
     sim.step(req.n_steps)
     k, pk, nm = sim.power_spectrum(m, nb)
@@ -36,6 +37,68 @@ def _mix():
                     want_state=True)]
 
 
+def _large_mix():
+    # the large boxes of the serving mix (128^3, 256^3 particles) next to
+    # small ones, and low-memory boxes (three tile passes per step) among them
+    from paper_2003_03931_gb300.serve import Request
+    return [Request(np=256, nc=128, n_steps=3, seed=21, slope=-1.5, want_state=True),
+            Request(np=32, nc=16, n_steps=5, seed=22, slope=-1.2, want_state=True),
+            Request(np=128, nc=64, n_steps=4, seed=23, slope=-1.8, want_state=True),
+            Request(np=64, nc=32, n_steps=3, seed=24, slope=-1.5, want_state=True, lowmem=True),
+            Request(np=128, nc=64, n_steps=2, seed=25, slope=-2.0, want_state=True, lowmem=True),
+            Request(np=64, nc=32, n_steps=4, seed=26, slope=-1.0, want_state=True)]
+
+
+def _check_against_solo(reqs, res):
+    for req, r in zip(reqs, res):
+        assert r.status == 0
+        k, pk, nm, st = _solo(req)
+        np.testing.assert_array_equal(r.nmodes, nm)
+        np.testing.assert_allclose(r.k, k, rtol=1e-12)
+        np.testing.assert_allclose(r.pk, pk, rtol=1e-12)
+        np.testing.assert_array_equal(r.counts, st["counts"])
+        a = cell_sorted_records(r.counts, r.streams.T)
+        b = cell_sorted_records(st["counts"], st["streams"].T)
+        np.testing.assert_array_equal(a, b)
+        assert np.float32(r.sigma) == np.float32(st["scalars"]["sigma"])
+        assert r.a == st["scalars"]["a"]
+        assert r.particle_steps == req.n * req.n_steps
+        assert r.t_arrival <= r.t_admit <= r.t_done
+
+
+@pytest.mark.parametrize("kw", [
+    dict(max_active=6, share_tables=True, graphs=True, priorities=True, steps_per_chunk=2),
+    dict(max_active=3, share_tables=False, graphs=False, priorities=True, steps_per_chunk=1),
+])
+def test_large_and_lowmem_boxes_equal_solo_runs(kw):
+    need_gpu()
+    from paper_2003_03931_gb300.serve import Engine, run_stream
+    reqs = _large_mix()
+    eng = Engine(8 << 30, **kw)
+    res = run_stream(eng, reqs, timeout=600)
+    stats = eng.stats()
+    eng.close()
+    assert stats["completed"] == len(reqs) and stats["failed"] == 0
+    _check_against_solo(reqs, res)
+
+
+def test_request_flags_are_checked():
+    need_gpu()
+    from paper_2003_03931_gb300 import _lib
+    from paper_2003_03931_gb300.serve import Engine, Request
+    eng = Engine(1 << 28, max_active=2)
+    req = Request(np=32, nc=16, n_steps=2, seed=3)
+    nb = req.mesh()[1]
+    k, pk, nm = np.zeros(nb), np.zeros(nb), np.zeros(nb, np.int64)
+    import ctypes
+    r = _lib.Request(32, 16, 2, 0, 0, 2, 0.02, 1.0, 3, -1.5, np.pi / 2, 0.3, 0.0,
+                     k.ctypes.data, pk.ctypes.data, nm.ctypes.data, None, None)
+    rid = ctypes.c_int64()
+    rc = eng.lib.pmpm_batch_submit(eng.h, ctypes.byref(r), ctypes.byref(rid))
+    assert rc == _lib.PMPM_EINVAL
+    eng.close()
+
+
 @pytest.mark.parametrize("kw", [
     dict(max_active=4, share_tables=True, graphs=True, priorities=True, steps_per_chunk=2),
     dict(max_active=6, share_tables=True, graphs=False, priorities=False, steps_per_chunk=1,
@@ -53,20 +116,7 @@ def test_mixed_batch_equals_solo_runs(kw):
     assert stats["completed"] == len(reqs) and stats["failed"] == 0
     assert stats["table_builds"] == (3 if kw["share_tables"] else len(reqs))
     assert stats["launches"] > 0
-    for req, r in zip(reqs, res):
-        assert r.status == 0
-        k, pk, nm, st = _solo(req)
-        np.testing.assert_array_equal(r.nmodes, nm)
-        np.testing.assert_allclose(r.k, k, rtol=1e-12)
-        np.testing.assert_allclose(r.pk, pk, rtol=1e-12)
-        np.testing.assert_array_equal(r.counts, st["counts"])
-        a = cell_sorted_records(r.counts, r.streams.T)
-        b = cell_sorted_records(st["counts"], st["streams"].T)
-        np.testing.assert_array_equal(a, b)
-        assert np.float32(r.sigma) == np.float32(st["scalars"]["sigma"])
-        assert r.a == st["scalars"]["a"]
-        assert r.particle_steps == req.n * req.n_steps
-        assert r.t_arrival <= r.t_admit <= r.t_done
+    _check_against_solo(reqs, res)
 
 
 def test_admission_within_a_tight_arena():
