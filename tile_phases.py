@@ -1,11 +1,12 @@
-"""Per-phase clock breakdown of the tile pass (a diagnostic, not the product).
+"""Per-phase clock breakdown of the tile pass: a measurement tool beside
+bench.py (the library itself is not built with it).
 
 Builds a second copy of the library with -DPMPM_PHASE_CLOCKS, in which
 thread 0 of every tile CTA stamps clock64() after each block barrier of the
 tile pass, runs a box, and prints the mean cycles per phase over the first
 4096 tiles of the chosen steps:
 
-    python -m paper_2003_03931_gb300.tile_phases [--workload c3_512] [--steps 1 10 20]
+    python tile_phases.py [--workload c3_512] [--steps 1 10 20]
 """
 
 import argparse
@@ -15,8 +16,10 @@ import sys
 
 import numpy as np
 
-HERE = os.path.dirname(os.path.abspath(__file__))
-PROF_LIB = os.path.join(HERE, "_build_phases", "libpmpm_phases.so")
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+PKG = os.path.join(ROOT, "paper_2003_03931_gb300")
+PROF_LIB = os.path.join(PKG, "_build_phases", "libpmpm_phases.so")
 
 # stamp k closes phase k - 1; names follow the kernel's phase order
 PHASES = ["prologue (loads, zero)", "halo scan + cell maps", "deposit + long-range gather",
@@ -34,13 +37,13 @@ def main(argv=None):
     ap.add_argument("--workload", default="c3_512")
     ap.add_argument("--steps", type=int, nargs="+", default=[1, 10, 20])
     args = ap.parse_args(argv)
-    from . import build
+    from paper_2003_03931_gb300 import build
     build.build(defines=("PMPM_PHASE_CLOCKS",), lib=PROF_LIB,
-                build_dir=os.path.join(HERE, "_build_phases"))
-    from . import _lib
+                build_dir=os.path.join(PKG, "_build_phases"))
+    from paper_2003_03931_gb300 import _lib
     _lib.LIB_PATH = PROF_LIB
-    from . import synth
-    from .sim import SimConfig, Simulation
+    from paper_2003_03931_gb300 import synth
+    from paper_2003_03931_gb300.sim import SimConfig, Simulation
     w = dict(synth.WORKLOADS[args.workload])
     w["n_steps"] = max(w["n_steps"], max(args.steps) + 1)
     sim = Simulation(SimConfig(**w))
