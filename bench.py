@@ -1,23 +1,23 @@
 #!/usr/bin/env python3
 """Benchmark of the PM-PM step (particle-steps/s) on GB300.
 
-Default workload: 512^3 particles, 256^3 coarse cells, 1024^3 fine cells in
-tiles of 16/20 fine cells + 6-cell buffer, Zel'dovich ICs (power-law
-spectrum, seeded), a = 0.02 -> 1 over warmup + steps steps.  One JSON line
-on rank 0.  With one GPU the line also carries a serving measurement: a
-mixed stream of whole-box requests through the batched engine against
-sequential plain stepping (--serving, --serving-rates, --serving-only).
+Headline workload: 2048^3 particles (51.5 GB at 6 bytes per particle) on
+1024^3 coarse cells and a 4096^3 fine mesh in tiles of 16/20 fine cells + a
+6-cell buffer, stepped by the low-memory step (three tile passes per step) on
+one GPU; Zel'dovich ICs from a seeded power-law spectrum; a = 0.02 -> 1 over
+all steps.  Beside it the line carries the same measurement at 512^3
+particles (default step, one tile pass), the plain float32 full-mesh PM with
+the same total force kernel at 512^3 ("vs plain GPU form"; at 2048^3 its
+mesh alone would not fit), the measured FP32 FMA peak that the tile passes'
+roofline divides by, the tile transforms done by cuFFT, the FP64 oracle on
+the host cores, and the serving measurement (a mixed stream of whole-box
+requests through the batched engine against sequential plain stepping).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Under torchrun each rank evolves its own box (independent replicas, weak
 scaling); value is the particle-steps of all ranks over the slowest rank's
 time.  --impl reference times the FP64 oracle on the host cores instead.
-
-Optional objects on the line (one GPU): --fma-probe measures the FP32 FMA
-peak and uses it as the roofline's denominator; --library-fft times the
-tile transforms done by torch.fft (cuFFT) instead; --plain-pm STEPS times
-the plain float32 full-mesh PM step (class PlainPM) on the same particles.
 """
 
 import os
@@ -51,25 +51,26 @@ TILE_FILES = ["paper_2003_03931_gb300/csrc/tile_core.cuh", "paper_2003_03931_gb3
 def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="c3_512")
-    ap.add_argument("--e2e-steps", type=int, default=8)
+    ap.add_argument("--workload", default="c4_2048")
+    ap.add_argument("--side-workload", default="c3_512",
+                    help="a second box measured beside the headline (one GPU; empty: none)")
+    ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving", type=int, default=120,
                     help="requests in the serving measurement (0: skip)")
-    ap.add_argument("--serving-rates", default="1.0",
+    ap.add_argument("--serving-rates", default="0.5,1.0,1.5",
                     help="Poisson arrival rates for the latency runs, as fractions of the "
                          "sequential capacity (comma list; empty: skip)")
     ap.add_argument("--serving-only", action="store_true")
-    ap.add_argument("--fma-probe", action="store_true",
-                    help="measure the FP32 FMA peak with the library's probe and use it as the peak")
-    ap.add_argument("--library-fft", action="store_true",
-                    help="also time the tile transforms with torch.fft (cuFFT) for comparison")
-    ap.add_argument("--plain-pm", type=int, default=0, metavar="STEPS",
-                    help="also time STEPS steps of the plain float32 full-mesh PM comparator")
+    ap.add_argument("--no-fma-probe", action="store_true",
+                    help="divide by the lanes x clock FP32 peak instead of the measured one")
+    ap.add_argument("--no-library-fft", action="store_true")
+    ap.add_argument("--plain-pm", type=int, default=3, metavar="STEPS",
+                    help="steps of the plain float32 full-mesh PM comparator (0: skip)")
     return ap.parse_args(argv)
 
 
@@ -84,9 +85,47 @@ def tile_flops_per_launch(nc, tile_max=5):
     return 4 * 2.5 * m * math.log2(m) * nt ** 3
 
 
-def fp32_peak_tflops(sm_mhz):
-    """152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x SM clock."""
-    return SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+def fp32_peak_tflops(sm_mhz, sms=SM_COUNT):
+    """SMs x 128 FP32 lanes x 2 FLOP (FMA) x SM clock."""
+    return sms * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+# Algorithmic HBM bytes of the memory-bound stages: (per particle, per coarse
+# cell), the least each stage must move.
+HBM_STAGE_BYTES = {
+    # position bins in; counts and offsets in, int64 density out
+    "coarse_deposit": (3, 20),
+    # density in and spectrum out, spectrum in and F_l out (one pass each way)
+    "coarse_fft_green": (0, 36),
+    # counts and momentum sums in; offsets and v_c out
+    "hist_scan_cell_means": (0, 48),
+    "scan_cell_means": (0, 48),
+    # new codes and momenta in, v_c in
+    "dispersion": (24, 12),
+    # new codes and momenta in, store out; v_c and offsets in
+    "encode_scatter": (30, 20),
+}
+
+
+def stage_rooflines(stage_ms, n, ncells, hbm_gbs, tile_flops, fp32_tflops):
+    """Per-stage achieved rate against its roofline: HBM stages in GB/s of
+    algorithmic bytes over the measured copy bandwidth, tile passes in
+    TFLOP/s of algorithmic FLOPs over the FP32 FMA peak."""
+    out = {}
+    for name, ms in stage_ms.items():
+        if ms <= 0:
+            continue
+        if name in HBM_STAGE_BYTES:
+            bp, bc = HBM_STAGE_BYTES[name]
+            gb = (bp * n + bc * ncells) / 1e9
+            rate = gb / (ms / 1e3)
+            out[name] = {"bound": "hbm", "ms": ms, "algorithmic_gb": gb, "achieved": rate,
+                         "unit": "GB/s", "peak": hbm_gbs, "frac": rate / hbm_gbs if hbm_gbs else None}
+        elif name.startswith("tile"):
+            rate = tile_flops / (ms / 1e3) / 1e12
+            out[name] = {"bound": "alu", "ms": ms, "achieved": rate, "unit": "TFLOP/s",
+                         "peak": fp32_tflops, "frac": rate / fp32_tflops}
+    return out
 
 
 def _code_only(text):
@@ -105,10 +144,11 @@ def source_hash(paths):
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload):
+def recorded_traffic(workload, lowmem=False):
     """DRAM bytes per tile-pass launch from the committed ncu summary, if it
     was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", f"tile_pass_{workload}.md")
+    name = f"tile_pass_lowmem_{workload}.md" if lowmem else f"tile_pass_{workload}.md"
+    path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
     vals = {}
@@ -219,6 +259,19 @@ def time_oracle_steps(np_side, nc, warmup, steps):
     return np_side ** 3 * steps / dt, dt
 
 
+# The oracle's bounded sample of every workload: steps of a 128^3-particle
+# box (64^3 coarse, 256^3 fine), the same per-particle work as the 512^3 and
+# 2048^3 boxes (8 particles per coarse cell, 8 fine cells per particle).
+ORACLE_SAMPLE = (128, 64)
+
+
+def oracle_sample_text(steps, seconds):
+    return ("FP64 oracle, %d step(s) of a %d^3-particle box (%d^3 coarse, %d^3 fine cells: "
+            "the same 8 particles per coarse cell and 8 fine cells per particle as the "
+            "timed workload), %.1f s" % (steps, ORACLE_SAMPLE[0], ORACLE_SAMPLE[1],
+                                         4 * ORACLE_SAMPLE[1], seconds))
+
+
 def oracle_cores():
     # numpy.fft (pocketfft) and np.add.at run on one thread; no BLAS is used
     return 1
@@ -226,28 +279,27 @@ def oracle_cores():
 
 # ------------------------------------------------------------------ our arm
 
-def run_ours(args):
-    import numpy as np
+def measure_box(workload, K, W, E, local, world, rank):
+    """One box: ICs, W warm-up steps, K steps timed with CUDA events on the
+    library's stream (clocks sampled meanwhile, per-stage times recorded),
+    then E end-to-end steps through the C ABI from pinned host buffers (load
+    the store, step, fetch the store).  Returns the measurement and the
+    still-open sim."""
     import torch
 
     from paper_2003_03931_gb300 import synth
     from paper_2003_03931_gb300.sim import SimConfig, Simulation
 
-    world, rank, local = dist_setup(args)
-    torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    w = dict(synth.WORKLOADS[args.workload])
-    K, W = args.steps, args.warmup
-    E = 0 if args.no_e2e else args.e2e_steps
+    w = dict(synth.WORKLOADS[workload])
     w["n_steps"] = W + K + E
     cfg = SimConfig(**w)
     sim = Simulation(cfg, device=f"cuda:{local}")
     stream = sim.stream
+    t_ic = time.perf_counter()
     sim.ic_zeldovich(1 + rank, **synth.IC_SPECTRUM)
     sim.step(W)
     sim.sync()
+    t_ic = time.perf_counter() - t_ic
 
     def barrier():
         if world > 1:
@@ -272,7 +324,6 @@ def run_ours(args):
     sim.sync()
     t = reduce_max(t, f"cuda:{local}")
 
-    # end to end through the C ABI with pinned host buffers
     e2e = None
     if E:
         n, C = cfg.n, cfg.ncells
@@ -294,116 +345,213 @@ def run_ours(args):
         te = reduce_max(time.perf_counter() - t0, f"cuda:{local}")
         per = (3 * pb + 3) * n + 4 * C + 12 * C + 32
         e2e = {"value": job_rate(n * E, world, te), "unit": UNIT, "h2d_bytes_per_step": per,
-               "d2h_bytes_per_step": per, "steps": E}
-
-    if rank != 0:
-        sim.close()
-        return None
-
-    n = cfg.n
-    value = job_rate(n * K, world, t)
-    flops = tile_flops_per_launch(cfg.nc, cfg.tile_max)
-    # the low-memory step launches the tile pass three times (stages 2, 4, 5)
-    tile_launches = 3 if cfg.lowmem else 1
-    tile_ms = stages[2] + (stages[4] + stages[5] if cfg.lowmem else 0.0)
-    tile_s = tile_ms / 1000.0 / (K * tile_launches)
-    sm_max = clocks.get("sm_max_mhz") or measured_peaks().get("sm_max_mhz") or 2070.0
-    peak = fp32_peak_tflops(sm_max)
-    achieved = flops / tile_s / 1e12 if tile_s > 0 else None
-    roofline = {"bound": "alu", "kernel": "k_tile (tile fine PM + kick + drift)",
-                "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak if achieved else None,
-                "traffic": recorded_traffic(args.workload),
-                "peak_basis": "FP32 FMA: 152 SMs x 128 lanes x 2 x %d MHz (max SM clock)" % sm_max,
-                "flops_per_launch": flops, "avg_launch_ms": tile_s * 1000.0,
-                "launches_per_step": tile_launches}
-    if args.fma_probe:
-        measured = probe_fp32_tflops(torch.device(f"cuda:{local}"))
-        roofline.update({"peak": measured, "frac": achieved / measured if achieved else None,
-                         "peak_derived": peak,
-                         "peak_basis": "measured: FP32 FMA probe (pmpm_probe_fma), best of 5"})
-    hbm = measured_peaks().get("hbm_gbs")
+               "d2h_bytes_per_step": per, "steps": E,
+               "what": "per step: pmpm_load of the whole state from pinned host memory, "
+                       "pmpm_step, pmpm_fetch of the whole state back"}
+        del host
     stage_names = ["coarse_deposit", "coarse_fft_green", "tile_pm_kick_drift", "hist_scan_cell_means",
                    "dispersion", "encode_scatter"]
     if cfg.lowmem:
         stage_names = ["coarse_deposit", "coarse_fft_green", "tile_pass_count", "scan_cell_means",
                        "tile_pass_dispersion", "tile_pass_scatter"]
+    return {"cfg": cfg, "sim": sim, "t": t, "K": K, "W": W, "value": job_rate(cfg.n * K, world, t),
+            "stages": {k: v / K for k, v in zip(stage_names, stages)}, "launches": launches,
+            "clocks": clocks, "e2e": e2e, "setup_s": t_ic, "workspace_gb": sim.workspace.numel() / 1e9}
+
+
+def box_roofline(m, workload, fp32_peak, peak_basis, hbm):
+    """The dominant kernel's roofline (the tile pass) and every stage's."""
+    cfg = m["cfg"]
+    flops = tile_flops_per_launch(cfg.nc, cfg.tile_max)
+    tile_stages = [k for k in m["stages"] if k.startswith("tile")]
+    tile_ms = sum(m["stages"][k] for k in tile_stages)
+    launches = len(tile_stages)
+    avg_ms = tile_ms / launches
+    achieved = flops / (avg_ms / 1e3) / 1e12
+    kernel = ("k_tile_lowmem (three tile passes: counting, dispersion, scatter)" if cfg.lowmem
+              else "k_tile (tile fine PM + kick + drift)")
+    roof = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": fp32_peak,
+            "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+            "traffic": recorded_traffic(workload, lowmem=cfg.lowmem),
+            "peak_basis": peak_basis, "flops_per_launch": flops, "avg_launch_ms": avg_ms,
+            "launches_per_step": launches}
+    stages = stage_rooflines(m["stages"], cfg.n, cfg.ncells, hbm, flops, fp32_peak)
+    return roof, stages
+
+
+def box_config(m, workload, world):
+    cfg = m["cfg"]
+    n = cfg.n
+    return {"workload": workload, "particles": n, "np": cfg.np, "nc": cfg.nc, "nf": 4 * cfg.nc,
+            "step": "low-memory (3 tile passes)" if cfg.lowmem else "default",
+            "workspace_gb": m["workspace_gb"], "tile_fine": "16/20 + 6 buffer in 32^3",
+            "schedule": f"a 0.02->1 in {cfg.n_steps} steps, timed steps {m['W'] + 1}..{m['W'] + m['K']}",
+            "parallelism": f"replicas x{world}", "bytes_per_particle_store": 3 * cfg.pos_bytes + 3,
+            "l2": "inputs larger than L2 (%.0f MB particle store)" % ((3 * cfg.pos_bytes + 3) * n / 1e6)}
+
+
+def run_ours(args):
+    import torch
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device(f"cuda:{local}")
+    K, W = args.steps, args.warmup
+    E = 0 if args.no_e2e else args.e2e_steps
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    m = measure_box(args.workload, K, W, E, local, world, rank)
+    m["sim"].close()
+    del m["sim"]
+    torch.cuda.empty_cache()
+    if rank != 0:
+        return None
+
+    sm_max = m["clocks"].get("sm_max_mhz") or measured_peaks().get("sm_max_mhz") or 2070.0
+    derived = fp32_peak_tflops(sm_max, sms)
+    peak, basis = derived, "FP32 FMA: %d SMs x 128 lanes x 2 x %d MHz (max SM clock)" % (sms, sm_max)
+    if not args.no_fma_probe:
+        peak = probe_fp32_tflops(dev)
+        basis = "measured: FP32 FMA probe (pmpm_probe_fma), best of 5"
+    hbm = measured_peaks().get("hbm_gbs")
+    roof, stage_roof = box_roofline(m, args.workload, peak, basis, hbm)
+    if not args.no_fma_probe:
+        roof["peak_derived"] = derived
     out = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
-        "warmup": W, "ms_per_step": t / K * 1000.0, "higher_is_better": True,
+        "metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": W, "ms_per_step": m["t"] / K * 1000.0, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "particles": n, "np": cfg.np, "nc": cfg.nc,
-                   "step": "low-memory (3 tile passes)" if cfg.lowmem else "default",
-                   "workspace_gb": sim.workspace.numel() / 1e9,
-                   "nf": 4 * cfg.nc, "tile_fine": "16/20 + 6 buffer in 32^3",
-                   "schedule": f"a 0.02->1 in {cfg.n_steps} steps, timed steps {W + 1}..{W + K}",
-                   "parallelism": f"replicas x{world}",
-                   "bytes_per_particle_store": 3 * cfg.pos_bytes + 3,
-                   "l2": "inputs larger than L2 (%.0f MB particle store)" % ((3 * cfg.pos_bytes + 3) * n / 1e6)},
-        "e2e": e2e,
-        "gpu_launches": launches,
-        "roofline": roofline,
-        "stage_ms_per_step": {k: v / K for k, v in zip(stage_names, stages)},
+        "config": box_config(m, args.workload, world),
+        "e2e": m["e2e"],
+        "gpu_launches": m["launches"],
+        "roofline": roof,
+        "stage_ms_per_step": m["stages"],
+        "stage_roofline": stage_roof,
         "hbm_peak_gbs": hbm,
-        "clocks": clocks,
+        "clocks": m["clocks"],
+        "setup_s": m["setup_s"],
     }
     if world == 1 and not args.no_cpu_baseline:
-        v, dt = time_oracle_steps(128, 64, 0, 1)
+        v, dt = time_oracle_steps(ORACLE_SAMPLE[0], ORACLE_SAMPLE[1], 0, 2)
         out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": oracle_cores(), "kind": "oracle",
-                               "sample": "one FP64 oracle step of a 128^3-particle box "
-                                         "(64^3 coarse, 256^3 fine: the same 8 particles per "
-                                         "coarse cell and 8 fine cells per particle), %.1f s" % dt}
-    if world == 1 and args.library_fft:
-        nt = -(-cfg.nc // cfg.tile_max)
-        s_lib = time_library_tile_transforms(nt ** 3, f"cuda:{local}")
-        out["library_fft_tiles"] = {
-            "ms_per_step": s_lib * 1000.0 * tile_launches, "tiles": nt ** 3,
-            "ours_tile_pass_ms_per_step": tile_ms / K,
-            "what": "torch.fft (cuFFT) over batched 32^3 boxes in device memory: 1 R2C + 3 "
-                    "(complex multiply, C2R) per tile, the transforms alone; the tile pass also "
-                    "deposits, interpolates, kicks and drifts"}
-    if world == 1 and args.plain_pm:
-        out["plain_gpu_pm"] = run_plain_pm(cfg, sim, args.plain_pm, 1)
-        out["plain_gpu_pm"]["ours_over_plain"] = value / out["plain_gpu_pm"]["value"]
-    sim.close()
+                               "sample": oracle_sample_text(2, dt)}
+    side = None
+    if world == 1 and args.side_workload and args.side_workload != args.workload:
+        s = measure_box(args.side_workload, K, W, 0 if args.no_e2e else 8, local, world, rank)
+        sroof, sstages = box_roofline(s, args.side_workload, peak, basis, hbm)
+        side = {"value": s["value"], "unit": UNIT, "ms_per_step": s["t"] / K * 1000.0,
+                "config": box_config(s, args.side_workload, world), "e2e": s["e2e"],
+                "gpu_launches": s["launches"], "roofline": sroof, "stage_ms_per_step": s["stages"],
+                "stage_roofline": sstages, "clocks": s["clocks"]}
+        cfg = s["cfg"]
+        if not args.no_library_fft:
+            nt = -(-cfg.nc // cfg.tile_max)
+            s_lib = time_library_tile_transforms(nt ** 3, f"cuda:{local}")
+            side["library_fft_tiles"] = {
+                "ms_per_step": s_lib * 1000.0, "tiles": nt ** 3,
+                "ours_tile_pass_ms_per_step": s["stages"]["tile_pm_kick_drift"],
+                "what": "torch.fft (cuFFT) over batched 32^3 boxes in device memory: 1 R2C + 3 "
+                        "(complex multiply, C2R) per tile, the transforms alone; the tile pass also "
+                        "deposits, interpolates, kicks and drifts"}
+        if args.plain_pm:
+            plain = run_plain_pm(cfg, s["sim"], args.plain_pm, 1)
+            plain["ours_over_plain"] = s["value"] / plain["value"]
+            side["plain_gpu_pm"] = plain
+            out["plain_gpu_pm"] = dict(plain, workload=args.side_workload)
+        s["sim"].close()
+        del s["sim"]
+        torch.cuda.empty_cache()
+        out[args.side_workload] = side
+    if args.workload == "c4_2048":
+        out["plain_gpu_pm_at_workload"] = {
+            "feasible": False,
+            "why": "a float32 4096^3 mesh is 275 GB and its spectrum as much again, more than "
+                   "the GPU's 288 GB; the compressed step holds the whole box in %.0f GB"
+                   % m["workspace_gb"]}
     if world == 1 and args.serving:
         out["serving"] = run_serving(args, f"cuda:{local}")
     return out
 
 
+def periodic_kernel_spectra(nf, device, alpha=0.35, reach=16, dtype=None):
+    """Spectra of the unit-G periodic pair force (a unit mass, all its images
+    and the removed mean density) sampled at the integer separations of an
+    nf^3 mesh of unit cells, one per component: the kernel's DFT is i S_d
+    (the sampled kernel is real and odd), S_d float32 [nf, nf, nf/2 + 1].
+    The force is split as Ewald did: a Gaussian-damped Fourier sum, which is
+    exactly an inverse DFT once the damping has made the modes past the
+    mesh's Nyquist frequency negligible (exp(-pi^2 / 4 alpha^2) = 2e-9 at
+    alpha = 0.35 per cell), plus erfc-screened real-space terms of the
+    nearest image within `reach` cells on each axis (below 1e-12 of the
+    force beyond).  Built once per mesh in float64 (returned as `dtype`,
+    float32 by default)."""
+    import torch
+    # nearest images only: the reach stays inside half the box (the screened
+    # terms are below 1e-12 of the force past 15 cells)
+    reach = min(reach, nf // 2 - 1)
+    if reach < 15:
+        raise ValueError("mesh too small for the real-space part")
+    f64 = torch.float64
+    two_pi = 2.0 * math.pi
+    n = torch.fft.fftfreq(nf, d=1.0 / nf, device=device, dtype=f64)
+    nr = torch.fft.rfftfreq(nf, d=1.0 / nf, device=device, dtype=f64)
+    kz = (two_pi / nf * n).view(-1, 1, 1)
+    ky = (two_pi / nf * n).view(1, -1, 1)
+    kx = (two_pi / nf * nr).view(1, 1, -1)
+    k2 = kx * kx + ky * ky + kz * kz
+    k2[0, 0, 0] = 1.0
+    # Fourier part: F~(k) = 4 pi i k / k^2 exp(-k^2 / 4 alpha^2); modes on a
+    # Nyquist plane alias with their mirror images and are dropped
+    damp = (4.0 * math.pi) * torch.exp(-k2 / (4.0 * alpha * alpha)) / k2
+    del k2
+    damp[0, 0, 0] = 0.0
+    half = nf // 2
+    damp[half, :, :] = 0.0
+    damp[:, half, :] = 0.0
+    damp[:, :, half] = 0.0
+    # real-space part: -d/|d|^3 (erfc(alpha r) + 2 alpha r / sqrt(pi) e^(-alpha^2 r^2))
+    d = torch.arange(-reach, reach + 1, device=device, dtype=f64)
+    dz, dy, dx = torch.meshgrid(d, d, d, indexing="ij")
+    r = torch.sqrt(dx * dx + dy * dy + dz * dz)
+    r[reach, reach, reach] = 1.0
+    fac = (torch.special.erfc(alpha * r) + 2.0 * alpha * r / math.sqrt(math.pi) *
+           torch.exp(-(alpha * r) ** 2)) / r ** 3
+    fac[reach, reach, reach] = 0.0
+    iz = torch.remainder(dz.long(), nf)
+    iy = torch.remainder(dy.long(), nf)
+    ix = torch.remainder(dx.long(), nf)
+    out = []
+    for kd, dd in ((kx, dx), (ky, dy), (kz, dz)):
+        field = torch.fft.irfftn((1j * kd) * damp, s=(nf, nf, nf))
+        field[iz, iy, ix] += -dd * fac
+        out.append(torch.fft.rfftn(field).imag.to(dtype or torch.float32))
+        del field
+    return out
+
+
 class PlainPM:
     """The plain particle-mesh step that the compressed PM-PM step is measured
-    against: float32 positions (fine cells) and momenta, 24 bytes per
-    particle; CIC deposit on the whole fine mesh (4 nc per side); one
-    real-to-complex FFT; the potential 4 pi / k^2 (the transform of 1/r,
-    unit masses) and, per component, its two-point central difference
-    (i sin k_d) through one complex-to-real FFT;
-    CIC gather; the library's kick-drift schedule (equal steps in log a,
-    momenta at the geometric mid-steps).  torch.fft is cuFFT on the GPU.
-    The same code runs on CPU tensors, so its arithmetic is tested there.
-    Measurement only: not the library's method (no force split, no
-    compression)."""
+    against: one full-resolution mesh with the same total force kernel.
+    Float32 positions (fine cells) and momenta, 24 bytes per particle; CIC
+    deposit on the whole fine mesh (4 nc per side); one real-to-complex FFT;
+    per component the multiply by the spectrum of the periodic pair force
+    sampled at the fine-mesh separations (the kernel whose short- and
+    long-range parts the two-level method splits between the fine tiles and
+    the coarse mesh) and one complex-to-real FFT; CIC gather; the library's
+    kick-drift schedule (equal steps in log a, momenta at the geometric
+    mid-steps).  torch.fft is cuFFT on the GPU.  The same code runs on CPU
+    tensors, so its arithmetic is tested there.  Measurement only: no force
+    split, no compression."""
 
-    def __init__(self, x, p, nf, a_init, a_final, n_steps, step=0):
+    def __init__(self, x, p, nf, a_init, a_final, n_steps, step=0, spectra=None):
         import torch
         self.torch = torch
         self.x, self.p, self.L, self.N = x, p, nf, x.shape[1]
         self.a = [a_init * (a_final / a_init) ** (i / n_steps) for i in range(n_steps + 1)]
         self.step_i = step
-        dev = x.device
-        two_pi = 2.0 * math.pi
-        k = torch.fft.fftfreq(nf, device=dev) * two_pi       # rad per fine cell
-        kr = torch.fft.rfftfreq(nf, device=dev) * two_pi
-        k2 = kr.view(1, 1, -1) ** 2 + k.view(1, -1, 1) ** 2 + k.view(-1, 1, 1) ** 2
-        k2[0, 0, 0] = 1.0
-        self.inv_k2 = (4.0 * math.pi) / k2
-        self.inv_k2[0, 0, 0] = 0.0
-        del k2
-        # two-point central difference of the potential: i sin(k_d)
-        kg, kgr = torch.sin(k), torch.sin(kr)
-        kg[nf // 2] = 0.0
-        kgr[-1] = 0.0
-        self.k = (kgr.view(1, 1, -1), kg.view(1, -1, 1), kg.view(-1, 1, 1))   # x, y, z
+        self.S = spectra if spectra is not None else periodic_kernel_spectra(nf, x.device)
 
     def _corners(self):
         torch = self.torch
@@ -422,7 +570,7 @@ class PlainPM:
             yield idx, w
 
     def force(self):
-        """g at every particle, float32 [3, N]."""
+        """g = sum_j K_per(x - x_j) at every particle (CIC both ways), float32 [3, N]."""
         torch, L = self.torch, self.L
         rho = torch.zeros(L * L * L, dtype=torch.float32, device=self.x.device)
         for idx, w in self._corners():
@@ -431,7 +579,7 @@ class PlainPM:
         del rho
         g = torch.empty_like(self.x)
         for d in range(3):
-            gd = torch.fft.irfftn(rho_k * (1j * self.k[d] * self.inv_k2), s=(L, L, L)).reshape(-1)
+            gd = torch.fft.irfftn(rho_k * (1j * self.S[d]), s=(L, L, L)).reshape(-1)
             acc = torch.zeros_like(self.x[0])
             for idx, w in self._corners():
                 acc += w * gd[idx]
@@ -541,9 +689,9 @@ def run_plain_pm(cfg, sim, steps, warmup):
     t = e0.elapsed_time(e1) / 1000.0
     return {"value": cfg.n * steps / t, "unit": UNIT, "ms_per_step": t / steps * 1000.0,
             "steps": steps, "warmup": warmup, "bytes_per_particle": 24,
-            "method": "float32 x, p; CIC on the whole (4 nc)^3 fine mesh; torch.fft (cuFFT) R2C + "
-                      "3 C2R of the potential 4 pi / k^2 differenced by i sin k; CIC gather; "
-                      "same kick-drift"}
+            "method": "float32 x, p; CIC on the whole (4 nc)^3 fine mesh; torch.fft (cuFFT) R2C, "
+                      "3 x (multiply by the spectrum of the periodic pair force sampled on the "
+                      "fine mesh, C2R); CIC gather; same kick-drift"}
 
 
 SERVING_ARENA = 48 << 30
@@ -605,16 +753,16 @@ def run_reference(args):
     if rank != 0:
         return None
     K, W = args.steps, args.warmup
-    # a bounded sample of the workload per step: a 64^3-particle box with the
-    # same per-particle work (8 particles per coarse cell, 8 fine cells each)
-    v, dt = time_oracle_steps(64, 32, W, K)
-    sample = ("FP64 oracle, %d timed steps of a 64^3-particle box (32^3 coarse, 128^3 fine; "
-              "same per-particle work as the %s workload), %.1f s" % (K, args.workload, dt))
+    # each step a bounded sample of the workload: one oracle step of the
+    # 128^3-particle box (same per-particle work)
+    v, dt = time_oracle_steps(ORACLE_SAMPLE[0], ORACLE_SAMPLE[1], W, K)
+    sample = oracle_sample_text(K, dt) + " after %d untimed" % W
     return {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": K,
             "warmup": W, "ms_per_step": dt / K * 1000.0, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": args.workload, "parallelism": "host cores"},
+            "config": {"workload": args.workload, "timed_box": "%d^3 particles (bounded sample)"
+                       % ORACLE_SAMPLE[0], "parallelism": "host cores"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle_cores(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
