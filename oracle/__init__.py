@@ -17,6 +17,7 @@ cic       integer cloud-in-cell mass assignment / interpolation (Sec. II)
 kernels   coarse (long-range) and fine (short-range) force kernels, Eq. 1
 force     full-mesh PM-PM force per particle (Sec. II, Eq. 1)
 dynamics  kick-drift step and the cell-ordered re-encode (Sec. III-A)
+cosmology LambdaCDM background and linear growth (Sec. IV-A.2)
 ic        Zel'dovich initial conditions (Sec. IV-A.2)
 power     power spectrum (Sec. IV-D)
 direct    brute-force convolutions used only to pin the FFT path
@@ -26,4 +27,4 @@ docstring.  Functions with no independent pin say "parity unpinned"; at the
 time of writing there are none.
 """
 
-from . import codec, cic, kernels, force, dynamics, ic, power, direct  # noqa: F401
+from . import codec, cic, kernels, force, cosmology, dynamics, ic, power, direct  # noqa: F401

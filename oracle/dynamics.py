@@ -4,7 +4,8 @@ Test infrastructure only (see ``oracle/__init__``).
 
 Readings (the paper gives neither the integrator nor the units):
 
-* Einstein-de Sitter background, H0 = 1, time variable a, lengths in fine
+* Einstein-de Sitter background unless a ``cosmology.Cosmology`` is given
+  (its LambdaCDM factors reduce to these), H0 = 1, time variable a, lengths in fine
   cells, particle mass 1, mean density rho_bar = N / nf^3.  Momentum
   p = a^2 dx/dt.  Poisson: lap(phi) = (3/2) delta / a, so the force is
   -grad(phi) = (3 / (8 pi rho_bar a)) g with g the unit-G field of ``force``.
@@ -46,15 +47,20 @@ def schedule(a_init, a_final, n_steps):
     return a_init * (a_final / a_init) ** (n / n_steps)
 
 
-def step_factors(a_init, a_final, n_steps, n, n_particles, nf):
+def step_factors(a_init, a_final, n_steps, n, n_particles, nf, cosmo=None):
     """(kick factor, drift factor) of step n, float64.
 
     kick: multiplies g; drift: multiplies p to give dx in fine cells.
+    cosmo: a ``cosmology.Cosmology`` for a LambdaCDM background (its
+    integrals over a); None is Einstein-de Sitter in closed form.
     """
     a = schedule(a_init, a_final, n_steps)
     a_lo = a[0] if n == 0 else math.sqrt(a[n - 1] * a[n])
     a_hi = math.sqrt(a[n] * a[n + 1])
     rho_bar = n_particles / float(nf) ** 3
+    if cosmo is not None:
+        kick = 3.0 * cosmo.om / (8.0 * math.pi * rho_bar) * cosmo.kick_integral(a_lo, a_hi)
+        return kick, cosmo.drift_integral(a[n], a[n + 1])
     kick = 3.0 / (8.0 * math.pi * rho_bar) * 2.0 * (math.sqrt(a_hi) - math.sqrt(a_lo))
     drift = 2.0 * (1.0 / math.sqrt(a[n]) - 1.0 / math.sqrt(a[n + 1]))
     return kick, drift
@@ -158,11 +164,12 @@ def kick_drift(Q, p32, g, kick, drift, nc, pos_bytes=1):
 class Simulation:
     """Plain PM-PM evolution of a compressed state (oracle)."""
 
-    def __init__(self, nc, a_init, a_final, n_steps, pos_bytes=1):
+    def __init__(self, nc, a_init, a_final, n_steps, pos_bytes=1, cosmo=None):
         self.nc = nc
         self.nf = 4 * nc
         self.a_init, self.a_final, self.n_steps = a_init, a_final, n_steps
         self.pos_bytes = pos_bytes
+        self.cosmo = cosmo
         self.op = force_mod.ForceOperator(nc, pos_bytes)
 
     def forces(self, state):
@@ -177,7 +184,7 @@ class Simulation:
         p = state.momenta()
         g = self.op.particle_force(Q)
         kick, drift = step_factors(self.a_init, self.a_final, self.n_steps, n,
-                                   Q.shape[0], self.nf)
+                                   Q.shape[0], self.nf, self.cosmo)
         Q_new, p_new = kick_drift(Q, p, g, kick, drift, self.nc, self.pos_bytes)
         return encode(Q_new, p_new, self.nc, a[n + 1], n + 1, self.pos_bytes)
 

@@ -88,11 +88,14 @@ def displacement(seed, n_p, nf, slope, k_c):
     return np.stack(psi)
 
 
-def zeldovich(seed, n_p, nc, a_init, slope=-1.5, k_c=np.pi / 2, rms_disp=0.3, pos_bytes=1):
+def zeldovich(seed, n_p, nc, a_init, slope=-1.5, k_c=np.pi / 2, rms_disp=0.3, pos_bytes=1,
+              cosmo=None):
     """Compressed initial state at a_init (steps 1-6).
 
     Returns (state, x float64 [N,3], p float64 [N,3]) with particles in
-    lattice order for x and p.
+    lattice order for x and p.  cosmo: a ``cosmology.Cosmology``; the
+    growing-mode momentum is then p = a^2 E f (x - q) instead of the
+    Einstein-de Sitter sqrt(a) (x - q).
     """
     nf = 4 * nc
     psi = displacement(seed, n_p, nf, slope, k_c)
@@ -104,7 +107,10 @@ def zeldovich(seed, n_p, nc, a_init, slope=-1.5, k_c=np.pi / 2, rms_disp=0.3, po
     spacing = nf / n_p
     q = (np.stack([qx.ravel(), qy.ravel(), qz.ravel()], axis=1) + 0.5) * spacing
     x = q + a_init * psi
-    p = a_init ** 1.5 * psi
+    if cosmo is None:
+        p = a_init ** 1.5 * psi
+    else:
+        p = cosmo.ic_momentum_factor(a_init) * (a_init * psi)
     U = 64 if pos_bytes == 1 else 16384
     B = 256 if pos_bytes == 1 else 65536
     Q = np.mod(np.floor(x * U).astype(np.int64), nc * B)
