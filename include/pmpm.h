@@ -113,6 +113,12 @@ typedef struct pmpm_config {
     double  a_final;         /* last scale factor */
     int32_t n_steps;         /* steps of the schedule */
     int32_t reserved2;
+    double  omega_m;         /* background (Sec. IV-A.2; H0 = 1): matter density today;
+                                0 with omega_l 0 = Einstein-de Sitter (Omega_m = 1) */
+    double  omega_l;         /* cosmological constant today; curvature 1 - omega_m - omega_l.
+                                The kick and drift factors are integrals of 1/(a^2 E) and
+                                1/(a^3 E) over the step, E(a) = H(a)/H0, and the
+                                Zel'dovich momenta follow the growing mode */
 } pmpm_config;
 
 typedef struct pmpm_scalars {
@@ -127,6 +133,18 @@ typedef struct pmpm_sim pmpm_sim;
 /* Device bytes a sim of this configuration needs.  Host-only, no GPU call.
  * Returns PMPM_EINVAL for unsupported configurations. */
 int pmpm_workspace_bytes(const pmpm_config* cfg, size_t* bytes);
+
+/* The float64 factors of step `step` (0 <= step < n_steps) of a
+ * configuration's schedule, host only: *kick multiplies the unit-G field g
+ * (3 Omega_m / (8 pi rho_bar) times the integral of 1/(a^2 E) from the
+ * previous half step to the next), *drift multiplies p to give the
+ * displacement in fine cells (the integral of 1/(a^3 E) over the step), and
+ * *ic_momentum is the Zel'dovich momentum per unit displacement at a_init
+ * (a^2 E f; sqrt(a_init) for Einstein-de Sitter).  Sec. IV-A.2's background;
+ * the integrator itself is not given by the paper (kick-drift leapfrog, steps
+ * equal in log a).  PMPM_EINVAL for a bad configuration or step. */
+int pmpm_step_factors(const pmpm_config* cfg, int32_t step, double* kick, double* drift,
+                      double* ic_momentum);
 
 /* Create a sim on the current CUDA device.  d_workspace: device pointer,
  * 256-byte aligned, at least pmpm_workspace_bytes() bytes, owned by the
@@ -298,7 +316,8 @@ typedef struct pmpm_batch_config {
     int32_t max_active;      /* boxes resident at once, 1..1024 (1 = one after another) */
     int32_t share_tables;    /* 1: force tables built once per nc, kept in the arena */
     int32_t graphs;          /* 1: steps replayed as CUDA graphs (pmpm_graph_mode) */
-    int32_t priorities;      /* 1: smaller boxes on higher-priority streams */
+    int32_t priorities;      /* 0: one priority; 1: smaller boxes on higher-priority
+                                streams; 2: larger boxes on higher-priority streams */
     int32_t steps_per_chunk; /* steps enqueued at a time per box (>= 1) */
     int32_t chunks_in_flight;/* chunks a box may have queued ahead (>= 1) */
 } pmpm_batch_config;

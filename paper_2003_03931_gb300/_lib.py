@@ -44,7 +44,7 @@ ERROR_NAMES = {
 
 # every entry point the header declares, for the export check
 EXPORTS = [
-    "pmpm_workspace_bytes", "pmpm_init", "pmpm_init_like", "pmpm_graph_mode",
+    "pmpm_workspace_bytes", "pmpm_step_factors", "pmpm_init", "pmpm_init_like", "pmpm_graph_mode",
     "pmpm_ic_zeldovich", "pmpm_step",
     "pmpm_power_spectrum", "pmpm_fetch", "pmpm_fetch_tile_density", "pmpm_load", "pmpm_sync",
     "pmpm_stage_times",
@@ -72,7 +72,7 @@ class Config(ctypes.Structure):
         ("a_init", ctypes.c_double),
         ("a_final", ctypes.c_double),
         ("n_steps", ctypes.c_int32),
-        ("reserved2", ctypes.c_int32),
+        ("reserved2", ctypes.c_int32), ("omega_m", ctypes.c_double), ("omega_l", ctypes.c_double),
     ]
 
 
@@ -158,6 +158,8 @@ def load():
     lib.pmpm_fetch.argtypes = [P, ctypes.c_int32, P, ctypes.c_size_t]
     lib.pmpm_load.argtypes = [P, ctypes.c_int32, P, ctypes.c_size_t]
     lib.pmpm_fetch_tile_density.argtypes = [P, ctypes.c_int32, P, ctypes.c_size_t, P, P]
+    D = ctypes.POINTER(ctypes.c_double)
+    lib.pmpm_step_factors.argtypes = [ctypes.POINTER(Config), ctypes.c_int32, D, D, D]
     lib.pmpm_sync.argtypes = [P]
     lib.pmpm_stage_times.argtypes = [P, ctypes.c_int32, P, ctypes.c_int32, P]
     lib.pmpm_destroy.argtypes = [P]

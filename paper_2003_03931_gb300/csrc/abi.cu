@@ -16,6 +16,7 @@
 #include <new>
 
 #include "pmpm_impl.cuh"
+#include "cosmo.h"
 
 namespace pmpm {
 
@@ -59,6 +60,17 @@ static int validate(const pmpm_config* c, char* msg, size_t len) {
         return snprintf(msg, len, "need 0 < a_init <= a_final and n_steps >= 1"), PMPM_EINVAL;
     if (c->flags & ~PMPM_FLAG_LOWMEM)
         return snprintf(msg, len, "unknown flags 0x%x", (unsigned)c->flags), PMPM_EINVAL;
+    if (!(c->omega_m >= 0.0) || !(c->omega_l >= 0.0) || (c->omega_m == 0.0 && c->omega_l != 0.0))
+        return snprintf(msg, len, "need omega_m > 0 and omega_l >= 0, or both 0 (Einstein-de Sitter)"),
+               PMPM_EINVAL;
+    if (c->omega_m > 0.0) {
+        const Background b = background_of(c->omega_m, c->omega_l);
+        for (int i = 0; i <= 64; ++i) {
+            const double a = c->a_init * pow(c->a_final / c->a_init, i / 64.0);
+            if (!(bg_E2(b, a) > 0.0))
+                return snprintf(msg, len, "no expanding background at a = %g", a), PMPM_EINVAL;
+        }
+    }
     return PMPM_OK;
 }
 
@@ -78,6 +90,7 @@ static void derive(Sim& s, const pmpm_config* c) {
     s.nblocks_scan = (s.ncells + 4095) / 4096;
     s.lowmem = (c->flags & PMPM_FLAG_LOWMEM) != 0;
     s.pb = c->pos_bytes == 2 ? 2 : 1;
+    s.ic_pfac = c->a_init * bg_ic_momentum_factor(background_of(c->omega_m, c->omega_l), c->a_init);
     s.lm_ctas = s.lowmem ? kLowmemCtas : 0;
 }
 
@@ -308,19 +321,33 @@ __global__ void k_step_advance(int* step, float* kd, const float* factors, int n
     kd[1] = v < n_steps ? factors[2 * v + 1] : 0.f;
 }
 
+static double cfg_a(const pmpm_config& c, int64_t n) {
+    return c.a_init * pow(c.a_final / c.a_init, (double)n / (double)c.n_steps);
+}
+
+// float64 kick factor (multiplies g) and drift factor (multiplies p, fine
+// cells) of step n: momenta at the half steps a_{n+1/2} = sqrt(a_n a_{n+1}),
+// the first kick from a_0; the integrals of the background (cosmo.h)
+static void step_factors(const pmpm_config& c, int64_t np3, int n, double* kick, double* drift) {
+    const Background b = background_of(c.omega_m, c.omega_l);
+    const double nf = 4.0 * c.nc;
+    const double rho_bar = (double)np3 / (nf * nf * nf);
+    const double an = cfg_a(c, n), an1 = cfg_a(c, n + 1);
+    const double a_lo = n == 0 ? c.a_init : sqrt(cfg_a(c, n - 1) * an);
+    const double a_hi = sqrt(an * an1);
+    *kick = 3.0 * b.om / (8.0 * 3.141592653589793238462643383279502884 * rho_bar) *
+            bg_kick_integral(b, a_lo, a_hi);
+    *drift = bg_drift_integral(b, an, an1);
+}
+
 // float32 kick and drift factors of every step of the schedule (R7), in
 // device memory so that a captured step can replay at any step index
 static void fill_factors(Sim& s) {
     const int S = s.cfg.n_steps;
     float* f = new float[2 * S];
-    const double rho_bar = (double)s.n / ((double)s.nf * s.nf * s.nf);
     for (int n = 0; n < S; ++n) {
-        const double an = sched_a(s, n), an1 = sched_a(s, n + 1);
-        const double a_lo = n == 0 ? s.cfg.a_init : sqrt(sched_a(s, n - 1) * an);
-        const double a_hi = sqrt(an * an1);
-        const double kick = 3.0 / (8.0 * 3.141592653589793238462643383279502884 * rho_bar) * 2.0 *
-                            (sqrt(a_hi) - sqrt(a_lo));
-        const double drift = 2.0 * (1.0 / sqrt(an) - 1.0 / sqrt(an1));
+        double kick, drift;
+        step_factors(s.cfg, s.n, n, &kick, &drift);
         f[2 * n] = (float)kick;
         f[2 * n + 1] = (float)(drift * (s.pb == 2 ? PosFmt<2>::kCodesPerFine : PosFmt<1>::kCodesPerFine));
     }
@@ -539,6 +566,21 @@ int pmpm_workspace_bytes(const pmpm_config* cfg, size_t* bytes) {
     derive(*s, cfg);
     *bytes = layout(*s, nullptr);
     delete s;
+    return PMPM_OK;
+}
+
+int pmpm_step_factors(const pmpm_config* cfg, int32_t step, double* kick, double* drift,
+                      double* ic_momentum) {
+    char msg[256];
+    int rc = validate(cfg, msg, sizeof(msg));
+    if (rc) {
+        snprintf(g_init_msg, sizeof(g_init_msg), "%s", msg);
+        return rc;
+    }
+    if (step < 0 || step >= cfg->n_steps || !kick || !drift || !ic_momentum) return PMPM_EINVAL;
+    const int64_t np3 = (int64_t)cfg->np * cfg->np * cfg->np;
+    step_factors(*cfg, np3, step, kick, drift);
+    *ic_momentum = bg_ic_momentum_factor(background_of(cfg->omega_m, cfg->omega_l), cfg->a_init);
     return PMPM_OK;
 }
 

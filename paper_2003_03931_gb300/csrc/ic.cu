@@ -2,7 +2,8 @@
 // spectrum P(k) = k^slope exp(-(k/k_c)^2), in float64 on the device:
 //   white noise (SplitMix64 counters 2i, 2i+1; Box-Muller) -> DFT ->
 //   Psi~_d = i k_d / k^2 sqrt(P) w~ (k = 0 and Nyquist planes zeroed) ->
-//   inverse DFT -> rms normalisation -> x = q + a Psi, p = a^(3/2) Psi ->
+//   inverse DFT -> rms normalisation -> x = q + a Psi, p = a^(3/2) Psi (EdS; a^2 E f a Psi
+//   in LambdaCDM) ->
 //   Q = floor(64 x) mod (256 nc), p in float32 -> cell-ordered encode.
 #include "pmpm_impl.cuh"
 
@@ -110,13 +111,12 @@ __global__ void k_ic_scale(int nblk, int64_t n, double a_init, double rms_disp, 
 }
 
 template <int PB>
-__global__ void k_ic_particles(int np, int nc, double a_init, const double* __restrict__ psi,
+__global__ void k_ic_particles(int np, int nc, double a_init, double pfac, const double* __restrict__ psi,
                                const double* __restrict__ scale_p, int32_t* __restrict__ Qn,
                                float* __restrict__ Pn) {
     const int64_t n = (int64_t)np * np * np;
     const double scale = *scale_p;
     const double spacing = 4.0 * nc / (double)np;
-    const double a15 = pow(a_init, 1.5);
     const int64_t M = (int64_t)nc * PosFmt<PB>::kBins;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -128,7 +128,7 @@ __global__ void k_ic_particles(int np, int nc, double a_init, const double* __re
             int64_t Q = (int64_t)floor(x * (double)PosFmt<PB>::kCodesPerFine) % M;
             if (Q < 0) Q += M;
             Qn[d * n + i] = (int32_t)Q;
-            Pn[d * n + i] = (float)(a15 * ps);
+            Pn[d * n + i] = (float)(pfac * ps);
         }
     }
 }
@@ -260,7 +260,7 @@ int ic_zeldovich(Sim& s, uint64_t seed, double slope, double kc, double rms) {
     double* scale = partial + 3 * nblk;
     k_ic_scale<<<1, 1, 0, st>>>(nblk, n, s.cfg.a_init, rms, partial, scale);
     auto kp = s.pb == 2 ? k_ic_particles<2> : k_ic_particles<1>;
-    kp<<<grid_for(n, 256), 256, 0, st>>>(np, s.nc, s.cfg.a_init, psi, scale, s.Qn, s.Pn);
+    kp<<<grid_for(n, 256), 256, 0, st>>>(np, s.nc, s.cfg.a_init, s.ic_pfac, psi, scale, s.Qn, s.Pn);
     s.launches += 6 + 3 * 2;
     if ((rc = check_launch(s, "ic"))) return rc;
     s.a = s.cfg.a_init;

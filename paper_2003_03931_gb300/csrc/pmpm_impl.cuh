@@ -20,6 +20,7 @@ struct Sim {
     int device = 0;
     int nc = 0, nf = 0, np = 0, nt = 0, tile_max = 0, pk_max = 0, fft_max = 0;
     int pb = 1;                                 // bytes per position bin (1 or 2)
+    double ic_pfac = 0.0;                       // Zel'dovich p per unit of a_init Psi (a_init^1.5 in EdS)
     int64_t n = 0, ncells = 0;
     cudaStream_t stream = nullptr;
     uint8_t* ws = nullptr;

@@ -152,7 +152,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(int64_t ncells, con
 // Where the encode kernels read each particle's new codes Q and momenta p:
 // the per-particle buffers of the default step, or, for the low-memory
 // initial conditions, the float32 displacement field (x = q + a Psi,
-// p = a^(3/2) Psi, Q = floor(64 x) mod 256 nc; Sec. IV-A.2).
+// p = a^(3/2) Psi in EdS (a^2 E f a Psi in LambdaCDM), Q = floor(64 x) mod 256 nc;
+// Sec. IV-A.2).
 struct QPArrays {
     const int32_t* Q;
     const float* P;
@@ -467,7 +468,7 @@ int encode_from_qp(Sim& s, bool counts_ready) {
 // re-encode, reading the field instead of per-particle buffers).
 int encode_from_psi(Sim& s, const double* scale) {
     cudaStream_t st = s.stream;
-    const QPFromPsi src{s.ic_psi, scale, s.np, s.nc, s.cfg.a_init, pow(s.cfg.a_init, 1.5),
+    const QPFromPsi src{s.ic_psi, scale, s.np, s.nc, s.cfg.a_init, s.ic_pfac,
                         4.0 * s.nc / (double)s.np, s.n};
     s.cur = 1;
     const int nxt = 0;

@@ -26,6 +26,8 @@ class SimConfig:
     vel_bytes: int = 1
     pk_mesh_max: int = 0
     lowmem: bool = False    # three tile passes per step, no per-particle intermediate
+    omega_m: float = 0.0    # background: 0, 0 = Einstein-de Sitter; else LambdaCDM (Sec. IV-A.2)
+    omega_l: float = 0.0
 
     def to_c(self):
         c = _lib.Config()
@@ -33,6 +35,7 @@ class SimConfig:
         c.pos_bytes, c.vel_bytes, c.pk_mesh_max = self.pos_bytes, self.vel_bytes, self.pk_mesh_max
         c.flags = _lib.FLAG_LOWMEM if self.lowmem else 0
         c.a_init, c.a_final, c.n_steps = self.a_init, self.a_final, self.n_steps
+        c.omega_m, c.omega_l = self.omega_m, self.omega_l
         return c
 
     @property
@@ -65,6 +68,17 @@ def workspace_bytes(cfg):
     c = cfg.to_c()
     _lib.check(lib.pmpm_workspace_bytes(ctypes.byref(c), ctypes.byref(out)))
     return out.value
+
+
+def step_factors(cfg, step):
+    """(kick, drift, ic_momentum) of one step of cfg's schedule (float64,
+    host only; pmpm_step_factors)."""
+    lib = _lib.load()
+    k, d, p = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    c = cfg.to_c()
+    _lib.check(lib.pmpm_step_factors(ctypes.byref(c), step, ctypes.byref(k), ctypes.byref(d),
+                                     ctypes.byref(p)))
+    return k.value, d.value, p.value
 
 
 def codec_tables():

@@ -18,6 +18,13 @@ WORKLOADS = {
     "c4sub_256_pos2": dict(np=256, nc=128, a_init=0.02, a_final=1.0, n_steps=20, pos_bytes=2),
     # small ragged-tile case: 7 tiles of 4/5 coarse cells per side
     "ragged_32": dict(np=32, nc=32, a_init=0.02, a_final=1.0, n_steps=10),
+    # the 256^3 box with the low-memory step (profiling the three tile passes)
+    "c4sub_256_lowmem": dict(np=256, nc=128, a_init=0.02, a_final=1.0, n_steps=20, lowmem=True),
+    # the paper's LambdaCDM background (Omega_m = 0.258, flat) from z = 99
+    "lcdm_32": dict(np=32, nc=16, a_init=0.01, a_final=1.0, n_steps=10, omega_m=0.258,
+                    omega_l=0.742),
+    "lcdm_128": dict(np=128, nc=64, a_init=0.01, a_final=1.0, n_steps=20, omega_m=0.258,
+                     omega_l=0.742),
     # 2048^3 particles (51.5 GB at 6 B/particle) on one GPU: low-memory step
     "c4_2048": dict(np=2048, nc=1024, a_init=0.02, a_final=1.0, n_steps=20, lowmem=True),
 }

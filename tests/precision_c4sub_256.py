@@ -84,11 +84,15 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--out", default=None)
-    ap.add_argument("--workdir", default=os.path.join(ROOT, "gpurun_out", "precision_work"))
+    ap.add_argument("--workdir", default=None,
+                    help="where the oracle processes leave their arrays (default: a temporary "
+                         "directory, removed at the end)")
     args = ap.parse_args(argv)
+    import shutil
+    import tempfile
+    own = args.workdir is None
+    args.workdir = tempfile.mkdtemp(prefix="pmpm_precision_") if own else args.workdir
     os.makedirs(args.workdir, exist_ok=True)
-    for f in os.listdir(args.workdir):
-        os.remove(os.path.join(args.workdir, f))
     n_schedule = 20
     # the oracle processes start before this process touches the GPU
     ctx = mp.get_context("spawn")
@@ -138,6 +142,8 @@ def main(argv=None):
     results["oracle_1_byte_vs_2_byte_pk"] = _pk_err(r1["k"], r1["pk"], r2["pk"])
     for p in procs.values():
         p.join()
+    if own:
+        shutil.rmtree(args.workdir, ignore_errors=True)
     text = json.dumps(results, indent=1)
     print(text)
     if args.out:

@@ -111,3 +111,26 @@ def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
     monkeypatch.setattr(_lib, "_lib", None)
     with pytest.raises(ImportError):
         _lib.load()
+
+
+def test_step_factors_match_the_oracle(lib):
+    # the library's float64 schedule factors (its own quadrature of the
+    # background, Sec. IV-A.2) against the oracle's (scipy), EdS and LambdaCDM
+    import math
+
+    from oracle import cosmology, dynamics
+    from paper_2003_03931_gb300.sim import SimConfig, step_factors
+    for om, ol, ai in ((0.0, 0.0, 0.02), (0.258, 0.742, 0.01), (0.3, 0.0, 0.05)):
+        cfg = SimConfig(np=32, nc=16, a_init=ai, a_final=1.0, n_steps=12, omega_m=om, omega_l=ol)
+        cos = cosmology.Cosmology(om, ol) if om else None
+        for n in range(12):
+            k, d, pf = step_factors(cfg, n)
+            ko, do = dynamics.step_factors(ai, 1.0, 12, n, 32 ** 3, 64, cos)
+            assert abs(k / ko - 1) < 1e-12 and abs(d / do - 1) < 1e-12, (om, n, k, ko, d, do)
+        ref = cos.ic_momentum_factor(ai) if cos else math.sqrt(ai)
+        assert abs(pf / ref - 1) < 1e-11, (om, pf, ref)
+    from paper_2003_03931_gb300._lib import PMPM_EINVAL, PmpmError
+    for om, ol in ((0.0, 0.7), (-0.1, 0.0), (0.1, 5.0)):
+        with pytest.raises(PmpmError) as e:
+            step_factors(SimConfig(np=32, nc=16, omega_m=om, omega_l=ol), 0)
+        assert e.value.code == PMPM_EINVAL
