@@ -192,10 +192,15 @@ cudaEvent_t take_event(pmpm_batch& b) {
     return e;
 }
 
+// priorities 1: the smaller the box, the higher its stream's priority (short
+// requests are not held up behind a large box's tile pass); 2: the larger the
+// box, the higher (the large boxes, which make the latency tail, keep the
+// GPU and the small ones fill the gaps)
 int stream_priority(const pmpm_batch& b, int np) {
     if (!b.c.priorities) return 0;
     int level = 0;
     for (int v = np; v > 32; v >>= 1) ++level;
+    if (b.c.priorities == 2) level = std::max(0, 3 - level);
     return std::min(b.prio_least, b.prio_greatest + level);   // greatest is numerically lowest
 }
 
@@ -465,9 +470,10 @@ int pmpm_batch_create(const pmpm_batch_config* cfg, void* d_arena, size_t arena_
                       pmpm_batch** out) {
     if (!cfg || !out || !d_arena) return PMPM_EINVAL;
     if (cfg->max_active < 1 || cfg->max_active > 1024 || cfg->steps_per_chunk < 1 ||
-        cfg->chunks_in_flight < 1) {
+        cfg->chunks_in_flight < 1 || cfg->priorities < 0 || cfg->priorities > 2) {
         snprintf(g_batch_msg, sizeof(g_batch_msg),
-                 "max_active in [1, 1024], steps_per_chunk >= 1, chunks_in_flight >= 1");
+                 "max_active in [1, 1024], steps_per_chunk >= 1, chunks_in_flight >= 1, "
+                 "priorities 0, 1 or 2");
         return PMPM_EINVAL;
     }
     if (reinterpret_cast<uintptr_t>(d_arena) % kArenaAlign) {
