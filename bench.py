@@ -455,6 +455,7 @@ def run_ours(args):
                 "what": "torch.fft (cuFFT) over batched 32^3 boxes in device memory: 1 R2C + 3 "
                         "(complex multiply, C2R) per tile, the transforms alone; the tile pass also "
                         "deposits, interpolates, kicks and drifts"}
+            out["library_fft_tiles"] = dict(side["library_fft_tiles"], workload=args.side_workload)
         if args.plain_pm:
             plain = run_plain_pm(cfg, s["sim"], args.plain_pm, 1)
             plain["ours_over_plain"] = s["value"] / plain["value"]
@@ -698,8 +699,36 @@ SERVING_ARENA = 48 << 30
 SEQUENTIAL = dict(max_active=1, share_tables=False, graphs=False, priorities=False,
                   steps_per_chunk=4, chunks_in_flight=2)
 SEQUENTIAL_SHARED = dict(SEQUENTIAL, share_tables=True)
-BATCHED = dict(max_active=16, share_tables=True, graphs=True, priorities=True, steps_per_chunk=4,
+BATCHED = dict(max_active=16, share_tables=True, graphs=True, priorities=1, steps_per_chunk=4,
                chunks_in_flight=2)
+# the same engine with the larger boxes on the higher-priority streams
+BATCHED_LARGE_FIRST = dict(BATCHED, priorities=2)
+# fewer boxes resident at once: less sharing of the GPU between large boxes
+BATCHED_CAPPED = dict(BATCHED, max_active=4)
+
+
+def alone_rates(device, sizes=(32, 64, 128, 256), steps=10, warmup=2):
+    """Stepping throughput of one box of each size alone on the GPU
+    (particle-steps/s, CUDA events around `steps` steps)."""
+    import torch
+
+    from paper_2003_03931_gb300 import synth
+    from paper_2003_03931_gb300.sim import SimConfig, Simulation
+    out = {}
+    for np_ in sizes:
+        sim = Simulation(SimConfig(np=np_, nc=np_ // 2, n_steps=steps + warmup), device=device)
+        sim.ic_zeldovich(3, **synth.IC_SPECTRUM)
+        sim.step(warmup)
+        sim.sync()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(sim.stream)
+        sim.step(steps)
+        e1.record(sim.stream)
+        e1.synchronize()
+        out[str(np_)] = np_ ** 3 * steps / (e0.elapsed_time(e1) / 1000.0)
+        sim.close()
+    return out
 
 
 def run_serving(args, device):
@@ -726,6 +755,20 @@ def run_serving(args, device):
     seq = go(SEQUENTIAL, reqs)
     seq_shared = go(SEQUENTIAL_SHARED, reqs)
     bat = go(BATCHED, reqs)
+    bat_large = go(BATCHED_LARGE_FIRST, reqs)
+    bat_cap = go(BATCHED_CAPPED, reqs)
+    # Ceiling of any batching of this mix: even if every particle-step ran at
+    # the best rate one box reaches alone (the GPU filled by one box), the
+    # stream's steps would take sum(work) / max rate; ICs and P(k) only add.
+    rates = alone_rates(device)
+    work = sum(r.n * r.n_steps for r in reqs)
+    best = max(rates.values())
+    ceiling = {"alone_rates": rates, "particle_steps": work,
+               "steps_at_best_rate_s": work / best,
+               "sequential_makespan_s": seq["makespan_s"],
+               "ratio_vs_sequential": seq["makespan_s"] / (work / best),
+               "what": "sequential makespan over (all particle-steps / the best one-box rate): "
+                       "the most any batching of this stream can gain, ICs and P(k) aside"}
     out = {
         "workload": "%d requests: 32^3/64^3/128^3/256^3 particles (weights .4/.3/.2/.1, nc = np/2), "
                     "10-40 steps a 0.02->1, slopes U[-2,-1], seeds 1000+i; P(k) on an np^3 mesh "
@@ -734,7 +777,12 @@ def run_serving(args, device):
         "sequential": dict(seq, config=SEQUENTIAL),
         "sequential_shared_tables": dict(seq_shared, config=SEQUENTIAL_SHARED),
         "batched": dict(bat, config=BATCHED),
+        "batched_large_first": dict(bat_large, config=BATCHED_LARGE_FIRST),
+        "batched_max4": dict(bat_cap, config=BATCHED_CAPPED),
         "throughput_ratio_vs_sequential": bat["particle_steps_per_s"] / seq["particle_steps_per_s"],
+        "throughput_ratio_large_first_vs_sequential":
+            bat_large["particle_steps_per_s"] / seq["particle_steps_per_s"],
+        "ceiling": ceiling,
         "throughput_ratio_vs_sequential_shared_tables":
             bat["particle_steps_per_s"] / seq_shared["particle_steps_per_s"],
         "latency": [],
@@ -744,7 +792,8 @@ def run_serving(args, device):
         arr = with_arrivals(reqs, rate=f * cap, seed=1)
         out["latency"].append({"rate_fraction_of_sequential_capacity": f,
                                "rate_requests_per_s": f * cap,
-                               "sequential": go(SEQUENTIAL, arr), "batched": go(BATCHED, arr)})
+                               "sequential": go(SEQUENTIAL, arr), "batched": go(BATCHED, arr),
+                               "batched_max4": go(BATCHED_CAPPED, arr)})
     return out
 
 

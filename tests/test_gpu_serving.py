@@ -69,6 +69,7 @@ def _check_against_solo(reqs, res):
 @pytest.mark.parametrize("kw", [
     dict(max_active=6, share_tables=True, graphs=True, priorities=True, steps_per_chunk=2),
     dict(max_active=3, share_tables=False, graphs=False, priorities=True, steps_per_chunk=1),
+    dict(max_active=4, share_tables=True, graphs=True, priorities=2, steps_per_chunk=3),
 ])
 def test_large_and_lowmem_boxes_equal_solo_runs(kw):
     need_gpu()

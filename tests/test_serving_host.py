@@ -106,7 +106,8 @@ def test_batch_create_rejects_bad_arguments(lib):
     good = _lib.BatchConfig(4, 1, 0, 1, 2, 2)
     assert lib.pmpm_batch_create(ctypes.byref(good), None, 1 << 20, ctypes.byref(h)) == _lib.PMPM_EINVAL
     for bad in (_lib.BatchConfig(0, 1, 0, 1, 2, 2), _lib.BatchConfig(4, 1, 0, 1, 0, 2),
-                _lib.BatchConfig(4, 1, 0, 1, 2, 0)):
+                _lib.BatchConfig(4, 1, 0, 1, 2, 0), _lib.BatchConfig(4, 1, 0, 3, 2, 2),
+                _lib.BatchConfig(4, 1, 0, -1, 2, 2)):
         assert lib.pmpm_batch_create(ctypes.byref(bad), ctypes.c_void_p(1 << 20), 1 << 20,
                                      ctypes.byref(h)) == _lib.PMPM_EINVAL
         assert b"max_active" in lib.pmpm_batch_last_error(None)
