@@ -99,6 +99,16 @@ extern "C" {
                                 float64).  PMPM_DECODED_Q/P, PMPM_FORCE and loading
                                 PMPM_QP are not available. */
 
+#define PMPM_FLAG_FINE_FP16 2 /* Precision option (Sec. III-A stores particles in
+                                1 or 2 bytes; this stores the fine-mesh field
+                                compactly too): the tile pass keeps each tile's
+                                density spectrum in FP16 (the density scaled by a
+                                power of two per tile to stay in range) while every
+                                transform, Green multiply and force sum runs in
+                                float32.  Results differ from the default step by the
+                                FP16 rounding (about 1e-3 of the force); default
+                                step only (not with PMPM_FLAG_LOWMEM). */
+
 typedef struct pmpm_config {
     int32_t np;              /* particles per side of the initial lattice, N = np^3 */
     int32_t nc;              /* coarse cells per side (>= 8); fine mesh 4*nc */
@@ -320,6 +330,11 @@ typedef struct pmpm_batch_config {
                                 streams; 2: larger boxes on higher-priority streams */
     int32_t steps_per_chunk; /* steps enqueued at a time per box (>= 1) */
     int32_t chunks_in_flight;/* chunks a box may have queued ahead (>= 1) */
+    int32_t large_np;        /* boxes with np >= large_np are "large" (0: none is) */
+    int32_t max_large;       /* large boxes resident at once (0: no limit); an arrived
+                                large request over the limit is passed over by later
+                                requests that can start, and keeps its place for the
+                                next free large slot */
 } pmpm_batch_config;
 
 typedef struct pmpm_batch_stats {

@@ -31,6 +31,7 @@ QP = 9
 STEP_QP = 10
 
 FLAG_LOWMEM = 1
+FLAG_FINE_FP16 = 2
 
 ERROR_NAMES = {
     PMPM_EINVAL: "PMPM_EINVAL",
@@ -110,6 +111,7 @@ class BatchConfig(ctypes.Structure):
         ("max_active", ctypes.c_int32), ("share_tables", ctypes.c_int32),
         ("graphs", ctypes.c_int32), ("priorities", ctypes.c_int32),
         ("steps_per_chunk", ctypes.c_int32), ("chunks_in_flight", ctypes.c_int32),
+        ("large_np", ctypes.c_int32), ("max_large", ctypes.c_int32),
     ]
 
 

@@ -58,8 +58,10 @@ static int validate(const pmpm_config* c, char* msg, size_t len) {
                PMPM_EINVAL;
     if (!(c->a_init > 0.0) || !(c->a_final >= c->a_init) || c->n_steps < 1)
         return snprintf(msg, len, "need 0 < a_init <= a_final and n_steps >= 1"), PMPM_EINVAL;
-    if (c->flags & ~PMPM_FLAG_LOWMEM)
+    if (c->flags & ~(PMPM_FLAG_LOWMEM | PMPM_FLAG_FINE_FP16))
         return snprintf(msg, len, "unknown flags 0x%x", (unsigned)c->flags), PMPM_EINVAL;
+    if ((c->flags & PMPM_FLAG_LOWMEM) && (c->flags & PMPM_FLAG_FINE_FP16))
+        return snprintf(msg, len, "FP16 tile storage is an option of the default step"), PMPM_EINVAL;
     if (!(c->omega_m >= 0.0) || !(c->omega_l >= 0.0) || (c->omega_m == 0.0 && c->omega_l != 0.0))
         return snprintf(msg, len, "need omega_m > 0 and omega_l >= 0, or both 0 (Einstein-de Sitter)"),
                PMPM_EINVAL;
@@ -89,6 +91,7 @@ static void derive(Sim& s, const pmpm_config* c) {
     if (s.pk_max > s.fft_max) s.fft_max = s.pk_max;
     s.nblocks_scan = (s.ncells + 4095) / 4096;
     s.lowmem = (c->flags & PMPM_FLAG_LOWMEM) != 0;
+    s.fp16 = (c->flags & PMPM_FLAG_FINE_FP16) != 0;
     s.pb = c->pos_bytes == 2 ? 2 : 1;
     s.ic_pfac = c->a_init * bg_ic_momentum_factor(background_of(c->omega_m, c->omega_l), c->a_init);
     s.lm_ctas = s.lowmem ? kLowmemCtas : 0;
@@ -781,17 +784,29 @@ int pmpm_load(pmpm_sim* h, int32_t what, const void* src, size_t bytes) {
             if (bytes != 4 * C) return set_error(s, PMPM_EINVAL, "counts need %zu bytes", 4 * C);
             // the kernels index the particle streams through these counts:
             // they must be non-negative and add up to N
+            // (the copy starts first; a branch-free pass over the host array
+            // checks them meanwhile, and a refused load leaves no state)
             const int32_t* c = static_cast<const int32_t*>(src);
-            int64_t total = 0;
-            for (size_t i = 0; i < C; ++i) {
-                if (c[i] < 0) return set_error(s, PMPM_EINVAL, "negative count");
-                total += c[i];
-            }
-            if (total != s.n)
-                return set_error(s, PMPM_EINVAL, "counts add up to %lld, not N = %lld",
-                                 (long long)total, (long long)s.n);
             e = cudaMemcpyAsync(s.counts[s.cur], src, bytes, cudaMemcpyHostToDevice, s.stream);
             s.offsets_valid = false;
+            s.loaded &= ~2;
+            int64_t total = 0;
+            int32_t lowest = 0;
+            for (size_t i = 0; i < C; ++i) {
+                total += c[i];
+                lowest = c[i] < lowest ? c[i] : lowest;
+            }
+            if (lowest < 0) {
+                cudaStreamSynchronize(s.stream);
+                s.have_state = false;
+                return set_error(s, PMPM_EINVAL, "negative count");
+            }
+            if (total != s.n) {
+                cudaStreamSynchronize(s.stream);
+                s.have_state = false;
+                return set_error(s, PMPM_EINVAL, "counts add up to %lld, not N = %lld",
+                                 (long long)total, (long long)s.n);
+            }
             s.loaded |= 2;
             break;
         }

@@ -72,6 +72,7 @@ struct Sim {
     float* Pn = nullptr;                        // [3][N] (aliases scratch; default step)
 
     // low-memory step (PMPM_FLAG_LOWMEM)
+    bool fp16 = false;                          // PMPM_FLAG_FINE_FP16: tile spectrum stored as FP16
     bool lowmem = false;
     int lm_ctas = 0;                            // scratch slots (kLowmemCtas)
     float* lm_sp = nullptr;                     // [ctas][3][kLowmemCap] per-CTA momenta

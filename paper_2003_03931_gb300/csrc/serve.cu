@@ -149,6 +149,8 @@ double now_s(const pmpm_batch& b) {
 
 bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
+bool is_large(const pmpm_batch& b, int np) { return b.c.large_np > 0 && np >= b.c.large_np; }
+
 // pmpm_config of a request; PMPM_OK when the sim and its P(k) mesh are valid
 int request_config(const pmpm_request& r, pmpm_config* c, int* nmesh, int* nbins, char* msg,
                    size_t len) {
@@ -401,14 +403,24 @@ int progress(pmpm_batch& b, bool* did) {
         }
         ++i;
     }
-    // 2. admit arrived requests in FIFO order
+    // 2. admit arrived requests in FIFO order; a large request over the
+    // large-box limit is passed over (it keeps its place in the queue)
     const double t = now_s(b);
-    while ((int)b.active.size() < b.c.max_active && !b.queue.empty()) {
-        auto head = b.queue.begin();
+    int n_large = 0;
+    if (b.c.max_large > 0)
+        for (Job* a : b.active) n_large += is_large(b, a->r.np);
+    auto head = b.queue.begin();
+    while ((int)b.active.size() < b.c.max_active && head != b.queue.end()) {
         if (head->first.first > t) break;
         Job* j = head->second;
+        const bool large = b.c.max_large > 0 && is_large(b, j->r.np);
+        if (large && n_large >= b.c.max_large) {
+            ++head;
+            continue;
+        }
         if (!admit(b, j)) break;    // waits for arena space
-        b.queue.erase(head);
+        n_large += large;
+        head = b.queue.erase(head);
         *did = true;
     }
     // 3. keep every active job chunks_in_flight chunks ahead
@@ -470,10 +482,11 @@ int pmpm_batch_create(const pmpm_batch_config* cfg, void* d_arena, size_t arena_
                       pmpm_batch** out) {
     if (!cfg || !out || !d_arena) return PMPM_EINVAL;
     if (cfg->max_active < 1 || cfg->max_active > 1024 || cfg->steps_per_chunk < 1 ||
-        cfg->chunks_in_flight < 1 || cfg->priorities < 0 || cfg->priorities > 2) {
+        cfg->chunks_in_flight < 1 || cfg->priorities < 0 || cfg->priorities > 2 ||
+        cfg->large_np < 0 || cfg->max_large < 0) {
         snprintf(g_batch_msg, sizeof(g_batch_msg),
                  "max_active in [1, 1024], steps_per_chunk >= 1, chunks_in_flight >= 1, "
-                 "priorities 0, 1 or 2");
+                 "priorities 0, 1 or 2, large_np and max_large >= 0");
         return PMPM_EINVAL;
     }
     if (reinterpret_cast<uintptr_t>(d_arena) % kArenaAlign) {

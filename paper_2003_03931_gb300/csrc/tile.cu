@@ -23,11 +23,12 @@ __device__ unsigned long long g_phase[4096 * kMarks];
     } while (0)
 #endif
 
-template <int D, bool LM, int PB>
+template <int D, bool LM, int PB, typename CT>
 __device__ __forceinline__ void tile_component(int tid, const TileGeom& g, const TileParams& P,
-                                               const float* gS, const float2* C, float2* W,
+                                               const float* gS, const CT* C, float2* W,
                                                TileCells cells, CtaScratch cs,
-                                               unsigned long long& lo, unsigned long long& hi) {
+                                               unsigned long long& lo, unsigned long long& hi,
+                                               float gscale) {
     __syncthreads();
     PMPM_MARK(7 + 4 * D);
     if (D > 0) {   // the x force's inverse z ran with the forward z pass
@@ -41,7 +42,7 @@ __device__ __forceinline__ void tile_component(int tid, const TileGeom& g, const
     tile_inv_x(tid, g, W);
     __syncthreads();
     PMPM_MARK(10 + 4 * D);
-    tile_interp<D, LM, PB>(tid, g, P, W, cells, cs, lo, hi);
+    tile_interp<D, LM, PB>(tid, g, P, W, cells, cs, lo, hi, gscale);
 }
 
 // 128-bit block sum of the dispersion terms (low-memory mode 3), staged in
@@ -80,11 +81,12 @@ __device__ __forceinline__ void tile_sigma_flush(int tid, const TileParams& P, f
 // The whole tile: prologue, cell tables, deposit, forward transform, then
 // per force component the Green multiply, inverse transform and
 // interpolation (phases of tile_core.cuh with a block barrier between).
-template <bool LM, int PB>
+// CT: storage of the tile spectrum, float2 or (FP16 storage option) __half2.
+template <bool LM, int PB, typename CT = float2>
 __device__ __forceinline__ void tile_body(int tile, const TileParams& P,
                                           unsigned char* tile_smem, CtaScratch cs) {
     uint32_t* R = reinterpret_cast<uint32_t*>(tile_smem);
-    float2* C = reinterpret_cast<float2*>(tile_smem);
+    CT* C = reinterpret_cast<CT*>(tile_smem);
     float2* W = reinterpret_cast<float2*>(tile_smem + (size_t)kTileR * 4);
     float* gS = reinterpret_cast<float*>(tile_smem + (size_t)kTileR * 4 + (size_t)kTileW * 8);
     int* O = reinterpret_cast<int*>(gS + kGreenPacked);
@@ -103,7 +105,21 @@ __device__ __forceinline__ void tile_body(int tile, const TileParams& P,
     tile_deposit_flat<LM, PB>(tid, g, P, R, cells, cs);
     __syncthreads();
     PMPM_MARK(3);
-    tile_fwd_x(tid, R);
+    // FP16 storage: the density less its mean over the halo box (the k = 0
+    // mode, where the short-range kernel vanishes) is scaled by 2^-e so that
+    // every spectrum value, at most 2 x 2^22 per particle of the box (the
+    // forward x transform doubles), stays below 2^15; the interpolation
+    // undoes the scale exactly
+    float scale = 1.f, gscale = 2.384185791015625e-07f, mean = 0.f;
+    if (!std::is_same<CT, float2>::value) {
+        const int total = cells.pre[kHaloMax];
+        const int e = 8 + (total > 1 ? 32 - __clz(total - 1) : 0);
+        scale = ldexpf(1.f, -e);
+        gscale = ldexpf(1.f, e - 22);
+        const int hx = g.c1[0] - g.c0[0] + 4, hy = g.c1[1] - g.c0[1] + 4, hz = g.c1[2] - g.c0[2] + 4;
+        mean = (float)total * 2097152.f / (64.f * (float)(hx * hy * hz));
+    }
+    tile_fwd_x<CT>(tid, R, scale, mean);
     __syncthreads();
     PMPM_MARK(4);
     tile_fwd_y(tid, C);
@@ -111,9 +127,9 @@ __device__ __forceinline__ void tile_body(int tile, const TileParams& P,
     PMPM_MARK(5);
     tile_fwd_z_inv_z0(tid, g, gS, C, W);
     unsigned long long lo = 0, hi = 0;
-    tile_component<0, LM, PB>(tid, g, P, gS, C, W, cells, cs, lo, hi);
-    tile_component<1, LM, PB>(tid, g, P, gS, C, W, cells, cs, lo, hi);
-    tile_component<2, LM, PB>(tid, g, P, gS, C, W, cells, cs, lo, hi);
+    tile_component<0, LM, PB>(tid, g, P, gS, C, W, cells, cs, lo, hi, gscale);
+    tile_component<1, LM, PB>(tid, g, P, gS, C, W, cells, cs, lo, hi, gscale);
+    tile_component<2, LM, PB>(tid, g, P, gS, C, W, cells, cs, lo, hi, gscale);
     if (LM && P.mode == 3) tile_sigma_flush(tid, P, W, lo, hi);
     __syncthreads();
     PMPM_MARK(19);
@@ -121,11 +137,11 @@ __device__ __forceinline__ void tile_body(int tile, const TileParams& P,
 
 // One CTA per tile; one fits an SM at a time (the tile needs 232 KB of shared
 // memory).
-// PB: bytes per position bin.
-template <int PB>
+// PB: bytes per position bin; CT: storage of the tile spectrum.
+template <int PB, typename CT>
 __global__ void __launch_bounds__(kTileThreads, 1) k_tile(TileParams P) {
     extern __shared__ __align__(16) unsigned char tile_smem[];
-    tile_body<false, PB>((int)blockIdx.x, P, tile_smem, CtaScratch{nullptr, nullptr});
+    tile_body<false, PB, CT>((int)blockIdx.x, P, tile_smem, CtaScratch{nullptr, nullptr});
 }
 
 // Low-memory passes (modes 2-4): one CTA per tile, like k_tile.  A tile's
@@ -170,8 +186,10 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_density(TileParams P, 
 }
 
 void tile_setup() {
-    cudaFuncSetAttribute(k_tile<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemBytes);
-    cudaFuncSetAttribute(k_tile<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemBytes);
+    cudaFuncSetAttribute(k_tile<1, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemBytes);
+    cudaFuncSetAttribute(k_tile<2, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemBytes);
+    cudaFuncSetAttribute(k_tile<1, __half2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemBytes);
+    cudaFuncSetAttribute(k_tile<2, __half2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemBytes);
     cudaFuncSetAttribute(k_tile_lowmem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemBytes);
     cudaFuncSetAttribute(k_tile_density<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemBytes);
     cudaFuncSetAttribute(k_tile_density<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemBytes);
@@ -228,8 +246,10 @@ int tile_pass(Sim& s, int mode, float* G) {
         P.out = s.streams[nxt];
     }
     if (mode >= 2) k_tile_lowmem<<<grid, kTileThreads, kTileSmemBytes, s.stream>>>(P);
-    else if (s.pb == 2) k_tile<2><<<grid, kTileThreads, kTileSmemBytes, s.stream>>>(P);
-    else k_tile<1><<<grid, kTileThreads, kTileSmemBytes, s.stream>>>(P);
+    else if (s.fp16 && s.pb == 2) k_tile<2, __half2><<<grid, kTileThreads, kTileSmemBytes, s.stream>>>(P);
+    else if (s.fp16) k_tile<1, __half2><<<grid, kTileThreads, kTileSmemBytes, s.stream>>>(P);
+    else if (s.pb == 2) k_tile<2, float2><<<grid, kTileThreads, kTileSmemBytes, s.stream>>>(P);
+    else k_tile<1, float2><<<grid, kTileThreads, kTileSmemBytes, s.stream>>>(P);
     s.launches++;
     return check_launch(s, "tile pass");
 }

@@ -32,6 +32,10 @@
 // barrier between phases.
 #pragma once
 
+#include <cuda_fp16.h>
+
+#include <type_traits>
+
 #include "common.cuh"
 #include "regfft.cuh"
 
@@ -118,6 +122,16 @@ PMPM_HD int widx(int kx, int ky, int zo) { return ((zo << 5) + ky) * 16 + (kx ^ 
 // the float view of widx: word xo of the pair (xo >> 1) ^ (yo & 15), i.e.
 // xo ^ 2 (yo & 15) (an even XOR keeps the low bit)
 PMPM_HD int wfidx(int xo, int yo, int zo) { return ((zo << 5) + yo) * 32 + (xo ^ ((yo & 15) << 1)); }
+
+// The tile spectrum C is stored as float2 (the default) or, with the FP16
+// storage option, as __half2 at the same index (half the bytes; every
+// transform still computes in float32 registers).
+PMPM_HD float2 cload(const float2* C, int i) { return C[i]; }
+PMPM_HD void cstore(float2* C, int i, float2 v) { C[i] = v; }
+#ifdef __CUDA_ARCH__
+__device__ __forceinline__ float2 cload(const __half2* C, int i) { return __half22float2(C[i]); }
+__device__ __forceinline__ void cstore(__half2* C, int i, float2 v) { C[i] = __float22half2_rn(v); }
+#endif
 
 #ifdef __CUDA_ARCH__
 PMPM_HD uint32_t smem_add_u32(uint32_t* p, uint32_t v) { return atomicAdd(p, v); }
@@ -692,30 +706,44 @@ PMPM_HD void tile_deposit_flat(int tid, const TileGeom& g, const TileParams& P, 
 }
 
 // --- phase 2: forward real transform along x (1024 rows, 2 per thread) -----
-PMPM_HD void tile_fwd_x(int tid, uint32_t* R) {
-    float2* C = reinterpret_cast<float2*>(R);
+// A float2 row of C takes the bytes of its own density row, so each thread
+// transforms in place.  A __half2 row takes half of them, landing on another
+// thread's row: the rows are then read, transformed and, after a barrier,
+// written, one row per thread at a time.  There the density less `mean` (an
+// estimate of the box's mean; it only moves the k = 0 mode, where the
+// short-range kernel vanishes) is scaled by the power of two `scale`, so that
+// FP16 holds the fluctuations, not the mean, within its range.
+template <typename CT = float2>
+PMPM_HD void tile_fwd_x(int tid, uint32_t* R, float scale = 1.f, float mean = 0.f) {
+    CT* C = reinterpret_cast<CT*>(R);
+    constexpr bool kHalf = !std::is_same<CT, float2>::value;
     for (int r = tid; r < 1024; r += kTileThreads) {
         const int y = r & 31, z = r >> 5;
         float x[32];
 #pragma unroll
-        for (int n = 0; n < 32; ++n) x[n] = u32_to_f32(R[ridx(n, y, z)]);
+        for (int n = 0; n < 32; ++n) x[n] = kHalf ? (u32_to_f32(R[ridx(n, y, z)]) - mean) * scale
+                                                  : u32_to_f32(R[ridx(n, y, z)]);
         float2 X[17];
         rfft32x2(x, X);
-        C[cidx(0, y, z)] = make_float2(X[0].x, X[16].x);   // pack Nyquist
+#ifdef __CUDA_ARCH__
+        if (kHalf) __syncthreads();
+#endif
+        cstore(C, cidx(0, y, z), make_float2(X[0].x, X[16].x));   // pack Nyquist
 #pragma unroll
-        for (int k = 1; k < 16; ++k) C[cidx(k, y, z)] = X[k];
+        for (int k = 1; k < 16; ++k) cstore(C, cidx(k, y, z), X[k]);
     }
 }
 
 // --- phase 3: forward complex transform along y (512 pencils) --------------
-PMPM_HD void tile_fwd_y(int tid, float2* C) {
+template <typename CT>
+PMPM_HD void tile_fwd_y(int tid, CT* C) {
     const int kx = tid & 15, z = tid >> 4;
     float2 a[32];
 #pragma unroll
-    for (int k = 0; k < 32; ++k) a[bitrev<5>(k)] = C[cidx(kx, k, z)];
+    for (int k = 0; k < 32; ++k) a[bitrev<5>(k)] = cload(C, cidx(kx, k, z));
     fft_dit<32, -1>(a);
 #pragma unroll
-    for (int k = 0; k < 32; ++k) C[cidx(kx, k, z)] = a[k];
+    for (int k = 0; k < 32; ++k) cstore(C, cidx(kx, k, z), a[k]);
 }
 
 // |signed frequency| and its sign for a 32-point index
@@ -737,8 +765,8 @@ PMPM_HD int green_tri(int b, int c) {
 // Thread mapping of the z passes: warp w owns kx = w and lane l owns ky = l,
 // so warp 0 alone carries the packed kx = 0 / 16 pencils and the other warps
 // run without divergence; every half-warp touches 16 distinct bank pairs.
-template <int D, typename Spec>
-PMPM_HD void inv_z_pencil(int kx, int ky, int nz, const float* gS, Spec spec, const float2* C,
+template <int D, typename Spec, typename CT>
+PMPM_HD void inv_z_pencil(int kx, int ky, int nz, const float* gS, Spec spec, const CT* C,
                           float2* W) {
     const int ay = kabs32(ky);
     float2 a[32];
@@ -783,7 +811,7 @@ PMPM_HD void inv_z_pencil(int kx, int ky, int nz, const float* gS, Spec spec, co
         for (int kz = 0; kz < 32; ++kz) {
             const int az = kabs32(kz);
             const float2 Z = spec(kz);
-            const float2 Zp = C[cidx(0, (32 - ky) & 31, (32 - kz) & 31)];
+            const float2 Zp = cload(C, cidx(0, (32 - ky) & 31, (32 - kz) & 31));
             float s0, s16;
             if (D == 2) {
                 const float sz = (az == 0 || az == 16) ? 0.f : ksgn32(kz);
@@ -807,10 +835,10 @@ PMPM_HD void inv_z_pencil(int kx, int ky, int nz, const float* gS, Spec spec, co
         if (zo < nz) W[widx(kx, ky, zo)] = a[zo + kBuffer - 1];
 }
 
-template <int D>
-PMPM_HD void tile_inv_z(int tid, const TileGeom& g, const float* gS, const float2* C, float2* W) {
+template <int D, typename CT>
+PMPM_HD void tile_inv_z(int tid, const TileGeom& g, const float* gS, const CT* C, float2* W) {
     const int kx = tid >> 5, ky = tid & 31;
-    inv_z_pencil<D>(kx, ky, g.T[2] + 2, gS, [&](int kz) { return C[cidx(kx, ky, kz)]; }, C, W);
+    inv_z_pencil<D>(kx, ky, g.T[2] + 2, gS, [&](int kz) { return cload(C, cidx(kx, ky, kz)); }, C, W);
 }
 
 // --- phase 4 + 5a of the x force: forward transform along z, then at once
@@ -818,14 +846,15 @@ PMPM_HD void tile_inv_z(int tid, const TileGeom& g, const float* gS, const float
 // registers (the stored spectrum serves the y and z forces).  Same thread
 // mapping as the inverse z passes; every half-warp touches 16 distinct bank
 // pairs of the (kx ^ ky) swizzle.
-PMPM_HD void tile_fwd_z_inv_z0(int tid, const TileGeom& g, const float* gS, float2* C, float2* W) {
+template <typename CT>
+PMPM_HD void tile_fwd_z_inv_z0(int tid, const TileGeom& g, const float* gS, CT* C, float2* W) {
     const int kx = tid >> 5, ky = tid & 31;
     float2 a[32];
 #pragma unroll
-    for (int k = 0; k < 32; ++k) a[bitrev<5>(k)] = C[cidx(kx, ky, k)];
+    for (int k = 0; k < 32; ++k) a[bitrev<5>(k)] = cload(C, cidx(kx, ky, k));
     fft_dit<32, -1>(a);
 #pragma unroll
-    for (int k = 0; k < 32; ++k) C[cidx(kx, ky, k)] = a[k];
+    for (int k = 0; k < 32; ++k) cstore(C, cidx(kx, ky, k), a[k]);
     inv_z_pencil<0>(kx, ky, g.T[2] + 2, gS, [&](int kz) { return a[kz]; }, C, W);
 }
 
@@ -918,7 +947,8 @@ PMPM_HD void lowmem_particle(const TileParams& P, const int32_t (&q)[3], const f
 // LM: the low-memory passes (modes 2-4); otherwise modes 0 and 1.
 template <int D, bool LM, int PB>
 PMPM_HD void tile_interp(int tid, const TileGeom& g, const TileParams& P, const float2* W,
-                         TileCells c, CtaScratch cs, unsigned long long& lo, unsigned long long& hi) {
+                         TileCells c, CtaScratch cs, unsigned long long& lo, unsigned long long& hi,
+                         float gscale = 2.384185791015625e-07f) {
     using F = PosFmt<PB>;
     constexpr int U = LM ? 1 : 2;   // particles per thread per iteration, loads issued together
     const float* Wf = reinterpret_cast<const float*>(W);
@@ -995,8 +1025,9 @@ PMPM_HD void tile_interp(int tid, const TileGeom& g, const TileParams& P, const 
                 gf += w * Wf[wfidx(lo3[0] + dx, lo3[1] + dy, lo3[2] + dz)];
             }
             // weights in units of 2^-21, and the forward x transform (rfft32x2)
-            // leaves the whole spectrum doubled: 2^-22
-            const float gval = gf * 2.384185791015625e-07f + gcd[u];
+            // leaves the whole spectrum doubled: gscale = 2^-22 (over the
+            // density's scale with FP16 spectrum storage; a power of two)
+            const float gval = gf * gscale + gcd[u];
             if (!lm && P.mode == 0) {
                 slot[D * n + j[u]] = gval;
                 continue;

@@ -68,13 +68,14 @@ class Engine:
     """A batch engine over one device arena (a torch uint8 tensor)."""
 
     def __init__(self, arena_bytes, max_active=32, share_tables=True, graphs=False,
-                 priorities=True, steps_per_chunk=2, chunks_in_flight=2, device="cuda:0"):
+                 priorities=True, steps_per_chunk=2, chunks_in_flight=2, device="cuda:0",
+                 large_np=0, max_large=0):
         import torch
         self.lib = _lib.load()
         self.device = torch.device(device)
         self.arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device=self.device)
         c = _lib.BatchConfig(max_active, int(share_tables), int(graphs), int(priorities),
-                             steps_per_chunk, chunks_in_flight)
+                             steps_per_chunk, chunks_in_flight, large_np, max_large)
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             rc = self.lib.pmpm_batch_create(ctypes.byref(c), ctypes.c_void_p(self.arena.data_ptr()),

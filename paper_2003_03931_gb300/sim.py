@@ -26,6 +26,7 @@ class SimConfig:
     vel_bytes: int = 1
     pk_mesh_max: int = 0
     lowmem: bool = False    # three tile passes per step, no per-particle intermediate
+    fine_fp16: bool = False # tile spectrum stored as FP16 (PMPM_FLAG_FINE_FP16)
     omega_m: float = 0.0    # background: 0, 0 = Einstein-de Sitter; else LambdaCDM (Sec. IV-A.2)
     omega_l: float = 0.0
 
@@ -33,7 +34,7 @@ class SimConfig:
         c = _lib.Config()
         c.np, c.nc, c.tile_max, c.buffer = self.np, self.nc, self.tile_max, self.buffer
         c.pos_bytes, c.vel_bytes, c.pk_mesh_max = self.pos_bytes, self.vel_bytes, self.pk_mesh_max
-        c.flags = _lib.FLAG_LOWMEM if self.lowmem else 0
+        c.flags = (_lib.FLAG_LOWMEM if self.lowmem else 0) | (_lib.FLAG_FINE_FP16 if self.fine_fp16 else 0)
         c.a_init, c.a_final, c.n_steps = self.a_init, self.a_final, self.n_steps
         c.omega_m, c.omega_l = self.omega_m, self.omega_l
         return c

@@ -83,6 +83,31 @@ def test_large_and_lowmem_boxes_equal_solo_runs(kw):
     _check_against_solo(reqs, res)
 
 
+def test_large_box_limit():
+    # large_np = 128, max_large = 1: two 128^3 boxes are never resident
+    # together, later small requests pass a waiting large one, and every box
+    # still ends as it does alone
+    need_gpu()
+    from paper_2003_03931_gb300.serve import Engine, Request, run_stream
+    reqs = [Request(np=128, nc=64, n_steps=4, seed=31, want_state=True),
+            Request(np=128, nc=64, n_steps=3, seed=32, want_state=True),
+            Request(np=32, nc=16, n_steps=3, seed=33, want_state=True),
+            Request(np=64, nc=32, n_steps=2, seed=34, want_state=True),
+            Request(np=128, nc=64, n_steps=2, seed=35, want_state=True),
+            Request(np=32, nc=16, n_steps=4, seed=36, want_state=True)]
+    eng = Engine(4 << 30, max_active=4, share_tables=True, graphs=False, priorities=1,
+                 steps_per_chunk=1, large_np=128, max_large=1)
+    res = run_stream(eng, reqs, timeout=600)
+    eng.close()
+    big = sorted((r.t_admit, r.t_done) for r in res if r.request.np == 128)
+    for (a0, d0), (a1, d1) in zip(big, big[1:]):
+        assert a1 >= d0 - 1e-3
+    # the small requests behind the second large one did not wait for it
+    second_big_admit = big[1][0]
+    assert min(r.t_admit for r in res if r.request.seed in (33, 34)) < second_big_admit
+    _check_against_solo(reqs, res)
+
+
 def test_request_flags_are_checked():
     need_gpu()
     from paper_2003_03931_gb300 import _lib

@@ -152,3 +152,30 @@ def test_graph_mode_and_shared_tables_are_bitwise_identical():
         np.testing.assert_array_equal(a, b)
     eager.close()
     graph.close()
+
+
+def test_refused_counts_leave_no_state():
+    # counts are checked on the host before any kernel indexes with them; a
+    # refused load leaves the sim without a state until a valid one is loaded
+    need_gpu()
+    from paper_2003_03931_gb300 import _lib
+    from paper_2003_03931_gb300._lib import PMPM_EINVAL, PMPM_ESTATE, PmpmError
+    w = synth.WORKLOADS["c1_32"]
+    sim = make_sim(**w)
+    sim.ic_zeldovich(3, **synth.IC_SPECTRUM)
+    st = sim.fetch_state()
+    bad = st["counts"].copy()
+    bad[0] += 1                                   # adds up to N + 1
+    neg = st["counts"].copy()
+    neg[0] = -1                                   # adds up to N, one negative
+    neg[1] += st["counts"][0] + 1
+    for counts in (bad, neg):
+        with pytest.raises(PmpmError) as e:
+            sim._load(_lib.COUNTS, counts)
+        assert e.value.code == PMPM_EINVAL
+        with pytest.raises(PmpmError) as e:
+            sim.step(1)
+        assert e.value.code == PMPM_ESTATE
+    sim.load_state(st)
+    sim.step(1)
+    sim.close()

@@ -107,7 +107,8 @@ def test_batch_create_rejects_bad_arguments(lib):
     assert lib.pmpm_batch_create(ctypes.byref(good), None, 1 << 20, ctypes.byref(h)) == _lib.PMPM_EINVAL
     for bad in (_lib.BatchConfig(0, 1, 0, 1, 2, 2), _lib.BatchConfig(4, 1, 0, 1, 0, 2),
                 _lib.BatchConfig(4, 1, 0, 1, 2, 0), _lib.BatchConfig(4, 1, 0, 3, 2, 2),
-                _lib.BatchConfig(4, 1, 0, -1, 2, 2)):
+                _lib.BatchConfig(4, 1, 0, -1, 2, 2), _lib.BatchConfig(4, 1, 0, 1, 2, 2, -1, 1),
+                _lib.BatchConfig(4, 1, 0, 1, 2, 2, 256, -1)):
         assert lib.pmpm_batch_create(ctypes.byref(bad), ctypes.c_void_p(1 << 20), 1 << 20,
                                      ctypes.byref(h)) == _lib.PMPM_EINVAL
         assert b"max_active" in lib.pmpm_batch_last_error(None)
