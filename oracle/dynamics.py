@@ -24,11 +24,17 @@ Readings (the paper gives neither the integrator nor the units):
   2^-24, the int64 sum S is exact, and v_c = fl32(fl32(S) 2^-24 / n), a
   float32 division of the rounded sum (the paper fixes v_c = <v>, not how
   its stored value is rounded).
-  The isotropic dispersion is sigma^2 = sum_i sum_d (p_id - v_c,d)^2 / (3N),
-  with each squared float32 difference rounded to a multiple of 2^-32 and
-  summed exactly; sigma^2 = fl64(hi) 2^64 + fl64(lo) in units of 2^-32 of the
-  128-bit sum, divided by 3N, and sigma = fl32(sqrt(sigma^2)), or 2^-24 when
-  the sum is 0.  u then follows ``codec.encode_velocity``.
+  The isotropic dispersion sigma^2 is the variance of Delta v = v - <v>
+  about the cell average <v> (Eq. 3 defines v_c as that average and the
+  velocity map by the variance of Delta v), taken exactly over the same
+  fixed-point momenta P = round(p 2^24) that give the cell sums S: per cell
+  and axis sum_i (P_i - S/n)^2 = sum_i P_i^2 - S^2/n, so
+  sigma^2 = (T - U) 2^-48 / (3N) with T = sum over particles and axes of P^2
+  and U = sum over cells and axes of floor(S^2 / n) (integers; the floor
+  moves sigma^2 by less than one unit of 2^-48 per cell and axis).  The
+  128-bit integer T - U is converted as fl64(hi) 2^64 + fl64(lo), scaled by
+  2^-48 and divided by 3N; sigma = fl32(sqrt(sigma^2)), or 2^-24 when
+  T - U is 0.  u then follows ``codec.encode_velocity``.
 """
 
 import math
@@ -38,7 +44,6 @@ import numpy as np
 from . import codec, force as force_mod
 
 P_FIX_BITS = 24      # p rounded to multiples of 2^-24 for the cell sums
-D2_FIX_BITS = 32     # squared deviations rounded to multiples of 2^-32
 SIGMA_FLOOR = 2.0 ** -24
 
 
@@ -96,10 +101,15 @@ class State:
         return codec.positions_from_codes(self.codes(), self.pos_bytes)
 
 
+def fixed_momenta(p32):
+    """P = round(p 2^24) (half to even), int64, the fixed point of the cell sums."""
+    P = np.rint(np.asarray(p32, dtype=np.float32).astype(np.float64) * 2.0 ** P_FIX_BITS)
+    return P.astype(np.int64)
+
+
 def cell_means(cell, p32, ncells):
     """v_c per cell from fixed-point sums (see module docstring)."""
-    P = np.rint(np.asarray(p32, dtype=np.float32).astype(np.float64) * 2.0 ** P_FIX_BITS)
-    P = P.astype(np.int64)
+    P = fixed_momenta(p32)
     S = np.zeros((ncells, 3), dtype=np.int64)
     np.add.at(S, cell, P)
     n = np.bincount(cell, minlength=ncells).astype(np.int64)
@@ -110,24 +120,39 @@ def cell_means(cell, p32, ncells):
     return vc, S, n
 
 
-def dispersion(p32, vc_of_particle):
-    """sigma (float32) and the exact 128-bit integer sum it comes from."""
-    d = (np.asarray(p32, dtype=np.float32) - np.asarray(vc_of_particle, dtype=np.float32))
-    d = d.astype(np.float32).astype(np.float64)
-    D = np.rint(d * d * 2.0 ** D2_FIX_BITS)
-    if D.size and D.max() >= 2.0 ** 64:
-        raise OverflowError("velocity deviation too large for the dispersion sum")
-    Du = D.astype(np.uint64).ravel()
-    # exact 128-bit sum: split each term into 32-bit halves, sum each half in
-    # int64 (no overflow below 2^31 terms), recombine with Python integers
-    lo32 = (Du & np.uint64(0xFFFFFFFF)).astype(np.int64).sum(dtype=np.int64)
-    hi32 = (Du >> np.uint64(32)).astype(np.int64).sum(dtype=np.int64)
-    total = (int(hi32) << 32) + int(lo32)
-    hi, lo = total >> 64, total & ((1 << 64) - 1)
-    n3 = 3 * d.shape[0]
+def _sum_of_squares(P):
+    """Exact sum of P^2 over an int64 array with |P| < 2^44 (Python integer):
+    P = a 2^22 + b with 0 <= b < 2^22, each part's sum taken in int64 chunks."""
+    P = np.asarray(P, dtype=np.int64).ravel()
+    a = P >> 22
+    b = P & ((1 << 22) - 1)
+    total = 0
+    for i in range(0, P.size, 1 << 16):
+        aa, bb = a[i:i + (1 << 16)], b[i:i + (1 << 16)]
+        total += (int((aa * aa).sum(dtype=np.int64)) << 44) + \
+            (int((2 * aa * bb).sum(dtype=np.int64)) << 22) + int((bb * bb).sum(dtype=np.int64))
+    return total
+
+
+def dispersion(p32, S, n):
+    """sigma (float32) and the exact integer T - U it comes from, from the
+    momenta p32 [N, 3] and the cell sums S [C, 3] and counts n [C] of
+    ``cell_means`` (see module docstring)."""
+    P = fixed_momenta(p32)
+    if P.size and np.abs(P).max() >= 2 ** 44:
+        raise OverflowError("momentum too large for the fixed-point moments")
+    T = _sum_of_squares(P)
+    U = 0
+    nz = np.nonzero(n > 0)[0]
+    for srow, cnt in zip(S[nz].tolist(), n[nz].tolist()):
+        for v in srow:
+            U += (v * v) // cnt
+    total = T - U
+    n3 = 3 * P.shape[0]
     if total == 0 or n3 == 0:
         return np.float32(SIGMA_FLOOR), total
-    s2 = (float(hi) * 2.0 ** 64 + float(lo)) * 2.0 ** -D2_FIX_BITS / float(n3)
+    hi, lo = total >> 64, total & ((1 << 64) - 1)
+    s2 = (float(hi) * 2.0 ** 64 + float(lo)) * 2.0 ** -48 / float(n3)
     return np.float32(math.sqrt(s2)), total
 
 
@@ -140,8 +165,8 @@ def encode(Q, p32, nc, a, step=0, pos_bytes=1):
     cell = codec.flatten_cell(c, nc)
     ncells = nc ** 3
     counts = np.bincount(cell, minlength=ncells)
-    vc, _, _ = cell_means(cell, p32, ncells)
-    sigma, _ = dispersion(p32, vc[cell])
+    vc, S, n = cell_means(cell, p32, ncells)
+    sigma, _ = dispersion(p32, S, n)
     u = codec.encode_velocity(p32, vc[cell], sigma)
     order = np.argsort(cell, kind="stable")
     mdtype = np.uint8 if B == 256 else np.uint16

@@ -124,12 +124,47 @@ def test_encode_invariants_and_exact_sums():
             assert st.vc[c, d] == ref
             exact = S / len(members) * 2.0 ** -24
             assert abs(float(st.vc[c, d]) - exact) <= 2.5e-7 * abs(exact) + 1e-12
-    # sigma against the exact integer sum
-    vcp = st.vc[cell_in]
-    dev = (p - vcp).astype(np.float32).astype(np.float64)
-    exact = sum(int(round(float(v) * float(v) * 2.0 ** 32)) for v in dev.ravel())
-    s2 = exact * 2.0 ** -32 / (3 * N)
+    # sigma: the variance of the fixed-point momenta about the exact cell
+    # means, against exact rationals (Python Fractions), per cell and axis
+    from fractions import Fraction
+    ex = Fraction(0)
+    floor_sum = 0
+    cells = {}
+    for i, c in enumerate(cell_in.tolist()):
+        cells.setdefault(c, []).append(i)
+    for members in cells.values():
+        for d in range(3):
+            vals = [P[i][d] for i in members]
+            mean = Fraction(sum(vals), len(vals))
+            ex += sum((Fraction(v) - mean) ** 2 for v in vals)
+            floor_sum += sum(v * v for v in vals) - (sum(vals) ** 2) // len(vals)
+    _, total = dynamics.dispersion(p, *dynamics.cell_means(cell_in, p, nc ** 3)[1:])
+    assert total == floor_sum
+    # the floor moves the sum by less than one unit per cell and axis
+    assert 0 <= total - ex < 3 * len(cells)
+    s2 = float(ex) * 2.0 ** -48 / (3 * N)
     assert abs(float(st.sigma) - math.sqrt(s2)) <= 1e-7 * math.sqrt(s2)
-    # and sigma is close to the plain float64 dispersion
+    # and sigma is close to the plain float64 dispersion about the stored means
+    vcp = st.vc[cell_in]
     plain = math.sqrt(((p.astype(np.float64) - vcp) ** 2).sum() / (3 * N))
     assert abs(float(st.sigma) - plain) < 1e-6 * plain
+
+
+def test_dispersion_moments_are_exact_for_large_momenta():
+    # momenta near the 2^20 range limit: P^2 near 2^88, sums past 2^64 and
+    # the per-cell floor(S^2/n), all against Python integers
+    rng = np.random.default_rng(12)
+    P = rng.integers(-(2 ** 44) + 1, 2 ** 44, size=(5000, 3))
+    assert dynamics._sum_of_squares(P) == sum(int(v) * int(v) for v in P.ravel())
+    p = (rng.normal(size=(2000, 3)) * 2e5).astype(np.float32)
+    cell = rng.integers(0, 27, size=2000)
+    vc, S, n = dynamics.cell_means(cell, p, 27)
+    sig, total = dynamics.dispersion(p, S, n)
+    Pf = [[int(round(float(v) * 2 ** 24)) for v in row] for row in p]
+    T = sum(v * v for row in Pf for v in row)
+    U = sum((int(S[c, d]) ** 2) // int(n[c]) for c in range(27) if n[c] for d in range(3))
+    assert total == T - U and total > 2 ** 64
+    # invariant under reordering the particles
+    perm = rng.permutation(2000)
+    _, S2, n2 = dynamics.cell_means(cell[perm], p[perm], 27)
+    assert dynamics.dispersion(p[perm], S2, n2)[1] == total
