@@ -82,23 +82,23 @@ extern "C" {
 /* pmpm_config.flags */
 #define PMPM_FLAG_LOWMEM 1   /* Low-memory step for the largest boxes.  The step
                                 keeps no per-particle intermediate: the tile pass
-                                (Sec. II) runs three times per step, first to count
-                                the particles of every new cell and sum their
-                                momenta, then to sum the squared deviations that
-                                give sigma (Eq. 3), then to re-encode and scatter
-                                (Sec. III-A).  Every pass recomputes the same forces,
-                                so the new store is the one the default step writes.
+                                (Sec. II) runs twice per step, first to count the
+                                particles of every new cell and sum their momenta
+                                and squared momenta (which give v_c and sigma,
+                                Eq. 3), then to re-encode and scatter (Sec. III-A).
+                                Both passes compute the same forces, so the new
+                                store is the one the default step writes.
                                 About 24.5 bytes per particle of workspace instead
                                 of 83 (2048^3 particles fit in one GB300), for about
-                                three times the tile work.  A tile may hold at most
+                                twice the tile work.  A tile may hold at most
                                 65,536 of its own particles, and the device at most
                                 160 SM ids (each SM keeps a scratch slot; both
                                 PMPM_EOVERFLOW above).
                                 Initial conditions use float32 transforms and a
                                 float32 displacement field (the default uses
-                                float64).  PMPM_DECODED_Q/P, PMPM_FORCE and loading
-                                PMPM_QP are not available. */
-
+                                float64).  PMPM_DECODED_Q/P, PMPM_FORCE,
+                                PMPM_STEP_QP and loading PMPM_QP are not
+                                available. */
 #define PMPM_FLAG_FINE_FP16 2 /* Precision option (Sec. III-A stores particles in
                                 1 or 2 bytes; this stores the fine-mesh field
                                 compactly too): the tile pass keeps each tile's

@@ -133,7 +133,7 @@ static size_t layout_lowmem(Sim& s, uint8_t* base) {
     s.d_factors = reinterpret_cast<float*>(take(8 * (size_t)s.cfg.n_steps));
     s.d_step = reinterpret_cast<int*>(take(4));
     s.d_kd = reinterpret_cast<float*>(take(8));
-    s.d2 = reinterpret_cast<unsigned long long*>(take(16));
+    s.d2 = reinterpret_cast<unsigned long long*>(take(64));
     for (int b = 0; b < 2; ++b) s.sigma_d[b] = reinterpret_cast<float*>(take(4));
     s.lm_sp = reinterpret_cast<float*>(take(4 * 3 * (size_t)kLowmemCap * s.lm_ctas));
     s.lm_sq = reinterpret_cast<int32_t*>(take(4 * 2 * (size_t)kLowmemCap * s.lm_ctas));
@@ -209,7 +209,7 @@ size_t layout(Sim& s, uint8_t* base) {
     }
     s.fill = reinterpret_cast<int32_t*>(take(4 * (size_t)C));
     s.S = reinterpret_cast<unsigned long long*>(take(24 * (size_t)C));
-    s.d2 = reinterpret_cast<unsigned long long*>(take(16));
+    s.d2 = reinterpret_cast<unsigned long long*>(take(64));
     s.rho_c = reinterpret_cast<long long*>(take(8 * (size_t)C));
     s.cA = reinterpret_cast<float2*>(take(8 * (size_t)C));
     s.cB1 = reinterpret_cast<float2*>(take(8 * (size_t)C));
@@ -299,7 +299,7 @@ static int sync_and_check(Sim& s) {
         if (flags & kErrCount) return set_error(s, PMPM_ECOUNT, "particle count not conserved");
         return set_error(s, PMPM_EOVERFLOW,
                          "device range check failed (flags 0x%x: 1 fine density, 2 momentum, "
-                         "4 velocity deviation, 16 non-finite, 32 drift, 64 more than %d own "
+                         "16 non-finite, 32 drift, 64 more than %d own "
                          "particles in a tile, 128 an SM id of %d or more)", flags, kLowmemCap,
                          kLowmemCtas);
     }
@@ -376,6 +376,7 @@ static int enqueue_step(Sim& s) {
     } else {
         cudaMemsetAsync(s.counts[1 - s.cur], 0, sizeof(int32_t) * s.ncells, s.stream);
         cudaMemsetAsync(s.S, 0, sizeof(unsigned long long) * 3 * s.ncells, s.stream);
+        cudaMemsetAsync(s.d2, 0, 64, s.stream);
         if ((rc = tile_pass(s, 1, nullptr))) return rc;
         prof_mark(s, 2);
         if ((rc = encode_from_qp(s, true))) return rc;

@@ -23,7 +23,6 @@ constexpr int kTileMaxCoarse = 5;                // largest tile, coarse cells
 constexpr int kTileOut = kTileMaxCoarse * kRatio + 2;   // fine nodes a tile gathers from (22)
 constexpr int kGreenS = kTileFFT / 2 + 1;        // 17: |k| range of the tile Green table
 constexpr int kPFixBits = 24;    // momenta rounded to 2^-24 for the cell sums
-constexpr int kD2FixBits = 32;   // squared deviations rounded to 2^-32
 constexpr float kSigmaFloor = 5.9604644775390625e-08f;  // 2^-24
 constexpr int kLowmemCap = 65536;   // own particles per tile the low-memory scratch holds
 
@@ -31,7 +30,6 @@ constexpr int kLowmemCap = 65536;   // own particles per tile the low-memory scr
 enum : uint32_t {
     kErrFineOverflow = 1u,    // a fine tile node exceeded 2^32 - 1 weight units
     kErrMomentum = 2u,        // |p| too large for the 2^-24 fixed-point sums
-    kErrDeviation = 4u,       // |p - v_c| >= 2^16 (dispersion sum range)
     kErrCount = 8u,           // counts do not add up to N
     kErrNaN = 16u,            // non-finite momentum or force
     kErrDrift = 32u,          // drift larger than the int32 code range
@@ -103,23 +101,64 @@ PMPM_HD uint32_t encode_momentum(float p, float vc, float sigma, const float* E,
     return (uint32_t)u;
 }
 
-// round-half-even(d^2 2^32) for a float32 d with |d| < 2^16, in integers:
-// d = m 2^(E - 150) exactly, so d^2 2^32 = m^2 2^(2E - 268) with m^2 < 2^48.
-// A right shift by r rounds half to even as (x + 2^(r-1) - 1 + bit r of x)
-// >> r (checked against the plain remainder test for every float below
-// 2^16).  The dispersion of Eq. 3 is the exact sum of these terms.
-PMPM_HD unsigned long long sq_fix32(float d) {
-    union { float f; uint32_t u; } bits;
-    bits.f = d;
-    const uint32_t b = bits.u & 0x7fffffffu;
-    const uint32_t E = b >> 23, M = b & 0x7fffffu;
-    const uint32_t m = E ? (M | 0x800000u) : M;
-    const unsigned long long m2 = (unsigned long long)m * m;
-    const int sh = 2 * (E ? (int)E : 1) - 268;
-    if (sh >= 0) return m2 << sh;
-    const int r = -sh;
-    if (r > 49) return 0ull;                       // value below 1/4
-    return (m2 + ((1ull << (r - 1)) - 1ull) + ((m2 >> r) & 1ull)) >> r;
+// --------------------------------------------------------- 128-bit moments
+// The dispersion of Eq. 3 comes from exact integer moments of the fixed-point
+// momenta P (below): T = sum P^2 over particles and U = sum floor(S^2 / n)
+// over cells, each kept as a (lo, hi) pair of 64-bit words.
+PMPM_HD unsigned long long umulhi64(unsigned long long a, unsigned long long b) {
+#ifdef __CUDA_ARCH__
+    return __umul64hi(a, b);
+#else
+    return (unsigned long long)(((unsigned __int128)a * b) >> 64);
+#endif
+}
+
+// (lo, hi) += x^2 for |x| < 2^63
+PMPM_HD void add_square128(long long x, unsigned long long& lo, unsigned long long& hi) {
+    const unsigned long long u = x < 0 ? (unsigned long long)(-x) : (unsigned long long)x;
+    const unsigned long long l = u * u;
+    lo += l;
+    hi += umulhi64(u, u) + (lo < l ? 1ull : 0ull);
+}
+
+// (lo, hi) added to a global 128-bit total held as four 32-bit digits in
+// 64-bit words (value = sum d[i] 2^(32 i)): four additions whose result is
+// not read back, so no thread waits on them, and every word stays below
+// 2^64 for up to 2^32 additions.  combine128 folds the digits back.
+PMPM_HD void add128_digits(unsigned long long* d, unsigned long long lo, unsigned long long hi) {
+#ifdef __CUDA_ARCH__
+    if (lo & 0xffffffffull) atomicAdd(&d[0], lo & 0xffffffffull);
+    if (lo >> 32) atomicAdd(&d[1], lo >> 32);
+    if (hi & 0xffffffffull) atomicAdd(&d[2], hi & 0xffffffffull);
+    if (hi >> 32) atomicAdd(&d[3], hi >> 32);
+#else
+    d[0] += lo & 0xffffffffull;
+    d[1] += lo >> 32;
+    d[2] += hi & 0xffffffffull;
+    d[3] += hi >> 32;
+#endif
+}
+
+PMPM_HD void combine128(const unsigned long long* d, unsigned long long& lo, unsigned long long& hi) {
+    const unsigned __int128 v = (unsigned __int128)d[0] + ((unsigned __int128)d[1] << 32) +
+                                ((unsigned __int128)d[2] << 64) + ((unsigned __int128)d[3] << 96);
+    lo = (unsigned long long)v;
+    hi = (unsigned long long)(v >> 64);
+}
+
+// (lo, hi) += floor(S^2 / n) for n >= 1: S^2 = h 2^64 + l, then long
+// division by n in 32-bit digits (every partial remainder is below n < 2^31)
+PMPM_HD void add_square_over_n128(long long S, int n, unsigned long long& lo,
+                                  unsigned long long& hi) {
+    const unsigned long long u = S < 0 ? (unsigned long long)(-S) : (unsigned long long)S;
+    const unsigned long long l = u * u, h = umulhi64(u, u), d = (unsigned long long)n;
+    const unsigned long long qh = h / d, r = h % d;
+    const unsigned long long t1 = (r << 32) | (l >> 32);
+    const unsigned long long q1 = t1 / d, r1 = t1 % d;
+    const unsigned long long t2 = (r1 << 32) | (l & 0xffffffffull);
+    const unsigned long long ql = (q1 << 32) | (t2 / d);
+    lo += ql;
+    hi += qh + (lo < ql ? 1ull : 0ull);
 }
 
 // round-half-even(p 2^24) for a float32 p with |p| < 2^20, in integers (the

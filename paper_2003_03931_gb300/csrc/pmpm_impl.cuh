@@ -43,7 +43,7 @@ struct Sim {
     // step buffers
     int32_t* fill = nullptr;                    // [nc^3]
     unsigned long long* S = nullptr;            // [3][nc^3] fixed-point momentum sums
-    unsigned long long* d2 = nullptr;           // [2] 128-bit dispersion sum (lo, hi)
+    unsigned long long* d2 = nullptr;           // [8] T = sum P^2, U = sum floor(S^2/n), 32-bit digits
     long long* rho_c = nullptr;                 // [nc^3]
     float2* cA = nullptr;                       // [nc^3] coarse spectra
     float2* cB1 = nullptr;
@@ -129,7 +129,7 @@ void fft_setup();
 int scan_counts(Sim& s, const int32_t* counts, int64_t* offsets);
 int encode_from_qp(Sim& s, bool counts_ready);
 int scan_and_means(Sim& s, int nxt);
-int lowmem_passes(Sim& s);             // the three tile passes of a low-memory step
+int lowmem_passes(Sim& s);             // the two tile passes of a low-memory step
 int encode_from_psi(Sim& s, const double* scale);   // low-memory ICs -> store 0
 int decode_state(Sim& s);              // -> s.Qn, s.Pn
 int ic_zeldovich(Sim& s, uint64_t seed, double slope, double kc, double rms);

@@ -196,17 +196,45 @@ __device__ __forceinline__ int key3(const int32_t (&q)[3], int nc) {
     return (q[0] >> sh) + nc * ((q[1] >> sh) + nc * (q[2] >> sh));
 }
 
-// New-cell counts and fixed-point momentum sums.  Each thread takes kHistIlp
+// (lo, hi) of every thread of the block added to the 128-bit total held as
+// digits in dst[0..3]: a warp then a block reduction, then add128_digits
+__device__ __forceinline__ void block_add128(unsigned long long lo, unsigned long long hi,
+                                             unsigned long long* dst) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long l2 = __shfl_down_sync(0xffffffffu, lo, o);
+        const unsigned long long h2 = __shfl_down_sync(0xffffffffu, hi, o);
+        lo += l2;
+        hi += h2 + (lo < l2 ? 1ull : 0ull);
+    }
+    __shared__ unsigned long long shl[32], shh[32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { shl[warp] = lo; shh[warp] = hi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        lo = 0; hi = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            lo += shl[w];
+            hi += shh[w] + (lo < shl[w] ? 1ull : 0ull);
+        }
+        add128_digits(dst, lo, hi);
+    }
+}
+
+// New-cell counts, fixed-point momentum sums S and the second moment
+// T = sum P^2 of Eq. 3's dispersion (digits d2[0..3]).  Each thread takes kHistIlp
 // particles at a time and issues all their loads before the atomics; the
 // sums are integers, so their order does not matter.  (Grouping the lanes of
 // a warp by cell before the atomics measured no faster: the kernel waits on
 // its loads, not on atomic throughput.)
 constexpr int kHistIlp = 4;
 template <int PB, class Src>
-__global__ void k_hist(Src src, int64_t n, int nc, int32_t* counts, unsigned long long* S,
-                       uint32_t* err) {
+__global__ void __launch_bounds__(256) k_hist(Src src, int64_t n, int nc, int32_t* counts,
+                                              unsigned long long* S, unsigned long long* d2,
+                                              uint32_t* err) {
     const int64_t ncells = (int64_t)nc * nc * nc;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long tlo = 0, thi = 0;
     for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < n;
          i0 += stride * kHistIlp) {
         int32_t q[kHistIlp][3];
@@ -229,90 +257,57 @@ __global__ void k_hist(Src src, int64_t n, int nc, int32_t* counts, unsigned lon
                 if (fabsf(p[u][d]) < 1048576.f) fx = fix24_rn(p[u][d]);
                 else atomicOr(err, p[u][d] == p[u][d] ? kErrMomentum : kErrNaN);
                 atomicAdd(&S[d * ncells + key], (unsigned long long)fx);
+                add_square128(fx, tlo, thi);
             }
         }
     }
+    block_add128(tlo, thi, d2);
 }
 
-// 128-bit sum of round((p - v_c)^2 2^32).  Each thread takes kSigmaIlp
-// particles at a time and issues all their loads before using any.
-constexpr int kSigmaIlp = 4;
-template <int PB, class Src>
-__global__ void __launch_bounds__(256) k_sigma(Src src, int64_t n, int nc,
-                                               const float* __restrict__ vc,
-                                               unsigned long long* d2, uint32_t* err) {
-    const int64_t ncells = (int64_t)nc * nc * nc;
-    const float* vcd[3] = {vc, vc + ncells, vc + 2 * ncells};
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+// U = sum over cells and axes of floor(S^2 / n) into the digits d2[4..7]
+// (the cell-mean part of Eq. 3's dispersion; the new counts and sums S)
+__global__ void __launch_bounds__(256) k_cell_moment(int64_t ncells, const int32_t* __restrict__ counts,
+                                                     const unsigned long long* __restrict__ S,
+                                                     unsigned long long* d2) {
     unsigned long long lo = 0, hi = 0;
-    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < n;
-         i0 += stride * kSigmaIlp) {
-        int key[kSigmaIlp];
-        float p[kSigmaIlp][3], v[kSigmaIlp][3];
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncells;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const int cnt = counts[c];
+        if (cnt <= 0) continue;
 #pragma unroll
-        for (int u = 0; u < kSigmaIlp; ++u) {
-            const int64_t i = i0 + u * stride;
-            int32_t q[3] = {0, 0, 0};
-            p[u][0] = p[u][1] = p[u][2] = 0.f;
-            if (i < n) src.load(i, q, p[u]);
-            key[u] = i < n ? key3<PB>(q, nc) : -1;
-        }
-#pragma unroll
-        for (int u = 0; u < kSigmaIlp; ++u)
-#pragma unroll
-            for (int d = 0; d < 3; ++d) v[u][d] = key[u] >= 0 ? vcd[d][key[u]] : 0.f;
-#pragma unroll
-        for (int u = 0; u < kSigmaIlp; ++u) {
-            if (key[u] < 0) continue;
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                const float dev = __fsub_rn(p[u][d], v[u][d]);
-                if (!(fabsf(dev) < 65536.f)) {
-                    atomicOr(err, kErrDeviation);
-                    continue;
-                }
-                const unsigned long long t = sq_fix32(dev);
-                lo += t;
-                if (lo < t) ++hi;
-            }
-        }
+        for (int d = 0; d < 3; ++d) add_square_over_n128((long long)S[d * ncells + c], cnt, lo, hi);
     }
-    // warp then block reduction of (hi, lo) with carries
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long l2 = __shfl_down_sync(0xffffffffu, lo, o);
-        const unsigned long long h2 = __shfl_down_sync(0xffffffffu, hi, o);
-        lo += l2;
-        hi += h2 + (lo < l2 ? 1ull : 0ull);
-    }
-    __shared__ unsigned long long shl[8], shh[8];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) { shl[warp] = lo; shh[warp] = hi; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        lo = 0; hi = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            lo += shl[w];
-            hi += shh[w] + (lo < shl[w] ? 1ull : 0ull);
-        }
-        const unsigned long long old = atomicAdd(&d2[0], lo);
-        const unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
-        if (hi + carry) atomicAdd(&d2[1], hi + carry);
-    }
+    block_add128(lo, hi, d2 + 4);
 }
 
+// sigma = fl32(sqrt((T - U) 2^-48 / 3N)), 2^-24 when T - U = 0 (T and U
+// from the digits d2[0..3] and d2[4..7]; Eq. 3's dispersion about the exact
+// cell means)
 __global__ void k_sigma_final(const unsigned long long* d2, int64_t n, float* sigma) {
-    const unsigned long long lo = d2[0], hi = d2[1];
+    unsigned long long tl, th, ul, uh;
+    combine128(d2, tl, th);
+    combine128(d2 + 4, ul, uh);
+    const unsigned long long lo = tl - ul;
+    const unsigned long long hi = th - uh - (tl < ul ? 1ull : 0ull);
     float s;
     if (lo == 0 && hi == 0) {
         s = kSigmaFloor;
     } else {
         const double v = __dadd_rn(__dmul_rn(__ull2double_rn(hi), 18446744073709551616.0),
                                    __ull2double_rn(lo));
-        const double s2 = __ddiv_rn(__dmul_rn(v, 0x1p-32), (double)(3 * n));
+        const double s2 = __ddiv_rn(__dmul_rn(v, 0x1p-48), (double)(3 * n));
         s = __double2float_rn(__dsqrt_rn(s2));
     }
     *sigma = s;
+}
+
+// The dispersion after the counts, sums S and T of the new cells: U per
+// cell, then sigma of buffer nxt.
+static void finish_sigma(Sim& s, int nxt) {
+    k_cell_moment<<<grid_for(s.ncells, 256, 152 * 8), 256, 0, s.stream>>>(s.ncells, s.counts[nxt], s.S,
+                                                                           s.d2);
+    k_sigma_final<<<1, 1, 0, s.stream>>>(s.d2, s.n, s.sigma_d[nxt]);
+    s.launches += 2;
 }
 
 // Re-encode (Eq. 2-3) into the slot offsets[cell] + rank of each particle.
@@ -435,20 +430,16 @@ int encode_from_qp(Sim& s, bool counts_ready) {
     if (!counts_ready) {
         cudaMemsetAsync(s.counts[nxt], 0, sizeof(int32_t) * s.ncells, st);
         cudaMemsetAsync(s.S, 0, sizeof(unsigned long long) * 3 * s.ncells, st);
+        cudaMemsetAsync(s.d2, 0, 64, st);
         auto kh = s.pb == 2 ? k_hist<2, QPArrays> : k_hist<1, QPArrays>;
         kh<<<grid_for(s.n, 256, 152 * 8), 256, 0, st>>>(QPArrays{s.Qn, s.Pn, s.n}, s.n, s.nc,
-                                                         s.counts[nxt], s.S, s.err);
+                                                         s.counts[nxt], s.S, s.d2, s.err);
         s.launches++;
     }
     int rc = scan_and_means(s, nxt);
     if (rc) return rc;
     prof_mark(s, 3);
-    cudaMemsetAsync(s.d2, 0, 16, st);
-    auto ks = s.pb == 2 ? k_sigma<2, QPArrays> : k_sigma<1, QPArrays>;
-    ks<<<grid_for(s.n, 256, 152 * 8), 256, 0, st>>>(QPArrays{s.Qn, s.Pn, s.n}, s.n, s.nc, s.vc[nxt],
-                                                     s.d2, s.err);
-    k_sigma_final<<<1, 1, 0, st>>>(s.d2, s.n, s.sigma_d[nxt]);
-    s.launches += 2;
+    finish_sigma(s, nxt);
     prof_mark(s, 4);
     auto kc = s.pb == 2 ? k_scatter<2, QPArrays> : k_scatter<1, QPArrays>;
     kc<<<grid_for(s.n, 256), 256, 0, st>>>(QPArrays{s.Qn, s.Pn, s.n}, s.n, s.nc, s.vc[nxt],
@@ -474,16 +465,16 @@ int encode_from_psi(Sim& s, const double* scale) {
     const int nxt = 0;
     cudaMemsetAsync(s.counts[nxt], 0, sizeof(int32_t) * s.ncells, st);
     cudaMemsetAsync(s.S, 0, sizeof(unsigned long long) * 3 * s.ncells, st);
-    k_hist<1><<<grid_for(s.n, 256, 152 * 8), 256, 0, st>>>(src, s.n, s.nc, s.counts[nxt], s.S, s.err);
+    cudaMemsetAsync(s.d2, 0, 64, st);
+    k_hist<1><<<grid_for(s.n, 256, 152 * 8), 256, 0, st>>>(src, s.n, s.nc, s.counts[nxt], s.S, s.d2,
+                                                           s.err);
     s.launches++;
     int rc = scan_and_means(s, nxt);
     if (rc) return rc;
-    cudaMemsetAsync(s.d2, 0, 16, st);
-    k_sigma<1><<<grid_for(s.n, 256, 152 * 8), 256, 0, st>>>(src, s.n, s.nc, s.vc[nxt], s.d2, s.err);
-    k_sigma_final<<<1, 1, 0, st>>>(s.d2, s.n, s.sigma_d[nxt]);
+    finish_sigma(s, nxt);
     k_scatter<1><<<grid_for(s.n, 256), 256, 0, st>>>(src, s.n, s.nc, s.vc[nxt], s.offsets[nxt], s.fill,
                                                   s.sigma_d[nxt], s.Eedge, s.streams[nxt], s.err);
-    s.launches += 3;
+    s.launches += 1;
     s.cur = nxt;
     s.offsets_valid = true;
     s.have_state = true;
@@ -491,23 +482,22 @@ int encode_from_psi(Sim& s, const double* scale) {
     return check_launch(s, "encode");
 }
 
-// The three low-memory tile passes of one step (PMPM_FLAG_LOWMEM): new-cell
-// counts and momentum sums, scan and cell means, the exact dispersion sum,
-// then re-encode and scatter into the other store buffer.
+// The two low-memory tile passes of one step (PMPM_FLAG_LOWMEM): new-cell
+// counts, momentum sums and their second moment; scan, cell means and the
+// dispersion of Eq. 3 from those sums; then re-encode and scatter into the
+// other store buffer.
 int lowmem_passes(Sim& s) {
     const int nxt = 1 - s.cur;
     cudaStream_t st = s.stream;
     int rc;
     cudaMemsetAsync(s.counts[nxt], 0, sizeof(int32_t) * s.ncells, st);
     cudaMemsetAsync(s.S, 0, sizeof(unsigned long long) * 3 * s.ncells, st);
+    cudaMemsetAsync(s.d2, 0, 64, st);
     if ((rc = tile_pass(s, 2, nullptr))) return rc;
     prof_mark(s, 2);
     if ((rc = scan_and_means(s, nxt))) return rc;
     prof_mark(s, 3);
-    cudaMemsetAsync(s.d2, 0, 16, st);
-    if ((rc = tile_pass(s, 3, nullptr))) return rc;
-    k_sigma_final<<<1, 1, 0, st>>>(s.d2, s.n, s.sigma_d[nxt]);
-    s.launches++;
+    finish_sigma(s, nxt);
     prof_mark(s, 4);
     if ((rc = tile_pass(s, 4, nullptr))) return rc;
     prof_mark(s, 5);

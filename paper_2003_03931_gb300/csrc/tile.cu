@@ -45,8 +45,10 @@ __device__ __forceinline__ void tile_component(int tid, const TileGeom& g, const
     tile_interp<D, LM, PB>(tid, g, P, W, cells, cs, lo, hi, gscale);
 }
 
-// 128-bit block sum of the dispersion terms (low-memory mode 3), staged in
-// the free W area, added to d2 by thread 0.
+// 128-bit block sum of the second moment T = sum P^2 of the tile's own
+// particles' new momenta (the default step's fused sums and the low-memory
+// counting pass), staged in the free W area, added to the digits d2[0..3]
+// by thread 0 (no atomic is waited for: the CTA ends right after).
 __device__ __forceinline__ void tile_sigma_flush(int tid, const TileParams& P, float2* W,
                                                  unsigned long long lo, unsigned long long hi) {
     unsigned long long* sh = reinterpret_cast<unsigned long long*>(W);
@@ -70,11 +72,7 @@ __device__ __forceinline__ void tile_sigma_flush(int tid, const TileParams& P, f
             lo += sh[2 * w];
             hi += sh[2 * w + 1] + (lo < sh[2 * w] ? 1ull : 0ull);
         }
-        if (lo | hi) {
-            const unsigned long long old = atomicAdd(&P.d2[0], lo);
-            const unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
-            if (hi + carry) atomicAdd(&P.d2[1], hi + carry);
-        }
+        add128_digits(P.d2, lo, hi);
     }
 }
 
@@ -130,7 +128,8 @@ __device__ __forceinline__ void tile_body(int tile, const TileParams& P,
     tile_component<0, LM, PB>(tid, g, P, gS, C, W, cells, cs, lo, hi, gscale);
     tile_component<1, LM, PB>(tid, g, P, gS, C, W, cells, cs, lo, hi, gscale);
     tile_component<2, LM, PB>(tid, g, P, gS, C, W, cells, cs, lo, hi, gscale);
-    if (LM && P.mode == 3) tile_sigma_flush(tid, P, W, lo, hi);
+    if ((LM && P.mode == 2) || (!LM && P.mode == 1 && P.counts_new != nullptr))
+        tile_sigma_flush(tid, P, W, lo, hi);
     __syncthreads();
     PMPM_MARK(19);
 }
@@ -144,7 +143,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(TileParams P) {
     tile_body<false, PB, CT>((int)blockIdx.x, P, tile_smem, CtaScratch{nullptr, nullptr});
 }
 
-// Low-memory passes (modes 2-4): one CTA per tile, like k_tile.  A tile's
+// Low-memory passes (modes 2 and 4): one CTA per tile, like k_tile.  A tile's
 // scratch slot is its SM's (one tile CTA fits an SM at a time, so no two
 // running CTAs share a slot).  (A persistent loop over tiles with the body
 // out of line was 10% slower: the out-of-line body reads the parameters
@@ -230,6 +229,7 @@ int tile_pass(Sim& s, int mode, float* G) {
     if (mode == 1) {
         P.counts_new = s.counts[1 - s.cur];
         P.S = s.S;
+        P.d2 = s.d2;
     }
     if (mode >= 2) {
         const int nxt = 1 - s.cur;

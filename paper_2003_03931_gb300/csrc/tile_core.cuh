@@ -75,15 +75,15 @@ struct TileParams {
     int32_t* Qn;                  // [3][N] new codes (mode 1)
     float* Pn;                    // [3][N] new momenta (mode 1)
     uint32_t* err;
-    // low-memory passes: mode 2 counts the new cells and sums their momenta,
-    // mode 3 sums the squared deviations (Eq. 3), mode 4 re-encodes and
-    // scatters (Sec. III-A); per-CTA scratch of kLowmemCap own particles
+    // low-memory passes: mode 2 counts the new cells and sums their momenta
+    // and squared momenta, mode 4 re-encodes and scatters (Sec. III-A);
+    // per-CTA scratch of kLowmemCap own particles
     float* sp;                    // [CTAs][3][kLowmemCap] parked long-range force, new momenta
     int32_t* sq;                  // [CTAs][2][kLowmemCap] new codes of components 0 and 1
     int32_t* counts_new;          // [nc^3] (modes 1 and 2)
     unsigned long long* S;        // [3][nc^3] momentum sums in units of 2^-24 (modes 1 and 2)
-    const float* vc_new;          // [3][nc^3] (modes 3, 4)
-    unsigned long long* d2;       // [2] 128-bit dispersion sum (mode 3)
+    const float* vc_new;          // [3][nc^3] (mode 4)
+    unsigned long long* d2;       // [4] digits of T = sum P^2 of the new momenta (modes 1, 2)
     const int64_t* offsets_new;   // [nc^3 + 1] (mode 4)
     int32_t* fill;                // [nc^3] slots taken per new cell (mode 4)
     const float* sigma_new;       // device scalar (mode 4)
@@ -898,9 +898,9 @@ __host__ __device__ __noinline__ void tile_inv_x(int tid, const TileGeom& g, flo
 // --- phase 5d: interpolate component D to the tile's own particles, add the
 // parked long-range part, then (mode 1) kick and drift that component.
 // Low-memory passes: the new cell of one particle from its three new codes,
-// then mode 2 (count and momentum sums, as the default step's histogram),
-// mode 3 (squared deviation from the new cell mean, exact 128-bit sum in
-// lo/hi), or mode 4 (slot in the new cell, Eq. 2-3 re-encode).
+// then mode 2 (count, momentum sums and the 128-bit second moment in lo/hi,
+// as the default step's fused histogram) or mode 4 (slot in the new cell,
+// Eq. 2-3 re-encode).
 PMPM_HD void lowmem_particle(const TileParams& P, const int32_t (&q)[3], const float (&p)[3],
                              float sigma_new, unsigned long long& lo, unsigned long long& hi) {
     const int64_t C = (int64_t)P.nc * P.nc * P.nc;
@@ -913,18 +913,7 @@ PMPM_HD void lowmem_particle(const TileParams& P, const int32_t (&q)[3], const f
             if (fabsf(p[d]) < 1048576.f) fx = fix24_rn(p[d]);
             else flag_error(P.err, p[d] == p[d] ? kErrMomentum : kErrNaN);
             gmem_add_u64(&P.S[d * C + key], (unsigned long long)fx);
-        }
-    } else if (P.mode == 3) {
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            const float dev = fsub_rn(p[d], P.vc_new[d * C + key]);
-            if (!(fabsf(dev) < 65536.f)) {
-                flag_error(P.err, kErrDeviation);
-                continue;
-            }
-            const unsigned long long t = sq_fix32(dev);
-            lo += t;
-            if (lo < t) ++hi;
+            add_square128(fx, lo, hi);
         }
     } else {
         // every pass recomputes the same codes, so a cell never receives more
@@ -944,7 +933,7 @@ PMPM_HD void lowmem_particle(const TileParams& P, const int32_t (&q)[3], const f
     }
 }
 
-// LM: the low-memory passes (modes 2-4); otherwise modes 0 and 1.
+// LM: the low-memory passes (modes 2 and 4); otherwise modes 0 and 1.
 template <int D, bool LM, int PB>
 PMPM_HD void tile_interp(int tid, const TileGeom& g, const TileParams& P, const float2* W,
                          TileCells c, CtaScratch cs, unsigned long long& lo, unsigned long long& hi,
@@ -1064,6 +1053,7 @@ PMPM_HD void tile_interp(int tid, const TileGeom& g, const TileParams& P, const 
                         if (fabsf(pa[d]) < 1048576.f) fx = fix24_rn(pa[d]);
                         else flag_error(P.err, pa[d] == pa[d] ? kErrMomentum : kErrNaN);
                         gmem_add_u64(&P.S[d * ncells + key], (unsigned long long)fx);
+                        add_square128(fx, lo, hi);
                     }
                 }
                 continue;

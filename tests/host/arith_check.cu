@@ -38,32 +38,43 @@ static void check_fix24() {
     printf("fix24 %lld %lld\n", n, bad);
 }
 
-// round-half-even of d^2 2^32 from the exact square (m^2 < 2^48) and a
-// remainder test
-static void check_sq() {
+// The 128-bit moments of the dispersion: (lo, hi) += x^2 and
+// (lo, hi) += floor(S^2 / n), against unsigned __int128 arithmetic, for
+// random and extreme arguments, accumulated over many terms (carries)
+static void check_moments() {
     long long n = 0, bad = 0;
-    for (int i = 0; i < 4000000; ++i) {
-        const float d = bits_float((uint32_t)next_u64() & 0x7fffffffu);
-        if (!(d < 65536.f)) continue;
+    unsigned long long lo = 0, hi = 0, lo2 = 0, hi2 = 0;
+    unsigned __int128 ref = 0, ref2 = 0;
+    for (int i = 0; i < 2000000; ++i) {
+        long long x = (long long)(next_u64() >> (i % 3 == 0 ? 19 : 21));   // up to 2^45
+        if (next_u64() & 1) x = -x;
+        if (i % 101 == 0) x = (i & 1) ? (1ll << 44) - 1 : -((1ll << 44) - 1);
+        const unsigned __int128 ux = (unsigned __int128)(x < 0 ? -x : x);
+        add_square128(x, lo, hi);
+        ref += ux * ux;
+        int cnt = (int)(next_u64() % 70000) + 1;
+        if (i % 97 == 0) cnt = (i & 1) ? 1 : 2147483647;
+        add_square_over_n128(x, cnt, lo2, hi2);
+        ref2 += ux * ux / (unsigned)cnt;
         ++n;
-        uint32_t u;
-        memcpy(&u, &d, 4);
-        const uint32_t E = u >> 23, M = u & 0x7fffffu;
-        const unsigned long long m = E ? (M | 0x800000u) : M;
-        const int e = (E ? (int)E : 1) - 150;
-        const unsigned long long m2 = m * m;
-        const int sh = 2 * e + 32;
-        unsigned long long ref;
-        if (sh >= 0) ref = m2 << sh;
-        else if (-sh > 60) ref = 0;
-        else {
-            const int r = -sh;
-            const unsigned long long q = m2 >> r, rem = m2 - (q << r), half = 1ull << (r - 1);
-            ref = q + ((rem > half || (rem == half && (q & 1))) ? 1 : 0);
-        }
-        if (sq_fix32(d) != ref) ++bad;
+        if (lo != (unsigned long long)ref || hi != (unsigned long long)(ref >> 64)) ++bad;
+        if (lo2 != (unsigned long long)ref2 || hi2 != (unsigned long long)(ref2 >> 64)) ++bad;
     }
-    printf("sq_fix32 %lld %lld\n", n, bad);
+    // the sums pass 2^64 many times over
+    if (hi == 0 || hi2 == 0) ++bad;
+    // the 32-bit-digit totals the kernels add to without reading back
+    unsigned long long dig[4] = {0, 0, 0, 0};
+    unsigned __int128 ref3 = 0;
+    for (int i = 0; i < 200000; ++i) {
+        const unsigned long long a = next_u64(), b = next_u64() >> (i % 5 == 0 ? 0 : 20);
+        add128_digits(dig, a, b);
+        ref3 += ((unsigned __int128)b << 64) | a;
+        ++n;
+    }
+    unsigned long long l3, h3;
+    combine128(dig, l3, h3);
+    if (l3 != (unsigned long long)ref3 || h3 != (unsigned long long)(ref3 >> 64)) ++bad;
+    printf("moments %lld %lld\n", n, bad);
 }
 
 static void check_rhe() {
@@ -178,7 +189,7 @@ static void check_encode() {
 int main() {
     check_fix24();
     check_encode();
-    check_sq();
+    check_moments();
     check_rhe();
     double e = 0;
     for (int t = 0; t < 20; ++t) {

@@ -822,12 +822,12 @@ static void check_interp(long long& n, long long& bad, double& err, int mode) {
     bad += errw != 0u;
 }
 
-// The low-memory passes (modes 2-4, one tile body each, own particles in a
-// CTA scratch slot instead of global arrays) against the default pass (mode
-// 1) of the same tile with the same force fields: mode 2's new-cell counts
-// and momentum sums equal mode 1's fused sums exactly; mode 3's 128-bit
-// dispersion sum equals the exact sum of round-half-even((p - v_c)^2 2^32)
-// over mode 1's momenta; mode 4 writes into each new cell's slots exactly
+// The low-memory passes (modes 2 and 4, one tile body each, own particles in
+// a CTA scratch slot instead of global arrays) against the default pass
+// (mode 1) of the same tile with the same force fields: mode 2's new-cell
+// counts and momentum sums equal mode 1's fused sums exactly, and both
+// passes' 128-bit second moment sum P^2 equals the exact sum over mode 1's
+// momenta (past 2^64 in the crowded tile); mode 4 writes into each new cell's slots exactly
 // the records that mode 1's codes and momenta give (position byte, and the
 // Eq. 3 bin by the definition: the number of edges at or below t).
 template <int D, bool LM>
@@ -843,9 +843,8 @@ static void check_lowmem(long long& n, long long& bad) {
     std::vector<float> Fl(3 * nc3), green(kGreenPacked, 0.f), Td(256), vc(3 * nc3), vcn(3 * nc3), E(256);
     for (auto& v : Fl) v = (float)((double)(next_u64() >> 11) * 0x1p-53 * 2.0 - 1.0);
     for (auto& v : vc) v = (float)((double)(next_u64() >> 11) * 0x1p-53 * 40.0 - 20.0);
-    // new cell means far from the momenta: the dispersion sum passes 2^64
-    // (the 128-bit carry is exercised), and a wide sigma_new keeps the Eq. 3
-    // bins spread
+    // new cell means spread widely and a wide sigma_new keep the Eq. 3 bins
+    // of the scatter pass spread
     for (auto& v : vcn) v = (float)((double)(next_u64() >> 11) * 0x1p-53 * 4000.0 - 2000.0);
     for (int i = 0; i < 256; ++i) Td[i] = (float)(std::tan(M_PI * ((i + 0.5) / 256.0 - 0.5)) * 0.25);
     E[0] = -INFINITY;
@@ -928,7 +927,7 @@ static void check_lowmem(long long& n, long long& bad) {
     for (const auto& tt : tiles) {
         const TileGeom g = tile_geom(tt[0] + nt * (tt[1] + nt * tt[2]), nc, nt);
         const unsigned long long seed = next_u64() | 1ull;
-        unsigned long long lo = 0, hi = 0;
+        unsigned long long lo = 0, hi = 0, lo2 = 0, hi2 = 0;
         // default pass: new codes, momenta and fused sums
         P.counts_new = cnew.data();
         P.S = S.data();
@@ -940,7 +939,7 @@ static void check_lowmem(long long& n, long long& bad) {
         P.S = S2.data();
         std::fill(cnew2.begin(), cnew2.end(), 0);
         std::fill(S2.begin(), S2.end(), 0ull);
-        run(g, 2, seed, lo, hi);
+        run(g, 2, seed, lo2, hi2);
         for (int64_t i = 0; i < nc3; ++i) {
             ++n;
             bad += cnew2[i] != cnew[i] || S2[i] != S[i] || S2[nc3 + i] != S[nc3 + i] || S2[2 * nc3 + i] != S[2 * nc3 + i];
@@ -956,30 +955,19 @@ static void check_lowmem(long long& n, long long& bad) {
         auto key_of = [&](int64_t j) {
             return Qn[j] / 256 + nc * (Qn[np + j] / 256 + nc * (Qn[2 * np + j] / 256));
         };
-        // mode 3: exact dispersion sum
+        // the second moment T = sum P^2 of the new momenta (P = round(p 2^24)),
+        // the same from both passes and equal to the exact sum
         unsigned __int128 ref = 0;
         for (int64_t j : own)
             for (int d = 0; d < 3; ++d) {
-                const float dev = Pn[d * np + j] - vcn[d * nc3 + key_of(j)];
-                int ex;
-                const double fr = std::frexp((double)dev, &ex);              // dev = fr 2^ex
-                const unsigned long long m = (unsigned long long)std::fabs(std::ldexp(fr, 24));   // 24-bit
-                const unsigned long long m2 = m * m;                         // dev^2 = m2 2^(2 ex - 48)
-                const int sh = 2 * ex - 48 + 32;
-                unsigned long long t;
-                if (sh >= 0) t = m2 << sh;
-                else if (-sh >= 64) t = 0;
-                else {
-                    const int r = -sh;
-                    const unsigned long long q = m2 >> r, rem = m2 - (q << r), half = 1ull << (r - 1);
-                    t = rem > half || (rem == half && (q & 1)) ? q + 1 : q;
-                }
-                ref += t;
+                const long long fx = fix24_rn(Pn[d * np + j]);
+                const unsigned __int128 u = (unsigned __int128)(fx < 0 ? -fx : fx);
+                ref += u * u;
             }
-        lo = hi = 0;
-        run(g, 3, seed, lo, hi);
         ++n;
         bad += lo != (unsigned long long)ref || hi != (unsigned long long)(ref >> 64);
+        ++n;
+        bad += lo2 != lo || hi2 != hi;
         if (&tt == &tiles[0]) {   // the crowded tile's sum passes 2^64
             ++n;
             bad += hi == 0;

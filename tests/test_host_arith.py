@@ -49,7 +49,7 @@ def layout(tmp_path_factory):
     return _run_host_check(tmp_path_factory, "tile_check")
 
 
-@pytest.mark.parametrize("name", ["fix24", "sq_fix32", "round_half_even"])
+@pytest.mark.parametrize("name", ["fix24", "moments", "round_half_even"])
 def test_integer_rounding_matches_definition(results, name):
     cases, fails, _ = results[name]
     assert cases > 1_000_000 and fails == 0
