@@ -80,20 +80,20 @@ extern "C" {
                                     particle (Sec. II) */
 
 /* pmpm_config.flags */
-#define PMPM_FLAG_LOWMEM 1   /* Low-memory step for the largest boxes.  The step
-                                keeps no per-particle intermediate: the tile pass
-                                (Sec. II) runs twice per step, first to count the
-                                particles of every new cell and sum their momenta
-                                and squared momenta (which give v_c and sigma,
-                                Eq. 3), then to re-encode and scatter (Sec. III-A).
-                                Both passes compute the same forces, so the new
-                                store is the one the default step writes.
-                                About 24.5 bytes per particle of workspace instead
-                                of 83 (2048^3 particles fit in one GB300), for about
-                                twice the tile work.  A tile may hold at most
-                                65,536 of its own particles, and the device at most
-                                160 SM ids (each SM keeps a scratch slot; both
-                                PMPM_EOVERFLOW above).
+#define PMPM_FLAG_LOWMEM 1   /* Low-memory step for the largest boxes.  The tile
+                                pass (Sec. II) keeps only the new momenta (float32,
+                                12 bytes per particle, in the space the coarse mesh
+                                uses earlier in the step), not the new codes, and
+                                counts the new cells and sums their momenta and
+                                squared momenta (which give v_c and sigma, Eq. 3).
+                                The re-encode (Sec. III-A) then derives each
+                                particle's new codes again from its old codes and
+                                new momentum, with the same integer drift, so the
+                                new store is the one the default step writes.
+                                The momentum sums and F_l share the next store's
+                                space.  About 30.5 bytes per particle of workspace
+                                instead of 83 (2048^3 particles: 262.5 GB, which
+                                fits one GB300).
                                 Initial conditions use float32 transforms and a
                                 float32 displacement field (the default uses
                                 float64).  PMPM_DECODED_Q/P, PMPM_FORCE,

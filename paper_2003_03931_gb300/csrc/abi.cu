@@ -94,20 +94,27 @@ static void derive(Sim& s, const pmpm_config* c) {
     s.fp16 = (c->flags & PMPM_FLAG_FINE_FP16) != 0;
     s.pb = c->pos_bytes == 2 ? 2 : 1;
     s.ic_pfac = c->a_init * bg_ic_momentum_factor(background_of(c->omega_m, c->omega_l), c->a_init);
-    s.lm_ctas = s.lowmem ? kLowmemCtas : 0;
 }
 
-// Low-memory layout (PMPM_FLAG_LOWMEM).  No per-particle intermediate; the
-// temporaries of the different phases share one region U, and the float32
-// initial-condition fields overlay the store:
-//   [small][P1: store 0, counts 0, offsets 0, v_c 0][U][P2: store 1, counts 1,
-//    offsets 1, v_c 1, F_l][tile scratch]
-//   U holds, at different times: the new-cell sums S and slot counters (tile
-//   passes and IC encode), the coarse mesh and spectra (coarse force), the
-//   power-spectrum mesh, the force-table scratch (init).
-//   ICs: the transform work array (8N) starts at P1; the displacement field
-//   psi (12N) starts after P1 + S + fill (and after the work array), so the
-//   IC encode can write store 0 and its cell arrays while psi is read.
+// Low-memory layout (PMPM_FLAG_LOWMEM).  The new codes are never stored (the
+// re-encode derives them from the old store and the new momenta), and the
+// buffers of the different phases share space:
+//   [small][P0: store 0, counts 0, offsets 0, v_c 0][P1: the same for 1][fill][U]
+//   Store b's region, max(6N, 36C) bytes, also holds the momentum sums S and
+//   F_l of a step whose next buffer is b (lowmem_bind): both are dead before
+//   the re-encode writes the store.
+//   U holds, at different times: the coarse mesh and spectra (coarse force),
+//   the new momenta Pn (tile pass to re-encode), the float32 displacement
+//   field (ICs), the power-spectrum mesh, the force-table scratch (init).
+//   ICs: the transform work array (8N) starts at P0 (P0 + P1 >= 12N).
+static size_t lowmem_sf_bytes(int64_t C) { return align_up(24 * (size_t)C) + 12 * (size_t)C; }
+
+void lowmem_bind(Sim& s, int nxt) {
+    uint8_t* r = s.streams[nxt];
+    s.S = reinterpret_cast<unsigned long long*>(r);
+    s.Fl = reinterpret_cast<float*>(r + align_up(24 * (size_t)s.ncells));
+}
+
 static size_t layout_lowmem(Sim& s, uint8_t* base) {
     size_t off = 0;
     auto take = [&](size_t bytes) -> uint8_t* {
@@ -135,58 +142,44 @@ static size_t layout_lowmem(Sim& s, uint8_t* base) {
     s.d_kd = reinterpret_cast<float*>(take(8));
     s.d2 = reinterpret_cast<unsigned long long*>(take(64));
     for (int b = 0; b < 2; ++b) s.sigma_d[b] = reinterpret_cast<float*>(take(4));
-    s.lm_sp = reinterpret_cast<float*>(take(4 * 3 * (size_t)kLowmemCap * s.lm_ctas));
-    s.lm_sq = reinterpret_cast<int32_t*>(take(4 * 2 * (size_t)kLowmemCap * s.lm_ctas));
     off = align_up(off);
-    const size_t p1 = off;
-    // P1
-    s.streams[0] = take(6 * (size_t)N);   // low-memory sims store 1-byte positions
-    s.counts[0] = reinterpret_cast<int32_t*>(take(4 * (size_t)C));
-    s.offsets[0] = reinterpret_cast<int64_t*>(take(8 * (size_t)(C + 1)));
-    s.vc[0] = reinterpret_cast<float*>(take(12 * (size_t)C));
+    const size_t p0 = off;
+    // P0, P1 (low-memory sims store 1-byte positions)
+    size_t store_b = 6 * (size_t)N;
+    if (lowmem_sf_bytes(C) > store_b) store_b = lowmem_sf_bytes(C);
+    for (int b = 0; b < 2; ++b) {
+        s.streams[b] = take(store_b);
+        s.counts[b] = reinterpret_cast<int32_t*>(take(4 * (size_t)C));
+        s.offsets[b] = reinterpret_cast<int64_t*>(take(8 * (size_t)(C + 1)));
+        s.vc[b] = reinterpret_cast<float*>(take(12 * (size_t)C));
+    }
+    s.fill = reinterpret_cast<int32_t*>(take(4 * (size_t)C));
     off = align_up(off);
     // U
     const size_t u0 = off;
-    const size_t sf = align_up(24 * (size_t)C) + align_up(4 * (size_t)C);
     const size_t coarse_b = 4 * align_up(8 * (size_t)C);
     const size_t pk3 = (size_t)s.pk_max * s.pk_max * s.pk_max;
     const size_t pk_b = 16 * pk3 + 512;
     const size_t green_b = green_scratch_bytes(s.nc);
-    size_t ub = sf;
+    size_t ub = 12 * (size_t)N;
     if (coarse_b > ub) ub = coarse_b;
     if (pk_b > ub) ub = pk_b;
     if (green_b > ub) ub = green_b;
     if (base) {
         uint8_t* u = base + u0;
-        s.S = reinterpret_cast<unsigned long long*>(u);
-        s.fill = reinterpret_cast<int32_t*>(u + align_up(24 * (size_t)C));
         s.rho_c = reinterpret_cast<long long*>(u);
         s.cA = reinterpret_cast<float2*>(u + align_up(8 * (size_t)C));
         s.cB1 = reinterpret_cast<float2*>(u + 2 * align_up(8 * (size_t)C));
         s.cB2 = reinterpret_cast<float2*>(u + 3 * align_up(8 * (size_t)C));
         s.scratch = u;
+        s.Pn = reinterpret_cast<float*>(u);
+        s.ic_psi = reinterpret_cast<float*>(u);
+        s.ic_work = reinterpret_cast<float2*>(base + p0);
+        lowmem_bind(s, 1);
     }
     s.scratch_bytes = ub;
-    off = u0 + ub;
-    // P2
-    s.streams[1] = take(6 * (size_t)N);
-    s.counts[1] = reinterpret_cast<int32_t*>(take(4 * (size_t)C));
-    s.offsets[1] = reinterpret_cast<int64_t*>(take(8 * (size_t)(C + 1)));
-    s.vc[1] = reinterpret_cast<float*>(take(12 * (size_t)C));
-    s.Fl = reinterpret_cast<float*>(take(12 * (size_t)C));
-    off = align_up(off);
-    // IC overlay
-    size_t psi0 = align_up(u0 + sf);
-    const size_t work_end = p1 + 8 * (size_t)N;
-    if (align_up(work_end) > psi0) psi0 = align_up(work_end);
-    const size_t psi_end = psi0 + 12 * (size_t)N;
-    if (base) {
-        s.ic_work = reinterpret_cast<float2*>(base + p1);
-        s.ic_psi = reinterpret_cast<float*>(base + psi0);
-    }
     s.Qn = nullptr;
-    s.Pn = nullptr;
-    if (psi_end > off) off = psi_end;
+    off = u0 + ub;
     return align_up(off);
 }
 
@@ -299,9 +292,7 @@ static int sync_and_check(Sim& s) {
         if (flags & kErrCount) return set_error(s, PMPM_ECOUNT, "particle count not conserved");
         return set_error(s, PMPM_EOVERFLOW,
                          "device range check failed (flags 0x%x: 1 fine density, 2 momentum, "
-                         "16 non-finite, 32 drift, 64 more than %d own "
-                         "particles in a tile, 128 an SM id of %d or more)", flags, kLowmemCap,
-                         kLowmemCtas);
+                         "16 non-finite, 32 drift)", flags);
     }
     return PMPM_OK;
 }
@@ -367,20 +358,17 @@ void set_device_step(Sim& s, int64_t step) {
 static int enqueue_step(Sim& s) {
     int rc;
     prof_mark(s, -1);
+    if (s.lowmem) lowmem_bind(s, 1 - s.cur);   // S and F_l in the next store's region
     if ((rc = coarse_deposit(s))) return rc;
     prof_mark(s, 0);
     if ((rc = coarse_force(s))) return rc;
     prof_mark(s, 1);
-    if (s.lowmem) {
-        if ((rc = lowmem_passes(s))) return rc;
-    } else {
-        cudaMemsetAsync(s.counts[1 - s.cur], 0, sizeof(int32_t) * s.ncells, s.stream);
-        cudaMemsetAsync(s.S, 0, sizeof(unsigned long long) * 3 * s.ncells, s.stream);
-        cudaMemsetAsync(s.d2, 0, 64, s.stream);
-        if ((rc = tile_pass(s, 1, nullptr))) return rc;
-        prof_mark(s, 2);
-        if ((rc = encode_from_qp(s, true))) return rc;
-    }
+    cudaMemsetAsync(s.counts[1 - s.cur], 0, sizeof(int32_t) * s.ncells, s.stream);
+    cudaMemsetAsync(s.S, 0, sizeof(unsigned long long) * 3 * s.ncells, s.stream);
+    cudaMemsetAsync(s.d2, 0, 64, s.stream);
+    if ((rc = tile_pass(s, 1, nullptr))) return rc;
+    prof_mark(s, 2);
+    if ((rc = s.lowmem ? encode_from_parked(s) : encode_from_qp(s, true))) return rc;
     k_step_advance<<<1, 1, 0, s.stream>>>(s.d_step, s.d_kd, s.d_factors, s.cfg.n_steps);
     s.launches++;
     return check_launch(s, "step");

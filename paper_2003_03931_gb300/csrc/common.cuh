@@ -24,7 +24,6 @@ constexpr int kTileOut = kTileMaxCoarse * kRatio + 2;   // fine nodes a tile gat
 constexpr int kGreenS = kTileFFT / 2 + 1;        // 17: |k| range of the tile Green table
 constexpr int kPFixBits = 24;    // momenta rounded to 2^-24 for the cell sums
 constexpr float kSigmaFloor = 5.9604644775390625e-08f;  // 2^-24
-constexpr int kLowmemCap = 65536;   // own particles per tile the low-memory scratch holds
 
 // ---------------------------------------------------------------- error flags
 enum : uint32_t {
@@ -33,8 +32,6 @@ enum : uint32_t {
     kErrCount = 8u,           // counts do not add up to N
     kErrNaN = 16u,            // non-finite momentum or force
     kErrDrift = 32u,          // drift larger than the int32 code range
-    kErrScratch = 64u,        // a tile has more own particles than the low-memory scratch holds
-    kErrSlot = 128u,          // an SM id beyond the low-memory scratch slots
 };
 
 #ifdef __CUDA_ARCH__
@@ -61,6 +58,27 @@ PMPM_HD int fetch_add_i32(int32_t* p, int32_t v) { int o = *p; *p = o + v; retur
 // Eq. 3 decode: p = v_c + sigma * T[u], each operation an IEEE float32 op.
 PMPM_HD float decode_momentum(float vc, float sigma, float tu) {
     return fadd_rn(vc, fmul_rn(sigma, tu));
+}
+
+// The integer drift of one position code: q + round-half-up(fl32(p * drift))
+// (drift in codes per unit momentum), wrapped into [0, M) (M = nc bins per
+// side).  A shift beyond the int32 code range is flagged and dropped.  The
+// tile pass and the low-memory step's re-encode both call this, so the codes
+// they derive from the same momentum are the same.
+PMPM_HD int drift_code(int q, float p, float drift, int M, uint32_t* err) {
+    const float xq = fmul_rn(p, drift);
+    // |dq| < 1e9 and codes below 2^26: the sum fits in 32 bits
+    int dq = 0;
+    if (fabsf(xq) < 1.0e9f) dq = (int)floorf(fadd_rn(xq, 0.5f));
+    else flag_error(err, kErrDrift);
+    // periodic wrap; a division only for the rare particle that crosses the
+    // box boundary
+    int qn = q + dq;
+    if (qn < 0 || qn >= M) {
+        qn %= M;
+        if (qn < 0) qn += M;
+    }
+    return qn;
 }
 
 // Eq. 4: the paper's fast arctangent, |x| <= 1 branch and its reflection

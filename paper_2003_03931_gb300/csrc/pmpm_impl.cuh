@@ -12,7 +12,6 @@
 namespace pmpm {
 
 constexpr int kStages = 6;          // see pmpm_stage_times
-constexpr int kLowmemCtas = 160;    // low-memory scratch slots, one per SM id (%smid)
 constexpr int kEventRing = 4096;
 
 struct Sim {
@@ -69,14 +68,11 @@ struct Sim {
     uint8_t* scratch = nullptr;
     size_t scratch_bytes = 0;
     int32_t* Qn = nullptr;                      // [3][N] (aliases scratch; default step)
-    float* Pn = nullptr;                        // [3][N] (aliases scratch; default step)
+    float* Pn = nullptr;                        // [3][N] (aliases scratch)
 
     // low-memory step (PMPM_FLAG_LOWMEM)
     bool fp16 = false;                          // PMPM_FLAG_FINE_FP16: tile spectrum stored as FP16
     bool lowmem = false;
-    int lm_ctas = 0;                            // scratch slots (kLowmemCtas)
-    float* lm_sp = nullptr;                     // [ctas][3][kLowmemCap] per-CTA momenta
-    int32_t* lm_sq = nullptr;                   // [ctas][2][kLowmemCap] per-CTA codes
     float2* ic_work = nullptr;                  // [N] float32 IC transform (overlays the store)
     float* ic_psi = nullptr;                    // [3][N] float32 displacement field
 
@@ -129,7 +125,8 @@ void fft_setup();
 int scan_counts(Sim& s, const int32_t* counts, int64_t* offsets);
 int encode_from_qp(Sim& s, bool counts_ready);
 int scan_and_means(Sim& s, int nxt);
-int lowmem_passes(Sim& s);             // the two tile passes of a low-memory step
+int encode_from_parked(Sim& s);       // low-memory step: re-encode from the old store and Pn
+void lowmem_bind(Sim& s, int nxt);    // low-memory layout: S and F_l in store nxt's region
 int encode_from_psi(Sim& s, const double* scale);   // low-memory ICs -> store 0
 int decode_state(Sim& s);              // -> s.Qn, s.Pn
 int ic_zeldovich(Sim& s, uint64_t seed, double slope, double kc, double rms);

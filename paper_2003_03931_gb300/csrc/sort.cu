@@ -310,10 +310,58 @@ static void finish_sigma(Sim& s, int nxt) {
     s.launches += 2;
 }
 
-// Re-encode (Eq. 2-3) into the slot offsets[cell] + rank of each particle.
-// Lanes with the same new cell take consecutive ranks from one atomic.  Each
-// warp handles two particles per lane at a time, and the cell's offset and
-// mean momentum are loaded before the rank atomic returns.
+// Slots and Eq. 2-3 codes of two particles per lane: slot = offsets[cell] +
+// rank, m = Q mod 256 (or 65536) and the Eq. 3 code u.  Every lane of the warp
+// calls (live[u] false: no particle).  Lanes with the same new cell take
+// consecutive ranks from one atomic; the cell's offset range and mean
+// momentum are loaded before the rank atomic returns.  A rank past the
+// cell's count (counts that do not match the codes) is flagged, not written.
+template <int PB>
+__device__ __forceinline__ void scatter_two(const int32_t (&q)[2][3], const float (&p)[2][3],
+                                            const bool (&live)[2], int64_t n, int nc,
+                                            const float* const (&vcd)[3],
+                                            const int64_t* __restrict__ offsets, int32_t* fill,
+                                            float sigma, const float* Es, uint8_t* __restrict__ out,
+                                            uint32_t* err) {
+    const int lane = threadIdx.x & 31;
+    int64_t off[2], end[2];
+    int key[2];
+    float v[2][3];
+    int first[2];
+    unsigned peers[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) key[u] = live[u] ? key3<PB>(q[u], nc) : -1 - lane;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const bool l = key[u] >= 0;
+        off[u] = l ? offsets[key[u]] : 0;
+        end[u] = l ? offsets[key[u] + 1] : 0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) v[u][d] = l ? vcd[d][key[u]] : 0.f;
+        peers[u] = __match_any_sync(0xffffffffu, key[u]);
+        first[u] = 0;
+        if (l && lane == __ffs(peers[u]) - 1) first[u] = atomicAdd(&fill[key[u]], __popc(peers[u]));
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        first[u] = __shfl_sync(0xffffffffu, first[u], __ffs(peers[u]) - 1);
+        if (key[u] < 0) continue;
+        const int64_t slot = off[u] + first[u] + __popc(peers[u] & ((1u << lane) - 1u));
+        if (slot >= end[u]) {
+            atomicOr(err, kErrCount);
+            continue;
+        }
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if (PB == 1) out[d * n + slot] = (uint8_t)(q[u][d] & 255);
+            else reinterpret_cast<uint16_t*>(out + 2 * d * n)[slot] = (uint16_t)(q[u][d] & 65535);
+            out[(3 * PB + d) * n + slot] = (uint8_t)encode_momentum(p[u][d], v[u][d], sigma, Es, err);
+        }
+    }
+}
+
+// Re-encode (Eq. 2-3) of the particles a source gives, in any order.  Each
+// warp handles two particles per lane at a time.
 template <int PB, class Src>
 __global__ void k_scatter(Src src, int64_t n, int nc, const float* __restrict__ vc,
                           const int64_t* __restrict__ offsets, int32_t* fill,
@@ -323,50 +371,132 @@ __global__ void k_scatter(Src src, int64_t n, int nc, const float* __restrict__ 
     const float sigma = *sigma_p;
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const float* vcd[3] = {vc, vc + ncells, vc + 2 * ncells};
+    const float* const vcd[3] = {vc, vc + ncells, vc + 2 * ncells};
     // the Eq. 3 bin edges, looked up once or twice per component
     __shared__ float Es[256];
     for (int k = threadIdx.x; k < 256; k += blockDim.x) Es[k] = E[k];
     __syncthreads();
     for (int64_t base = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); base < n;
          base += 2 * stride) {
-        int64_t i[2], off[2];
-        int key[2];
         int32_t q[2][3];
-        float p[2][3], v[2][3];
-        int first[2];
-        unsigned peers[2];
+        float p[2][3];
+        bool live[2];
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
-            i[u] = base + u * stride + lane;
-            const bool live = i[u] < n;
+            const int64_t i = base + u * stride + lane;
+            live[u] = i < n;
             q[u][0] = q[u][1] = q[u][2] = 0;
             p[u][0] = p[u][1] = p[u][2] = 0.f;
-            if (live) src.load(i[u], q[u], p[u]);
-            key[u] = live ? key3<PB>(q[u], nc) : -1 - lane;
+            if (live[u]) src.load(i, q[u], p[u]);
         }
+        scatter_two<PB>(q, p, live, n, nc, vcd, offsets, fill, sigma, Es, out, err);
+    }
+}
+
+// The old cell c of store index j (offsets[c] <= j < offsets[c + 1]) by a
+// 32-way search of one warp: every lane calls with the same j and gets c.
+__device__ int64_t warp_find_cell(const int64_t* __restrict__ offsets, int64_t ncells, int64_t j) {
+    const int lane = threadIdx.x & 31;
+    int64_t lo = 0, hi = ncells;   // offsets[lo] <= j < offsets[hi] (offsets[ncells] = N)
+    while (hi - lo > 1) {
+        const int64_t pr = lo + (((hi - lo) * lane) >> 5);   // lane 0 probes lo itself
+        const unsigned b = __ballot_sync(0xffffffffu, offsets[pr] <= j);
+        const int k = 31 - __clz(b);
+        const int64_t nlo = __shfl_sync(0xffffffffu, pr, k);
+        const int64_t nhi = k < 31 ? __shfl_sync(0xffffffffu, pr, k + 1) : hi;
+        lo = nlo;
+        hi = nhi;
+    }
+    return lo;
+}
+
+constexpr int kParkThreads = 256;
+constexpr int kParkSpan = 2 * kParkThreads;   // particles per block iteration
+constexpr int kParkWin = 128;                 // old cells per window of offsets
+
+// Low-memory step: re-encode from the old store and the new momenta Pn the
+// tile pass left (no new codes were stored).  Particle j of the old store,
+// in old cell c with bins m, moves to Q = drift_code(256 c + m, p) per axis:
+// the same integer drift as the tile pass, so the same codes.  Each block
+// takes a contiguous range of the old store; the old cell of each particle
+// comes from windows of the old offsets staged in shared memory (the next
+// window only where a particle lies beyond the current one).
+__global__ void __launch_bounds__(kParkThreads, 4)
+k_scatter_parked(int64_t n, int nc, int64_t chunk, const int64_t* __restrict__ offs_old,
+                 const uint8_t* __restrict__ st_old, const float* __restrict__ Pn,
+                 const float* __restrict__ kd, const float* __restrict__ vc,
+                 const int64_t* __restrict__ offsets, int32_t* fill,
+                 const float* __restrict__ sigma_p, const float* __restrict__ E,
+                 uint8_t* __restrict__ out, uint32_t* err) {
+    __shared__ float Es[256];
+    __shared__ int64_t win[kParkWin + 1];
+    __shared__ int64_t cnext;
+    const int64_t ncells = (int64_t)nc * nc * nc;
+    const int64_t j0 = (int64_t)blockIdx.x * chunk;
+    if (j0 >= n) return;
+    const int64_t j1 = j0 + chunk < n ? j0 + chunk : n;
+    const int tid = threadIdx.x;
+    for (int k = tid; k < 256; k += kParkThreads) Es[k] = E[k];
+    if (tid < 32) {
+        const int64_t c = warp_find_cell(offs_old, ncells, j0);
+        if (tid == 0) cnext = c;
+    }
+    const float drift = kd[1], sigma = *sigma_p;
+    const int M = nc * kBins;
+    const float* const vcd[3] = {vc, vc + ncells, vc + 2 * ncells};
+    for (int64_t base = j0; base < j1; base += kParkSpan) {
+        __syncthreads();   // cnext is written; the last window is read
+        int64_t cw = cnext;
+        int64_t j[2], cell[2];
+        bool live[2];
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
-            const bool live = key[u] >= 0;
-            off[u] = live ? offsets[key[u]] : 0;
-#pragma unroll
-            for (int d = 0; d < 3; ++d) v[u][d] = live ? vcd[d][key[u]] : 0.f;
-            peers[u] = __match_any_sync(0xffffffffu, key[u]);
-            first[u] = 0;
-            if (live && lane == __ffs(peers[u]) - 1) first[u] = atomicAdd(&fill[key[u]], __popc(peers[u]));
+            j[u] = base + u * kParkThreads + tid;
+            live[u] = j[u] < j1;
+            cell[u] = -1;
         }
+        // every particle of this span lies in cell cw or after it
+        for (;;) {
+            for (int k = tid; k <= kParkWin; k += kParkThreads)
+                win[k] = offs_old[cw + k < ncells ? cw + k : ncells];
+            __syncthreads();
+            bool need = false;
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                if (!live[u] || cell[u] >= 0) continue;
+                if (j[u] >= win[kParkWin]) {
+                    need = true;
+                    continue;
+                }
+                int lo = 0, hi = kParkWin;   // win[lo] <= j < win[hi]
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (win[mid] <= j[u]) lo = mid; else hi = mid;
+                }
+                cell[u] = cw + lo;
+            }
+            if (!__syncthreads_or(need)) break;
+            cw += kParkWin;
+        }
+        // the next span starts in the cell of this span's last particle
+        const int64_t jl = (base + kParkSpan < j1 ? base + kParkSpan : j1) - 1;
+        int32_t q[2][3];
+        float p[2][3];
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
-            first[u] = __shfl_sync(0xffffffffu, first[u], __ffs(peers[u]) - 1);
-            if (key[u] < 0) continue;
-            const int64_t slot = off[u] + first[u] + __popc(peers[u] & ((1u << lane) - 1u));
+            q[u][0] = q[u][1] = q[u][2] = 0;
+            p[u][0] = p[u][1] = p[u][2] = 0.f;
+            if (!live[u]) continue;
+            if (j[u] == jl) cnext = cell[u];
+            const int64_t c = cell[u];
+            const int cc[3] = {(int)(c % nc), (int)((c / nc) % nc), (int)(c / ((int64_t)nc * nc))};
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                if (PB == 1) out[d * n + slot] = (uint8_t)(q[u][d] & 255);
-                else reinterpret_cast<uint16_t*>(out + 2 * d * n)[slot] = (uint16_t)(q[u][d] & 65535);
-                out[(3 * PB + d) * n + slot] = (uint8_t)encode_momentum(p[u][d], v[u][d], sigma, Es, err);
+                p[u][d] = Pn[d * n + j[u]];
+                q[u][d] = drift_code(cc[d] * kBins + st_old[d * n + j[u]], p[u][d], drift, M, err);
             }
         }
+        scatter_two<1>(q, p, live, n, nc, vcd, offsets, fill, sigma, Es, out, err);
     }
 }
 
@@ -463,6 +593,7 @@ int encode_from_psi(Sim& s, const double* scale) {
                         4.0 * s.nc / (double)s.np, s.n};
     s.cur = 1;
     const int nxt = 0;
+    lowmem_bind(s, nxt);   // S in store 0's region until the scatter writes it
     cudaMemsetAsync(s.counts[nxt], 0, sizeof(int32_t) * s.ncells, st);
     cudaMemsetAsync(s.S, 0, sizeof(unsigned long long) * 3 * s.ncells, st);
     cudaMemsetAsync(s.d2, 0, 64, st);
@@ -482,30 +613,30 @@ int encode_from_psi(Sim& s, const double* scale) {
     return check_launch(s, "encode");
 }
 
-// The two low-memory tile passes of one step (PMPM_FLAG_LOWMEM): new-cell
-// counts, momentum sums and their second moment; scan, cell means and the
-// dispersion of Eq. 3 from those sums; then re-encode and scatter into the
-// other store buffer.
-int lowmem_passes(Sim& s) {
+// The rest of a low-memory step (PMPM_FLAG_LOWMEM) after its tile pass,
+// which counted the new cells, summed their momenta and left the new
+// momenta in s.Pn: scan, cell means and the dispersion of Eq. 3, then the
+// re-encode from the old store into the other store buffer.
+int encode_from_parked(Sim& s) {
     const int nxt = 1 - s.cur;
-    cudaStream_t st = s.stream;
-    int rc;
-    cudaMemsetAsync(s.counts[nxt], 0, sizeof(int32_t) * s.ncells, st);
-    cudaMemsetAsync(s.S, 0, sizeof(unsigned long long) * 3 * s.ncells, st);
-    cudaMemsetAsync(s.d2, 0, 64, st);
-    if ((rc = tile_pass(s, 2, nullptr))) return rc;
-    prof_mark(s, 2);
-    if ((rc = scan_and_means(s, nxt))) return rc;
+    int rc = scan_and_means(s, nxt);
+    if (rc) return rc;
     prof_mark(s, 3);
     finish_sigma(s, nxt);
     prof_mark(s, 4);
-    if ((rc = tile_pass(s, 4, nullptr))) return rc;
+    const int grid = grid_for(s.n, kParkSpan, 152 * 4);
+    int64_t chunk = (s.n + grid - 1) / grid;
+    chunk = (chunk + kParkSpan - 1) / kParkSpan * kParkSpan;
+    k_scatter_parked<<<grid, kParkThreads, 0, s.stream>>>(
+        s.n, s.nc, chunk, s.offsets[s.cur], s.streams[s.cur], s.Pn, s.d_kd, s.vc[nxt], s.offsets[nxt],
+        s.fill, s.sigma_d[nxt], s.Eedge, s.streams[nxt], s.err);
+    s.launches++;
     prof_mark(s, 5);
     s.cur = nxt;
     s.offsets_valid = true;
     s.have_state = true;
     s.loaded = 15;
-    return check_launch(s, "low-memory step");
+    return check_launch(s, "low-memory encode");
 }
 
 int decode_state(Sim& s) {

@@ -26,7 +26,7 @@ __device__ unsigned long long g_phase[4096 * kMarks];
 template <int D, bool LM, int PB, typename CT>
 __device__ __forceinline__ void tile_component(int tid, const TileGeom& g, const TileParams& P,
                                                const float* gS, const CT* C, float2* W,
-                                               TileCells cells, CtaScratch cs,
+                                               TileCells cells,
                                                unsigned long long& lo, unsigned long long& hi,
                                                float gscale) {
     __syncthreads();
@@ -42,13 +42,13 @@ __device__ __forceinline__ void tile_component(int tid, const TileGeom& g, const
     tile_inv_x(tid, g, W);
     __syncthreads();
     PMPM_MARK(10 + 4 * D);
-    tile_interp<D, LM, PB>(tid, g, P, W, cells, cs, lo, hi, gscale);
+    tile_interp<D, LM, PB>(tid, g, P, W, cells, lo, hi, gscale);
 }
 
 // 128-bit block sum of the second moment T = sum P^2 of the tile's own
-// particles' new momenta (the default step's fused sums and the low-memory
-// counting pass), staged in the free W area, added to the digits d2[0..3]
-// by thread 0 (no atomic is waited for: the CTA ends right after).
+// particles' new momenta (the fused sums of mode 1), staged in the free W
+// area, added to the digits d2[0..3] by thread 0 (no atomic is waited for:
+// the CTA ends right after).
 __device__ __forceinline__ void tile_sigma_flush(int tid, const TileParams& P, float2* W,
                                                  unsigned long long lo, unsigned long long hi) {
     unsigned long long* sh = reinterpret_cast<unsigned long long*>(W);
@@ -80,9 +80,10 @@ __device__ __forceinline__ void tile_sigma_flush(int tid, const TileParams& P, f
 // per force component the Green multiply, inverse transform and
 // interpolation (phases of tile_core.cuh with a block barrier between).
 // CT: storage of the tile spectrum, float2 or (FP16 storage option) __half2.
+// LM: the low-memory step (new codes not stored).
 template <bool LM, int PB, typename CT = float2>
 __device__ __forceinline__ void tile_body(int tile, const TileParams& P,
-                                          unsigned char* tile_smem, CtaScratch cs) {
+                                          unsigned char* tile_smem) {
     uint32_t* R = reinterpret_cast<uint32_t*>(tile_smem);
     CT* C = reinterpret_cast<CT*>(tile_smem);
     float2* W = reinterpret_cast<float2*>(tile_smem + (size_t)kTileR * 4);
@@ -100,7 +101,7 @@ __device__ __forceinline__ void tile_body(int tile, const TileParams& P,
     tile_cells_map(tid, g, cells);
     __syncthreads();
     PMPM_MARK(2);
-    tile_deposit_flat<LM, PB>(tid, g, P, R, cells, cs);
+    tile_deposit_flat<PB>(tid, g, P, R, cells);
     __syncthreads();
     PMPM_MARK(3);
     // FP16 storage: the density less its mean over the halo box (the k = 0
@@ -125,39 +126,22 @@ __device__ __forceinline__ void tile_body(int tile, const TileParams& P,
     PMPM_MARK(5);
     tile_fwd_z_inv_z0(tid, g, gS, C, W);
     unsigned long long lo = 0, hi = 0;
-    tile_component<0, LM, PB>(tid, g, P, gS, C, W, cells, cs, lo, hi, gscale);
-    tile_component<1, LM, PB>(tid, g, P, gS, C, W, cells, cs, lo, hi, gscale);
-    tile_component<2, LM, PB>(tid, g, P, gS, C, W, cells, cs, lo, hi, gscale);
-    if ((LM && P.mode == 2) || (!LM && P.mode == 1 && P.counts_new != nullptr))
-        tile_sigma_flush(tid, P, W, lo, hi);
+    tile_component<0, LM, PB>(tid, g, P, gS, C, W, cells, lo, hi, gscale);
+    tile_component<1, LM, PB>(tid, g, P, gS, C, W, cells, lo, hi, gscale);
+    tile_component<2, LM, PB>(tid, g, P, gS, C, W, cells, lo, hi, gscale);
+    if (P.mode == 1 && P.counts_new != nullptr) tile_sigma_flush(tid, P, W, lo, hi);
     __syncthreads();
     PMPM_MARK(19);
 }
 
 // One CTA per tile; one fits an SM at a time (the tile needs 232 KB of shared
 // memory).
-// PB: bytes per position bin; CT: storage of the tile spectrum.
-template <int PB, typename CT>
+// PB: bytes per position bin; CT: storage of the tile spectrum; LM: the
+// low-memory step.
+template <int PB, typename CT, bool LM = false>
 __global__ void __launch_bounds__(kTileThreads, 1) k_tile(TileParams P) {
     extern __shared__ __align__(16) unsigned char tile_smem[];
-    tile_body<false, PB, CT>((int)blockIdx.x, P, tile_smem, CtaScratch{nullptr, nullptr});
-}
-
-// Low-memory passes (modes 2 and 4): one CTA per tile, like k_tile.  A tile's
-// scratch slot is its SM's (one tile CTA fits an SM at a time, so no two
-// running CTAs share a slot).  (A persistent loop over tiles with the body
-// out of line was 10% slower: the out-of-line body reads the parameters
-// through memory instead of the constant bank.)
-__global__ void __launch_bounds__(kTileThreads, 1) k_tile_lowmem(TileParams P) {
-    extern __shared__ __align__(16) unsigned char tile_smem[];
-    unsigned smid;
-    asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
-    if (smid >= (unsigned)kLowmemCtas) {
-        if (threadIdx.x == 0) flag_error(P.err, kErrSlot);
-        return;
-    }
-    const CtaScratch cs{P.sp + (size_t)smid * 3 * kLowmemCap, P.sq + (size_t)smid * 2 * kLowmemCap};
-    tile_body<true, 1>((int)blockIdx.x, P, tile_smem, cs);
+    tile_body<LM, PB, CT>((int)blockIdx.x, P, tile_smem);
 }
 
 // One tile's fine-mesh box right after the deposit, written out in x-fastest
@@ -189,7 +173,8 @@ void tile_setup() {
     cudaFuncSetAttribute(k_tile<2, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemBytes);
     cudaFuncSetAttribute(k_tile<1, __half2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemBytes);
     cudaFuncSetAttribute(k_tile<2, __half2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemBytes);
-    cudaFuncSetAttribute(k_tile_lowmem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemBytes);
+    cudaFuncSetAttribute(k_tile<1, float2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kTileSmemBytes);
     cudaFuncSetAttribute(k_tile_density<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemBytes);
     cudaFuncSetAttribute(k_tile_density<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemBytes);
 }
@@ -224,29 +209,18 @@ int tile_pass(Sim& s, int mode, float* G) {
     TileParams P = base_params(s);
     P.mode = mode;
     P.G = G;
-    const int ntiles = s.nt * s.nt * s.nt;
-    int grid = ntiles;
+    const int grid = s.nt * s.nt * s.nt;
     if (mode == 1) {
         P.counts_new = s.counts[1 - s.cur];
         P.S = s.S;
         P.d2 = s.d2;
     }
-    if (mode >= 2) {
-        const int nxt = 1 - s.cur;
-        P.sp = s.lm_sp;
-        P.sq = s.lm_sq;
-        P.counts_new = s.counts[nxt];
-        P.S = s.S;
-        P.vc_new = s.vc[nxt];
-        P.d2 = s.d2;
-        P.offsets_new = s.offsets[nxt];
-        P.fill = s.fill;
-        P.sigma_new = s.sigma_d[nxt];
-        P.E = s.Eedge;
-        P.out = s.streams[nxt];
-    }
-    if (mode >= 2) k_tile_lowmem<<<grid, kTileThreads, kTileSmemBytes, s.stream>>>(P);
-    else if (s.fp16 && s.pb == 2) k_tile<2, __half2><<<grid, kTileThreads, kTileSmemBytes, s.stream>>>(P);
+    if (s.lowmem) {
+        // the low-memory step keeps the new momenta only (s.Pn); the new codes
+        // are derived again by its re-encode
+        P.Qn = nullptr;
+        k_tile<1, float2, true><<<grid, kTileThreads, kTileSmemBytes, s.stream>>>(P);
+    } else if (s.fp16 && s.pb == 2) k_tile<2, __half2><<<grid, kTileThreads, kTileSmemBytes, s.stream>>>(P);
     else if (s.fp16) k_tile<1, __half2><<<grid, kTileThreads, kTileSmemBytes, s.stream>>>(P);
     else if (s.pb == 2) k_tile<2, float2><<<grid, kTileThreads, kTileSmemBytes, s.stream>>>(P);
     else k_tile<1, float2><<<grid, kTileThreads, kTileSmemBytes, s.stream>>>(P);

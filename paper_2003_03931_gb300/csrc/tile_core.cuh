@@ -72,29 +72,15 @@ struct TileParams {
     const float* kd;              // [2] of the current step: fl32 kick factor (multiplies g)
                                   // and drift factor in position codes (multiplies p)
     float* G;                     // [3][N] (mode 0)
-    int32_t* Qn;                  // [3][N] new codes (mode 1)
+    int32_t* Qn;                  // [3][N] new codes (mode 1; null in the low-memory step,
+                                  // whose re-encode derives them from the old store and Pn)
     float* Pn;                    // [3][N] new momenta (mode 1)
     uint32_t* err;
-    // low-memory passes: mode 2 counts the new cells and sums their momenta
-    // and squared momenta, mode 4 re-encodes and scatters (Sec. III-A);
-    // per-CTA scratch of kLowmemCap own particles
-    float* sp;                    // [CTAs][3][kLowmemCap] parked long-range force, new momenta
-    int32_t* sq;                  // [CTAs][2][kLowmemCap] new codes of components 0 and 1
-    int32_t* counts_new;          // [nc^3] (modes 1 and 2)
-    unsigned long long* S;        // [3][nc^3] momentum sums in units of 2^-24 (modes 1 and 2)
-    const float* vc_new;          // [3][nc^3] (mode 4)
-    unsigned long long* d2;       // [4] digits of T = sum P^2 of the new momenta (modes 1, 2)
-    const int64_t* offsets_new;   // [nc^3 + 1] (mode 4)
-    int32_t* fill;                // [nc^3] slots taken per new cell (mode 4)
-    const float* sigma_new;       // device scalar (mode 4)
-    const float* E;               // [256] velocity bin edges (mode 4)
-    uint8_t* out;                 // [6][N] new store (mode 4)
-};
-
-// This CTA's part of the low-memory scratch.
-struct CtaScratch {
-    float* sp;       // [3][kLowmemCap]
-    int32_t* sq;     // [2][kLowmemCap]
+    // mode 1 with counts_new: the last interpolation also adds each particle
+    // to its new cell's count, momentum sums and the second moment
+    int32_t* counts_new;          // [nc^3]
+    unsigned long long* S;        // [3][nc^3] momentum sums in units of 2^-24
+    unsigned long long* d2;       // [4] digits of T = sum P^2 of the new momenta
 };
 
 struct TileGeom {
@@ -382,14 +368,13 @@ PMPM_HD void tile_prologue(int tid, const TileGeom& g, const TileParams& P, Tile
         gv[u] = i < kGreenPacked ? P.green[i] : 0.f;
     }
     const float td = tid < 256 ? P.Tdec[tid] : 0.f;
-    float sc[4] = {0.f, 0.f, 0.f, 0.f};
+    float sc[3] = {0.f, 0.f, 0.f};
     if (tid == 0) {
         sc[0] = *P.sigma;
         if (P.mode >= 1) {
             sc[1] = P.kd[0];
             sc[2] = P.kd[1];
         }
-        if (P.mode == 4) sc[3] = *P.sigma_new;
     }
     tile_zero(tid, R);
 #pragma unroll
@@ -416,7 +401,6 @@ PMPM_HD void tile_prologue(int tid, const TileGeom& g, const TileParams& P, Tile
         c.misc[4] = f32_to_bits(sc[0]);
         c.misc[5] = f32_to_bits(sc[1]);
         c.misc[6] = f32_to_bits(sc[2]);
-        c.misc[7] = f32_to_bits(sc[3]);
     }
 }
 
@@ -655,10 +639,9 @@ PMPM_HD void tile_deposit_halo(int tid, const TileGeom& g, const TileParams& P, 
 }
 
 // the long-range force of the tile's own particles, parked in their output
-// slots (low-memory passes: the CTA's scratch)
-template <bool LM, int PB>
-PMPM_HD void tile_gather_coarse(int tid, const TileGeom& g, const TileParams& P, TileCells c,
-                                CtaScratch cs) {
+// slots
+template <int PB>
+PMPM_HD void tile_gather_coarse(int tid, const TileGeom& g, const TileParams& P, TileCells c) {
     float* slot = P.mode == 0 ? P.G : P.Pn;
     const int ptotal = c.ppre[kOwnMax];
     const int64_t obase = own_base(c);
@@ -682,27 +665,17 @@ PMPM_HD void tile_gather_coarse(int tid, const TileGeom& g, const TileParams& P,
             if (j[u] < 0) continue;
             float gc[3];
             coarse_gather_win<PB>(fl_window(c), g, Q[u], gc);
-            if (LM) {
-                const int v = v0 + u * kTileThreads;
-                if (v >= kLowmemCap) {
-                    flag_error(P.err, kErrScratch);
-                    continue;
-                }
-#pragma unroll
-                for (int e = 0; e < 3; ++e) cs.sp[e * kLowmemCap + v] = gc[e];
-                continue;
-            }
 #pragma unroll
             for (int e = 0; e < 3; ++e) slot[e * P.n + j[u]] = gc[e];
         }
     }
 }
 
-template <bool LM, int PB>
+template <int PB>
 PMPM_HD void tile_deposit_flat(int tid, const TileGeom& g, const TileParams& P, uint32_t* R,
-                               TileCells c, CtaScratch cs) {
+                               TileCells c) {
     tile_deposit_halo<PB>(tid, g, P, R, c);
-    tile_gather_coarse<LM, PB>(tid, g, P, c, cs);
+    tile_gather_coarse<PB>(tid, g, P, c);
 }
 
 // --- phase 2: forward real transform along x (1024 rows, 2 per thread) -----
@@ -896,62 +869,30 @@ __host__ __device__ __noinline__ void tile_inv_x(int tid, const TileGeom& g, flo
 }
 
 // --- phase 5d: interpolate component D to the tile's own particles, add the
-// parked long-range part, then (mode 1) kick and drift that component.
-// Low-memory passes: the new cell of one particle from its three new codes,
-// then mode 2 (count, momentum sums and the 128-bit second moment in lo/hi,
-// as the default step's fused histogram) or mode 4 (slot in the new cell,
-// Eq. 2-3 re-encode).
-PMPM_HD void lowmem_particle(const TileParams& P, const int32_t (&q)[3], const float (&p)[3],
-                             float sigma_new, unsigned long long& lo, unsigned long long& hi) {
-    const int64_t C = (int64_t)P.nc * P.nc * P.nc;
-    const int64_t key = (int64_t)(q[0] >> 8) + P.nc * ((int64_t)(q[1] >> 8) + (int64_t)P.nc * (q[2] >> 8));
-    if (P.mode == 2) {
-        gmem_add_i32(&P.counts_new[key], 1);
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            long long fx = 0;
-            if (fabsf(p[d]) < 1048576.f) fx = fix24_rn(p[d]);
-            else flag_error(P.err, p[d] == p[d] ? kErrMomentum : kErrNaN);
-            gmem_add_u64(&P.S[d * C + key], (unsigned long long)fx);
-            add_square128(fx, lo, hi);
-        }
-    } else {
-        // every pass recomputes the same codes, so a cell never receives more
-        // particles than the counting pass gave it; checked all the same
-        const int rank = fetch_add_i32(&P.fill[key], 1);
-        const int64_t slot = P.offsets_new[key] + rank;
-        if (slot >= P.offsets_new[key + 1]) {
-            flag_error(P.err, kErrCount);
-            return;
-        }
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            P.out[d * P.n + slot] = (uint8_t)(q[d] & 255);
-            P.out[(3 + d) * P.n + slot] =
-                (uint8_t)encode_momentum(p[d], P.vc_new[d * C + key], sigma_new, P.E, P.err);
-        }
-    }
-}
-
-// LM: the low-memory passes (modes 2 and 4); otherwise modes 0 and 1.
+// parked long-range part, then (mode 1) kick and drift that component.  The
+// last component also adds each particle to its new cell's count and sums
+// (the re-encode's histogram, fused here so that the codes and momenta are
+// not read back by another pass).  LM (the low-memory step): the new codes
+// are not stored; the fused sums derive the codes of the first two
+// components from the old codes and the new momenta, as the re-encode does.
 template <int D, bool LM, int PB>
 PMPM_HD void tile_interp(int tid, const TileGeom& g, const TileParams& P, const float2* W,
-                         TileCells c, CtaScratch cs, unsigned long long& lo, unsigned long long& hi,
+                         TileCells c, unsigned long long& lo, unsigned long long& hi,
                          float gscale = 2.384185791015625e-07f) {
     using F = PosFmt<PB>;
-    constexpr int U = LM ? 1 : 2;   // particles per thread per iteration, loads issued together
+    constexpr int U = 2;   // particles per thread per iteration, loads issued together
     const float* Wf = reinterpret_cast<const float*>(W);
     const int64_t ncells = (int64_t)P.nc * P.nc * P.nc;
     const int64_t n = P.n;
-    constexpr bool lm = LM;
+    const int M = P.nc * F::kBins;
     const float sigma = bits_to_f32(c.misc[4]);
     const float kick = bits_to_f32(c.misc[5]), drift = bits_to_f32(c.misc[6]);
-    const float sigma_new = bits_to_f32(c.misc[7]);
     const uint8_t* ud = D == 0 ? P.u0 : (D == 1 ? P.u1 : P.u2);
     float* slot = P.mode == 0 ? P.G : P.Pn;
     const int ptotal = c.ppre[kOwnMax];
     const int64_t base = own_base(c);
     const float* vcD = P.vc + D * ncells;
+    const bool fuse = D == 2 && P.mode == 1 && P.counts_new != nullptr;
     for (int v0 = tid; v0 < ptotal; v0 += U * kTileThreads) {
         int64_t j[U];
         int Q[U][3], cell[U];   // codes below nc 65536 <= 2^26, cells below 2^30
@@ -959,15 +900,11 @@ PMPM_HD void tile_interp(int tid, const TileGeom& g, const TileParams& P, const 
         int u8[U];
         int32_t q01[U][2];
         float p01[U][2];
-        // default step: the last component also adds each particle to its new
-        // cell's count and momentum sums (the re-encode's histogram, fused
-        // here so the codes and momenta are not read back by another pass)
-        const bool fuse = !lm && D == 2 && P.mode == 1 && P.counts_new != nullptr;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int v = v0 + u * kTileThreads;
             const int p = prefix_find<kOwnMax>(c.ppre, v < ptotal ? v : 0);
-            j[u] = (v < ptotal && (!lm || v < kLowmemCap)) ? base + c.prel[p] + (v - c.ppre[p]) : -1;
+            j[u] = v < ptotal ? base + c.prel[p] + (v - c.ppre[p]) : -1;
             const int cx = g.c0[0] + p % kOwnDim, cy = g.c0[1] + (p / kOwnDim) % kOwnDim,
                       cz = g.c0[2] + p / (kOwnDim * kOwnDim);
             cell[u] = cx + P.nc * (cy + P.nc * cz);
@@ -975,14 +912,16 @@ PMPM_HD void tile_interp(int tid, const TileGeom& g, const TileParams& P, const 
                 Q[u][0] = cx * F::kBins + load_bin<PB>(P.m0, j[u]);
                 Q[u][1] = cy * F::kBins + load_bin<PB>(P.m1, j[u]);
                 Q[u][2] = cz * F::kBins + load_bin<PB>(P.m2, j[u]);
-                gcd[u] = lm ? cs.sp[D * kLowmemCap + v] : slot[D * n + j[u]];
-                if (lm || P.mode >= 1) {
+                gcd[u] = slot[D * n + j[u]];
+                if (P.mode >= 1) {
                     u8[u] = ud[j[u]];
                     vcd[u] = vcD[cell[u]];
                 }
                 if (fuse) {
-                    q01[u][0] = P.Qn[j[u]];
-                    q01[u][1] = P.Qn[n + j[u]];
+                    if (!LM) {
+                        q01[u][0] = P.Qn[j[u]];
+                        q01[u][1] = P.Qn[n + j[u]];
+                    }
                     p01[u][0] = P.Pn[j[u]];
                     p01[u][1] = P.Pn[n + j[u]];
                 }
@@ -1017,56 +956,35 @@ PMPM_HD void tile_interp(int tid, const TileGeom& g, const TileParams& P, const 
             // leaves the whole spectrum doubled: gscale = 2^-22 (over the
             // density's scale with FP16 spectrum storage; a power of two)
             const float gval = gf * gscale + gcd[u];
-            if (!lm && P.mode == 0) {
+            if (P.mode == 0) {
                 slot[D * n + j[u]] = gval;
                 continue;
             }
             // kick (Eq. 3 decode, then p += kick * g) and integer drift
             const float pv = decode_momentum(vcd[u], sigma, c.Td[u8[u]]);
             const float pn = fadd_rn(pv, fmul_rn(kick, gval));
-            const float xq = fmul_rn(pn, drift);
             if (!(pn == pn) || !(gval == gval)) flag_error(P.err, kErrNaN);
             if (fabsf(pn) >= 1048576.f) flag_error(P.err, kErrMomentum);
-            // |dq| < 1e9 and codes below 2^26: the sum fits in 32 bits
-            int dq = 0;
-            if (fabsf(xq) < 1.0e9f) dq = (int)floorf(fadd_rn(xq, 0.5f));
-            else flag_error(P.err, kErrDrift);
-            const int M = P.nc * F::kBins;
-            // periodic wrap; a division only for the rare particle that
-            // crosses the box boundary
-            int qn = Q[u][D] + dq;
-            if (qn < 0 || qn >= M) {
-                qn %= M;
-                if (qn < 0) qn += M;
+            const int qn = drift_code(Q[u][D], pn, drift, M, P.err);
+            if (!LM) P.Qn[D * n + j[u]] = (int32_t)qn;
+            P.Pn[D * n + j[u]] = pn;
+            if (!fuse) continue;
+            if (LM) {
+                q01[u][0] = drift_code(Q[u][0], p01[u][0], drift, M, P.err);
+                q01[u][1] = drift_code(Q[u][1], p01[u][1], drift, M, P.err);
             }
-            if (!lm) {
-                P.Qn[D * n + j[u]] = (int32_t)qn;
-                P.Pn[D * n + j[u]] = pn;
-                if (fuse) {
-                    const int32_t qa[3] = {q01[u][0], q01[u][1], qn};
-                    const float pa[3] = {p01[u][0], p01[u][1], pn};
-                    const int key = (qa[0] >> F::kShift) + P.nc * ((qa[1] >> F::kShift) + P.nc * (qa[2] >> F::kShift));
-                    gmem_add_i32(&P.counts_new[key], 1);
+            const int32_t qa[3] = {q01[u][0], q01[u][1], qn};
+            const float pa[3] = {p01[u][0], p01[u][1], pn};
+            const int key = (qa[0] >> F::kShift) + P.nc * ((qa[1] >> F::kShift) + P.nc * (qa[2] >> F::kShift));
+            gmem_add_i32(&P.counts_new[key], 1);
 #pragma unroll
-                    for (int d = 0; d < 3; ++d) {
-                        long long fx = 0;
-                        if (fabsf(pa[d]) < 1048576.f) fx = fix24_rn(pa[d]);
-                        else flag_error(P.err, pa[d] == pa[d] ? kErrMomentum : kErrNaN);
-                        gmem_add_u64(&P.S[d * ncells + key], (unsigned long long)fx);
-                        add_square128(fx, lo, hi);
-                    }
-                }
-                continue;
+            for (int d = 0; d < 3; ++d) {
+                long long fx = 0;
+                if (fabsf(pa[d]) < 1048576.f) fx = fix24_rn(pa[d]);
+                else flag_error(P.err, pa[d] == pa[d] ? kErrMomentum : kErrNaN);
+                gmem_add_u64(&P.S[d * ncells + key], (unsigned long long)fx);
+                add_square128(fx, lo, hi);
             }
-            const int v = v0 + u * kTileThreads;
-            if (D < 2) {
-                cs.sp[D * kLowmemCap + v] = pn;
-                cs.sq[D * kLowmemCap + v] = (int32_t)qn;
-                continue;
-            }
-            const int32_t qa[3] = {cs.sq[v], cs.sq[kLowmemCap + v], (int32_t)qn};
-            const float pa[3] = {cs.sp[v], cs.sp[kLowmemCap + v], pn};
-            lowmem_particle(P, qa, pa, sigma_new, lo, hi);
         }
     }
 }

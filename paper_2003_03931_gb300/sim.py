@@ -25,7 +25,7 @@ class SimConfig:
     pos_bytes: int = 1
     vel_bytes: int = 1
     pk_mesh_max: int = 0
-    lowmem: bool = False    # two tile passes per step, no per-particle intermediate
+    lowmem: bool = False    # low-memory step: new momenta kept, new codes derived again
     fine_fp16: bool = False # tile spectrum stored as FP16 (PMPM_FLAG_FINE_FP16)
     omega_m: float = 0.0    # background: 0, 0 = Einstein-de Sitter; else LambdaCDM (Sec. IV-A.2)
     omega_l: float = 0.0

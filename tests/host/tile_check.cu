@@ -447,7 +447,7 @@ static void check_deposit(long long& n, long long& bad, double& err) {
         for (int t = 0; t < kTileThreads; ++t) tile_cells_scan(t, g, c);
         for (int t = 0; t < kTileThreads; ++t) tile_cells_map(t, g, c);
         for (int t = 0; t < kTileThreads; ++t)
-            tile_deposit_flat<false, PB>(t, g, P, R, c, CtaScratch{nullptr, nullptr});
+            tile_deposit_flat<PB>(t, g, P, R, c);
         // the same phases with the threads in reverse order (another order
         // of the integer adds) leave the same density, word for word
         {
@@ -456,7 +456,7 @@ static void check_deposit(long long& n, long long& bad, double& err) {
             for (int t = kTileThreads - 1; t >= 0; --t) tile_cells_scan(t, g, c);
             for (int t = kTileThreads - 1; t >= 0; --t) tile_cells_map(t, g, c);
             for (int t = kTileThreads - 1; t >= 0; --t)
-                tile_deposit_flat<false, PB>(t, g, P, R, c, CtaScratch{nullptr, nullptr});
+                tile_deposit_flat<PB>(t, g, P, R, c);
             ++n;
             bad += memcmp(first.data(), R, sizeof(uint32_t) * kTileR) != 0;
         }
@@ -659,7 +659,7 @@ template <int D, int PB>
 static void run_interp(const TileGeom& g, const TileParams& P, const float2* W, TileCells c) {
     unsigned long long lo = 0, hi = 0;
     for (int t = 0; t < kTileThreads; ++t)
-        tile_interp<D, false, PB>(t, g, P, W, c, CtaScratch{nullptr, nullptr}, lo, hi);
+        tile_interp<D, false, PB>(t, g, P, W, c, lo, hi);
 }
 
 template <int PB>
@@ -728,7 +728,7 @@ static void check_interp(long long& n, long long& bad, double& err, int mode) {
         for (int t = 0; t < kTileThreads; ++t) tile_cells_scan(t, g, c);
         for (int t = 0; t < kTileThreads; ++t) tile_cells_map(t, g, c);
         for (int t = 0; t < kTileThreads; ++t)
-            tile_deposit_flat<false, PB>(t, g, P, R, c, CtaScratch{nullptr, nullptr});
+            tile_deposit_flat<PB>(t, g, P, R, c);
         // the tile's own particles and their cells
         std::vector<int64_t> own;
         std::vector<int> ocell;
@@ -822,44 +822,35 @@ static void check_interp(long long& n, long long& bad, double& err, int mode) {
     bad += errw != 0u;
 }
 
-// The low-memory passes (modes 2 and 4, one tile body each, own particles in
-// a CTA scratch slot instead of global arrays) against the default pass
-// (mode 1) of the same tile with the same force fields: mode 2's new-cell
-// counts and momentum sums equal mode 1's fused sums exactly, and both
-// passes' 128-bit second moment sum P^2 equals the exact sum over mode 1's
-// momenta (past 2^64 in the crowded tile); mode 4 writes into each new cell's slots exactly
-// the records that mode 1's codes and momenta give (position byte, and the
-// Eq. 3 bin by the definition: the number of edges at or below t).
+// The low-memory tile pass (mode 1 without stored codes) against the default
+// pass of the same tile with the same force fields: the same new momenta
+// bit for bit, the same new-cell counts and momentum sums, the same 128-bit
+// second moment sum P^2 (equal to the exact sum over the momenta, past 2^64
+// in the crowded tile); and the codes the low-memory re-encode derives from
+// the old store and those momenta (drift_code) are the default pass's codes.
 template <int D, bool LM>
 static void run_interp_lm(const TileGeom& g, const TileParams& P, const float2* W, TileCells c,
-                          CtaScratch cs, unsigned long long& lo, unsigned long long& hi) {
-    for (int t = 0; t < kTileThreads; ++t) tile_interp<D, LM, 1>(t, g, P, W, c, cs, lo, hi);
+                          unsigned long long& lo, unsigned long long& hi) {
+    for (int t = 0; t < kTileThreads; ++t) tile_interp<D, LM, 1>(t, g, P, W, c, lo, hi);
 }
 
 static void check_lowmem(long long& n, long long& bad) {
     const int nc = 32, nt = tile_count(nc, 5);
     Box<1> box(nc, 20, 4, 27);
     const int64_t nc3 = (int64_t)nc * nc * nc, np = box.n;
-    std::vector<float> Fl(3 * nc3), green(kGreenPacked, 0.f), Td(256), vc(3 * nc3), vcn(3 * nc3), E(256);
+    std::vector<float> Fl(3 * nc3), green(kGreenPacked, 0.f), Td(256), vc(3 * nc3);
     for (auto& v : Fl) v = (float)((double)(next_u64() >> 11) * 0x1p-53 * 2.0 - 1.0);
     for (auto& v : vc) v = (float)((double)(next_u64() >> 11) * 0x1p-53 * 40.0 - 20.0);
-    // new cell means spread widely and a wide sigma_new keep the Eq. 3 bins
-    // of the scatter pass spread
-    for (auto& v : vcn) v = (float)((double)(next_u64() >> 11) * 0x1p-53 * 4000.0 - 2000.0);
     for (int i = 0; i < 256; ++i) Td[i] = (float)(std::tan(M_PI * ((i + 0.5) / 256.0 - 0.5)) * 0.25);
-    E[0] = -INFINITY;
-    for (int k = 1; k < 256; ++k) E[k] = (float)std::tan(M_PI * (k / 256.0 - 0.5));
     std::vector<uint8_t> u[3];
     for (int e = 0; e < 3; ++e) {
         u[e].resize(np);
         for (auto& x : u[e]) x = (uint8_t)(next_u64() & 255);
     }
-    std::vector<float> Pn(3 * np), sp(3 * kLowmemCap);
-    std::vector<int32_t> Qn(3 * np), sq(2 * kLowmemCap), cnew(nc3), cnew2(nc3), fill(nc3);
-    std::vector<int64_t> offn(nc3 + 1);
+    std::vector<float> Pn(3 * np), Pn2(3 * np);
+    std::vector<int32_t> Qn(3 * np), cnew(nc3), cnew2(nc3);
     std::vector<unsigned long long> S(3 * nc3), S2(3 * nc3);
-    std::vector<uint8_t> out(6 * np);
-    const float sigma = 2.0f, sigma_new = 300.0f, kd[2] = {0.75f, 3.3f};
+    const float sigma = 2.0f, kd[2] = {0.75f, 3.3f};
     uint32_t errw = 0;
     TileParams P{};
     P.nc = nc;
@@ -879,15 +870,8 @@ static void check_lowmem(long long& n, long long& bad) {
     P.green = green.data();
     P.Fl = Fl.data();
     P.kd = kd;
-    P.Qn = Qn.data();
-    P.Pn = Pn.data();
+    P.mode = 1;
     P.err = &errw;
-    P.vc_new = vcn.data();
-    P.offsets_new = offn.data();
-    P.fill = fill.data();
-    P.sigma_new = &sigma_new;
-    P.E = E.data();
-    P.out = out.data();
     std::vector<unsigned char> smem(kTileSmemBytes);
     unsigned char* base = smem.data();
     uint32_t* R = reinterpret_cast<uint32_t*>(base);
@@ -895,20 +879,14 @@ static void check_lowmem(long long& n, long long& bad) {
     float* Wf = reinterpret_cast<float*>(W);
     float* gS = reinterpret_cast<float*>(base + (size_t)kTileR * 4 + (size_t)kTileW * 8);
     int* O = reinterpret_cast<int*>(gS + kGreenPacked);
-    const CtaScratch cs{sp.data(), sq.data()};
-    // one tile body in the given mode, the force fields drawn from seed
-    auto run = [&](const TileGeom& g, int mode, unsigned long long seed, unsigned long long& lo,
+    // one tile body, the force fields drawn from seed
+    auto run = [&](const TileGeom& g, bool lm, unsigned long long seed, unsigned long long& lo,
                    unsigned long long& hi) {
-        P.mode = mode;
-        const bool lm = mode >= 2;
         const TileCells c = tile_cells(W, O);
         for (int t = 0; t < kTileThreads; ++t) tile_prologue(t, g, P, c, R, gS);
         for (int t = 0; t < kTileThreads; ++t) tile_cells_scan(t, g, c);
         for (int t = 0; t < kTileThreads; ++t) tile_cells_map(t, g, c);
-        for (int t = 0; t < kTileThreads; ++t) {
-            if (lm) tile_deposit_flat<true, 1>(t, g, P, R, c, cs);
-            else tile_deposit_flat<false, 1>(t, g, P, R, c, cs);
-        }
+        for (int t = 0; t < kTileThreads; ++t) tile_deposit_flat<1>(t, g, P, R, c);
         const unsigned long long saved = rng_state;
         rng_state = seed;
         for (int D = 0; D < 3; ++D) {
@@ -917,9 +895,9 @@ static void check_lowmem(long long& n, long long& bad) {
                 for (int yo = 0; yo < g.T[1] + 2; ++yo)
                     for (int xo = 0; xo < g.T[0] + 2; ++xo)
                         Wf[wfidx(xo, yo, zo)] = (float)((double)(next_u64() >> 11) * 0x1p-53 * 2e3 - 1e3);
-            if (D == 0) lm ? run_interp_lm<0, true>(g, P, W, c, cs, lo, hi) : run_interp_lm<0, false>(g, P, W, c, cs, lo, hi);
-            if (D == 1) lm ? run_interp_lm<1, true>(g, P, W, c, cs, lo, hi) : run_interp_lm<1, false>(g, P, W, c, cs, lo, hi);
-            if (D == 2) lm ? run_interp_lm<2, true>(g, P, W, c, cs, lo, hi) : run_interp_lm<2, false>(g, P, W, c, cs, lo, hi);
+            if (D == 0) lm ? run_interp_lm<0, true>(g, P, W, c, lo, hi) : run_interp_lm<0, false>(g, P, W, c, lo, hi);
+            if (D == 1) lm ? run_interp_lm<1, true>(g, P, W, c, lo, hi) : run_interp_lm<1, false>(g, P, W, c, lo, hi);
+            if (D == 2) lm ? run_interp_lm<2, true>(g, P, W, c, lo, hi) : run_interp_lm<2, false>(g, P, W, c, lo, hi);
         }
         rng_state = saved;
     };
@@ -929,40 +907,61 @@ static void check_lowmem(long long& n, long long& bad) {
         const unsigned long long seed = next_u64() | 1ull;
         unsigned long long lo = 0, hi = 0, lo2 = 0, hi2 = 0;
         // default pass: new codes, momenta and fused sums
+        P.Qn = Qn.data();
+        P.Pn = Pn.data();
         P.counts_new = cnew.data();
         P.S = S.data();
         std::fill(cnew.begin(), cnew.end(), 0);
         std::fill(S.begin(), S.end(), 0ull);
-        run(g, 1, seed, lo, hi);
-        // mode 2: the same sums
+        run(g, false, seed, lo, hi);
+        // low-memory pass: momenta and the same sums, no codes
+        P.Qn = nullptr;
+        P.Pn = Pn2.data();
         P.counts_new = cnew2.data();
         P.S = S2.data();
         std::fill(cnew2.begin(), cnew2.end(), 0);
         std::fill(S2.begin(), S2.end(), 0ull);
-        run(g, 2, seed, lo2, hi2);
+        run(g, true, seed, lo2, hi2);
         for (int64_t i = 0; i < nc3; ++i) {
             ++n;
             bad += cnew2[i] != cnew[i] || S2[i] != S[i] || S2[nc3 + i] != S[nc3 + i] || S2[2 * nc3 + i] != S[2 * nc3 + i];
         }
-        // the tile's own particles (mode 1 wrote their new codes and momenta)
+        // the tile's own particles
         std::vector<int64_t> own;
+        std::vector<int> own_cell;
         for (int z = g.c0[2]; z < g.c1[2]; ++z)
             for (int y = g.c0[1]; y < g.c1[1]; ++y)
                 for (int x = g.c0[0]; x < g.c1[0]; ++x) {
                     const int cell = x + nc * (y + nc * z);
-                    for (int64_t j = box.offsets[cell]; j < box.offsets[cell + 1]; ++j) own.push_back(j);
+                    for (int64_t j = box.offsets[cell]; j < box.offsets[cell + 1]; ++j) {
+                        own.push_back(j);
+                        own_cell.push_back(cell);
+                    }
                 }
-        auto key_of = [&](int64_t j) {
-            return Qn[j] / 256 + nc * (Qn[np + j] / 256 + nc * (Qn[2 * np + j] / 256));
-        };
+        int moved = 0;
+        for (size_t k = 0; k < own.size(); ++k) {
+            const int64_t j = own[k];
+            const int cc[3] = {own_cell[k] % nc, (own_cell[k] / nc) % nc, own_cell[k] / (nc * nc)};
+            for (int d = 0; d < 3; ++d) {
+                ++n;
+                const float p = Pn2[d * np + j];
+                bad += std::memcmp(&p, &Pn[d * np + j], 4) != 0;
+                const int q = drift_code(cc[d] * 256 + box.s[d][j], p, kd[1], nc * 256, &errw);
+                ++n;
+                bad += q != Qn[d * np + j];
+                moved += q / 256 != cc[d];
+            }
+        }
+        ++n;
+        bad += moved == 0;   // some particles change cell, so the check covers the wrap too
         // the second moment T = sum P^2 of the new momenta (P = round(p 2^24)),
         // the same from both passes and equal to the exact sum
         unsigned __int128 ref = 0;
         for (int64_t j : own)
             for (int d = 0; d < 3; ++d) {
                 const long long fx = fix24_rn(Pn[d * np + j]);
-                const unsigned __int128 u = (unsigned __int128)(fx < 0 ? -fx : fx);
-                ref += u * u;
+                const unsigned __int128 v = (unsigned __int128)(fx < 0 ? -fx : fx);
+                ref += v * v;
             }
         ++n;
         bad += lo != (unsigned long long)ref || hi != (unsigned long long)(ref >> 64);
@@ -972,64 +971,29 @@ static void check_lowmem(long long& n, long long& bad) {
             ++n;
             bad += hi == 0;
         }
-        // mode 4: slots of each new cell, records against the definition
-        int64_t acc = 0;
-        for (int64_t i = 0; i < nc3; ++i) {
-            offn[i] = acc;
-            acc += cnew[i];
-        }
-        offn[nc3] = acc;
-        std::fill(fill.begin(), fill.end(), 0);
-        std::fill(out.begin(), out.end(), (uint8_t)0);
-        run(g, 4, seed, lo, hi);
-        std::vector<std::vector<unsigned long long>> want(nc3), got(nc3);
-        for (int64_t j : own) {
-            const int key = key_of(j);
-            unsigned long long rec = 0;
-            for (int d = 0; d < 3; ++d) rec = rec << 8 | (unsigned long long)(Qn[d * np + j] & 255);
-            for (int d = 0; d < 3; ++d) {
-                const float t = (Pn[d * np + j] - vcn[d * nc3 + key]) / sigma_new;
-                int ub = 0;
-                for (int k = 1; k < 256; ++k) ub += E[k] <= t;
-                rec = rec << 8 | (unsigned long long)ub;
-            }
-            want[key].push_back(rec);
-        }
-        for (int64_t i = 0; i < nc3; ++i) {
-            for (int64_t sl = offn[i]; sl < offn[i + 1]; ++sl) {
-                unsigned long long rec = 0;
-                for (int f = 0; f < 6; ++f) rec = rec << 8 | out[f * np + sl];
-                got[i].push_back(rec);
-            }
-            std::sort(want[i].begin(), want[i].end());
-            std::sort(got[i].begin(), got[i].end());
-            ++n;
-            bad += want[i] != got[i] || fill[i] != cnew[i];
-        }
     }
     ++n;
     bad += errw != 0u;
 }
 
-// Error paths of the tile body that real inputs rarely reach.
-// (1) A tile with more own particles than the low-memory scratch holds
-//     (kLowmemCap): the deposit parks the first kLowmemCap forces, flags
-//     kErrScratch for the rest and writes nothing past the slot.
-// (2) A fine node whose weight passes 2^32 - 1 units (over 2048 particles
-//     on one node): the checked deposit path, taken when a cell holds more
-//     than 255 particles, flags kErrFineOverflow.
+// Error path of the tile body that real inputs rarely reach: a fine node
+// whose weight passes 2^32 - 1 units (over 2048 particles on one node).  The
+// checked deposit path, taken when a cell holds more than 255 particles,
+// flags kErrFineOverflow; the long-range force of every own particle (70,400
+// of them) is still parked in its slot and no other slot is written.
 static void check_error_paths(long long& n, long long& bad) {
     const int nc = 16, nt = tile_count(nc, 5);
     const int64_t nc3 = (int64_t)nc * nc * nc;
     std::vector<int32_t> counts(nc3, 0);
     std::vector<int64_t> offsets(nc3 + 1);
-    // tile 0 owns cells 0..3 per axis: 64 cells of 1100 particles (70,400
-    // own particles, past the scratch); cell (1,1,1) holds 2,600 particles
-    // in one bin, whose nodes pass 2^32 units
+    // tile 0 owns cells 0..3 per axis: 64 cells of 1100 particles; cell
+    // (1,1,1) holds 2,600 particles in one bin, whose nodes pass 2^32 units;
+    // one cell outside the tile holds 10 particles
     for (int z = 0; z < 4; ++z)
         for (int y = 0; y < 4; ++y)
             for (int x = 0; x < 4; ++x) counts[x + nc * (y + nc * z)] = 1100;
     counts[1 + nc * (1 + nc)] = 2600;
+    counts[8 + nc * (8 + nc * 8)] = 10;
     int64_t np = 0;
     for (int64_t i = 0; i < nc3; ++i) {
         offsets[i] = np;
@@ -1044,12 +1008,7 @@ static void check_error_paths(long long& n, long long& bad) {
     }
     std::vector<float> Fl(3 * nc3, 0.5f), green(kGreenPacked, 0.f), Td(256, 0.f);
     const float sigma = 1.f, kd[2] = {0.f, 0.f};
-    // scratch with a guard zone after each component's slot
-    constexpr int kGuard = 1024;
-    std::vector<float> sp(3 * (size_t)kLowmemCap + kGuard, -7.f);
-    std::vector<int32_t> sq(2 * (size_t)kLowmemCap + kGuard, -7);
-    std::vector<int32_t> cnew(nc3, 0);
-    std::vector<unsigned long long> S(3 * nc3, 0ull);
+    std::vector<float> Pn(3 * (size_t)np, -7.f);
     uint32_t errw = 0;
     TileParams P{};
     P.nc = nc;
@@ -1065,9 +1024,8 @@ static void check_error_paths(long long& n, long long& bad) {
     P.Tdec = Td.data();
     P.sigma = &sigma;
     P.kd = kd;
-    P.mode = 2;
-    P.counts_new = cnew.data();
-    P.S = S.data();
+    P.mode = 1;
+    P.Pn = Pn.data();
     P.err = &errw;
     std::vector<unsigned char> smem(kTileSmemBytes);
     unsigned char* base = smem.data();
@@ -1077,25 +1035,26 @@ static void check_error_paths(long long& n, long long& bad) {
     int* O = reinterpret_cast<int*>(gS + kGreenPacked);
     const TileGeom g = tile_geom(0, nc, nt);
     const TileCells c = tile_cells(W, O);
-    const CtaScratch cs{sp.data(), sq.data()};
     for (int t = 0; t < kTileThreads; ++t) tile_prologue(t, g, P, c, R, gS);
     for (int t = 0; t < kTileThreads; ++t) tile_cells_scan(t, g, c);
     for (int t = 0; t < kTileThreads; ++t) tile_cells_map(t, g, c);
-    for (int t = 0; t < kTileThreads; ++t) tile_deposit_flat<true, 1>(t, g, P, R, c, cs);
+    for (int t = 0; t < kTileThreads; ++t) tile_deposit_flat<1>(t, g, P, R, c);
     ++n;
-    bad += c.ppre[kOwnMax] <= kLowmemCap || c.misc[2] <= 255;   // the case is what it claims
+    bad += c.ppre[kOwnMax] != 64 * 1100 + 1500 || c.misc[2] <= 255;   // the case is what it claims
     ++n;
-    bad += (errw & kErrScratch) == 0u || (errw & kErrFineOverflow) == 0u;
-    // parked forces: slots 0..cap-1 of each component written (F_l = 0.5
-    // everywhere gathers to 0.5), the guard after the last untouched
-    for (int e = 0; e < 3; ++e)
-        for (int v = 0; v < kLowmemCap; v += 97) {
+    bad += (errw & kErrFineOverflow) == 0u;
+    // parked forces: every own slot of each component holds F_l = 0.5
+    // (gathered from a constant field), the outside cell's slots untouched
+    const int64_t own_end = offsets[nc3] - 10;
+    for (int e = 0; e < 3; ++e) {
+        for (int64_t j = 0; j < own_end; j += 97) {
             ++n;
-            bad += std::fabs(sp[(size_t)e * kLowmemCap + v] - 0.5f) > 1e-6f;
+            bad += std::fabs(Pn[(size_t)e * np + j] - 0.5f) > 1e-6f;
         }
-    for (int i = 0; i < kGuard; ++i) {
-        ++n;
-        bad += sp[3 * (size_t)kLowmemCap + i] != -7.f;
+        for (int64_t j = own_end; j < np; ++j) {
+            ++n;
+            bad += Pn[(size_t)e * np + j] != -7.f;
+        }
     }
 }
 

@@ -39,7 +39,7 @@ def _mix():
 
 def _large_mix():
     # the large boxes of the serving mix (128^3, 256^3 particles) next to
-    # small ones, and low-memory boxes (two tile passes per step) among them
+    # small ones, and low-memory boxes (new codes derived again by the re-encode) among them
     from paper_2003_03931_gb300.serve import Request
     return [Request(np=256, nc=128, n_steps=3, seed=21, slope=-1.5, want_state=True),
             Request(np=32, nc=16, n_steps=5, seed=22, slope=-1.2, want_state=True),

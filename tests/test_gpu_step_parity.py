@@ -166,7 +166,7 @@ def test_kick_and_drift_per_particle_match_oracle(np_, nc, evolve):
 
 @pytest.mark.parametrize("np_,nc,evolve", [(32, 16, 4), (64, 32, 5)])
 def test_lowmem_step_matches_oracle(np_, nc, evolve):
-    # the low-memory step (two tile passes, no per-particle intermediate)
+    # the low-memory step (new momenta kept, new codes derived again)
     # against the oracle's step directly
     need_gpu()
     st, orc = _oracle_start(np_, nc, evolve, seed=8)

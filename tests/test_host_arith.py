@@ -12,7 +12,7 @@ host programs built with nvcc:
   of a clustered box, the force on the output nodes against a plain
   float64 DFT convolution with a packed symmetric table, and the
   interpolation, kick, drift and fused new-cell sums against a plain gather,
-  and the low-memory passes against the default pass (host/tile_check.cu)."""
+  and the low-memory tile pass against the default pass (host/tile_check.cu)."""
 
 import os
 import shutil
@@ -104,15 +104,16 @@ def test_tile_interpolation_kick_drift(layout, mode):
     assert cases > 50_000 and fails == 0 and err < 1e-6, (cases, fails, err)
 
 
-def test_tile_lowmem_passes_match_default_pass(layout):
-    # counts and momentum sums, the 128-bit dispersion sum (past 2^64) and the
-    # scattered records of every new cell, all exact
+def test_tile_lowmem_pass_matches_default_pass(layout):
+    # new momenta bit for bit, counts and momentum sums, the 128-bit
+    # dispersion sum (past 2^64), and the codes the low-memory re-encode
+    # derives from the old store and the momenta: all exact
     cases, fails, _ = layout["lowmem"]
     assert cases > 100_000 and fails == 0, (cases, fails)
 
 
 def test_tile_error_paths_flag_and_stay_in_bounds(layout):
-    # a tile past the low-memory scratch flags it and writes nothing past
-    # its slot; a fine node past 2^32 units flags the overflow
+    # a fine node past 2^32 units flags the overflow; every own particle's
+    # long-range force is parked in its slot and no other slot is written
     cases, fails, _ = layout["error_paths"]
     assert cases > 1000 and fails == 0, (cases, fails)
