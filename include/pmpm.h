@@ -218,7 +218,10 @@ int pmpm_fetch_tile_density(pmpm_sim* sim, int32_t tile, uint32_t* host_dst, siz
 
 /* Replace part of the state from a host buffer (PMPM_STREAMS, PMPM_COUNTS,
  * PMPM_VC, PMPM_SCALARS, or PMPM_QP which encodes raw codes and momenta).
- * Synchronises. */
+ * Synchronises.  Counts are checked on the device right after their copy
+ * (every count >= 0, sum N) and codes on the host (inside the box), before
+ * any kernel indexes with them: PMPM_EINVAL, and the sim holds no state
+ * until a valid one is loaded. */
 int pmpm_load(pmpm_sim* sim, int32_t what, const void* host_src, size_t bytes);
 
 /* Wait for the sim's stream and report device-side error flags. */

@@ -289,6 +289,8 @@ static int sync_and_check(Sim& s) {
     if (flags) {
         cudaMemsetAsync(s.err, 0, 4, s.stream);
         cudaStreamSynchronize(s.stream);
+        if (flags & kErrLoadCounts)
+            return set_error(s, PMPM_EINVAL, "loaded counts negative or not adding up to N");
         if (flags & kErrCount) return set_error(s, PMPM_ECOUNT, "particle count not conserved");
         return set_error(s, PMPM_EOVERFLOW,
                          "device range check failed (flags 0x%x: 1 fine density, 2 momentum, "
@@ -772,29 +774,18 @@ int pmpm_load(pmpm_sim* h, int32_t what, const void* src, size_t bytes) {
         case PMPM_COUNTS: {
             if (bytes != 4 * C) return set_error(s, PMPM_EINVAL, "counts need %zu bytes", 4 * C);
             // the kernels index the particle streams through these counts:
-            // they must be non-negative and add up to N
-            // (the copy starts first; a branch-free pass over the host array
-            // checks them meanwhile, and a refused load leaves no state)
-            const int32_t* c = static_cast<const int32_t*>(src);
+            // they must be non-negative and add up to N, checked on the
+            // device right after the copy (before anything else on the
+            // stream); a refused load leaves no state
             e = cudaMemcpyAsync(s.counts[s.cur], src, bytes, cudaMemcpyHostToDevice, s.stream);
             s.offsets_valid = false;
             s.loaded &= ~2;
-            int64_t total = 0;
-            int32_t lowest = 0;
-            for (size_t i = 0; i < C; ++i) {
-                total += c[i];
-                lowest = c[i] < lowest ? c[i] : lowest;
-            }
-            if (lowest < 0) {
-                cudaStreamSynchronize(s.stream);
+            if (e != cudaSuccess) break;
+            check_loaded_counts(s);
+            const int rc = sync_and_check(s);
+            if (rc) {
                 s.have_state = false;
-                return set_error(s, PMPM_EINVAL, "negative count");
-            }
-            if (total != s.n) {
-                cudaStreamSynchronize(s.stream);
-                s.have_state = false;
-                return set_error(s, PMPM_EINVAL, "counts add up to %lld, not N = %lld",
-                                 (long long)total, (long long)s.n);
+                return rc;
             }
             s.loaded |= 2;
             break;

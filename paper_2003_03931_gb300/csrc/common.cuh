@@ -32,6 +32,7 @@ enum : uint32_t {
     kErrCount = 8u,           // counts do not add up to N
     kErrNaN = 16u,            // non-finite momentum or force
     kErrDrift = 32u,          // drift larger than the int32 code range
+    kErrLoadCounts = 64u,     // loaded counts negative or not adding up to N
 };
 
 #ifdef __CUDA_ARCH__

@@ -125,6 +125,7 @@ void fft_setup();
 int scan_counts(Sim& s, const int32_t* counts, int64_t* offsets);
 int encode_from_qp(Sim& s, bool counts_ready);
 int scan_and_means(Sim& s, int nxt);
+void check_loaded_counts(Sim& s);    // device check of loaded counts (kErrLoadCounts)
 int encode_from_parked(Sim& s);       // low-memory step: re-encode from the old store and Pn
 void lowmem_bind(Sim& s, int nxt);    // low-memory layout: S and F_l in store nxt's region
 int encode_from_psi(Sim& s, const double* scale);   // low-memory ICs -> store 0

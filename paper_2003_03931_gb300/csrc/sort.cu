@@ -411,16 +411,15 @@ __device__ int64_t warp_find_cell(const int64_t* __restrict__ offsets, int64_t n
 }
 
 constexpr int kParkThreads = 256;
-constexpr int kParkSpan = 2 * kParkThreads;   // particles per block iteration
-constexpr int kParkWin = 128;                 // old cells per window of offsets
+constexpr int kParkSpan = 64;   // particles per warp iteration (two per lane)
 
 // Low-memory step: re-encode from the old store and the new momenta Pn the
 // tile pass left (no new codes were stored).  Particle j of the old store,
 // in old cell c with bins m, moves to Q = drift_code(256 c + m, p) per axis:
-// the same integer drift as the tile pass, so the same codes.  Each block
+// the same integer drift as the tile pass, so the same codes.  Each warp
 // takes a contiguous range of the old store; the old cell of each particle
-// comes from windows of the old offsets staged in shared memory (the next
-// window only where a particle lies beyond the current one).
+// comes from a window of 32 old offsets, one per lane, searched through
+// shuffles (the next window only where a particle lies beyond it).
 __global__ void __launch_bounds__(kParkThreads, 4)
 k_scatter_parked(int64_t n, int nc, int64_t chunk, const int64_t* __restrict__ offs_old,
                  const uint8_t* __restrict__ st_old, const float* __restrict__ Pn,
@@ -429,72 +428,96 @@ k_scatter_parked(int64_t n, int nc, int64_t chunk, const int64_t* __restrict__ o
                  const float* __restrict__ sigma_p, const float* __restrict__ E,
                  uint8_t* __restrict__ out, uint32_t* err) {
     __shared__ float Es[256];
-    __shared__ int64_t win[kParkWin + 1];
-    __shared__ int64_t cnext;
-    const int64_t ncells = (int64_t)nc * nc * nc;
-    const int64_t j0 = (int64_t)blockIdx.x * chunk;
-    if (j0 >= n) return;
-    const int64_t j1 = j0 + chunk < n ? j0 + chunk : n;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31;
     for (int k = tid; k < 256; k += kParkThreads) Es[k] = E[k];
-    if (tid < 32) {
-        const int64_t c = warp_find_cell(offs_old, ncells, j0);
-        if (tid == 0) cnext = c;
-    }
+    __syncthreads();
+    const int64_t j0 = ((int64_t)blockIdx.x * (kParkThreads / 32) + (tid >> 5)) * chunk;
+    if (j0 >= n) return;   // whole warps
+    const int64_t j1 = j0 + chunk < n ? j0 + chunk : n;
+    const int64_t ncells = (int64_t)nc * nc * nc;
     const float drift = kd[1], sigma = *sigma_p;
     const int M = nc * kBins;
     const float* const vcd[3] = {vc, vc + ncells, vc + 2 * ncells};
+    int64_t cw = warp_find_cell(offs_old, ncells, j0);
+    // coordinates of cell cw, kept along with it (no division per particle)
+    int wx, wy, wz;
+    {
+        const int c = (int)cw, t = c / nc;
+        wz = t / nc;
+        wy = t - wz * nc;
+        wx = c - t * nc;
+    }
     for (int64_t base = j0; base < j1; base += kParkSpan) {
-        __syncthreads();   // cnext is written; the last window is read
-        int64_t cw = cnext;
-        int64_t j[2], cell[2];
+        int64_t j[2];
+        int cell[2], cc[2][3];   // cells below nc^3 <= 2^30
         bool live[2];
+        int32_t q[2][3];
+        float p[2][3];
+        // the particles' bins and new momenta, loaded before the cell search
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
-            j[u] = base + u * kParkThreads + tid;
+            j[u] = base + 32 * u + lane;
             live[u] = j[u] < j1;
             cell[u] = -1;
+            cc[u][0] = cc[u][1] = cc[u][2] = 0;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                q[u][d] = live[u] ? st_old[d * n + j[u]] : 0;
+                p[u][d] = live[u] ? Pn[d * n + j[u]] : 0.f;
+            }
         }
         // every particle of this span lies in cell cw or after it
         for (;;) {
-            for (int k = tid; k <= kParkWin; k += kParkThreads)
-                win[k] = offs_old[cw + k < ncells ? cw + k : ncells];
-            __syncthreads();
-            bool need = false;
+            const int64_t wv = offs_old[cw + lane < ncells ? cw + lane : ncells];
+            const int64_t wend = offs_old[cw + 32 < ncells ? cw + 32 : ncells];
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
-                if (!live[u] || cell[u] >= 0) continue;
-                if (j[u] >= win[kParkWin]) {
-                    need = true;
-                    continue;
+                // the largest k with offsets[cw + k] <= j (all lanes shuffle)
+                int k = 0;
+#pragma unroll
+                for (int b = 16; b > 0; b >>= 1) {
+                    const int64_t w = __shfl_sync(0xffffffffu, wv, k + b);
+                    if (w <= j[u]) k += b;
                 }
-                int lo = 0, hi = kParkWin;   // win[lo] <= j < win[hi]
-                while (hi - lo > 1) {
-                    const int mid = (lo + hi) >> 1;
-                    if (win[mid] <= j[u]) lo = mid; else hi = mid;
+                if (live[u] && cell[u] < 0 && j[u] < wend) {
+                    cell[u] = (int)(cw + k);
+                    int x = wx + k, y = wy, z = wz;
+                    while (x >= nc) {
+                        x -= nc;
+                        if (++y == nc) {
+                            y = 0;
+                            ++z;
+                        }
+                    }
+                    cc[u][0] = x;
+                    cc[u][1] = y;
+                    cc[u][2] = z;
                 }
-                cell[u] = cw + lo;
             }
-            if (!__syncthreads_or(need)) break;
-            cw += kParkWin;
+            const bool need = (live[0] && cell[0] < 0) || (live[1] && cell[1] < 0);
+            if (!__any_sync(0xffffffffu, need)) break;
+            cw += 32;
+            wx += 32;
+            while (wx >= nc) {
+                wx -= nc;
+                if (++wy == nc) {
+                    wy = 0;
+                    ++wz;
+                }
+            }
         }
         // the next span starts in the cell of this span's last particle
-        const int64_t jl = (base + kParkSpan < j1 ? base + kParkSpan : j1) - 1;
-        int32_t q[2][3];
-        float p[2][3];
+        const int last = (int)((j1 < base + kParkSpan ? j1 : base + kParkSpan) - 1 - base);
+        const int hi = last >= 32;
+        cw = __shfl_sync(0xffffffffu, hi ? cell[1] : cell[0], last & 31);
+        wx = __shfl_sync(0xffffffffu, hi ? cc[1][0] : cc[0][0], last & 31);
+        wy = __shfl_sync(0xffffffffu, hi ? cc[1][1] : cc[0][1], last & 31);
+        wz = __shfl_sync(0xffffffffu, hi ? cc[1][2] : cc[0][2], last & 31);
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
-            q[u][0] = q[u][1] = q[u][2] = 0;
-            p[u][0] = p[u][1] = p[u][2] = 0.f;
             if (!live[u]) continue;
-            if (j[u] == jl) cnext = cell[u];
-            const int64_t c = cell[u];
-            const int cc[3] = {(int)(c % nc), (int)((c / nc) % nc), (int)(c / ((int64_t)nc * nc))};
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                p[u][d] = Pn[d * n + j[u]];
-                q[u][d] = drift_code(cc[d] * kBins + st_old[d * n + j[u]], p[u][d], drift, M, err);
-            }
+            for (int d = 0; d < 3; ++d) q[u][d] = drift_code(cc[u][d] * kBins + q[u][d], p[u][d], drift, M, err);
         }
         scatter_two<1>(q, p, live, n, nc, vcd, offsets, fill, sigma, Es, out, err);
     }
@@ -536,6 +559,53 @@ int scan_counts(Sim& s, const int32_t* counts, int64_t* offsets) {
                                                              nullptr, nullptr, nullptr);
     s.launches += 3;
     return check_launch(s, "scan");
+}
+
+// Check of loaded counts on the device, before any kernel indexes the store
+// through them: every count >= 0 and their sum N.  acc[0] gathers the sum,
+// acc[1] the negative counts; the verdict sets kErrLoadCounts.
+__global__ void __launch_bounds__(256) k_counts_sum(int64_t ncells, const int32_t* __restrict__ counts,
+                                                    unsigned long long* acc) {
+    __shared__ long long ssum[8];
+    __shared__ unsigned sneg[8];
+    long long sum = 0;
+    unsigned neg = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ncells;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int c = counts[i];
+        sum += c;
+        neg += c < 0 ? 1u : 0u;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sum += __shfl_down_sync(0xffffffffu, sum, o);
+        neg += __shfl_down_sync(0xffffffffu, neg, o);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        ssum[warp] = sum;
+        sneg[warp] = neg;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            sum += ssum[w];
+            neg += sneg[w];
+        }
+        atomicAdd(&acc[0], (unsigned long long)sum);
+        if (neg) atomicAdd(&acc[1], (unsigned long long)neg);
+    }
+}
+
+__global__ void k_counts_verdict(const unsigned long long* acc, int64_t n, uint32_t* err) {
+    if ((long long)acc[0] != (long long)n || acc[1] != 0ull) atomicOr(err, kErrLoadCounts);
+}
+
+void check_loaded_counts(Sim& s) {
+    cudaMemsetAsync(s.d2, 0, 16, s.stream);
+    k_counts_sum<<<grid_for(s.ncells, 256, 152 * 8), 256, 0, s.stream>>>(s.ncells, s.counts[s.cur], s.d2);
+    k_counts_verdict<<<1, 1, 0, s.stream>>>(s.d2, s.n, s.err);
+    s.launches += 2;
 }
 
 // Offsets of the new counts, zeroed slot counters, and the new cell means
@@ -624,8 +694,9 @@ int encode_from_parked(Sim& s) {
     prof_mark(s, 3);
     finish_sigma(s, nxt);
     prof_mark(s, 4);
-    const int grid = grid_for(s.n, kParkSpan, 152 * 4);
-    int64_t chunk = (s.n + grid - 1) / grid;
+    const int grid = grid_for(s.n, kParkSpan * (kParkThreads / 32), 152 * 4);
+    const int64_t warps = (int64_t)grid * (kParkThreads / 32);
+    int64_t chunk = (s.n + warps - 1) / warps;
     chunk = (chunk + kParkSpan - 1) / kParkSpan * kParkSpan;
     k_scatter_parked<<<grid, kParkThreads, 0, s.stream>>>(
         s.n, s.nc, chunk, s.offsets[s.cur], s.streams[s.cur], s.Pn, s.d_kd, s.vc[nxt], s.offsets[nxt],
