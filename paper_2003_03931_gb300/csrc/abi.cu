@@ -126,7 +126,7 @@ static size_t layout_lowmem(Sim& s, uint8_t* base) {
     const int64_t N = s.n, C = s.ncells;
     // small persistent items
     const size_t h = s.nc / 2 + 1;
-    s.green_coarse = reinterpret_cast<float*>(take(4 * h * h * h));
+    s.green_coarse = reinterpret_cast<float4*>(take(16 * h * h * h));
     s.green_fine = reinterpret_cast<float*>(take(4 * (size_t)kGreenS * kGreenS * kGreenS));
     s.green_packed = reinterpret_cast<float*>(take(4 * (size_t)kGreenS * kGreenS * (kGreenS + 1) / 2));
     s.Tdec = reinterpret_cast<float*>(take(4 * 256));
@@ -209,7 +209,7 @@ size_t layout(Sim& s, uint8_t* base) {
     s.cB2 = reinterpret_cast<float2*>(take(8 * (size_t)C));
     s.Fl = reinterpret_cast<float*>(take(12 * (size_t)C));
     const size_t h = s.nc / 2 + 1;
-    s.green_coarse = reinterpret_cast<float*>(take(4 * h * h * h));
+    s.green_coarse = reinterpret_cast<float4*>(take(16 * h * h * h));
     s.green_fine = reinterpret_cast<float*>(take(4 * (size_t)kGreenS * kGreenS * kGreenS));
     s.green_packed = reinterpret_cast<float*>(take(4 * (size_t)kGreenS * kGreenS * (kGreenS + 1) / 2));
     s.Tdec = reinterpret_cast<float*>(take(4 * 256));
@@ -493,7 +493,7 @@ GreenRefs sim_tables(const Sim& s) {
 
 size_t green_table_bytes(int nc, size_t part[3]) {
     const size_t hc = (size_t)(nc / 2 + 1);
-    part[0] = 4 * hc * hc * hc;
+    part[0] = 16 * hc * hc * hc;
     part[1] = 4 * (size_t)kGreenS * kGreenS * kGreenS;
     part[2] = 4 * (size_t)(kGreenS - 2) * kGreenS * (kGreenS + 1) / 2;
     return part[0] + part[1] + part[2];
@@ -502,7 +502,7 @@ size_t green_table_bytes(int nc, size_t part[3]) {
 int copy_tables(cudaStream_t st, const GreenRefs& dst, const GreenRefs& src, int nc) {
     size_t part[3];
     green_table_bytes(nc, part);
-    cudaError_t e = cudaMemcpyAsync(const_cast<float*>(dst.coarse), src.coarse, part[0],
+    cudaError_t e = cudaMemcpyAsync(const_cast<float4*>(dst.coarse), src.coarse, part[0],
                                     cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(const_cast<float*>(dst.fine), src.fine, part[1], cudaMemcpyDeviceToDevice, st);

@@ -113,11 +113,11 @@ __device__ __forceinline__ void kfold(int k, int nc, int& a, float& sg) {
     else { a = nc - k; sg = -1.f; }
 }
 
-__global__ void k_coarse_green(int nc, const float* __restrict__ table,
+__global__ void k_coarse_green(int nc, const float4* __restrict__ table,
                                const float2* __restrict__ A, float2* __restrict__ B1,
                                float2* __restrict__ B2) {
     const int64_t ncells = (int64_t)nc * nc * nc;
-    const int h = nc / 2 + 1;
+    const int64_t h = nc / 2 + 1;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ncells;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int kx = (int)(i % nc), ky = (int)((i / nc) % nc), kz = (int)(i / ((int64_t)nc * nc));
@@ -126,9 +126,9 @@ __global__ void k_coarse_green(int nc, const float* __restrict__ table,
         kfold(kx, nc, ax, sx);
         kfold(ky, nc, ay, sy);
         kfold(kz, nc, az, sz);
-        const float Sx = sx * table[((int64_t)ax * h + ay) * h + az];
-        const float Sy = sy * table[((int64_t)ay * h + ax) * h + az];
-        const float Sz = sz * table[((int64_t)az * h + ay) * h + ax];
+        // the three components' kernels at (|kx|, |ky|, |kz|), |kx| fastest
+        const float4 g = table[(az * h + ay) * h + ax];
+        const float Sx = sx * g.x, Sy = sy * g.y, Sz = sz * g.z;
         const float2 a = A[i];
         // B1 = a (S_y - i S_x),  B2 = a (-i S_z)
         B1[i] = make_float2(a.x * Sy + a.y * Sx, a.y * Sy - a.x * Sx);

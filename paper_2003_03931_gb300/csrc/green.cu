@@ -260,16 +260,33 @@ __global__ void k_coarse_table(int nc, Ewald e, const double2* X, float* table) 
     }
 }
 
+// The three components' coarse kernels per folded wavenumber, gathered for
+// the Green multiply: G[(az h + ay) h + ax] = (S(ax; ay, az), S(ay; ax, az),
+// S(az; ay, ax), 0) from the own-axis-first table T[(a h + b) h + c] =
+// S(a; b, c), so that a pass over the mesh (kx fastest) reads G in order.
+__global__ void k_coarse_table4(int nc, const float* __restrict__ T, float4* __restrict__ G) {
+    const int64_t h = nc / 2 + 1;
+    const int64_t total = h * h * h;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t az = i / (h * h), ay = (i / h) % h, ax = i % h;
+        G[i] = make_float4(T[(ax * h + ay) * h + az], T[(ay * h + ax) * h + az], T[(az * h + ay) * h + ax],
+                           0.f);
+    }
+}
+
 }  // namespace
 
 int build_green_tables(Sim& s) {
     const int nc = s.nc;
     const double L = 4.0 * nc;
     cudaStream_t st = s.stream;
-    // scratch (float64): Tsmall[343], Ks[1331], coarse mesh complex [nc^3]
+    // scratch: Tsmall[343], Ks[1331], coarse mesh complex [nc^3] (float64),
+    // then the own-axis-first coarse table [(nc/2+1)^3] (float32)
     double* Tsmall = reinterpret_cast<double*>(s.scratch);
     double* Ks = Tsmall + 343;
     double2* mesh = reinterpret_cast<double2*>(align_up(reinterpret_cast<uintptr_t>(Ks + 1331)));
+    float* T1 = reinterpret_cast<float*>(mesh + (size_t)nc * nc * nc);
     k_coarse_small<<<(343 * 32 + 255) / 256, 256, 0, st>>>(L, Tsmall);
     k_fine_values<<<(1331 * 32 + 255) / 256, 256, 0, st>>>(L, Tsmall, Ks);
     k_fine_table<<<(kGreenS * kGreenS * kGreenS * 32 + 255) / 256, 256, 0, st>>>(Ks, s.green_fine);
@@ -280,12 +297,14 @@ int build_green_tables(Sim& s) {
     int rc = fft3d<double>(s, mesh, nc, -1);
     if (rc) return rc;
     const int64_t h = nc / 2 + 1;
-    k_coarse_table<<<grid_for(h * h * h, 256), 256, 0, st>>>(nc, e, mesh, s.green_coarse);
+    k_coarse_table<<<grid_for(h * h * h, 256), 256, 0, st>>>(nc, e, mesh, T1);
+    k_coarse_table4<<<grid_for(h * h * h, 256), 256, 0, st>>>(nc, T1, s.green_coarse);
     return check_launch(s, "green tables");
 }
 
 size_t green_scratch_bytes(int nc) {
-    return 343 * 8 + 1331 * 8 + 512 + (size_t)nc * nc * nc * 16;
+    const size_t h = (size_t)(nc / 2 + 1);
+    return 343 * 8 + 1331 * 8 + 512 + (size_t)nc * nc * nc * 16 + 4 * h * h * h;
 }
 
 }  // namespace pmpm

@@ -48,7 +48,7 @@ struct Sim {
     float2* cB1 = nullptr;
     float2* cB2 = nullptr;
     float* Fl = nullptr;                        // [3][nc^3]
-    float* green_coarse = nullptr;              // [(nc/2+1)^3]
+    float4* green_coarse = nullptr;             // [(nc/2+1)^3] (S_x, S_y, S_z, 0), |kx| fastest
     float* green_fine = nullptr;                // [17^3]
     float* green_packed = nullptr;              // [17 x 153] b <= c half of green_fine
     float* Tdec = nullptr;                      // [256]
@@ -155,7 +155,7 @@ namespace pmpm {
 // Device pointers of the three force tables (Sec. II): the coarse-kernel
 // spectrum, the fine kernel K_s spectrum and its packed tile copy.
 struct GreenRefs {
-    const float* coarse;
+    const float4* coarse;
     const float* fine;
     const float* packed;
 };

@@ -305,7 +305,7 @@ bool admit(pmpm_batch& b, Job* j) {
             Table tb;
             tb.off = off;
             uint8_t* p = b.base + off;
-            tb.refs.coarse = reinterpret_cast<const float*>(p);
+            tb.refs.coarse = reinterpret_cast<const float4*>(p);
             p += (part[0] + kArenaAlign - 1) / kArenaAlign * kArenaAlign;
             tb.refs.fine = reinterpret_cast<const float*>(p);
             p += (part[1] + kArenaAlign - 1) / kArenaAlign * kArenaAlign;

@@ -417,11 +417,14 @@ constexpr int kParkSpan = 64;   // particles per warp iteration (two per lane)
 // tile pass left (no new codes were stored).  Particle j of the old store,
 // in old cell c with bins m, moves to Q = drift_code(256 c + m, p) per axis:
 // the same integer drift as the tile pass, so the same codes.  Each warp
-// takes a contiguous range of the old store; the old cell of each particle
-// comes from a window of 32 old offsets, one per lane, searched through
-// shuffles (the next window only where a particle lies beyond it).
+// takes whole rows of cells (x fastest), row r in turn by warp r mod W, so
+// the rows in flight at any time span several planes: a new cell's
+// particles, which come from its old neighbours, are scattered while its
+// part of the new store is still in L2.  Within a row, each particle's old
+// cell comes from a window of 32 old offsets, one per lane, searched
+// through shuffles (the next window only where a particle lies beyond it).
 __global__ void __launch_bounds__(kParkThreads, 4)
-k_scatter_parked(int64_t n, int nc, int64_t chunk, const int64_t* __restrict__ offs_old,
+k_scatter_parked(int64_t n, int nc, const int64_t* __restrict__ offs_old,
                  const uint8_t* __restrict__ st_old, const float* __restrict__ Pn,
                  const float* __restrict__ kd, const float* __restrict__ vc,
                  const int64_t* __restrict__ offsets, int32_t* fill,
@@ -431,95 +434,74 @@ k_scatter_parked(int64_t n, int nc, int64_t chunk, const int64_t* __restrict__ o
     const int tid = threadIdx.x, lane = tid & 31;
     for (int k = tid; k < 256; k += kParkThreads) Es[k] = E[k];
     __syncthreads();
-    const int64_t j0 = ((int64_t)blockIdx.x * (kParkThreads / 32) + (tid >> 5)) * chunk;
-    if (j0 >= n) return;   // whole warps
-    const int64_t j1 = j0 + chunk < n ? j0 + chunk : n;
-    const int64_t ncells = (int64_t)nc * nc * nc;
+    const int64_t ncells = (int64_t)nc * nc * nc, nrows = (int64_t)nc * nc;
     const float drift = kd[1], sigma = *sigma_p;
     const int M = nc * kBins;
     const float* const vcd[3] = {vc, vc + ncells, vc + 2 * ncells};
-    int64_t cw = warp_find_cell(offs_old, ncells, j0);
-    // coordinates of cell cw, kept along with it (no division per particle)
-    int wx, wy, wz;
-    {
-        const int c = (int)cw, t = c / nc;
-        wz = t / nc;
-        wy = t - wz * nc;
-        wx = c - t * nc;
-    }
-    for (int64_t base = j0; base < j1; base += kParkSpan) {
-        int64_t j[2];
-        int cell[2], cc[2][3];   // cells below nc^3 <= 2^30
-        bool live[2];
-        int32_t q[2][3];
-        float p[2][3];
-        // the particles' bins and new momenta, loaded before the cell search
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            j[u] = base + 32 * u + lane;
-            live[u] = j[u] < j1;
-            cell[u] = -1;
-            cc[u][0] = cc[u][1] = cc[u][2] = 0;
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                q[u][d] = live[u] ? st_old[d * n + j[u]] : 0;
-                p[u][d] = live[u] ? Pn[d * n + j[u]] : 0.f;
-            }
-        }
-        // every particle of this span lies in cell cw or after it
-        for (;;) {
-            const int64_t wv = offs_old[cw + lane < ncells ? cw + lane : ncells];
-            const int64_t wend = offs_old[cw + 32 < ncells ? cw + 32 : ncells];
+    const int64_t warps = (int64_t)gridDim.x * (kParkThreads / 32);
+    for (int64_t row = (int64_t)blockIdx.x * (kParkThreads / 32) + (tid >> 5); row < nrows; row += warps) {
+        // the row's particles; cw and (wx, wy, wz): the window's first cell
+        int64_t cw = row * nc;
+        const int64_t j1 = offs_old[cw + nc];
+        int wx = 0, wy = (int)(row % nc), wz = (int)(row / nc);
+        for (int64_t base = offs_old[cw]; base < j1; base += kParkSpan) {
+            int64_t j[2];
+            int cell[2], cc[2][3];   // cells below nc^3 <= 2^30
+            bool live[2];
+            int32_t q[2][3];
+            float p[2][3];
+            // the particles' bins and new momenta, loaded before the cell search
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
-                // the largest k with offsets[cw + k] <= j (all lanes shuffle)
-                int k = 0;
+                j[u] = base + 32 * u + lane;
+                live[u] = j[u] < j1;
+                cell[u] = -1;
+                cc[u][0] = cc[u][1] = cc[u][2] = 0;
 #pragma unroll
-                for (int b = 16; b > 0; b >>= 1) {
-                    const int64_t w = __shfl_sync(0xffffffffu, wv, k + b);
-                    if (w <= j[u]) k += b;
+                for (int d = 0; d < 3; ++d) {
+                    q[u][d] = live[u] ? st_old[d * n + j[u]] : 0;
+                    p[u][d] = live[u] ? Pn[d * n + j[u]] : 0.f;
                 }
-                if (live[u] && cell[u] < 0 && j[u] < wend) {
-                    cell[u] = (int)(cw + k);
-                    int x = wx + k, y = wy, z = wz;
-                    while (x >= nc) {
-                        x -= nc;
-                        if (++y == nc) {
-                            y = 0;
-                            ++z;
-                        }
+            }
+            // every particle of this span lies in cell cw or after it
+            for (;;) {
+                const int64_t wv = offs_old[cw + lane < ncells ? cw + lane : ncells];
+                const int64_t wend = offs_old[cw + 32 < ncells ? cw + 32 : ncells];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    // the largest k with offsets[cw + k] <= j (all lanes shuffle)
+                    int k = 0;
+#pragma unroll
+                    for (int b = 16; b > 0; b >>= 1) {
+                        const int64_t w = __shfl_sync(0xffffffffu, wv, k + b);
+                        if (w <= j[u]) k += b;
                     }
-                    cc[u][0] = x;
-                    cc[u][1] = y;
-                    cc[u][2] = z;
+                    if (live[u] && cell[u] < 0 && j[u] < wend) {
+                        // a particle of this row lies in a cell of this row
+                        cell[u] = (int)(cw + k);
+                        cc[u][0] = wx + k;
+                        cc[u][1] = wy;
+                        cc[u][2] = wz;
+                    }
                 }
+                const bool need = (live[0] && cell[0] < 0) || (live[1] && cell[1] < 0);
+                if (!__any_sync(0xffffffffu, need)) break;
+                cw += 32;
+                wx += 32;
             }
-            const bool need = (live[0] && cell[0] < 0) || (live[1] && cell[1] < 0);
-            if (!__any_sync(0xffffffffu, need)) break;
-            cw += 32;
-            wx += 32;
-            while (wx >= nc) {
-                wx -= nc;
-                if (++wy == nc) {
-                    wy = 0;
-                    ++wz;
-                }
+            // the next span starts in the cell of this span's last particle
+            const int last = (int)((j1 < base + kParkSpan ? j1 : base + kParkSpan) - 1 - base);
+            const int hi = last >= 32;
+            cw = __shfl_sync(0xffffffffu, hi ? cell[1] : cell[0], last & 31);
+            wx = __shfl_sync(0xffffffffu, hi ? cc[1][0] : cc[0][0], last & 31);
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                if (!live[u]) continue;
+#pragma unroll
+                for (int d = 0; d < 3; ++d) q[u][d] = drift_code(cc[u][d] * kBins + q[u][d], p[u][d], drift, M, err);
             }
+            scatter_two<1>(q, p, live, n, nc, vcd, offsets, fill, sigma, Es, out, err);
         }
-        // the next span starts in the cell of this span's last particle
-        const int last = (int)((j1 < base + kParkSpan ? j1 : base + kParkSpan) - 1 - base);
-        const int hi = last >= 32;
-        cw = __shfl_sync(0xffffffffu, hi ? cell[1] : cell[0], last & 31);
-        wx = __shfl_sync(0xffffffffu, hi ? cc[1][0] : cc[0][0], last & 31);
-        wy = __shfl_sync(0xffffffffu, hi ? cc[1][1] : cc[0][1], last & 31);
-        wz = __shfl_sync(0xffffffffu, hi ? cc[1][2] : cc[0][2], last & 31);
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            if (!live[u]) continue;
-#pragma unroll
-            for (int d = 0; d < 3; ++d) q[u][d] = drift_code(cc[u][d] * kBins + q[u][d], p[u][d], drift, M, err);
-        }
-        scatter_two<1>(q, p, live, n, nc, vcd, offsets, fill, sigma, Es, out, err);
     }
 }
 
@@ -694,12 +676,9 @@ int encode_from_parked(Sim& s) {
     prof_mark(s, 3);
     finish_sigma(s, nxt);
     prof_mark(s, 4);
-    const int grid = grid_for(s.n, kParkSpan * (kParkThreads / 32), 152 * 4);
-    const int64_t warps = (int64_t)grid * (kParkThreads / 32);
-    int64_t chunk = (s.n + warps - 1) / warps;
-    chunk = (chunk + kParkSpan - 1) / kParkSpan * kParkSpan;
+    const int grid = grid_for((int64_t)s.nc * s.nc, kParkThreads / 32, 152 * 4);
     k_scatter_parked<<<grid, kParkThreads, 0, s.stream>>>(
-        s.n, s.nc, chunk, s.offsets[s.cur], s.streams[s.cur], s.Pn, s.d_kd, s.vc[nxt], s.offsets[nxt],
+        s.n, s.nc, s.offsets[s.cur], s.streams[s.cur], s.Pn, s.d_kd, s.vc[nxt], s.offsets[nxt],
         s.fill, s.sigma_d[nxt], s.Eedge, s.streams[nxt], s.err);
     s.launches++;
     prof_mark(s, 5);

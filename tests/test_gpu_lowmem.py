@@ -1,8 +1,8 @@
 """GPU checks of the low-memory step (PMPM_FLAG_LOWMEM): from the same state
 it writes the same store as the default step (cell-sorted records, counts,
-v_c, sigma bit for bit), also when many tiles share each SM's scratch slot; its
-float32 initial conditions match the oracle's like the default ones; and the
-per-particle fetches it cannot serve fail cleanly."""
+v_c, sigma bit for bit), also at 256^3 where each warp of the re-encode takes
+several rows of cells; its float32 initial conditions match the oracle's like
+the default ones; and the per-particle fetches it cannot serve fail cleanly."""
 
 import numpy as np
 import pytest
@@ -21,7 +21,7 @@ def _state(sim):
             cell_sorted_records(st["counts"], rec))
 
 
-@pytest.mark.parametrize("name,steps", [("c1_32", 5), ("ragged_32", 4), ("c2_128", 3)])
+@pytest.mark.parametrize("name,steps", [("c1_32", 5), ("ragged_32", 4), ("c2_128", 3), ("c4sub_256", 1)])
 def test_lowmem_steps_equal_default_steps(name, steps):
     need_gpu()
     w = synth.WORKLOADS[name]
