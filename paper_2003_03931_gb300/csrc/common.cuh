@@ -165,19 +165,35 @@ PMPM_HD void combine128(const unsigned long long* d, unsigned long long& lo, uns
     hi = (unsigned long long)(v >> 64);
 }
 
-// (lo, hi) += floor(S^2 / n) for n >= 1: S^2 = h 2^64 + l, then long
-// division by n in 32-bit digits (every partial remainder is below n < 2^31)
+// (lo, hi) += floor(S^2 / n) for n >= 1 (n < 2^31): with |S| = a n + r
+// (0 <= r < n), S^2 / n = a^2 n + 2 a r + r^2 / n, whose first two terms are
+// integers, so floor(S^2 / n) = a^2 n + 2 a r + floor(r^2 / n).  Both
+// divisions take 32-bit operands when they fit (the usual case: |S| < 2^32
+// and n < 2^16), 64-bit ones otherwise.
 PMPM_HD void add_square_over_n128(long long S, int n, unsigned long long& lo,
                                   unsigned long long& hi) {
     const unsigned long long u = S < 0 ? (unsigned long long)(-S) : (unsigned long long)S;
-    const unsigned long long l = u * u, h = umulhi64(u, u), d = (unsigned long long)n;
-    const unsigned long long qh = h / d, r = h % d;
-    const unsigned long long t1 = (r << 32) | (l >> 32);
-    const unsigned long long q1 = t1 / d, r1 = t1 % d;
-    const unsigned long long t2 = (r1 << 32) | (l & 0xffffffffull);
-    const unsigned long long ql = (q1 << 32) | (t2 / d);
-    lo += ql;
-    hi += qh + (lo < ql ? 1ull : 0ull);
+    const unsigned long long d = (unsigned long long)n;
+    unsigned long long a, r;
+    if ((u >> 32) == 0) {
+        const uint32_t a32 = (uint32_t)u / (uint32_t)n;
+        a = a32;
+        r = (uint32_t)u - a32 * (uint32_t)n;
+    } else {
+        a = u / d;
+        r = u - a * d;
+    }
+    const unsigned long long q3 = r < 65536ull ? (unsigned long long)((uint32_t)(r * r) / (uint32_t)n)
+                                               : (r * r) / d;
+    // a < 2^63 / n, so a^2 n < 2^126 / n and 2 a r < 2^64: 128-bit sums
+    const unsigned long long a2l = a * a, a2h = umulhi64(a, a);          // a^2
+    const unsigned long long pl = a2l * d, ph = a2h * d + umulhi64(a2l, d);   // a^2 n
+    const unsigned long long ar = 2ull * a * r;                          // < 2^64 (r < n)
+    unsigned long long vl = pl + ar, vh = ph + (vl < pl ? 1ull : 0ull);
+    vl += q3;
+    vh += vl < q3 ? 1ull : 0ull;
+    lo += vl;
+    hi += vh + (lo < vl ? 1ull : 0ull);
 }
 
 // round-half-even(p 2^24) for a float32 p with |p| < 2^20, in integers (the

@@ -25,8 +25,12 @@
 //      during the deposit and used by every interpolation phase, a few
 //      per-tile scalars, and the velocity decode table T of Eq. 3 (2 KB).
 // Index swizzles (x ^ y) make every pencil pass free of bank conflicts.  The
-// transforms are the register FFTs of regfft.cuh (decimation in time with
-// fused multiply-add butterflies).
+// data-dependent accesses are not: the deposit's atomics and the force
+// gathers at particle positions meet about 3 extra wavefronts per warp access
+// (32 random addresses would meet 2.5), and the Green-table reads of the
+// inverse z passes fewer; together they account for the conflicts a profile
+// of the tile pass counts.  The transforms are the register FFTs of
+// regfft.cuh (decimation in time with fused multiply-add butterflies).
 //
 // Each phase is a per-thread function; the kernel calls them with a block
 // barrier between phases.

@@ -46,9 +46,11 @@ static void check_moments() {
     unsigned long long lo = 0, hi = 0, lo2 = 0, hi2 = 0;
     unsigned __int128 ref = 0, ref2 = 0;
     for (int i = 0; i < 2000000; ++i) {
-        long long x = (long long)(next_u64() >> (i % 3 == 0 ? 19 : 21));   // up to 2^45
+        // up to 2^45, and below 2^32 (the divisions' 32-bit path) a third of the time
+        long long x = (long long)(next_u64() >> (i % 3 == 0 ? 19 : (i % 3 == 1 ? 21 : 34)));
         if (next_u64() & 1) x = -x;
         if (i % 101 == 0) x = (i & 1) ? (1ll << 44) - 1 : -((1ll << 44) - 1);
+        if (i == 7 || i == 8) x = (i & 1) ? -0x7fffffffffffffffll : 0x7fffffffffffffffll;
         const unsigned __int128 ux = (unsigned __int128)(x < 0 ? -x : x);
         add_square128(x, lo, hi);
         ref += ux * ux;
