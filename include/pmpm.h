@@ -260,12 +260,11 @@ const char* pmpm_last_error(const pmpm_sim* sim);
  * Its scratch is one fixed array of about 4.2 MB in the library's device
  * memory, held by every GPU that loads the library until the process exits.
  * The first call on a device looks up that array's address and fills a
- * twiddle table there, synchronising the stream; make that first call before
- * any stream capture.  Every call copies its result to the host arrays and
- * waits for the stream before it returns.  All calls share the array: calls
- * whose GPU work overlaps (other streams, other host threads) race and give
- * wrong results.  Larger sizes return PMPM_EINVAL; pmpm_noalloc_last_error()
- * explains. */
+ * twiddle table there, synchronising the stream.  Every call copies its
+ * result to the host arrays and waits for the stream before it returns.
+ * All calls share the array: calls whose GPU work overlaps (other streams,
+ * other host threads) race and give wrong results.  Larger sizes return
+ * PMPM_EINVAL; pmpm_noalloc_last_error() explains. */
 int pmpm_power_spectrum_noalloc(int32_t nc, int64_t n, const uint8_t* d_m0,
                                 const uint8_t* d_m1, const uint8_t* d_m2,
                                 const int32_t* d_counts, int32_t nmesh, int32_t nbins,
