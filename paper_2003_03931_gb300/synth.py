@@ -20,7 +20,7 @@ WORKLOADS = {
     "ragged_32": dict(np=32, nc=32, a_init=0.02, a_final=1.0, n_steps=10),
     # the 512^3 box with the tile spectrum stored as FP16 (precision option)
     "c3_512_fp16": dict(np=512, nc=256, a_init=0.02, a_final=1.0, n_steps=20, fine_fp16=True),
-    # the 256^3 box with the low-memory step (profiling its tile passes)
+    # the 256^3 box with the low-memory step (profiling its tile pass and re-encode)
     "c4sub_256_lowmem": dict(np=256, nc=128, a_init=0.02, a_final=1.0, n_steps=20, lowmem=True),
     # the paper's LambdaCDM background (Omega_m = 0.258, flat) from z = 99
     "lcdm_32": dict(np=32, nc=16, a_init=0.01, a_final=1.0, n_steps=10, omega_m=0.258,
