@@ -91,8 +91,8 @@ extern "C" {
                                 new momentum, with the same integer drift, so the
                                 new store is the one the default step writes.
                                 The momentum sums and F_l share the next store's
-                                space.  About 30.5 bytes per particle of workspace
-                                instead of 83 (2048^3 particles: 262.5 GB, which
+                                space.  About 31 bytes per particle of workspace
+                                instead of 83 (2048^3 particles: 264 GB, which
                                 fits one GB300).
                                 Initial conditions use float32 transforms and a
                                 float32 displacement field (the default uses

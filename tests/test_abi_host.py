@@ -74,7 +74,7 @@ def test_init_without_device_fails_cleanly(lib):
 
 def test_lowmem_workspace_fits_2048_cubed(lib):
     # the low-memory step keeps only the new momenta (12 B per particle) and
-    # no codes; 2048^3 particles (nc = 1024) need about 30.5 bytes per
+    # no codes; 2048^3 particles (nc = 1024) need about 31 bytes per
     # particle, inside one GB300's HBM (284,208 MiB)
     from paper_2003_03931_gb300.sim import SimConfig, workspace_bytes
     from paper_2003_03931_gb300._lib import PmpmError
