@@ -1,14 +1,19 @@
 // sort.cu -- cell-ordered re-encode of the particles (Sec. III-A: the bins
 // m^i only locate a particle once the store is ordered by cell), with the
-// per-cell counts and the cell-mean velocity v_c of Eq. 3.
+// per-cell counts, the cell-mean velocity v_c and the dispersion sigma of
+// Eq. 3.
 //
-// Input: new codes Q [3][N] and momenta p [3][N] (float32), any order.
-//   hist    counts[c] and fixed-point momentum sums S[d][c] (int64, p rounded
-//           to 2^-24): exact integers, independent of order
+// Input: new codes Q [3][N] and momenta p [3][N] (float32), any order (the
+// default step), or the old store and the new momenta (the low-memory step,
+// which derives Q again with the tile pass's integer drift).
+//   hist    counts[c], fixed-point momentum sums S[d][c] (int64, P = p
+//           rounded to 2^-24) and T = sum P^2 (128 bits): exact integers,
+//           independent of order (fused into the tile pass in a step)
 //   scan    offsets = exclusive scan of counts (int64); v_c = fl32(fl32(S)
 //           2^-24 / n)
-//   sigma   sum over particles of round((p - v_c)^2 * 2^32) in 128 bits;
-//           sigma = fl32(sqrt(sum 2^-32 / 3N))
+//   sigma   U = sum over cells of floor(S^2 / n) (128 bits); sigma =
+//           fl32(sqrt((T - U) 2^-48 / 3N)), the dispersion about the exact
+//           cell means
 //   scatter slot = offsets[c] + rank (atomic per cell); m = Q mod 256 and the
 //           Eq. 3 code u (Eq. 4 guess + edge fix-up) written to the new store
 // Within-cell order is not specified; every quantity above is independent of
@@ -391,23 +396,6 @@ __global__ void k_scatter(Src src, int64_t n, int nc, const float* __restrict__ 
         }
         scatter_two<PB>(q, p, live, n, nc, vcd, offsets, fill, sigma, Es, out, err);
     }
-}
-
-// The old cell c of store index j (offsets[c] <= j < offsets[c + 1]) by a
-// 32-way search of one warp: every lane calls with the same j and gets c.
-__device__ int64_t warp_find_cell(const int64_t* __restrict__ offsets, int64_t ncells, int64_t j) {
-    const int lane = threadIdx.x & 31;
-    int64_t lo = 0, hi = ncells;   // offsets[lo] <= j < offsets[hi] (offsets[ncells] = N)
-    while (hi - lo > 1) {
-        const int64_t pr = lo + (((hi - lo) * lane) >> 5);   // lane 0 probes lo itself
-        const unsigned b = __ballot_sync(0xffffffffu, offsets[pr] <= j);
-        const int k = 31 - __clz(b);
-        const int64_t nlo = __shfl_sync(0xffffffffu, pr, k);
-        const int64_t nhi = k < 31 ? __shfl_sync(0xffffffffu, pr, k + 1) : hi;
-        lo = nlo;
-        hi = nhi;
-    }
-    return lo;
 }
 
 constexpr int kParkThreads = 256;
