@@ -5,8 +5,8 @@
 //  1. integer CIC of all particles on the nc^3 coarse mesh (int64, units
 //     2^-27 per particle): one thread per cell sums its particles' weights on
 //     the 27 surrounding nodes in 32-bit registers, an 8x8x4-cell brick
-//     collects them in shared memory and flushes one global atomic per
-//     touched node;
+//     collects them in shared memory (64-bit sums kept as two 32-bit words)
+//     and flushes one global atomic per touched node;
 //  2. delta = rho - mean (float64 subtraction, float32 storage), 3-D FFT;
 //  3. Green multiply: B1 = rho~ (K~_x + i K~_y), B2 = rho~ K~_z (K~ = -i S);
 //  4. two inverse FFTs give F_x + i F_y and F_z.
@@ -29,11 +29,16 @@ __global__ void __launch_bounds__(256) k_coarse_deposit(int nc, const int32_t* _
                                                         const uint8_t* __restrict__ m1,
                                                         const uint8_t* __restrict__ m2,
                                                         unsigned long long* rho) {
-    __shared__ unsigned long long acc[kNX * kNY * kNZ];
+    // the brick's node sums as 32-bit halves: a native 32-bit shared atomic on
+    // the low word, and the high word counts its wraps (at most one per add)
+    __shared__ uint32_t acc_lo[kNX * kNY * kNZ], acc_hi[kNX * kNY * kNZ];
     const int nbx = nc / kBX, nby = nc / kBY;
     const int bx = blockIdx.x % nbx, by = (blockIdx.x / nbx) % nby, bz = blockIdx.x / (nbx * nby);
     const int x0 = bx * kBX, y0 = by * kBY, z0 = bz * kBZ;
-    for (int i = threadIdx.x; i < kNX * kNY * kNZ; i += blockDim.x) acc[i] = 0ull;
+    for (int i = threadIdx.x; i < kNX * kNY * kNZ; i += blockDim.x) {
+        acc_lo[i] = 0u;
+        acc_hi[i] = 0u;
+    }
     __syncthreads();
     const int lx = threadIdx.x % kBX, ly = (threadIdx.x / kBX) % kBY, lz = threadIdx.x / (kBX * kBY);
     const int cx = x0 + lx, cy = y0 + ly, cz = z0 + lz;
@@ -87,12 +92,14 @@ __global__ void __launch_bounds__(256) k_coarse_deposit(int nc, const int32_t* _
         for (int k = 0; k < 27; ++k) {
             if (!a[k]) continue;
             const int dx = k % 3, dy = (k / 3) % 3, dz = k / 9;
-            atomicAdd(&acc[(lx + dx) + kNX * ((ly + dy) + kNY * (lz + dz))], (unsigned long long)a[k]);
+            const int i = (lx + dx) + kNX * ((ly + dy) + kNY * (lz + dz));
+            const uint32_t old = atomicAdd(&acc_lo[i], a[k]);
+            if (old + a[k] < old) atomicAdd(&acc_hi[i], 1u);
         }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < kNX * kNY * kNZ; i += blockDim.x) {
-        const unsigned long long v = acc[i];
+        const unsigned long long v = ((unsigned long long)acc_hi[i] << 32) | acc_lo[i];
         if (!v) continue;
         const int ix = i % kNX, iy = (i / kNX) % kNY, iz = i / (kNX * kNY);
         const int gx = wrap(x0 - 1 + ix, nc), gy = wrap(y0 - 1 + iy, nc), gz = wrap(z0 - 1 + iz, nc);
