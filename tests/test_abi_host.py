@@ -96,6 +96,33 @@ def test_lowmem_workspace_fits_2048_cubed(lib):
         _lib.check(lib.pmpm_workspace_bytes(ctypes.byref(cc), ctypes.byref(out)))
 
 
+@pytest.mark.parametrize("np_,nc", [(2048, 1024), (256, 128), (64, 16), (32, 32), (16, 32)])
+def test_lowmem_workspace_regions(lib, np_, nc):
+    # the low-memory layout: two stores (each max(6N, 36C) bytes: the next
+    # store's space also holds the step's momentum sums, 24 B/cell, and
+    # F_l, 12 B/cell) with their counts, offsets and v_c; the slot counters;
+    # one region taken in turn by the coarse mesh (4 x 8 B/cell), the kept
+    # momenta or the IC displacement field (12 B/particle), the P(k) mesh and
+    # the force-table scratch; and small tables (the coarse Green table, 16 B
+    # per folded wavenumber, the largest).  No per-particle codes.
+    from paper_2003_03931_gb300.sim import SimConfig, workspace_bytes
+
+    def al(x):
+        return (x + 255) // 256 * 256
+
+    N, C = np_ ** 3, nc ** 3
+    h = nc // 2 + 1
+    store = al(max(6 * N, al(24 * C) + 12 * C))
+    pair = 2 * (store + al(4 * C) + al(8 * (C + 1)) + al(12 * C))
+    pk = min(4 * nc, 512)
+    green = 343 * 8 + 1331 * 8 + 512 + 16 * C + 4 * h ** 3
+    U = max(12 * N, 4 * al(8 * C), 16 * pk ** 3 + 512, green)
+    big = pair + al(4 * C) + U
+    b = workspace_bytes(SimConfig(np=np_, nc=nc, n_steps=20, lowmem=True))
+    small = b - big
+    assert 16 * h ** 3 <= small <= 16 * h ** 3 + (8 << 20), (b, big)
+
+
 def test_fma_probe_rejects_bad_arguments(lib):
     # argument checks come before any CUDA call, so they run without a GPU
     f, ms = ctypes.c_double(), ctypes.c_float()
