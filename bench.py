@@ -284,6 +284,39 @@ def oracle_cores():
 
 # ------------------------------------------------------------------ our arm
 
+def pinned_state_bytes(cfg):
+    """Pinned host bytes of one rank's end-to-end buffers (store, counts,
+    v_c), each rounded up to a power of two as the pinned-memory cache
+    allocates them."""
+    def p2(x):
+        return 1 << (int(x) - 1).bit_length()
+    return p2((3 * cfg.pos_bytes + 3) * cfg.n) + p2(4 * cfg.ncells) + p2(12 * cfg.ncells)
+
+
+def host_memory_available():
+    """Bytes of host memory this process may still use: MemAvailable, capped
+    by the cgroup's limit where one is set; None if neither can be read."""
+    avail = None
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    avail = int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    try:
+        with open("/sys/fs/cgroup/memory.max") as f:
+            lim = f.read().strip()
+        with open("/sys/fs/cgroup/memory.current") as f:
+            cur = int(f.read().strip())
+        if lim != "max":
+            room = int(lim) - cur
+            avail = room if avail is None else min(avail, room)
+    except (OSError, ValueError):
+        pass
+    return avail
+
+
 def measure_box(workload, K, W, E, local, world, rank):
     """One box: ICs, W warm-up steps, K steps timed with CUDA events on the
     library's stream (clocks sampled meanwhile, per-stage times recorded),
@@ -330,6 +363,18 @@ def measure_box(workload, K, W, E, local, world, rank):
     t = reduce_max(t, f"cuda:{local}")
 
     e2e = None
+    if E:
+        # every rank on this node pins a copy of its whole state; skip the
+        # end-to-end leg on all ranks if the node's host memory cannot hold them
+        need = pinned_state_bytes(cfg)
+        local_ranks = int(os.environ.get("LOCAL_WORLD_SIZE", world))
+        avail = host_memory_available()
+        short = avail is not None and 1.25 * local_ranks * need > avail
+        if reduce_max(1.0 if short else 0.0, f"cuda:{local}") > 0.0:
+            e2e = {"value": None, "unit": UNIT,
+                   "skipped": "host memory: %d rank(s) x %.1f GB of pinned state exceed the %.1f GB "
+                              "available" % (local_ranks, need / 1e9, (avail or 0) / 1e9)}
+            E = 0
     if E:
         n, C = cfg.n, cfg.ncells
         pin = lambda shape, dt: torch.empty(shape, dtype=dt, pin_memory=True).numpy()
