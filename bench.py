@@ -369,7 +369,7 @@ def measure_box(workload, K, W, E, local, world, rank):
         need = pinned_state_bytes(cfg)
         local_ranks = int(os.environ.get("LOCAL_WORLD_SIZE", world))
         avail = host_memory_available()
-        short = avail is not None and 1.25 * local_ranks * need > avail
+        short = avail is not None and local_ranks * (need + (2 << 30)) > avail
         if reduce_max(1.0 if short else 0.0, f"cuda:{local}") > 0.0:
             e2e = {"value": None, "unit": UNIT,
                    "skipped": "host memory: %d rank(s) x %.1f GB of pinned state exceed the %.1f GB "
